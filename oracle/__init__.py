@@ -1,0 +1,254 @@
+"""ctypes front end of the FP64 CPU oracle (oracle/qbx_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by the smoke check and by the
+CPU-baseline leg of bench.py.  The product library never loads it.
+
+Coefficient arrays are complex128 of length (p+1)^2, ordered
+B_0^0, B_1^-1, B_1^0, B_1^1, ... (Section 4.1).  Point arrays are SoA (3, N)
+float64.  Lists are CSR (start[n_boxes+1], idx) in the order
+U, V, W-close, W-far, X-close, X-far (Section 5.2.3-5.2.4).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "qbx_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liborc.so")
+
+LIST_NAMES = ("U", "V", "Wclose", "Wfar", "Xclose", "Xfar")
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (plain C, -O2 -ffp-contract=off, no target-specific flags)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.c_void_p
+        d, i = C.c_double, C.c_int
+        L.orc_ylm.argtypes = [i, P, P]
+        L.orc_p2m.argtypes = [i, P, P, d, P, P]
+        L.orc_p2l.argtypes = [i, P, P, d, P, P]
+        L.orc_m2p.argtypes = [i, P, P, P]
+        L.orc_m2p.restype = d
+        L.orc_l2p.argtypes = [i, P, P, P]
+        L.orc_l2p.restype = d
+        L.orc_p2p.argtypes = [P, d, P, P]
+        L.orc_p2p.restype = d
+        for f in (L.orc_m2m, L.orc_l2l, L.orc_m2l):
+            f.argtypes = [i, P, P, i, P, P]
+        L.orc_build_tree.argtypes = [P, i, P, P, i, P, i, i, d, i]
+        L.orc_build_tree.restype = P
+        L.orc_tree_free.argtypes = [P]
+        L.orc_tree_info.argtypes = [P, P, P]
+        L.orc_tree_arrays.argtypes = [P] * 10
+        for f in (L.orc_build_lists, L.orc_build_lists_slow):
+            f.argtypes = [P]
+            f.restype = P
+        L.orc_lists_free.argtypes = [P]
+        L.orc_lists_nnz.argtypes = [P, i]
+        L.orc_lists_nnz.restype = C.c_int64
+        L.orc_lists_get.argtypes = [P, i, P, P]
+        L.orc_fmm_eval.argtypes = [P, P, P, i, P, P, P, P, P, i, P, P, i, i, i, P, P, P, P, i]
+        L.orc_direct_eval.argtypes = [P, i, P, P, P, P, P, i, P, P, i, i, P, P]
+        L.orc_lists_cost.argtypes = [P, P, i, i, P]
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _ncoef(p):
+    return (p + 1) * (p + 1)
+
+
+# ---------------------------------------------------------------- operators
+
+
+def ylm(p, v):
+    out = np.zeros(_ncoef(p), np.complex128)
+    v = _f64(v)
+    if lib().orc_ylm(p, _p(v), _p(out)) != 0:
+        raise ValueError("ylm of the zero vector")
+    return out
+
+
+def p2m(p, c, s, q, d=None):
+    out = np.zeros(_ncoef(p), np.complex128)
+    c, s, d = _f64(c), _f64(s), _f64(d)
+    lib().orc_p2m(p, _p(c), _p(s), float(q), _p(d), _p(out))
+    return out
+
+
+def p2l(p, c, s, q, d=None):
+    out = np.zeros(_ncoef(p), np.complex128)
+    c, s, d = _f64(c), _f64(s), _f64(d)
+    lib().orc_p2l(p, _p(c), _p(s), float(q), _p(d), _p(out))
+    return out
+
+
+def m2p(p, c, M, t):
+    c, t, M = _f64(c), _f64(t), np.ascontiguousarray(M, np.complex128)
+    return lib().orc_m2p(p, _p(c), _p(M), _p(t))
+
+
+def l2p(p, c, L, t):
+    c, t, L = _f64(c), _f64(t), np.ascontiguousarray(L, np.complex128)
+    return lib().orc_l2p(p, _p(c), _p(L), _p(t))
+
+
+def p2p(s, q, t, d=None):
+    s, t, d = _f64(s), _f64(t), _f64(d)
+    return lib().orc_p2p(_p(s), float(q), _p(d), _p(t))
+
+
+def _translate(fn, ps, c, B, pd, c2):
+    out = np.zeros(_ncoef(pd), np.complex128)
+    c, c2, B = _f64(c), _f64(c2), np.ascontiguousarray(B, np.complex128)
+    fn(ps, _p(c), _p(B), pd, _p(c2), _p(out))
+    return out
+
+
+def m2m(ps, c, M, pd, c2):
+    return _translate(lib().orc_m2m, ps, c, M, pd, c2)
+
+
+def l2l(ps, c, L, pd, c2):
+    return _translate(lib().orc_l2l, ps, c, L, pd, c2)
+
+
+def m2l(ps, c, M, pd, c2):
+    return _translate(lib().orc_m2l, ps, c, M, pd, c2)
+
+
+# ---------------------------------------------------------------- tree and lists
+
+
+@dataclass
+class Tree:
+    handle: int
+    n_boxes: int
+    n_levels: int
+    n_overfull: int
+    root_center: np.ndarray
+    root_radius: float
+    level: np.ndarray
+    coords: np.ndarray  # (n_boxes, 3) int64
+    center: np.ndarray  # (n_boxes, 3)
+    radius: np.ndarray  # |b|
+    parent: np.ndarray
+    child: np.ndarray  # (n_boxes, 8)
+    src_owner: np.ndarray
+    ctr_owner: np.ndarray
+    tgt_owner: np.ndarray
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.orc_tree_free(self.handle)
+            self.handle = 0
+
+
+def build_tree(src_xyz, ctr_xyz, ctr_r, tgt_xyz, n_max=32, t_f=0.9, max_depth=40) -> Tree:
+    s, c, r, t = _f64(src_xyz), _f64(ctr_xyz), _f64(ctr_r), _f64(tgt_xyz)
+    ns, nc, nt = s.shape[1], c.shape[1], t.shape[1]
+    h = lib().orc_build_tree(_p(s), ns, _p(c), _p(r), nc, _p(t), nt, n_max, t_f, max_depth)
+    info = np.zeros(6, np.int64)
+    root = np.zeros(4)
+    lib().orc_tree_info(h, _p(info), _p(root))
+    nb = int(info[0])
+    arr = dict(level=np.zeros(nb, np.int32), coords=np.zeros((nb, 3), np.int64), center=np.zeros((nb, 3)),
+               radius=np.zeros(nb), parent=np.zeros(nb, np.int32), child=np.zeros((nb, 8), np.int32),
+               src_owner=np.zeros(ns, np.int32), ctr_owner=np.zeros(nc, np.int32), tgt_owner=np.zeros(nt, np.int32))
+    lib().orc_tree_arrays(h, *[_p(arr[k]) for k in ("level", "coords", "center", "radius", "parent", "child",
+                                                        "src_owner", "ctr_owner", "tgt_owner")])
+    return Tree(h, nb, int(info[1]), int(info[2]), root[:3].copy(), float(root[3]), **arr)
+
+
+@dataclass
+class Lists:
+    handle: int
+    start: dict
+    idx: dict
+
+    def __del__(self):
+        if self.handle and _lib is not None:
+            _lib.orc_lists_free(self.handle)
+            self.handle = 0
+
+    def of(self, name, b):
+        return self.idx[name][self.start[name][b]:self.start[name][b + 1]]
+
+
+def build_lists(tree: Tree, slow: bool = False) -> Lists:
+    h = (lib().orc_build_lists_slow if slow else lib().orc_build_lists)(tree.handle)
+    start, idx = {}, {}
+    for k, name in enumerate(LIST_NAMES):
+        nnz = lib().orc_lists_nnz(h, k)
+        st = np.zeros(tree.n_boxes + 1, np.int32)
+        ix = np.zeros(max(nnz, 1), np.int32)
+        lib().orc_lists_get(h, k, _p(st), _p(ix))
+        start[name], idx[name] = st, ix[:nnz]
+    return Lists(h, start, idx)
+
+
+def lists_cost(tree: Tree, lists: Lists, p_qbx: int, p_fmm: int) -> dict:
+    out = np.zeros(6)
+    lib().orc_lists_cost(tree.handle, lists.handle, p_qbx, p_fmm, _p(out))
+    return dict(zip(LIST_NAMES, out))
+
+
+# ---------------------------------------------------------------- evaluation
+
+
+def fmm_eval(tree: Tree, lists: Lists, src_xyz, src_w, sigma, mu, src_n, ctr_xyz, tgt_xyz, tgt_ctr,
+             p_qbx, p_fmm, p_qbx_ctr=None, p_fmm_box=None, return_qbx_locals=False, qmax=None):
+    """GIGAQBX FMM (Algorithm 4): pot = S[sigma] + D[mu] at every target."""
+    s, w, sg, m_, n_ = _f64(src_xyz), _f64(src_w), _f64(sigma), _f64(mu), _f64(src_n)
+    c, t = _f64(ctr_xyz), _f64(tgt_xyz)
+    tc = np.ascontiguousarray(tgt_ctr, np.int32)
+    qc = None if p_qbx_ctr is None else np.ascontiguousarray(p_qbx_ctr, np.int8)
+    pb = None if p_fmm_box is None else np.ascontiguousarray(p_fmm_box, np.int8)
+    nt = t.shape[1]
+    pot = np.zeros(nt)
+    qm = qmax if qmax is not None else (p_qbx if qc is None else int(qc.max()))
+    ql = np.zeros((c.shape[1], _ncoef(qm)), np.complex128) if return_qbx_locals else None
+    rc = lib().orc_fmm_eval(tree.handle, lists.handle, _p(s), s.shape[1], _p(w), _p(sg), _p(m_), _p(n_), _p(c),
+                            c.shape[1], _p(t), _p(tc), nt, p_qbx, p_fmm, _p(qc), _p(pb), _p(pot), _p(ql), qm)
+    if rc != 0:
+        raise ValueError("particle counts do not match the tree")
+    return (pot, ql) if return_qbx_locals else pot
+
+
+def direct_eval(src_xyz, src_w, sigma, mu, src_n, ctr_xyz, tgt_xyz, tgt_ctr, p_qbx, p_qbx_ctr=None):
+    """Direct (unaccelerated) QBX, eqs. (qbxcoeff) and (qbxlocal); point targets by plain quadrature."""
+    s, w, sg, m_, n_ = _f64(src_xyz), _f64(src_w), _f64(sigma), _f64(mu), _f64(src_n)
+    c, t = _f64(ctr_xyz), _f64(tgt_xyz)
+    tc = np.ascontiguousarray(tgt_ctr, np.int32)
+    qc = None if p_qbx_ctr is None else np.ascontiguousarray(p_qbx_ctr, np.int8)
+    pot = np.zeros(t.shape[1])
+    lib().orc_direct_eval(_p(s), s.shape[1], _p(w), _p(sg), _p(m_), _p(n_), _p(c), c.shape[1], _p(t), _p(tc),
+                          t.shape[1], p_qbx, _p(qc), _p(pot))
+    return pot

@@ -1,0 +1,1342 @@
+/*
+ * Oracle for the GIGAQBX 3D Laplace evaluation (Wala & Kloeckner, "A Fast
+ * Algorithm for Quadrature by Expansion in Three Dimensions").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain, serial, FP64 C written for readability.
+ * Only the test suite, the smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code with the CUDA library.
+ *
+ * Notation follows the paper:
+ *   - Green's function G(x,y) = 1 / (4 pi |x - y|)                 (eq. laplace-fs-green)
+ *   - Y_n^m(theta, phi) = sqrt((2n+1)/(4pi) (n-|m|)!/(n+|m|)!)
+ *                         P_n^|m|(cos theta) e^{i m phi}             (eq. spherical-harmonics)
+ *     with P_n^m the associated Legendre function WITHOUT the
+ *     Condon-Shortley phase (the paper does not state one; G does not
+ *     depend on it).
+ *   - local coefficients  L_n^m = q/(2n+1) |s-c|^{-n-1} Y_n^{-m}(s-c)  (eq. local-expansion-coeff)
+ *     evaluated as        sum L_n^m |t-c|^n Y_n^m(t-c)
+ *   - multipole coeffs.   M_n^m = q/(2n+1) |s-c|^n Y_n^m(s-c)          (eq. mpole-expansion-coeff)
+ *     evaluated as        sum M_n^m |t-c|^{-n-1} Y_n^{-m}(t-c)
+ *   - coefficients of an order-p expansion are stored as (p+1)^2 complex
+ *     numbers B_0^0, B_1^-1, B_1^0, B_1^1, ... (Section 4.1).
+ *   - the double layer D u(x) = int d/dn(y) G(x,y) u(y) dS(y) (the kernel of
+ *     Green's formula in Section 6.1): every source-side operation has a
+ *     dipole form, the directional derivative n(y) . grad_y of the charge form.
+ *
+ * The translation operators (M2M, L2L, M2L, Section 4.1) are not printed in
+ * the paper; they are written here as plain double sums obtained by
+ * re-expanding solid harmonics with the addition theorems of the regular
+ * solid harmonics |x|^n Y_n^m and the irregular ones |x|^{-n-1} Y_n^m, in the
+ * paper's normalisation.
+ *
+ * Tree, interaction lists and the nine stages follow Section 5.2 and
+ * Algorithm 4; readings of passages the paper leaves open are noted where
+ * they are used.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+#define ORC_NMAX 96 /* highest harmonic degree supported by the factor tables */
+#define ORC_PI 3.14159265358979323846
+
+static double g_fact[2 * ORC_NMAX + 4];
+static int g_init = 0;
+
+static double g_afac[(ORC_NMAX + 1) * (ORC_NMAX + 1)];
+static double g_bfac[(ORC_NMAX + 1) * (ORC_NMAX + 1)];
+
+static inline int IDX(int n, int m) { return n * n + n + m; }
+
+static double Afac_eval(int n, int m);
+static double Bfac_eval(int n, int m);
+
+static void init_tables(void)
+{
+    if (g_init) return;
+    g_fact[0] = 1.0;
+    for (int i = 1; i < 2 * ORC_NMAX + 4; ++i) g_fact[i] = g_fact[i - 1] * (double)i;
+    for (int n = 0; n <= ORC_NMAX; ++n)
+        for (int m = -n; m <= n; ++m) {
+            g_afac[IDX(n, m)] = Afac_eval(n, m);
+            g_bfac[IDX(n, m)] = Bfac_eval(n, m);
+        }
+    g_init = 1;
+}
+
+/* ------------------------------------------------------------------------ */
+/* spherical harmonics (eq. spherical-harmonics)                              */
+/* ------------------------------------------------------------------------ */
+
+/* Normalised Legendre functions Pbar_n^m(x) = sqrt((2n+1)/(4pi)(n-m)!/(n+m)!) P_n^m(x),
+ * 0 <= m <= n <= p, stored at IDX(n, m), by the standard three-term
+ * recurrences for normalised functions (no Condon-Shortley phase). */
+static void legendre_norm(int p, double ct, double st, double *Pb)
+{
+    Pb[IDX(0, 0)] = 1.0 / sqrt(4.0 * ORC_PI);
+    for (int m = 0; m <= p; ++m) {
+        if (m > 0) Pb[IDX(m, m)] = sqrt((2.0 * m + 1.0) / (2.0 * m)) * st * Pb[IDX(m - 1, m - 1)];
+        if (m + 1 <= p) Pb[IDX(m + 1, m)] = sqrt(2.0 * m + 3.0) * ct * Pb[IDX(m, m)];
+        for (int n = m + 2; n <= p; ++n) {
+            double a = sqrt((4.0 * n * n - 1.0) / ((double)n * n - (double)m * m));
+            double b = sqrt((((double)(n - 1) * (n - 1)) - (double)m * m) / (4.0 * (n - 1) * (n - 1) - 1.0));
+            Pb[IDX(n, m)] = a * (ct * Pb[IDX(n - 1, m)] - b * Pb[IDX(n - 2, m)]);
+        }
+    }
+}
+
+/* Y_n^m at the direction of v for all n <= p, |m| <= n.  theta = acos(z/r) and
+ * phi = atan2(y, x) (Section 2.1); cos(theta) = z/r and sin(theta) = rho/r are
+ * used directly.  Returns r = |v|; Y is left untouched when r == 0. */
+static double ylm_dir(int p, const double v[3], cplx *Y)
+{
+    double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (r == 0.0) return 0.0;
+    double rho = sqrt(v[0] * v[0] + v[1] * v[1]);
+    double ct = v[2] / r, st = rho / r;
+    double phi = atan2(v[1], v[0]);
+    double Pb[(p + 1) * (p + 1)];
+    legendre_norm(p, ct, st, Pb);
+    for (int n = 0; n <= p; ++n)
+        for (int m = 0; m <= n; ++m) {
+            cplx e = cexp(I * (double)m * phi);
+            Y[IDX(n, m)] = Pb[IDX(n, m)] * e;
+            if (m > 0) Y[IDX(n, -m)] = Pb[IDX(n, m)] * conj(e);
+        }
+    return r;
+}
+
+/* regular solid harmonics |v|^n Y_n^m(v), n <= p */
+static void solid_reg(int p, const double v[3], cplx *out)
+{
+    double r = ylm_dir(p, v, out);
+    if (r == 0.0) {
+        for (int i = 0; i < (p + 1) * (p + 1); ++i) out[i] = 0.0;
+        out[0] = 1.0 / sqrt(4.0 * ORC_PI);
+        return;
+    }
+    double rn = 1.0;
+    for (int n = 0; n <= p; ++n) {
+        for (int m = -n; m <= n; ++m) out[IDX(n, m)] *= rn;
+        rn *= r;
+    }
+}
+
+/* irregular solid harmonics |v|^{-n-1} Y_n^m(v), n <= p, v != 0 */
+static void solid_irr(int p, const double v[3], cplx *out)
+{
+    double r = ylm_dir(p, v, out);
+    double rn = 1.0 / r;
+    for (int n = 0; n <= p; ++n) {
+        for (int m = -n; m <= n; ++m) out[IDX(n, m)] *= rn;
+        rn /= r;
+    }
+}
+
+/* Conversion factors between |x|^n Y_n^m and the polynomial harmonics used to
+ * write the addition theorems:
+ *   |x|^n Y_n^m          = Afac(n,m) * R_n^m(x),
+ *   |x|^{-n-1} Y_n^m     = Bfac(n,m) * S_n^m(x),
+ * where R_n^m(a+b) = sum_{k,l} R_k^l(a) R_{n-k}^{m-l}(b) and
+ *       conj S_n^m(X+y) = sum_{k,l} (-1)^k R_k^l(y) conj S_{n+k}^{m+l}(X), |y| < |X|. */
+static double Afac_eval(int n, int m)
+{
+    int am = m < 0 ? -m : m;
+    double s = (m < 0 && (am & 1)) ? -1.0 : 1.0;
+    return s * sqrt((2.0 * n + 1.0) / (4.0 * ORC_PI)) * sqrt(g_fact[n + am] * g_fact[n - am]);
+}
+
+static double Bfac_eval(int n, int m)
+{
+    int am = m < 0 ? -m : m;
+    double s = (m < 0 && (am & 1)) ? -1.0 : 1.0;
+    return s * sqrt((2.0 * n + 1.0) / (4.0 * ORC_PI)) / sqrt(g_fact[n + am] * g_fact[n - am]);
+}
+
+static inline double Afac(int n, int m) { return g_afac[IDX(n, m)]; }
+static inline double Bfac(int n, int m) { return g_bfac[IDX(n, m)]; }
+
+/* ------------------------------------------------------------------------ */
+/* source <-> expansion operators                                             */
+/* ------------------------------------------------------------------------ */
+
+/* Directional derivative d . grad of the regular solid harmonic |x|^n Y_n^m at x,
+ * given the table Rg of |x|^k Y_k^l for k <= n - 1, via the ladder relations
+ *   (dx - i dy) R_n^m = R_{n-1}^{m-1},  (dx + i dy) R_n^m = -R_{n-1}^{m+1},  dz R_n^m = R_{n-1}^m. */
+static cplx dreg(int n, int m, const cplx *Rg, const double d[3])
+{
+    if (n == 0) return 0.0;
+    cplx dw = d[0] + I * d[1], dwb = d[0] - I * d[1];
+    cplx acc = 0.0;
+    double A = Afac(n, m);
+    if (m + 1 <= n - 1) acc += -(dwb / 2.0) * (A / Afac(n - 1, m + 1)) * Rg[IDX(n - 1, m + 1)];
+    if (m - 1 >= -(n - 1)) acc += (dw / 2.0) * (A / Afac(n - 1, m - 1)) * Rg[IDX(n - 1, m - 1)];
+    if (m <= n - 1 && m >= -(n - 1)) acc += d[2] * (A / Afac(n - 1, m)) * Rg[IDX(n - 1, m)];
+    return acc;
+}
+
+/* Directional derivative d . grad of |x|^{-n-1} Y_n^m at x, given the table Ir of
+ * |x|^{-k-1} Y_k^l for k <= n + 1, via
+ *   dz S_n^m = -S_{n+1}^m,  (dx + i dy) S_n^m = -S_{n+1}^{m+1},  (dx - i dy) S_n^m = S_{n+1}^{m-1}. */
+static cplx dirr(int n, int m, const cplx *Ir, const double d[3])
+{
+    cplx dw = d[0] + I * d[1], dwb = d[0] - I * d[1];
+    double B = Bfac(n, m);
+    cplx acc = 0.0;
+    acc += -(dwb / 2.0) * (B / Bfac(n + 1, m + 1)) * Ir[IDX(n + 1, m + 1)];
+    acc += (dw / 2.0) * (B / Bfac(n + 1, m - 1)) * Ir[IDX(n + 1, m - 1)];
+    acc += -d[2] * (B / Bfac(n + 1, m)) * Ir[IDX(n + 1, m)];
+    return acc;
+}
+
+/* P2M: M_n^m += q/(2n+1) |s-c|^n Y_n^m(s-c) + dipole d . grad_s of the same. */
+static void p2m(int p, const double c[3], const double s[3], double q, const double *d, cplx *M)
+{
+    cplx Rg[(p + 1) * (p + 1)];
+    double v[3] = {s[0] - c[0], s[1] - c[1], s[2] - c[2]};
+    solid_reg(p, v, Rg);
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) {
+            cplx val = q * Rg[IDX(n, m)];
+            if (d) val += dreg(n, m, Rg, d);
+            M[IDX(n, m)] += val / (2.0 * n + 1.0);
+        }
+}
+
+/* P2L (also P2QBXL): L_n^m += q/(2n+1) |s-c|^{-n-1} Y_n^{-m}(s-c) + dipole form. */
+static void p2l(int p, const double c[3], const double s[3], double q, const double *d, cplx *L)
+{
+    cplx Ir[(p + 2) * (p + 2)];
+    double v[3] = {s[0] - c[0], s[1] - c[1], s[2] - c[2]};
+    solid_irr(p + 1, v, Ir);
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) {
+            cplx val = q * Ir[IDX(n, -m)];
+            if (d) val += dirr(n, -m, Ir, d);
+            L[IDX(n, m)] += val / (2.0 * n + 1.0);
+        }
+}
+
+/* M2P: sum M_n^m |t-c|^{-n-1} Y_n^{-m}(t-c) (real part). */
+static double m2p(int p, const double c[3], const cplx *M, const double t[3])
+{
+    cplx Ir[(p + 1) * (p + 1)];
+    double v[3] = {t[0] - c[0], t[1] - c[1], t[2] - c[2]};
+    solid_irr(p, v, Ir);
+    cplx acc = 0.0;
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) acc += M[IDX(n, m)] * Ir[IDX(n, -m)];
+    return creal(acc);
+}
+
+/* L2P (also QBXL2P, eq. qbxlocal): sum L_n^m |t-c|^n Y_n^m(t-c) (real part). */
+static double l2p(int p, const double c[3], const cplx *L, const double t[3])
+{
+    cplx Rg[(p + 1) * (p + 1)];
+    double v[3] = {t[0] - c[0], t[1] - c[1], t[2] - c[2]};
+    solid_reg(p, v, Rg);
+    cplx acc = 0.0;
+    for (int n = 0; n <= p; ++n)
+        for (int m = -n; m <= n; ++m) acc += L[IDX(n, m)] * Rg[IDX(n, m)];
+    return creal(acc);
+}
+
+/* P2P: point potential at t of a charge q and dipole d at s; coincident pairs skipped. */
+static double p2p(const double s[3], double q, const double *d, const double t[3])
+{
+    double v[3] = {t[0] - s[0], t[1] - s[1], t[2] - s[2]};
+    double r = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+    if (r == 0.0) return 0.0;
+    double val = q / (4.0 * ORC_PI * r);
+    if (d) val += (d[0] * v[0] + d[1] * v[1] + d[2] * v[2]) / (4.0 * ORC_PI * r * r * r);
+    return val;
+}
+
+/* ------------------------------------------------------------------------ */
+/* translation operators (Section 4.1), orders p_src -> p_dst                 */
+/* ------------------------------------------------------------------------ */
+
+/* M2M c -> c2: M2_n^m += 1/(2n+1) sum_{k,l} (2k+1) M_k^l |c-c2|^{n-k} Y_{n-k}^{m-l}(c-c2)
+ *                                   * A(n,m) / (A(k,l) A(n-k,m-l)). */
+static void m2m(int ps, const double c[3], const cplx *M, int pd, const double c2[3], cplx *M2)
+{
+    cplx Rg[(pd + 1) * (pd + 1)];
+    double v[3] = {c[0] - c2[0], c[1] - c2[1], c[2] - c2[2]};
+    solid_reg(pd, v, Rg);
+    for (int n = 0; n <= pd; ++n)
+        for (int m = -n; m <= n; ++m) {
+            cplx acc = 0.0;
+            for (int k = 0; k <= n && k <= ps; ++k)
+                for (int l = -k; l <= k; ++l) {
+                    int j = n - k, i = m - l;
+                    if (i < -j || i > j) continue;
+                    acc += (2.0 * k + 1.0) * M[IDX(k, l)] * Rg[IDX(j, i)] * (Afac(n, m) / (Afac(k, l) * Afac(j, i)));
+                }
+            M2[IDX(n, m)] += acc / (2.0 * n + 1.0);
+        }
+}
+
+/* L2L c -> c2: L2_k^l += sum_{n>=k,m} L_n^m |c2-c|^{n-k} Y_{n-k}^{m-l}(c2-c) A(n,m)/(A(k,l)A(n-k,m-l)). */
+static void l2l(int ps, const double c[3], const cplx *L, int pd, const double c2[3], cplx *L2)
+{
+    cplx Rg[(ps + 1) * (ps + 1)];
+    double v[3] = {c2[0] - c[0], c2[1] - c[1], c2[2] - c[2]};
+    solid_reg(ps, v, Rg);
+    for (int k = 0; k <= pd; ++k)
+        for (int l = -k; l <= k; ++l) {
+            cplx acc = 0.0;
+            for (int n = k; n <= ps; ++n)
+                for (int m = -n; m <= n; ++m) {
+                    int j = n - k, i = m - l;
+                    if (i < -j || i > j) continue;
+                    acc += L[IDX(n, m)] * Rg[IDX(j, i)] * (Afac(n, m) / (Afac(k, l) * Afac(j, i)));
+                }
+            L2[IDX(k, l)] += acc;
+        }
+}
+
+/* M2L cM -> cL: L_k^l += sum_{n,m} M_n^m (-1)^{k+l} B(n,-m) |X|^{-(n+k)-1} Y_{n+k}^{-(m+l)}(X)
+ *                                   / (A(k,l) B(n+k, -(m+l))),   X = cL - cM. */
+static void m2l(int ps, const double cM[3], const cplx *M, int pd, const double cL[3], cplx *L)
+{
+    int pt = ps + pd;
+    cplx Ir[(pt + 1) * (pt + 1)];
+    double X[3] = {cL[0] - cM[0], cL[1] - cM[1], cL[2] - cM[2]};
+    solid_irr(pt, X, Ir);
+    for (int k = 0; k <= pd; ++k)
+        for (int l = -k; l <= k; ++l) {
+            cplx acc = 0.0;
+            double sgn = ((k + l) & 1) ? -1.0 : 1.0;
+            for (int n = 0; n <= ps; ++n)
+                for (int m = -n; m <= n; ++m) {
+                    int j = n + k, i = -(m + l);
+                    acc += M[IDX(n, m)] * Ir[IDX(j, i)] * (Bfac(n, -m) / (Afac(k, l) * Bfac(j, i)));
+                }
+            L[IDX(k, l)] += sgn * acc;
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* exported single-operator entry points (used by the pin tests)              */
+/* ------------------------------------------------------------------------ */
+
+/* Y_n^m for direction v, n <= p; out is (p+1)^2 complex as interleaved re/im. */
+int orc_ylm(int p, const double *v, double *out)
+{
+    init_tables();
+    if (p < 0 || p > ORC_NMAX) return -1;
+    if (ylm_dir(p, v, (cplx *)out) == 0.0) return -1;
+    return 0;
+}
+
+int orc_p2m(int p, const double *c, const double *s, double q, const double *d, double *M)
+{
+    init_tables();
+    p2m(p, c, s, q, d, (cplx *)M);
+    return 0;
+}
+
+int orc_p2l(int p, const double *c, const double *s, double q, const double *d, double *L)
+{
+    init_tables();
+    p2l(p, c, s, q, d, (cplx *)L);
+    return 0;
+}
+
+double orc_m2p(int p, const double *c, const double *M, const double *t)
+{
+    init_tables();
+    return m2p(p, c, (const cplx *)M, t);
+}
+
+double orc_l2p(int p, const double *c, const double *L, const double *t)
+{
+    init_tables();
+    return l2p(p, c, (const cplx *)L, t);
+}
+
+double orc_p2p(const double *s, double q, const double *d, const double *t) { return p2p(s, q, d, t); }
+
+int orc_m2m(int ps, const double *c, const double *M, int pd, const double *c2, double *M2)
+{
+    init_tables();
+    m2m(ps, c, (const cplx *)M, pd, c2, (cplx *)M2);
+    return 0;
+}
+
+int orc_l2l(int ps, const double *c, const double *L, int pd, const double *c2, double *L2)
+{
+    init_tables();
+    l2l(ps, c, (const cplx *)L, pd, c2, (cplx *)L2);
+    return 0;
+}
+
+int orc_m2l(int ps, const double *cM, const double *M, int pd, const double *cL, double *L)
+{
+    init_tables();
+    m2l(ps, cM, (const cplx *)M, pd, cL, (cplx *)L);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* octree with target confinement (Section 5.2, Algorithm 4 Stage 1)          */
+/* ------------------------------------------------------------------------ */
+
+enum { KSRC = 0, KCTR = 1, KTGT = 2 };
+
+typedef struct {
+    int nb, cap, nlev;
+    int *level;
+    int64_t *ic;  /* 3 per box: integer coordinates at the box's level */
+    double *cen;  /* 3 per box */
+    double *hw;   /* |b|, the l-infinity radius */
+    int *parent;
+    int *child;   /* 8 per box, -1 = none */
+    int *level_start; /* nlev + 1 */
+    int np[3];
+    int *owner[3];
+    int *own_start[3]; /* nb + 1 (CSR over boxes) */
+    int *own_idx[3];   /* particle indices grouped by box, ascending within a box */
+    int *nsrc_sub;     /* sources in the subtree */
+    int *ntgt_sub;     /* centers + targets in the subtree */
+    int n_overfull;    /* leaves left above n_max because max_depth was reached */
+    double root_c[3], root_h;
+    double tf;
+} otree;
+
+static void tree_grow(otree *T)
+{
+    if (T->nb < T->cap) return;
+    T->cap = T->cap ? 2 * T->cap : 1024;
+    T->level = realloc(T->level, sizeof(int) * T->cap);
+    T->ic = realloc(T->ic, sizeof(int64_t) * 3 * T->cap);
+    T->cen = realloc(T->cen, sizeof(double) * 3 * T->cap);
+    T->hw = realloc(T->hw, sizeof(double) * T->cap);
+    T->parent = realloc(T->parent, sizeof(int) * T->cap);
+    T->child = realloc(T->child, sizeof(int) * 8 * T->cap);
+}
+
+static int tree_add(otree *T, int lev, const int64_t ic[3], const double c[3], double h, int parent)
+{
+    tree_grow(T);
+    int b = T->nb++;
+    T->level[b] = lev;
+    for (int d = 0; d < 3; ++d) {
+        T->ic[3 * b + d] = ic[d];
+        T->cen[3 * b + d] = c[d];
+    }
+    T->hw[b] = h;
+    T->parent[b] = parent;
+    for (int o = 0; o < 8; ++o) T->child[8 * b + o] = -1;
+    return b;
+}
+
+/* Center fits inside the target confinement region B2(sqrt(3)|b|(1+t_f), c_b) of a box
+ * with center cc and l-infinity radius h (Section 5.2.2): |x - cc|_2 + r <= sqrt(3) h (1 + t_f). */
+static int fits_tcr(const double x[3], double r, const double cc[3], double h, double tf)
+{
+    double dx = x[0] - cc[0], dy = x[1] - cc[1], dz = x[2] - cc[2];
+    double dist = sqrt(dx * dx + dy * dy + dz * dz);
+    return dist + r <= (sqrt(3.0) * h) * (1.0 + tf);
+}
+
+/* Octant of a point relative to a box center: bit d set iff x_d >= c_d (x = bit 0, y = 1, z = 2). */
+static int octant(const double x[3], const double c[3])
+{
+    return (x[0] >= c[0] ? 1 : 0) | (x[1] >= c[1] ? 2 : 0) | (x[2] >= c[2] ? 4 : 0);
+}
+
+static void get_pt(const double *xyz, int n, int i, double out[3])
+{
+    out[0] = xyz[i];
+    out[1] = xyz[n + i];
+    out[2] = xyz[2 * n + i];
+}
+
+/*
+ * Builds the tree.  Readings of Stage 1:
+ *  - root: centered at the midpoint of the bounding box of all points and balls,
+ *    rounded to a multiple of R/8, with R the smallest power of two >= 1.25 x the
+ *    largest half extent, so every box center is an exact dyadic number;
+ *  - a box splits when it owns more than n_max particles (sources + centers +
+ *    targets) and at least one particle would move to a child; points go to the
+ *    octant with "coordinate >= center" meaning the upper half; a center moves only
+ *    if its ball fits the child's TCR; only children receiving a particle are made;
+ *  - no box below level max_depth is made;
+ *  - boxes are numbered level by level, children in octant order, which is the
+ *    (level, Morton code) order.
+ */
+otree *orc_build_tree(const double *sxyz, int ns, const double *cxyz, const double *cr, int nc,
+                      const double *txyz, int nt, int nmax, double tf, int max_depth)
+{
+    init_tables();
+    otree *T = calloc(1, sizeof(otree));
+    T->np[KSRC] = ns;
+    T->np[KCTR] = nc;
+    T->np[KTGT] = nt;
+    T->tf = tf;
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    double x[3];
+    for (int i = 0; i < ns; ++i) {
+        get_pt(sxyz, ns, i, x);
+        for (int d = 0; d < 3; ++d) { lo[d] = fmin(lo[d], x[d]); hi[d] = fmax(hi[d], x[d]); }
+    }
+    for (int i = 0; i < nt; ++i) {
+        get_pt(txyz, nt, i, x);
+        for (int d = 0; d < 3; ++d) { lo[d] = fmin(lo[d], x[d]); hi[d] = fmax(hi[d], x[d]); }
+    }
+    for (int i = 0; i < nc; ++i) {
+        get_pt(cxyz, nc, i, x);
+        for (int d = 0; d < 3; ++d) { lo[d] = fmin(lo[d], x[d] - cr[i]); hi[d] = fmax(hi[d], x[d] + cr[i]); }
+    }
+    double mid[3], h = 0.0;
+    for (int d = 0; d < 3; ++d) {
+        mid[d] = 0.5 * (lo[d] + hi[d]);
+        h = fmax(h, 0.5 * (hi[d] - lo[d]));
+    }
+    double R = 1.0;
+    if (h > 0.0) {
+        while (R < 1.25 * h) R *= 2.0;
+        while (0.5 * R >= 1.25 * h) R *= 0.5;
+    }
+    double q8 = R / 8.0, c0[3];
+    for (int d = 0; d < 3; ++d) c0[d] = nearbyint(mid[d] / q8) * q8;
+    T->root_h = R;
+    for (int d = 0; d < 3; ++d) T->root_c[d] = c0[d];
+    int64_t ic0[3] = {0, 0, 0};
+    tree_add(T, 0, ic0, c0, R, -1);
+
+    int ntot = ns + nc + nt;
+    for (int k = 0; k < 3; ++k) T->owner[k] = calloc(T->np[k] > 0 ? T->np[k] : 1, sizeof(int));
+    const double *xyz_k[3] = {sxyz, cxyz, txyz};
+    int *lev_start = malloc(sizeof(int) * (max_depth + 3));
+    lev_start[0] = 0;
+    int nlev = 0;
+    int *dest = malloc(sizeof(int) * (ntot > 0 ? ntot : 1));
+    for (int lev = 0;; ++lev) {
+        int b0 = (lev == 0) ? 0 : lev_start[lev], b1 = T->nb;
+        if (b0 == b1) break;
+        nlev = lev + 1;
+        lev_start[lev + 1] = b1;
+        int nbl = b1 - b0;
+        int *cnt = calloc(nbl, sizeof(int));
+        int *movers = calloc(nbl, sizeof(int));
+        int *cmask = calloc(nbl, sizeof(int));
+        for (int k = 0, g = 0; k < 3; ++k)
+            for (int i = 0; i < T->np[k]; ++i, ++g) {
+                int o = T->owner[k][i];
+                if (o >= b0 && o < b1) cnt[o - b0]++;
+            }
+        for (int k = 0, g = 0; k < 3; ++k)
+            for (int i = 0; i < T->np[k]; ++i, ++g) {
+                dest[g] = -1;
+                int o = T->owner[k][i];
+                if (o < b0 || o >= b1) continue;
+                if (cnt[o - b0] <= nmax || lev >= max_depth) continue;
+                get_pt(xyz_k[k], T->np[k], i, x);
+                int oc = octant(x, &T->cen[3 * o]);
+                if (k == KCTR) {
+                    double hc = 0.5 * T->hw[o], cc[3];
+                    for (int d = 0; d < 3; ++d) cc[d] = T->cen[3 * o + d] + (((oc >> d) & 1) ? hc : -hc);
+                    if (!fits_tcr(x, cr[i], cc, hc, tf)) continue;
+                }
+                dest[g] = oc;
+                movers[o - b0]++;
+                cmask[o - b0] |= 1 << oc;
+            }
+        for (int bb = 0; bb < nbl; ++bb) {
+            int b = b0 + bb;
+            if (cnt[bb] > nmax && lev >= max_depth) T->n_overfull++;
+            if (movers[bb] == 0) continue;
+            double hc = 0.5 * T->hw[b];
+            for (int oc = 0; oc < 8; ++oc) {
+                if (!((cmask[bb] >> oc) & 1)) continue;
+                int64_t ic[3];
+                double cc[3];
+                for (int d = 0; d < 3; ++d) {
+                    int bit = (oc >> d) & 1;
+                    ic[d] = 2 * T->ic[3 * b + d] + bit;
+                    cc[d] = T->cen[3 * b + d] + (bit ? hc : -hc);
+                }
+                int nbx = tree_add(T, lev + 1, ic, cc, hc, b);
+                T->child[8 * b + oc] = nbx;
+            }
+        }
+        for (int k = 0, g = 0; k < 3; ++k)
+            for (int i = 0; i < T->np[k]; ++i, ++g)
+                if (dest[g] >= 0) T->owner[k][i] = T->child[8 * T->owner[k][i] + dest[g]];
+        free(cnt);
+        free(movers);
+        free(cmask);
+        if (lev + 1 > max_depth + 1) break;
+    }
+    free(dest);
+    T->nlev = nlev;
+    T->level_start = malloc(sizeof(int) * (nlev + 1));
+    for (int l = 0; l < nlev; ++l) T->level_start[l] = lev_start[l];
+    T->level_start[nlev] = T->nb;
+    free(lev_start);
+
+    /* owned particles grouped by box (counting sort, stable in the particle index) */
+    for (int k = 0; k < 3; ++k) {
+        T->own_start[k] = calloc(T->nb + 1, sizeof(int));
+        T->own_idx[k] = malloc(sizeof(int) * (T->np[k] > 0 ? T->np[k] : 1));
+        for (int i = 0; i < T->np[k]; ++i) T->own_start[k][T->owner[k][i] + 1]++;
+        for (int b = 0; b < T->nb; ++b) T->own_start[k][b + 1] += T->own_start[k][b];
+        int *fill = malloc(sizeof(int) * (T->nb + 1));
+        memcpy(fill, T->own_start[k], sizeof(int) * (T->nb + 1));
+        for (int i = 0; i < T->np[k]; ++i) T->own_idx[k][fill[T->owner[k][i]]++] = i;
+        free(fill);
+    }
+    T->nsrc_sub = calloc(T->nb, sizeof(int));
+    T->ntgt_sub = calloc(T->nb, sizeof(int));
+    for (int b = T->nb - 1; b >= 0; --b) {
+        T->nsrc_sub[b] += T->own_start[KSRC][b + 1] - T->own_start[KSRC][b];
+        T->ntgt_sub[b] += (T->own_start[KCTR][b + 1] - T->own_start[KCTR][b]) +
+                          (T->own_start[KTGT][b + 1] - T->own_start[KTGT][b]);
+        if (T->parent[b] >= 0) {
+            T->nsrc_sub[T->parent[b]] += T->nsrc_sub[b];
+            T->ntgt_sub[T->parent[b]] += T->ntgt_sub[b];
+        }
+    }
+    return T;
+}
+
+void orc_tree_free(otree *T)
+{
+    if (!T) return;
+    free(T->level); free(T->ic); free(T->cen); free(T->hw); free(T->parent); free(T->child);
+    free(T->level_start); free(T->nsrc_sub); free(T->ntgt_sub);
+    for (int k = 0; k < 3; ++k) { free(T->owner[k]); free(T->own_start[k]); free(T->own_idx[k]); }
+    free(T);
+}
+
+/* info: [n_boxes, n_levels, n_overfull, n_src, n_ctr, n_tgt] and root center/radius */
+void orc_tree_info(const otree *T, int64_t *info, double *root)
+{
+    info[0] = T->nb; info[1] = T->nlev; info[2] = T->n_overfull;
+    info[3] = T->np[0]; info[4] = T->np[1]; info[5] = T->np[2];
+    root[0] = T->root_c[0]; root[1] = T->root_c[1]; root[2] = T->root_c[2]; root[3] = T->root_h;
+}
+
+void orc_tree_arrays(const otree *T, int *level, int64_t *ic, double *cen, double *hw, int *parent, int *child,
+                     int *src_owner, int *ctr_owner, int *tgt_owner)
+{
+    memcpy(level, T->level, sizeof(int) * T->nb);
+    memcpy(ic, T->ic, sizeof(int64_t) * 3 * T->nb);
+    memcpy(cen, T->cen, sizeof(double) * 3 * T->nb);
+    memcpy(hw, T->hw, sizeof(double) * T->nb);
+    memcpy(parent, T->parent, sizeof(int) * T->nb);
+    memcpy(child, T->child, sizeof(int) * 8 * T->nb);
+    memcpy(src_owner, T->owner[0], sizeof(int) * T->np[0]);
+    memcpy(ctr_owner, T->owner[1], sizeof(int) * T->np[1]);
+    memcpy(tgt_owner, T->owner[2], sizeof(int) * T->np[2]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* interaction lists (Section 5.2.3-5.2.4)                                    */
+/* ------------------------------------------------------------------------ */
+
+enum { L_U = 0, L_V, L_WCLOSE, L_WFAR, L_XCLOSE, L_XFAR, L_N };
+
+typedef struct {
+    int nb;
+    int *start[L_N]; /* nb + 1 */
+    int *idx[L_N];
+} olists;
+
+static int is_leaf(const otree *T, int b)
+{
+    for (int o = 0; o < 8; ++o)
+        if (T->child[8 * b + o] >= 0) return 0;
+    return 1;
+}
+
+/* integer extent of a box in units of the finest level Lf: [lo, hi] per dimension */
+static void box_extent(const otree *T, int b, int Lf, int64_t lo[3], int64_t hi[3])
+{
+    int sh = Lf - T->level[b];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = T->ic[3 * b + d] << sh;
+        hi[d] = (T->ic[3 * b + d] + 1) << sh;
+    }
+}
+
+/* Adjacent: the closed cubes intersect and their interiors do not (exact integer test). */
+static int adjacent(const otree *T, int a, int b, int Lf)
+{
+    int64_t la[3], ha[3], lb[3], hb[3];
+    box_extent(T, a, Lf, la, ha);
+    box_extent(T, b, Lf, lb, hb);
+    int closed = 1, open = 1;
+    for (int d = 0; d < 3; ++d) {
+        if (la[d] > hb[d] || lb[d] > ha[d]) closed = 0;
+        if (!(la[d] < hb[d] && lb[d] < ha[d])) open = 0;
+    }
+    return closed && !open;
+}
+
+/* k-colleague: same level, inside the k-near neighborhood (|di| <= k per axis), not the box itself. */
+static int colleague(const otree *T, int a, int b, int k)
+{
+    if (T->level[a] != T->level[b] || a == b) return 0;
+    for (int d = 0; d < 3; ++d) {
+        int64_t di = T->ic[3 * a + d] - T->ic[3 * b + d];
+        if (di < -k || di > k) return 0;
+    }
+    return 1;
+}
+
+/* a adequately separated from TCR(b): l2 distance from the center of a to the boundary of
+ * TCR(b), taken as signed (negative inside), is at least 3|a|. */
+static int sep_a_tcrb(const otree *T, int a, int b)
+{
+    double dx = T->cen[3 * a] - T->cen[3 * b], dy = T->cen[3 * a + 1] - T->cen[3 * b + 1],
+           dz = T->cen[3 * a + 2] - T->cen[3 * b + 2];
+    double dist = sqrt(dx * dx + dy * dy + dz * dz);
+    return dist - (sqrt(3.0) * T->hw[b]) * (1.0 + T->tf) >= 3.0 * T->hw[a];
+}
+
+/* TCR(a) adequately separated from b: l-infinity distance from the center of a to the boundary
+ * of b, signed, is at least 3|a|(1 + t_f). */
+static int sep_tcra_b(const otree *T, int a, int b)
+{
+    double m = 0.0;
+    for (int d = 0; d < 3; ++d) m = fmax(m, fabs(T->cen[3 * a + d] - T->cen[3 * b + d]));
+    return m - T->hw[b] >= (3.0 * T->hw[a]) * (1.0 + T->tf);
+}
+
+static int is_desc(const otree *T, int d, int b) /* strict descendant */
+{
+    for (int w = T->parent[d]; w >= 0; w = T->parent[w])
+        if (w == b) return 1;
+    return 0;
+}
+
+static int finest_level(const otree *T) { return T->nlev - 1; }
+
+static int is_target_box(const otree *T, int b)
+{
+    return (T->own_start[KCTR][b + 1] - T->own_start[KCTR][b]) + (T->own_start[KTGT][b + 1] - T->own_start[KTGT][b]) > 0;
+}
+
+static int is_source_box(const otree *T, int b) { return T->own_start[KSRC][b + 1] - T->own_start[KSRC][b] > 0; }
+
+typedef struct {
+    int n, cap;
+    int *v;
+} ivec;
+
+static void iv_push(ivec *a, int x)
+{
+    if (a->n == a->cap) {
+        a->cap = a->cap ? 2 * a->cap : 16;
+        a->v = realloc(a->v, sizeof(int) * a->cap);
+    }
+    a->v[a->n++] = x;
+}
+
+static int cmp_int(const void *a, const void *b)
+{
+    int x = *(const int *)a, y = *(const int *)b;
+    return (x > y) - (x < y);
+}
+
+static void iv_sort_unique(ivec *a)
+{
+    if (a->n == 0) return;
+    qsort(a->v, a->n, sizeof(int), cmp_int);
+    int k = 1;
+    for (int i = 1; i < a->n; ++i)
+        if (a->v[i] != a->v[k - 1]) a->v[k++] = a->v[i];
+    a->n = k;
+}
+
+static int iv_has(const ivec *a, int x)
+{
+    for (int i = 0; i < a->n; ++i)
+        if (a->v[i] == x) return 1;
+    return 0;
+}
+
+static olists *lists_from_vecs(int nb, ivec *vec /* nb * L_N */)
+{
+    olists *Ls = calloc(1, sizeof(olists));
+    Ls->nb = nb;
+    for (int l = 0; l < L_N; ++l) {
+        Ls->start[l] = calloc(nb + 1, sizeof(int));
+        for (int b = 0; b < nb; ++b) Ls->start[l][b + 1] = Ls->start[l][b] + vec[b * L_N + l].n;
+        Ls->idx[l] = malloc(sizeof(int) * (Ls->start[l][nb] > 0 ? Ls->start[l][nb] : 1));
+        for (int b = 0; b < nb; ++b) {
+            memcpy(Ls->idx[l] + Ls->start[l][b], vec[b * L_N + l].v, sizeof(int) * vec[b * L_N + l].n);
+            free(vec[b * L_N + l].v);
+        }
+    }
+    free(vec);
+    return Ls;
+}
+
+/*
+ * Literal construction of the six lists: every definition of Section 5.2.3-5.2.4
+ * checked by brute force over all boxes (O(N_B^2) and worse).  Readings:
+ *  - k-colleagues exclude the box itself (otherwise a box would be its own
+ *    non-adjacent 2-colleague and List 3/4 would count its own sources twice);
+ *  - descendants are strict; "adjacent" is the exact integer test above;
+ *  - target box = owns a QBX center or a target; lists U, W are made for target
+ *    boxes, lists V, X for target and target-ancestor boxes;
+ *  - boxes whose subtree holds no source are left out of every list.
+ */
+olists *orc_build_lists_slow(const otree *T)
+{
+    int nb = T->nb, Lf = finest_level(T);
+    ivec *vec = calloc((size_t)nb * L_N, sizeof(ivec));
+    ivec *X = calloc(nb, sizeof(ivec));
+    for (int b = 0; b < nb; ++b) {
+        int tgt = is_target_box(T, b), tanc = T->ntgt_sub[b] > 0;
+        if (!tanc) continue;
+        /* List 4 of b */
+        for (int d = 0; d < nb; ++d) {
+            if (!is_leaf(T, d) || !is_source_box(T, d)) continue;
+            int in4 = 0;
+            if (T->parent[b] >= 0 && adjacent(T, d, T->parent[b], Lf) && !adjacent(T, d, b, Lf))
+                for (int a = T->parent[b]; a >= 0; a = T->parent[a])
+                    if (colleague(T, d, a, 2)) in4 = 1;
+            if (colleague(T, d, b, 2) && !adjacent(T, d, b, Lf)) in4 = 1;
+            if (in4) iv_push(&X[b], d);
+        }
+        if (tgt) {
+            /* List 1 */
+            for (int d = 0; d < nb; ++d)
+                if (is_leaf(T, d) && is_source_box(T, d) && (d == b || is_desc(T, d, b) || adjacent(T, d, b, Lf)))
+                    iv_push(&vec[b * L_N + L_U], d);
+            /* List 3, then its close/far split */
+            ivec W = {0};
+            for (int d = 0; d < nb; ++d) {
+                if (T->nsrc_sub[d] == 0) continue;
+                int inDT = 0;
+                for (int w = 0; w < nb && !inDT; ++w)
+                    if (colleague(T, w, b, 2) && is_desc(T, d, w)) inDT = 1;
+                if (!inDT || adjacent(T, d, b, Lf)) continue;
+                int ok = 1;
+                for (int w = T->parent[d]; w >= 0; w = T->parent[w]) {
+                    int wDT = 0;
+                    for (int u = 0; u < nb && !wDT; ++u)
+                        if (colleague(T, u, b, 2) && is_desc(T, w, u)) wDT = 1;
+                    if (wDT && !adjacent(T, w, b, Lf)) ok = 0;
+                }
+                if (ok) iv_push(&W, d);
+            }
+            for (int d = 0; d < nb; ++d) {
+                if (T->nsrc_sub[d] == 0) continue;
+                int inDW = iv_has(&W, d);
+                for (int i = 0; i < W.n && !inDW; ++i)
+                    if (is_desc(T, d, W.v[i])) inDW = 1;
+                if (!inDW) continue;
+                if (!sep_a_tcrb(T, d, b)) {
+                    if (is_leaf(T, d)) iv_push(&vec[b * L_N + L_WCLOSE], d);
+                } else {
+                    int ok = 1;
+                    for (int w = T->parent[d]; w >= 0; w = T->parent[w]) {
+                        int wDW = iv_has(&W, w);
+                        for (int i = 0; i < W.n && !wDW; ++i)
+                            if (is_desc(T, w, W.v[i])) wDW = 1;
+                        if (wDW && sep_a_tcrb(T, w, b)) ok = 0;
+                    }
+                    if (ok) iv_push(&vec[b * L_N + L_WFAR], d);
+                }
+            }
+            free(W.v);
+        }
+        /* List 2 */
+        if (T->parent[b] >= 0) {
+            int pb = T->parent[b];
+            for (int d = 0; d < nb; ++d) {
+                if (T->level[d] != T->level[b] || d == b || T->nsrc_sub[d] == 0) continue;
+                int pd = T->parent[d];
+                if (!(pd == pb || colleague(T, pd, pb, 2))) continue;
+                if (colleague(T, d, b, 2)) continue;
+                iv_push(&vec[b * L_N + L_V], d);
+            }
+        }
+    }
+    /* List 4 close/far: needs X of all ancestors */
+    for (int b = 0; b < nb; ++b) {
+        if (T->ntgt_sub[b] == 0) continue;
+        for (int d = 0; d < nb; ++d) {
+            int inX_anc = 0;
+            for (int w = b; w >= 0; w = T->parent[w])
+                if (iv_has(&X[w], d)) inX_anc = 1;
+            if (inX_anc && !sep_tcra_b(T, b, d)) iv_push(&vec[b * L_N + L_XCLOSE], d);
+        }
+    }
+    for (int b = 0; b < nb; ++b) {
+        if (T->ntgt_sub[b] == 0) continue;
+        for (int i = 0; i < X[b].n; ++i)
+            if (sep_tcra_b(T, b, X[b].v[i])) iv_push(&vec[b * L_N + L_XFAR], X[b].v[i]);
+        int pb = T->parent[b];
+        if (pb >= 0)
+            for (int i = 0; i < vec[pb * L_N + L_XCLOSE].n; ++i) {
+                int d = vec[pb * L_N + L_XCLOSE].v[i];
+                if (sep_tcra_b(T, b, d)) iv_push(&vec[b * L_N + L_XFAR], d);
+            }
+    }
+    for (int b = 0; b < nb; ++b) {
+        free(X[b].v);
+        for (int l = 0; l < L_N; ++l) iv_sort_unique(&vec[b * L_N + l]);
+    }
+    free(X);
+    return lists_from_vecs(nb, vec);
+}
+
+/* Morton order of two same-level integer coordinate triples (z most significant in
+ * each octal digit): the axis with the highest differing bit decides. */
+static int less_msb(uint64_t a, uint64_t b) { return a < b && a < (a ^ b); }
+
+static int morton_less(const int64_t *a, const int64_t *b)
+{
+    int dim = 2;
+    uint64_t best = (uint64_t)(a[2] ^ b[2]);
+    for (int d = 1; d >= 0; --d) {
+        uint64_t x = (uint64_t)(a[d] ^ b[d]);
+        if (less_msb(best, x)) { dim = d; best = x; }
+    }
+    return a[dim] < b[dim];
+}
+
+/* box at (level, ic) or -1; binary search over the level's boxes (Morton-sorted) */
+static int find_box(const otree *T, int lev, const int64_t ic[3])
+{
+    if (lev < 0 || lev >= T->nlev) return -1;
+    int64_t n = (int64_t)1 << lev;
+    for (int d = 0; d < 3; ++d)
+        if (ic[d] < 0 || ic[d] >= n) return -1;
+    int lo = T->level_start[lev], hi = T->level_start[lev + 1];
+    while (lo < hi) {
+        int mid = (lo + hi) / 2;
+        if (morton_less(&T->ic[3 * mid], ic)) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo < T->level_start[lev + 1] && T->ic[3 * lo] == ic[0] && T->ic[3 * lo + 1] == ic[1] && T->ic[3 * lo + 2] == ic[2])
+        return lo;
+    return -1;
+}
+
+static void colleagues(const otree *T, int b, int k, ivec *out)
+{
+    out->n = 0;
+    for (int dz = -k; dz <= k; ++dz)
+        for (int dy = -k; dy <= k; ++dy)
+            for (int dx = -k; dx <= k; ++dx) {
+                if (!dx && !dy && !dz) continue;
+                int64_t ic[3] = {T->ic[3 * b] + dx, T->ic[3 * b + 1] + dy, T->ic[3 * b + 2] + dz};
+                int d = find_box(T, T->level[b], ic);
+                if (d >= 0) iv_push(out, d);
+            }
+}
+
+static void leaf_desc_sources(const otree *T, int b, ivec *out)
+{
+    if (T->nsrc_sub[b] == 0) return;
+    if (is_leaf(T, b)) { iv_push(out, b); return; }
+    for (int o = 0; o < 8; ++o)
+        if (T->child[8 * b + o] >= 0) leaf_desc_sources(T, T->child[8 * b + o], out);
+}
+
+static void adj_leaves_below(const otree *T, int d, int b, int Lf, ivec *out)
+{
+    if (T->nsrc_sub[d] == 0 || !adjacent(T, d, b, Lf)) return;
+    if (is_leaf(T, d)) { iv_push(out, d); return; }
+    for (int o = 0; o < 8; ++o)
+        if (T->child[8 * d + o] >= 0) adj_leaves_below(T, T->child[8 * d + o], b, Lf, out);
+}
+
+/* List 3 search below a box d that is a descendant of a 2-colleague of b */
+static void list3_walk(const otree *T, int d, int b, int Lf, ivec *W)
+{
+    if (T->nsrc_sub[d] == 0) return;
+    if (!adjacent(T, d, b, Lf)) { iv_push(W, d); return; }
+    for (int o = 0; o < 8; ++o)
+        if (T->child[8 * d + o] >= 0) list3_walk(T, T->child[8 * d + o], b, Lf, W);
+}
+
+static void list3_split(const otree *T, int d, int b, ivec *cl, ivec *fa)
+{
+    if (T->nsrc_sub[d] == 0) return;
+    if (sep_a_tcrb(T, d, b)) { iv_push(fa, d); return; }
+    if (is_leaf(T, d)) { iv_push(cl, d); return; }
+    for (int o = 0; o < 8; ++o)
+        if (T->child[8 * d + o] >= 0) list3_split(T, T->child[8 * d + o], b, cl, fa);
+}
+
+/* Same lists as orc_build_lists_slow, built by walking neighborhoods. */
+olists *orc_build_lists(const otree *T)
+{
+    int nb = T->nb, Lf = finest_level(T);
+    ivec *vec = calloc((size_t)nb * L_N, sizeof(ivec));
+    ivec *X = calloc(nb, sizeof(ivec));
+    ivec C = {0}, CA = {0};
+    for (int b = 0; b < nb; ++b) {
+        if (T->ntgt_sub[b] == 0) continue;
+        int pb = T->parent[b];
+        colleagues(T, b, 2, &C);
+        /* List 4 */
+        for (int i = 0; i < C.n; ++i) {
+            int d = C.v[i];
+            if (is_leaf(T, d) && is_source_box(T, d) && !adjacent(T, d, b, Lf)) iv_push(&X[b], d);
+        }
+        for (int a = pb; a >= 0; a = T->parent[a]) {
+            colleagues(T, a, 2, &CA);
+            for (int i = 0; i < CA.n; ++i) {
+                int d = CA.v[i];
+                if (is_leaf(T, d) && is_source_box(T, d) && adjacent(T, d, pb, Lf) && !adjacent(T, d, b, Lf))
+                    iv_push(&X[b], d);
+            }
+        }
+        iv_sort_unique(&X[b]);
+        /* List 2 */
+        if (pb >= 0) {
+            colleagues(T, pb, 2, &CA);
+            iv_push(&CA, pb);
+            for (int i = 0; i < CA.n; ++i)
+                for (int o = 0; o < 8; ++o) {
+                    int d = T->child[8 * CA.v[i] + o];
+                    if (d < 0 || d == b || T->nsrc_sub[d] == 0) continue;
+                    if (colleague(T, d, b, 2)) continue;
+                    iv_push(&vec[b * L_N + L_V], d);
+                }
+        }
+        if (!is_target_box(T, b)) continue;
+        /* List 1: b if leaf, leaf descendants, adjacent leaves at this level or below, and coarser adjacent leaves */
+        ivec *U = &vec[b * L_N + L_U];
+        leaf_desc_sources(T, b, U);
+        for (int i = 0; i < C.n; ++i) adj_leaves_below(T, C.v[i], b, Lf, U);
+        for (int a = pb; a >= 0; a = T->parent[a]) {
+            colleagues(T, a, 1, &CA);
+            for (int i = 0; i < CA.n; ++i) {
+                int d = CA.v[i];
+                if (is_leaf(T, d) && is_source_box(T, d) && adjacent(T, d, b, Lf)) iv_push(U, d);
+            }
+        }
+        /* List 3 and its split */
+        ivec W = {0};
+        for (int i = 0; i < C.n; ++i)
+            for (int o = 0; o < 8; ++o) {
+                int d = T->child[8 * C.v[i] + o];
+                if (d >= 0) list3_walk(T, d, b, Lf, &W);
+            }
+        for (int i = 0; i < W.n; ++i) list3_split(T, W.v[i], b, &vec[b * L_N + L_WCLOSE], &vec[b * L_N + L_WFAR]);
+        free(W.v);
+    }
+    /* List 4 close/far, top-down (parents precede children in box order) */
+    for (int b = 0; b < nb; ++b) {
+        if (T->ntgt_sub[b] == 0) continue;
+        int pb = T->parent[b];
+        ivec cand = {0};
+        for (int i = 0; i < X[b].n; ++i) iv_push(&cand, X[b].v[i]);
+        if (pb >= 0)
+            for (int i = 0; i < vec[pb * L_N + L_XCLOSE].n; ++i) iv_push(&cand, vec[pb * L_N + L_XCLOSE].v[i]);
+        iv_sort_unique(&cand);
+        for (int i = 0; i < cand.n; ++i) {
+            int d = cand.v[i];
+            if (sep_tcra_b(T, b, d)) iv_push(&vec[b * L_N + L_XFAR], d);
+            else iv_push(&vec[b * L_N + L_XCLOSE], d);
+        }
+        free(cand.v);
+    }
+    for (int b = 0; b < nb; ++b) {
+        free(X[b].v);
+        for (int l = 0; l < L_N; ++l) iv_sort_unique(&vec[b * L_N + l]);
+    }
+    free(X);
+    free(C.v);
+    free(CA.v);
+    return lists_from_vecs(nb, vec);
+}
+
+void orc_lists_free(olists *Ls)
+{
+    if (!Ls) return;
+    for (int l = 0; l < L_N; ++l) { free(Ls->start[l]); free(Ls->idx[l]); }
+    free(Ls);
+}
+
+int64_t orc_lists_nnz(const olists *Ls, int which) { return Ls->start[which][Ls->nb]; }
+
+void orc_lists_get(const olists *Ls, int which, int *start, int *idx)
+{
+    memcpy(start, Ls->start[which], sizeof(int) * (Ls->nb + 1));
+    memcpy(idx, Ls->idx[which], sizeof(int) * Ls->start[which][Ls->nb]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Algorithm 4, Stages 2-9                                                    */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const double *sxyz, *tgxyz, *cxyz;
+    int ns, nc, nt;
+    double *q;   /* ns charges, w sigma */
+    double *dip; /* 3 * ns dipoles w mu n, or NULL */
+} srcset;
+
+static void src_q_d(const srcset *S, int j, double s[3], double *q, double d[3], int *has_d)
+{
+    get_pt(S->sxyz, S->ns, j, s);
+    *q = S->q[j];
+    *has_d = S->dip != NULL;
+    if (S->dip) { d[0] = S->dip[3 * j]; d[1] = S->dip[3 * j + 1]; d[2] = S->dip[3 * j + 2]; }
+}
+
+/* QBX local at center c (order q) += P2QBXL over all sources owned by the boxes of a list */
+static void direct_to_center(const otree *T, const srcset *S, const int *lst, int n, const double c[3], int q, cplx *Lq)
+{
+    double s[3], d[3], qq;
+    int hd;
+    for (int i = 0; i < n; ++i) {
+        int box = lst[i];
+        for (int k = T->own_start[KSRC][box]; k < T->own_start[KSRC][box + 1]; ++k) {
+            int j = T->own_idx[KSRC][k];
+            src_q_d(S, j, s, &qq, d, &hd);
+            p2l(q, c, s, qq, hd ? d : NULL, Lq);
+        }
+    }
+}
+
+static double direct_to_point(const otree *T, const srcset *S, const int *lst, int n, const double t[3])
+{
+    double s[3], d[3], qq, acc = 0.0;
+    int hd;
+    for (int i = 0; i < n; ++i) {
+        int box = lst[i];
+        for (int k = T->own_start[KSRC][box]; k < T->own_start[KSRC][box + 1]; ++k) {
+            int j = T->own_idx[KSRC][k];
+            src_q_d(S, j, s, &qq, d, &hd);
+            acc += p2p(s, qq, hd ? d : NULL, t);
+        }
+    }
+    return acc;
+}
+
+static int sq(int p) { return (p + 1) * (p + 1); }
+
+static void setup_sources(srcset *S, const double *sxyz, int ns, const double *w, const double *sigma,
+                          const double *mu, const double *nrm)
+{
+    S->sxyz = sxyz;
+    S->ns = ns;
+    S->q = calloc(ns > 0 ? ns : 1, sizeof(double));
+    S->dip = NULL;
+    for (int j = 0; j < ns; ++j) S->q[j] = sigma ? w[j] * sigma[j] : 0.0;
+    if (mu) {
+        S->dip = malloc(sizeof(double) * 3 * (ns > 0 ? ns : 1));
+        for (int j = 0; j < ns; ++j)
+            for (int d = 0; d < 3; ++d) S->dip[3 * j + d] = w[j] * mu[j] * nrm[d * ns + j];
+    }
+}
+
+/*
+ * GIGAQBX FMM (Algorithm 4, Stages 2-9).  pot[t] = S[sigma](t) + D[mu](t) at every target.
+ * Charges are w sigma, dipoles w mu n.  tgt_ctr[t] >= 0: t is evaluated through the QBX
+ * local of that center (Stage 9, second loop); tgt_ctr[t] < 0: t is a conventional
+ * (point) target.  Orders: per box p_fmm[b] (or the fixed p_fmm), per center p_qbx[c]
+ * (or the fixed p_qbx); a translation between different orders truncates or pads.
+ * If qbx_out is given it receives each center's QBX local, (qmax+1)^2 complex per center.
+ */
+int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, const double *w, const double *sigma,
+                 const double *mu, const double *nrm, const double *cxyz, int nc, const double *txyz,
+                 const int *tgt_ctr, int nt, int p_qbx, int p_fmm, const signed char *qctr, const signed char *pbox,
+                 double *pot, double *qbx_out, int qmax)
+{
+    init_tables();
+    if (ns != T->np[KSRC] || nc != T->np[KCTR] || nt != T->np[KTGT]) return -1;
+    srcset S;
+    setup_sources(&S, sxyz, ns, w, sigma, mu, nrm);
+    int nb = T->nb;
+    int pmax = p_fmm;
+    if (pbox) { pmax = 0; for (int b = 0; b < nb; ++b) if (pbox[b] > pmax) pmax = pbox[b]; }
+    int qm = p_qbx;
+    if (qctr) { qm = 0; for (int c = 0; c < nc; ++c) if (qctr[c] > qm) qm = qctr[c]; }
+    int nP = sq(pmax), nQ = sq(qm);
+    cplx *M = calloc((size_t)nb * nP, sizeof(cplx));
+    cplx *L = calloc((size_t)nb * nP, sizeof(cplx));
+    cplx *Lq = calloc((size_t)(nc > 0 ? nc : 1) * nQ, sizeof(cplx));
+    double *pnear = calloc(nt > 0 ? nt : 1, sizeof(double));
+    double s[3], d[3], c[3], t[3], qq;
+    int hd;
+#define PB(b) (pbox ? (int)pbox[b] : p_fmm)
+#define QC(cc) (qctr ? (int)qctr[cc] : p_qbx)
+
+    /* Stage 2: multipoles of leaves, then upward pass in postorder */
+    for (int b = 0; b < nb; ++b)
+        for (int k = T->own_start[KSRC][b]; k < T->own_start[KSRC][b + 1]; ++k) {
+            src_q_d(&S, T->own_idx[KSRC][k], s, &qq, d, &hd);
+            p2m(PB(b), &T->cen[3 * b], s, qq, hd ? d : NULL, &M[(size_t)b * nP]);
+        }
+    for (int b = nb - 1; b >= 1; --b) {
+        int pa = T->parent[b];
+        if (T->nsrc_sub[b] > 0) m2m(PB(b), &T->cen[3 * b], &M[(size_t)b * nP], PB(pa), &T->cen[3 * pa], &M[(size_t)pa * nP]);
+    }
+
+    /* Stages 3, 5(a), 6(a): direct interactions from U, W-close, X-close */
+    const int direct_lists[3] = {L_U, L_WCLOSE, L_XCLOSE};
+    for (int li = 0; li < 3; ++li) {
+        int l = direct_lists[li];
+        for (int b = 0; b < nb; ++b) {
+            const int *lst = Ls->idx[l] + Ls->start[l][b];
+            int n = Ls->start[l][b + 1] - Ls->start[l][b];
+            if (n == 0) continue;
+            for (int k = T->own_start[KTGT][b]; k < T->own_start[KTGT][b + 1]; ++k) {
+                int ti = T->own_idx[KTGT][k];
+                if (tgt_ctr[ti] >= 0) continue;
+                get_pt(txyz, nt, ti, t);
+                pnear[ti] += direct_to_point(T, &S, lst, n, t);
+            }
+            for (int k = T->own_start[KCTR][b]; k < T->own_start[KCTR][b + 1]; ++k) {
+                int ci = T->own_idx[KCTR][k];
+                get_pt(cxyz, nc, ci, c);
+                direct_to_center(T, &S, lst, n, c, QC(ci), &Lq[(size_t)ci * nQ]);
+            }
+        }
+    }
+
+    /* Stage 4: List 2 multipole-to-local */
+    for (int b = 0; b < nb; ++b)
+        for (int i = Ls->start[L_V][b]; i < Ls->start[L_V][b + 1]; ++i) {
+            int dd = Ls->idx[L_V][i];
+            m2l(PB(dd), &T->cen[3 * dd], &M[(size_t)dd * nP], PB(b), &T->cen[3 * b], &L[(size_t)b * nP]);
+        }
+
+    /* Stage 5(b): List 3 far multipoles at point targets and QBX centers */
+    for (int b = 0; b < nb; ++b)
+        for (int i = Ls->start[L_WFAR][b]; i < Ls->start[L_WFAR][b + 1]; ++i) {
+            int dd = Ls->idx[L_WFAR][i];
+            for (int k = T->own_start[KTGT][b]; k < T->own_start[KTGT][b + 1]; ++k) {
+                int ti = T->own_idx[KTGT][k];
+                if (tgt_ctr[ti] >= 0) continue;
+                get_pt(txyz, nt, ti, t);
+                pnear[ti] += m2p(PB(dd), &T->cen[3 * dd], &M[(size_t)dd * nP], t);
+            }
+            for (int k = T->own_start[KCTR][b]; k < T->own_start[KCTR][b + 1]; ++k) {
+                int ci = T->own_idx[KCTR][k];
+                get_pt(cxyz, nc, ci, c);
+                m2l(PB(dd), &T->cen[3 * dd], &M[(size_t)dd * nP], QC(ci), c, &Lq[(size_t)ci * nQ]);
+            }
+        }
+
+    /* Stage 6(b): List 4 far sources to local expansions of the box */
+    for (int b = 0; b < nb; ++b)
+        for (int i = Ls->start[L_XFAR][b]; i < Ls->start[L_XFAR][b + 1]; ++i) {
+            int dd = Ls->idx[L_XFAR][i];
+            for (int k = T->own_start[KSRC][dd]; k < T->own_start[KSRC][dd + 1]; ++k) {
+                src_q_d(&S, T->own_idx[KSRC][k], s, &qq, d, &hd);
+                p2l(PB(b), &T->cen[3 * b], s, qq, hd ? d : NULL, &L[(size_t)b * nP]);
+            }
+        }
+
+    /* Stage 7: downward pass in preorder */
+    for (int b = 1; b < nb; ++b) {
+        int pa = T->parent[b];
+        if (T->ntgt_sub[b] > 0) l2l(PB(pa), &T->cen[3 * pa], &L[(size_t)pa * nP], PB(b), &T->cen[3 * b], &L[(size_t)b * nP]);
+    }
+
+    /* Stage 8: box locals to QBX centers */
+    for (int b = 0; b < nb; ++b)
+        for (int k = T->own_start[KCTR][b]; k < T->own_start[KCTR][b + 1]; ++k) {
+            int ci = T->own_idx[KCTR][k];
+            get_pt(cxyz, nc, ci, c);
+            l2l(PB(b), &T->cen[3 * b], &L[(size_t)b * nP], QC(ci), c, &Lq[(size_t)ci * nQ]);
+        }
+
+    /* Stage 9: final potentials */
+    for (int b = 0; b < nb; ++b)
+        for (int k = T->own_start[KTGT][b]; k < T->own_start[KTGT][b + 1]; ++k) {
+            int ti = T->own_idx[KTGT][k];
+            get_pt(txyz, nt, ti, t);
+            int ci = tgt_ctr[ti];
+            if (ci < 0) {
+                pot[ti] = pnear[ti] + l2p(PB(b), &T->cen[3 * b], &L[(size_t)b * nP], t);
+            } else {
+                get_pt(cxyz, nc, ci, c);
+                pot[ti] = l2p(QC(ci), c, &Lq[(size_t)ci * nQ], t);
+            }
+        }
+    if (qbx_out)
+        for (int ci = 0; ci < nc; ++ci)
+            for (int i = 0; i < sq(qmax); ++i) {
+                cplx v = (i < nQ) ? Lq[(size_t)ci * nQ + i] : 0.0;
+                qbx_out[2 * ((size_t)ci * sq(qmax) + i)] = creal(v);
+                qbx_out[2 * ((size_t)ci * sq(qmax) + i) + 1] = cimag(v);
+            }
+#undef PB
+#undef QC
+    free(M); free(L); free(Lq); free(pnear); free(S.q); free(S.dip);
+    return 0;
+}
+
+/*
+ * Direct (unaccelerated) QBX: every source into every center's order-q local
+ * (eq. qbxcoeff discretised by the source quadrature), evaluated at the associated
+ * targets (eq. qbxlocal); point targets get the plain quadrature sum of G.
+ */
+int orc_direct_eval(const double *sxyz, int ns, const double *w, const double *sigma, const double *mu,
+                    const double *nrm, const double *cxyz, int nc, const double *txyz, const int *tgt_ctr, int nt,
+                    int p_qbx, const signed char *qctr, double *pot)
+{
+    init_tables();
+    srcset S;
+    setup_sources(&S, sxyz, ns, w, sigma, mu, nrm);
+    int qm = p_qbx;
+    if (qctr) { qm = 0; for (int c = 0; c < nc; ++c) if (qctr[c] > qm) qm = qctr[c]; }
+    cplx *Lq = malloc(sizeof(cplx) * sq(qm));
+    double s[3], d[3], c[3], t[3], qq;
+    int hd;
+    for (int ti = 0; ti < nt; ++ti) {
+        get_pt(txyz, nt, ti, t);
+        int ci = tgt_ctr[ti];
+        if (ci < 0) {
+            double acc = 0.0;
+            for (int j = 0; j < ns; ++j) {
+                src_q_d(&S, j, s, &qq, d, &hd);
+                acc += p2p(s, qq, hd ? d : NULL, t);
+            }
+            pot[ti] = acc;
+        } else {
+            int q = qctr ? qctr[ci] : p_qbx;
+            for (int i = 0; i < sq(q); ++i) Lq[i] = 0.0;
+            get_pt(cxyz, nc, ci, c);
+            for (int j = 0; j < ns; ++j) {
+                src_q_d(&S, j, s, &qq, d, &hd);
+                p2l(q, c, s, qq, hd ? d : NULL, Lq);
+            }
+            pot[ti] = l2p(q, c, Lq, t);
+        }
+    }
+    free(Lq); free(S.q); free(S.dip);
+    return 0;
+}
+
+/*
+ * Modeled operation counts per list (Table ilist-operation-counts), from the built lists:
+ * out = [U, V, W-close, W-far, X-close, X-far] with n_t = QBX centers owned by the target box.
+ */
+void orc_lists_cost(const otree *T, const olists *Ls, int p_qbx, int p_fmm, double *out)
+{
+    double q2 = (double)p_qbx * p_qbx, p3 = (double)p_fmm * p_fmm * p_fmm, p2 = (double)p_fmm * p_fmm;
+    for (int l = 0; l < L_N; ++l) out[l] = 0.0;
+    for (int b = 0; b < T->nb; ++b) {
+        double nt = T->own_start[KCTR][b + 1] - T->own_start[KCTR][b];
+        for (int l = 0; l < L_N; ++l)
+            for (int i = Ls->start[l][b]; i < Ls->start[l][b + 1]; ++i) {
+                int d = Ls->idx[l][i];
+                double nsd = T->own_start[KSRC][d + 1] - T->own_start[KSRC][d];
+                if (l == L_U || l == L_WCLOSE || l == L_XCLOSE) out[l] += q2 * nsd * nt;
+                else if (l == L_V) out[l] += p3;
+                else if (l == L_WFAR) out[l] += p3 * nt;
+                else out[l] += p2 * T->nsrc_sub[d];
+            }
+    }
+}

@@ -1,0 +1,19 @@
+"""Seeded synthetic inputs shared by the oracle tests, the CUDA-path tests and bench.py.
+
+This package only produces geometry and densities (mesh nodes, quadrature
+weights, normals, expansion centers and radii, targets and their center
+association).  It contains none of the evaluation method's arithmetic: no
+spherical-harmonic expansions, translations, trees or interaction lists.
+"""
+from .surfaces import (  # noqa: F401
+    Surface,
+    make_surface,
+    sphere_radius,
+    star_radius,
+    real_ylm,
+    triangle_rule,
+    greens_density,
+    random_harmonic_density,
+    volume_targets,
+    config_surface,
+)

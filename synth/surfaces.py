@@ -1,0 +1,367 @@
+"""Synthetic curved-triangle surfaces shaped like the paper's test geometries.
+
+Recipe (Section 6 test geometries; Section 2.3 discretization; Section 3.2
+expansion radii; eq. (expansion-centers)):
+
+* The regular icosahedron is split into 20 n^2 flat sub-triangles.  On each one,
+  15 equispaced barycentric points (degree 4) are projected radially onto the
+  surface ``x = r(x_hat) x_hat``; they define a degree-4 Lagrange element map
+  Psi_k from the unit right triangle (Section 2.3, element mappings).
+* Sources are the 15 nodes of a conical-product (Stroud) rule on each element:
+  5 Gauss-Jacobi(alpha=1, beta=0) points in the collapsed direction times
+  3 Gauss-Legendre points, exact for total degree 5.  Each source weight is the
+  rule weight times the area element |d1 Psi x d2 Psi| (Section 2.3).
+* The resolution measure eta_k (eq. stretch-factor) is the maximum over the
+  element's 15 quadrature and 15 geometry nodes of twice the largest singular
+  value of the map's Jacobian composed with the map from the bi-unit
+  equilateral triangle; the expansion radius is r_k = eta_k / 2
+  (eq. expansion-radii).
+* Two centers per node, x_i + r n_i (exterior) and x_i - r n_i (interior)
+  (eq. expansion-centers).  One on-surface target per center at x_i.
+
+Everything is float64 and deterministic for a given argument set.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# --------------------------------------------------------------------------
+# spherical harmonics used only to shape surfaces and densities
+# --------------------------------------------------------------------------
+
+
+def _legendre_nocs(n: int, m: int, x: np.ndarray) -> np.ndarray:
+    """Associated Legendre function P_n^m(x), m >= 0, without the (-1)^m phase."""
+    from scipy.special import lpmv
+
+    return ((-1.0) ** m) * lpmv(m, n, x)
+
+
+def real_ylm(n: int, m: int, xyz: np.ndarray) -> np.ndarray:
+    """Real basis harmonic of direction xyz (3, N): Re Y_n^m for m >= 0, Im Y_n^|m| for m < 0.
+
+    Y_n^m uses the normalisation of eq. (spherical-harmonics):
+    sqrt((2n+1)/(4 pi) (n-|m|)!/(n+|m|)!) P_n^|m|(cos theta) e^{i m phi}.
+    """
+    x, y, z = xyz
+    r = np.sqrt(x * x + y * y + z * z)
+    ct = np.clip(z / r, -1.0, 1.0)
+    ph = np.arctan2(y, x)
+    am = abs(m)
+    norm = math.sqrt((2 * n + 1) / (4 * math.pi) * math.factorial(n - am) / math.factorial(n + am))
+    base = norm * _legendre_nocs(n, am, ct)
+    return base * (np.cos(am * ph) if m >= 0 else np.sin(am * ph))
+
+
+def sphere_radius(xhat: np.ndarray) -> np.ndarray:
+    return np.ones(xhat.shape[1])
+
+
+def star_radius(terms):
+    """r(x_hat) = 1 + sum_k a_k Re Y_{n_k}^{m_k}(x_hat); terms = [(a, n, m), ...]."""
+
+    def radius(xhat: np.ndarray) -> np.ndarray:
+        r = np.ones(xhat.shape[1])
+        for a, n, m in terms:
+            r = r + a * real_ylm(n, m, xhat)
+        return r
+
+    return radius
+
+
+# --------------------------------------------------------------------------
+# reference-triangle quadrature
+# --------------------------------------------------------------------------
+
+
+def _golub_welsch_jacobi(npts: int, alpha: float, beta: float):
+    """Gauss-Jacobi nodes/weights on [-1, 1] for weight (1-t)^alpha (1+t)^beta (Golub-Welsch)."""
+    ab = alpha + beta
+    a = np.empty(npts)
+    b = np.empty(max(npts - 1, 0))
+    for k in range(npts):
+        den = (2 * k + ab) * (2 * k + ab + 2)
+        a[k] = (beta * beta - alpha * alpha) / den if den != 0 else (beta - alpha) / (ab + 2)
+    for k in range(1, npts):
+        num = 4.0 * k * (k + alpha) * (k + beta) * (k + ab)
+        den = (2 * k + ab) ** 2 * (2 * k + ab + 1) * (2 * k + ab - 1)
+        b[k - 1] = math.sqrt(num / den)
+    jac = np.diag(a) + np.diag(b, 1) + np.diag(b, -1)
+    t, v = np.linalg.eigh(jac)
+    mu0 = 2.0 ** (ab + 1) * math.gamma(alpha + 1) * math.gamma(beta + 1) / math.gamma(ab + 2)
+    w = mu0 * v[0, :] ** 2
+    return t, w
+
+
+def triangle_rule():
+    """15-node conical-product rule on the unit right triangle {u, v >= 0, u + v <= 1}.
+
+    Duffy collapse u = xi, v = (1 - xi) eta with Jacobian (1 - xi): 5-point
+    Gauss-Jacobi(1, 0) in xi and 3-point Gauss-Legendre in eta.  Exact for
+    every monomial u^a v^b with b <= 5 and a + b <= 9 (so total degree 5).
+    Returns (u, v, w) with sum(w) = 1/2.
+    """
+    tj, wj = _golub_welsch_jacobi(5, 1.0, 0.0)
+    xi = 0.5 * (tj + 1.0)
+    wxi = wj / 4.0
+    tl, wl = np.polynomial.legendre.leggauss(3)
+    eta = 0.5 * (tl + 1.0)
+    weta = 0.5 * wl
+    u = np.repeat(xi, 3)
+    v = (1.0 - u) * np.tile(eta, 5)
+    w = np.repeat(wxi, 3) * np.tile(weta, 5)
+    return u, v, w
+
+
+# degree-4 Lagrange element on the unit right triangle
+_GEO_IJ = [(i, j) for j in range(5) for i in range(5 - j)]  # 15 nodes (u, v) = (i/4, j/4)
+_MONO = [(a, b) for a in range(5) for b in range(5 - a)]
+
+
+def _lagrange_coeffs():
+    pts = np.array([(i / 4.0, j / 4.0) for i, j in _GEO_IJ])
+    vander = np.array([[p[0] ** a * p[1] ** b for a, b in _MONO] for p in pts])
+    return np.linalg.inv(vander)  # column k: monomial coefficients of basis k
+
+
+_LAG = _lagrange_coeffs()
+
+
+def _lagrange_eval(u: np.ndarray, v: np.ndarray):
+    """Values and (d/du, d/dv) of the 15 degree-4 Lagrange basis functions at (u, v)."""
+    mono = np.stack([u ** a * v ** b for a, b in _MONO], axis=-1)
+    du = np.stack([a * u ** max(a - 1, 0) * v ** b if a > 0 else 0 * u for a, b in _MONO], axis=-1)
+    dv = np.stack([b * u ** a * v ** max(b - 1, 0) if b > 0 else 0 * u for a, b in _MONO], axis=-1)
+    return mono @ _LAG, du @ _LAG, dv @ _LAG
+
+
+def _icosahedron():
+    phi = (1.0 + math.sqrt(5.0)) / 2.0
+    verts = []
+    for s1 in (-1.0, 1.0):
+        for s2 in (-1.0, 1.0):
+            verts += [(0.0, s1, s2 * phi), (s1, s2 * phi, 0.0), (s2 * phi, 0.0, s1)]
+    verts = np.array(verts)
+    verts /= np.linalg.norm(verts, axis=1)[:, None]
+    # faces: all triples of mutually nearest vertices (edge length is the minimum distance)
+    d = np.linalg.norm(verts[:, None, :] - verts[None, :, :], axis=-1)
+    emin = np.min(d[d > 1e-9])
+    adj = np.abs(d - emin) < 1e-9
+    faces = []
+    for a in range(12):
+        for b in range(a + 1, 12):
+            for c in range(b + 1, 12):
+                if adj[a, b] and adj[b, c] and adj[a, c]:
+                    A, B, C = verts[a], verts[b], verts[c]
+                    if np.dot(np.cross(B - A, C - A), A + B + C) < 0:
+                        b2, c2 = c, b
+                    else:
+                        b2, c2 = b, c
+                    faces.append((a, b2, c2))
+    assert len(faces) == 20
+    return verts, np.array(faces)
+
+
+def _flat_subtriangles(n_sub: int) -> np.ndarray:
+    """(K, 3, 3) flat sub-triangle vertices, outward-oriented, K = 20 n_sub^2."""
+    verts, faces = _icosahedron()
+    tris = []
+    for a, b, c in faces:
+        A, B, C = verts[a], verts[b], verts[c]
+
+        def P(i, j):
+            return A + (i / n_sub) * (B - A) + (j / n_sub) * (C - A)
+
+        for j in range(n_sub):
+            for i in range(n_sub - j):
+                tris.append((P(i, j), P(i + 1, j), P(i, j + 1)))
+                if i + j <= n_sub - 2:
+                    tris.append((P(i + 1, j), P(i + 1, j + 1), P(i, j + 1)))
+    return np.array(tris)
+
+
+# --------------------------------------------------------------------------
+# surface assembly
+# --------------------------------------------------------------------------
+
+
+@dataclass
+class Surface:
+    """Discretised surface.  Arrays of points are SoA (3, N), float64."""
+
+    n_elem: int
+    src_xyz: np.ndarray  # (3, N_S) quadrature nodes
+    src_w: np.ndarray  # (N_S,) rule weight x area element
+    src_n: np.ndarray  # (3, N_S) outward unit normals
+    src_elem: np.ndarray  # (N_S,) element index
+    elem_eta: np.ndarray  # (K,) resolution measure eta_k
+    ctr_xyz: np.ndarray  # (3, N_C) centers: [exterior (+) for all nodes, interior (-) for all nodes]
+    ctr_r: np.ndarray  # (N_C,) expansion radius
+    ctr_side: np.ndarray  # (N_C,) +1 exterior, -1 interior
+    tgt_xyz: np.ndarray  # (3, N_T) on-surface targets, one per center
+    tgt_ctr: np.ndarray  # (N_T,) int32 associated center
+    radius_fn: object = field(repr=False, default=None)
+
+    @property
+    def n_src(self) -> int:
+        return self.src_xyz.shape[1]
+
+    @property
+    def n_ctr(self) -> int:
+        return self.ctr_xyz.shape[1]
+
+
+_AINV = np.array([[math.sqrt(3.0), -1.0], [0.0, 2.0]]) / (2.0 * math.sqrt(3.0))  # inverse of [[2,1],[0,sqrt3]]
+
+
+def _stretch(du: np.ndarray, dv: np.ndarray) -> np.ndarray:
+    """2 sigma_1(J A^{-1}) for Jacobian columns du, dv (..., 3) (eq. stretch-factor)."""
+    c0 = du * _AINV[0, 0] + dv * _AINV[1, 0]
+    c1 = du * _AINV[0, 1] + dv * _AINV[1, 1]
+    g00 = np.sum(c0 * c0, -1)
+    g11 = np.sum(c1 * c1, -1)
+    g01 = np.sum(c0 * c1, -1)
+    tr = g00 + g11
+    det = g00 * g11 - g01 * g01
+    lam = 0.5 * (tr + np.sqrt(np.maximum(tr * tr - 4.0 * det, 0.0)))
+    return 2.0 * np.sqrt(lam)
+
+
+def make_surface(n_sub: int, radius_fn=sphere_radius, scale: float = 1.0, offset=(0.0, 0.0, 0.0)) -> Surface:
+    flat = _flat_subtriangles(n_sub)  # (K, 3, 3)
+    K = flat.shape[0]
+    V0, V1, V2 = flat[:, 0], flat[:, 1], flat[:, 2]
+    gi = np.array([i for i, _ in _GEO_IJ]) / 4.0
+    gj = np.array([j for _, j in _GEO_IJ]) / 4.0
+    pts = V0[:, None, :] + gi[None, :, None] * (V1 - V0)[:, None, :] + gj[None, :, None] * (V2 - V0)[:, None, :]
+    xhat = pts / np.linalg.norm(pts, axis=-1, keepdims=True)
+    rad = radius_fn(xhat.reshape(-1, 3).T).reshape(K, 15)
+    geo = xhat * rad[..., None] * scale + np.asarray(offset)[None, None, :]  # (K, 15, 3)
+
+    qu, qv, qw = triangle_rule()
+    phi, dphu, dphv = _lagrange_eval(qu, qv)  # (15 quad, 15 basis)
+    x = np.einsum("qb,kbd->kqd", phi, geo)
+    du = np.einsum("qb,kbd->kqd", dphu, geo)
+    dv = np.einsum("qb,kbd->kqd", dphv, geo)
+    cr = np.cross(du, dv)
+    area = np.linalg.norm(cr, axis=-1)
+    nrm = cr / area[..., None]
+    w = qw[None, :] * area
+
+    # resolution measure: max over quadrature + geometry nodes of the element
+    _, gdu, gdv = _lagrange_eval(gi, gj)
+    du_g = np.einsum("qb,kbd->kqd", gdu, geo)
+    dv_g = np.einsum("qb,kbd->kqd", gdv, geo)
+    eta = np.maximum(_stretch(du, dv).max(axis=1), _stretch(du_g, dv_g).max(axis=1))
+
+    src_xyz = np.ascontiguousarray(x.reshape(-1, 3).T)
+    src_n = np.ascontiguousarray(nrm.reshape(-1, 3).T)
+    src_w = np.ascontiguousarray(w.reshape(-1))
+    src_elem = np.repeat(np.arange(K, dtype=np.int32), 15)
+    r = 0.5 * eta[src_elem]
+    N = src_xyz.shape[1]
+    ctr = np.concatenate([src_xyz + r * src_n, src_xyz - r * src_n], axis=1)
+    ctr_r = np.concatenate([r, r])
+    side = np.concatenate([np.ones(N, np.int8), -np.ones(N, np.int8)])
+    tgt = np.concatenate([src_xyz, src_xyz], axis=1)
+    tctr = np.arange(2 * N, dtype=np.int32)
+    return Surface(K, src_xyz, src_w, src_n, src_elem, eta, np.ascontiguousarray(ctr), ctr_r, side,
+                   np.ascontiguousarray(tgt), tctr, radius_fn)
+
+
+# --------------------------------------------------------------------------
+# densities and off-surface targets
+# --------------------------------------------------------------------------
+
+
+def greens_density(surf: Surface, x0=(3.0, 1.0, 2.0)):
+    """u = 1/|x - x0| and its outward normal derivative at the sources.
+
+    Green's formula (Section 6.1): S(d_n u) - D(u) = u/2 on the surface for u
+    harmonic inside.  Returns (u, dudn) at the sources.
+    """
+    d = surf.src_xyz - np.asarray(x0)[:, None]
+    rr = np.sqrt(np.sum(d * d, axis=0))
+    u = 1.0 / rr
+    dudn = -np.sum(surf.src_n * d, axis=0) / rr ** 3
+    return u, dudn
+
+
+def random_harmonic_density(surf: Surface, nmax: int = 10, seed: int = 4):
+    """sum over n <= nmax, real basis index m, of c_nm Y~_n^m(x_hat), c_nm ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    xhat = surf.src_xyz / np.linalg.norm(surf.src_xyz, axis=0)
+    out = np.zeros(surf.n_src)
+    for n in range(nmax + 1):
+        for m in range(-n, n + 1):
+            out += rng.standard_normal() * real_ylm(n, m, xhat)
+    return out
+
+
+def volume_targets(surf: Surface, n: int = 10000, seed: int = 2, box: float = 2.0, eps_tgt: float = 0.05):
+    """Uniform points in [-box, box]^3 with target association (Algorithm 3).
+
+    Danger radius eta_k/2 around each source; an endangered target is matched
+    to the closest center on its preferred side (sign of (t - s*) . n(s*) for the
+    nearest source s*) within r_c (1 + eps_tgt).  Returns (xyz (3, n), ctr index
+    int32 with -1 = point target, flagged bool = endangered but unassociated).
+    """
+    from scipy.spatial import cKDTree
+
+    rng = np.random.default_rng(seed)
+    t = rng.uniform(-box, box, size=(n, 3))
+    src = surf.src_xyz.T
+    stree = cKDTree(src)
+    rdanger = 0.5 * surf.elem_eta[surf.src_elem]
+    dmax = rdanger.max()
+    dist, near = stree.query(t)
+    ctr_idx = np.full(n, -1, np.int32)
+    flagged = np.zeros(n, bool)
+    cand = np.nonzero(dist <= dmax)[0]
+    ctree = cKDTree(surf.ctr_xyz.T)
+    rmax = surf.ctr_r.max() * (1.0 + eps_tgt)
+    for i in cand:
+        idx = stree.query_ball_point(t[i], dmax)
+        idx = np.asarray(idx)
+        dd = np.linalg.norm(src[idx] - t[i], axis=1)
+        if not np.any(dd <= rdanger[idx]):
+            continue
+        s = near[i]
+        side = 1 if np.dot(t[i] - src[s], surf.src_n[:, s]) > 0 else -1
+        cidx = np.asarray(ctree.query_ball_point(t[i], rmax))
+        best, bestd = -1, np.inf
+        for c in np.sort(cidx):
+            if surf.ctr_side[c] != side:
+                continue
+            dc = np.linalg.norm(surf.ctr_xyz[:, c] - t[i])
+            if dc <= surf.ctr_r[c] * (1.0 + eps_tgt) and dc < bestd:
+                best, bestd = c, dc
+        if best >= 0:
+            ctr_idx[i] = best
+        else:
+            flagged[i] = True
+    return np.ascontiguousarray(t.T), ctr_idx, flagged
+
+
+# --------------------------------------------------------------------------
+# named workloads
+# --------------------------------------------------------------------------
+
+STAR_Y63 = [(0.3, 6, 3)]
+STAR_Y84_Y52 = [(0.25, 8, 4), (0.15, 5, 2)]
+
+
+def config_surface(name: str) -> Surface:
+    """Surfaces of the named workloads: sphere320, star8k, star40k, urchin79k."""
+    if name == "sphere320":
+        return make_surface(4, sphere_radius)
+    if name == "star8k":
+        return make_surface(20, star_radius(STAR_Y63))
+    if name == "star40k":
+        return make_surface(45, star_radius(STAR_Y63))
+    if name == "star79k":
+        return make_surface(63, star_radius(STAR_Y84_Y52))
+    raise KeyError(name)

@@ -1,0 +1,39 @@
+"""Input generator checks (no GPU): quadrature exactness, geometry and association."""
+import math
+
+import numpy as np
+
+from synth import make_surface, triangle_rule, volume_targets
+from synth.surfaces import STAR_Y63, star_radius
+
+
+def test_triangle_rule_monomial_exactness():
+    u, v, w = triangle_rule()
+    assert u.size == 15
+    for a in range(6):
+        for b in range(6 - a):
+            exact = math.factorial(a) * math.factorial(b) / math.factorial(a + b + 2)
+            assert abs(np.sum(w * u ** a * v ** b) - exact) < 1e-15
+
+
+def test_sphere_area_normals_and_radii(sphere320):
+    s = sphere320
+    assert s.n_src == 4800 and s.n_ctr == 9600
+    assert abs(s.src_w.sum() - 4 * math.pi) < 1e-5
+    assert np.allclose(np.linalg.norm(s.src_n, axis=0), 1.0)
+    assert np.all(np.sum(s.src_n * s.src_xyz, axis=0) > 0.99)
+    # radius = half the element size: flat sub-triangles of the icosahedron have edges ~ 0.27
+    assert 0.1 < s.ctr_r.min() and s.ctr_r.max() < 0.2
+    d = np.linalg.norm(s.ctr_xyz - np.concatenate([s.src_xyz, s.src_xyz], axis=1), axis=0)
+    assert np.allclose(d, s.ctr_r)
+
+
+def test_volume_target_association():
+    s = make_surface(4, star_radius(STAR_Y63))
+    t, ctr, flagged = volume_targets(s, n=2000, seed=2)
+    assoc = ctr >= 0
+    assert assoc.sum() > 0
+    d = np.linalg.norm(s.ctr_xyz[:, ctr[assoc]] - t[:, assoc], axis=0)
+    assert np.all(d <= s.ctr_r[ctr[assoc]] * 1.05 + 1e-15)
+    far = np.linalg.norm(t, axis=0) > 1.6
+    assert not np.any(assoc & far)
