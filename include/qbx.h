@@ -1,0 +1,162 @@
+/*
+ * qbx.h - C ABI of the GB300 GIGAQBX library (3D Laplace single- and double-layer
+ * potentials by quadrature by expansion, accelerated by the GIGAQBX FMM of
+ * Wala & Kloeckner, "A Fast Algorithm for Quadrature by Expansion in Three
+ * Dimensions", arXiv 1805.06106).
+ *
+ * Conventions shared by every entry point
+ *   - Pointers named *_dev are device pointers (CUDA global memory) owned by the
+ *     caller; host pointers are marked *_host.  Point arrays are structure-of-arrays
+ *     (3, N) float64: x[0..N), y[0..N), z[0..N).
+ *   - Every call that takes a `stream` (a cudaStream_t passed as void*, NULL = the
+ *     legacy default stream) enqueues its device work on that stream.  Calls that
+ *     return sizes or host data synchronize that stream before returning.
+ *   - Return value 0 on success, a negative QBX_ERR_* code otherwise; nothing is
+ *     printed and nothing aborts.  qbx_last_error() returns a message for the last
+ *     failure on the calling thread.  After an error no output is guaranteed.
+ *   - Handles (qbx_tree, qbx_lists) are owned by the library and released only by
+ *     the matching *_free call.  A tree keeps its own sorted copy of the geometry,
+ *     taken when it is built: rebuild the tree if the geometry changes.
+ *     Densities may change freely between qbx_eval calls.
+ */
+#ifndef QBX_H
+#define QBX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define QBX_OK 0
+#define QBX_ERR_INVALID_ARG (-1) /* NaN/Inf input, radius <= 0, bad order, bad index, mu without normals */
+#define QBX_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define QBX_ERR_OOM (-3)         /* device allocation failed */
+#define QBX_ERR_DEPTH (-4)       /* max_depth beyond what exact dyadic box geometry allows (> 50) */
+#define QBX_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+
+/* qbx_eval_opts.precision */
+#define QBX_FP64 0         /* every stage in FP64 */
+#define QBX_M2L_FP32 1     /* List 2 M2L and List 3-far M2QBXL in FP32; the rest FP64 */
+#define QBX_M2L_3XTF32 2   /* the same two stages as split-TF32 tensor-core products, FP32 accumulation */
+
+/* list identifiers for qbx_lists_nnz / qbx_lists_export (Section 5.2.3-5.2.4) */
+#define QBX_LIST_U 0      /* List 1 */
+#define QBX_LIST_V 1      /* List 2 */
+#define QBX_LIST_WCLOSE 2 /* List 3 close */
+#define QBX_LIST_WFAR 3   /* List 3 far */
+#define QBX_LIST_XCLOSE 4 /* List 4 close */
+#define QBX_LIST_XFAR 5   /* List 4 far */
+
+typedef struct qbx_tree qbx_tree;
+typedef struct qbx_lists qbx_lists;
+
+typedef struct {
+    int n_max;       /* split boxes owning more than n_max particles (Algorithm 4, Stage 1); >= 1 */
+    double t_f;      /* target confinement factor t_f (Section 5.2.2); >= 0 */
+    int max_depth;   /* deepest level created; 0 < max_depth <= 50 */
+    unsigned flags;  /* reserved, must be 0 */
+} qbx_tree_opts;
+
+typedef struct {
+    int64_t n_boxes, n_levels, n_src, n_ctr, n_tgt;
+    int64_t n_overfull;      /* leaves left above n_max because max_depth was reached */
+    double root_center[3];
+    double root_radius;      /* l-infinity radius |root| */
+} qbx_tree_info;
+
+/*
+ * Octree with target confinement (Algorithm 4 Stage 1; Section 5.2.1-5.2.2).
+ * The root is centered at the midpoint of the bounding box of all points and
+ * expansion balls, rounded to a multiple of R/8, R the smallest power of two at
+ * least 1.25 x the largest half extent.  A box owning more than n_max particles
+ * (sources + centers + targets) splits if some particle can move: points go to the
+ * octant "coordinate >= box center", a center goes to its octant child only if its
+ * ball lies inside the child's TCR, B2(sqrt(3)|child|(1+t_f)).  Only non-empty
+ * children are made.  Boxes are numbered by (level, Morton code).
+ *   src_xyz_dev (3,n_src), ctr_xyz_dev (3,n_ctr), ctr_r_dev (n_ctr, > 0), tgt_xyz_dev (3,n_tgt):
+ *   device arrays, read during the call only.  n_* >= 0, n_src + n_ctr + n_tgt >= 1.
+ *   out: receives a new handle.
+ * Errors: QBX_ERR_INVALID_ARG (non-finite coordinate, radius <= 0, bad options),
+ * QBX_ERR_DEPTH, QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_build_tree(const double *src_xyz_dev, int64_t n_src, const double *ctr_xyz_dev, const double *ctr_r_dev,
+                   int64_t n_ctr, const double *tgt_xyz_dev, int64_t n_tgt, const qbx_tree_opts *opts,
+                   qbx_tree **out, void *stream);
+
+/* Sizes of a built tree (host struct). */
+int qbx_tree_query(const qbx_tree *tree, qbx_tree_info *info_host);
+
+/*
+ * Copy the tree into caller arrays (device pointers, sizes from qbx_tree_query):
+ * level[n_boxes], coords[3*n_boxes] (integer box coordinates at the box's level,
+ * interleaved x,y,z), parent[n_boxes] (-1 for the root), child[8*n_boxes] (octant
+ * o = x_bit | y_bit<<1 | z_bit<<2, -1 = none), and the owning box of every source,
+ * center and target in input order.  Any pointer may be NULL to skip that array.
+ */
+int qbx_tree_export(const qbx_tree *tree, int32_t *level_dev, int64_t *coords_dev, int32_t *parent_dev,
+                    int32_t *child_dev, int32_t *src_owner_dev, int32_t *ctr_owner_dev, int32_t *tgt_owner_dev,
+                    void *stream);
+
+void qbx_tree_free(qbx_tree *tree);
+
+/*
+ * Interaction lists U (List 1), V (List 2), W-close/W-far (List 3 close/far),
+ * X-close/X-far (List 4 close/far) of Section 5.2.3-5.2.4, as CSR over boxes with
+ * each box's entries in ascending box order.  Lists U and W are made for boxes owning
+ * a center or a target, lists V and X for those boxes and their ancestors; boxes whose
+ * subtree holds no source appear in no list; k-colleagues exclude the box itself.
+ * The handle keeps a pointer to `tree`: free the lists before the tree.
+ * Errors: QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_build_lists(const qbx_tree *tree, qbx_lists **out, void *stream);
+
+/* Number of entries of list `which` (QBX_LIST_*). */
+int qbx_lists_nnz(const qbx_lists *lists, int which, int64_t *nnz_host);
+
+/* Copy list `which` as start[n_boxes+1], idx[nnz] (device pointers). */
+int qbx_lists_export(const qbx_lists *lists, int which, int32_t *start_dev, int32_t *idx_dev, void *stream);
+
+void qbx_lists_free(qbx_lists *lists);
+
+typedef struct {
+    int p_qbx;                    /* QBX order, 0 <= p_qbx <= 16 (ignored where p_qbx_per_ctr is given) */
+    int p_fmm;                    /* FMM order, 0 <= p_fmm <= 20 (ignored where p_fmm_per_box is given) */
+    const int8_t *p_qbx_per_ctr;  /* optional device array [n_ctr], per-center QBX order */
+    const int8_t *p_fmm_per_box;  /* optional device array [n_boxes], per-box FMM order */
+    int precision;                /* QBX_FP64, QBX_M2L_FP32 or QBX_M2L_3XTF32 */
+} qbx_eval_opts;
+
+/*
+ * GIGAQBX FMM evaluation (Algorithm 4, Stages 2-9) of
+ *     pot[t] = S[sigma](t) + D[mu](t),
+ *     S[sigma](x) = int G(x,y) sigma(y) dS(y),  D[mu](x) = int d/dn(y) G(x,y) mu(y) dS(y),
+ *     G(x,y) = 1/(4 pi |x-y|)                                   (eq. laplace-fs-green)
+ * discretised by the source quadrature: charges w sigma and dipoles w mu n at the
+ * sources.  A target t with tgt_ctr[t] = c >= 0 is evaluated through the order-p_qbx
+ * QBX local expansion at center c (eqs. qbxcoeff, qbxlocal); tgt_ctr[t] = -1 marks a
+ * conventional (point) target.
+ *   src_w_dev[n_src]   quadrature weight x area element (> 0)
+ *   sigma_dev[n_src]   single-layer density, or NULL for none
+ *   mu_dev[n_src]      double-layer density, or NULL for none
+ *   src_n_dev (3,n_src) unit outward normals; required iff mu_dev != NULL
+ *   tgt_ctr_dev[n_tgt] center index or -1
+ *   pot_dev[n_tgt]     output, overwritten
+ * All arrays are in the input order given to qbx_build_tree.  The first call with a
+ * given (orders, precision) allocates the library's workspace; later calls allocate
+ * nothing and may be captured in a CUDA graph.
+ * Errors: QBX_ERR_INVALID_ARG (orders out of range, p_qbx > p_fmm for fixed orders,
+ * mu without normals, tgt_ctr out of range), QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_eval(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev, const double *sigma_dev,
+             const double *mu_dev, const double *src_n_dev, const int32_t *tgt_ctr_dev,
+             const qbx_eval_opts *opts, double *pot_dev, void *stream);
+
+/* Message describing the last error on the calling thread ("" if none). */
+const char *qbx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QBX_H */

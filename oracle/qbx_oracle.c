@@ -499,7 +499,7 @@ otree *orc_build_tree(const double *sxyz, int ns, const double *cxyz, const doub
         h = fmax(h, 0.5 * (hi[d] - lo[d]));
     }
     double R = 1.0;
-    if (h > 0.0) {
+    if (h > 0.0 && h < 1e300) {
         while (R < 1.25 * h) R *= 2.0;
         while (0.5 * R >= 1.25 * h) R *= 0.5;
     }

@@ -1,0 +1,19 @@
+"""GB300 (sm_103a) GIGAQBX: FMM-accelerated QBX evaluation of 3D Laplace layer potentials.
+
+The C ABI is include/qbx.h (libqbx.so, built from csrc/ by build.py); binding.py
+marshals PyTorch CUDA tensors into it.
+"""
+from .binding import (  # noqa: F401
+    LIST_NAMES,
+    QBX_FP64,
+    QBX_M2L_3XTF32,
+    QBX_M2L_FP32,
+    Lists,
+    QbxError,
+    Tree,
+    lib,
+    library_path,
+    qbx_build_lists,
+    qbx_build_tree,
+    qbx_eval,
+)

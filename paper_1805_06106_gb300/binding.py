@@ -1,0 +1,180 @@
+"""Thin ctypes binding of libqbx (include/qbx.h).
+
+Argument marshalling only: PyTorch CUDA tensors provide device memory and the
+current stream; every step of the evaluation runs in the library's kernels.
+There is no CPU fallback: loading fails loudly if the library cannot be built or
+loaded.  Functions keep the C names.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+QBX_FP64, QBX_M2L_FP32, QBX_M2L_3XTF32 = 0, 1, 2
+LIST_NAMES = ("U", "V", "Wclose", "Wfar", "Xclose", "Xfar")
+
+
+class QbxError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libqbx error {code}: {msg}")
+        self.code = code
+
+
+class _TreeOpts(C.Structure):
+    _fields_ = [("n_max", C.c_int), ("t_f", C.c_double), ("max_depth", C.c_int), ("flags", C.c_uint)]
+
+
+class _TreeInfo(C.Structure):
+    _fields_ = [("n_boxes", C.c_int64), ("n_levels", C.c_int64), ("n_src", C.c_int64), ("n_ctr", C.c_int64),
+                ("n_tgt", C.c_int64), ("n_overfull", C.c_int64), ("root_center", C.c_double * 3),
+                ("root_radius", C.c_double)]
+
+
+class _EvalOpts(C.Structure):
+    _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("p_qbx_per_ctr", C.c_void_p),
+                ("p_fmm_per_box", C.c_void_p), ("precision", C.c_int)]
+
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) libqbx.so."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P, I64 = C.c_void_p, C.c_int64
+        L.qbx_build_tree.argtypes = [P, I64, P, P, I64, P, I64, C.POINTER(_TreeOpts), C.POINTER(P), P]
+        L.qbx_tree_query.argtypes = [P, C.POINTER(_TreeInfo)]
+        L.qbx_tree_export.argtypes = [P] * 9
+        L.qbx_tree_free.argtypes = [P]
+        L.qbx_tree_free.restype = None
+        L.qbx_build_lists.argtypes = [P, C.POINTER(P), P]
+        L.qbx_lists_nnz.argtypes = [P, C.c_int, C.POINTER(I64)]
+        L.qbx_lists_export.argtypes = [P, C.c_int, P, P, P]
+        L.qbx_lists_free.argtypes = [P]
+        L.qbx_lists_free.restype = None
+        L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
+        L.qbx_last_error.restype = C.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc):
+    if rc != 0:
+        raise QbxError(rc, lib().qbx_last_error().decode())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dev(x, dtype):
+    if x is None:
+        return None
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if x.dtype != dtype or not x.is_contiguous():
+        raise TypeError(f"expected a contiguous {dtype} tensor")
+    return x
+
+
+def _ptr(x):
+    return None if x is None else C.c_void_p(x.data_ptr())
+
+
+class Tree:
+    def __init__(self, handle):
+        self.handle = handle
+        info = _TreeInfo()
+        _check(lib().qbx_tree_query(handle, C.byref(info)))
+        self.info = info
+        self.n_boxes = info.n_boxes
+
+    def export(self):
+        """Tree arrays as CUDA tensors (level, coords, parent, child, src/ctr/tgt owner)."""
+        i = self.info
+        dev = torch.device("cuda")
+        out = dict(level=torch.empty(i.n_boxes, dtype=torch.int32, device=dev),
+                   coords=torch.empty((i.n_boxes, 3), dtype=torch.int64, device=dev),
+                   parent=torch.empty(i.n_boxes, dtype=torch.int32, device=dev),
+                   child=torch.empty((i.n_boxes, 8), dtype=torch.int32, device=dev),
+                   src_owner=torch.empty(i.n_src, dtype=torch.int32, device=dev),
+                   ctr_owner=torch.empty(i.n_ctr, dtype=torch.int32, device=dev),
+                   tgt_owner=torch.empty(i.n_tgt, dtype=torch.int32, device=dev))
+        _check(lib().qbx_tree_export(self.handle, *[_ptr(out[k]) for k in ("level", "coords", "parent", "child",
+                                                                            "src_owner", "ctr_owner", "tgt_owner")],
+                                     _stream()))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qbx_tree_free(self.handle)
+            self.handle = None
+
+
+class Lists:
+    def __init__(self, handle, tree):
+        self.handle = handle
+        self.tree = tree  # keeps the tree alive while the lists exist
+
+    def nnz(self, which):
+        v = C.c_int64()
+        _check(lib().qbx_lists_nnz(self.handle, which, C.byref(v)))
+        return v.value
+
+    def export(self):
+        out = {}
+        nb = self.tree.n_boxes
+        for k, name in enumerate(LIST_NAMES):
+            st = torch.empty(nb + 1, dtype=torch.int32, device="cuda")
+            ix = torch.empty(max(self.nnz(k), 1), dtype=torch.int32, device="cuda")
+            _check(lib().qbx_lists_export(self.handle, k, _ptr(st), _ptr(ix), _stream()))
+            out[name] = (st, ix[: self.nnz(k)])
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qbx_lists_free(self.handle)
+            self.handle = None
+
+
+def qbx_build_tree(src_xyz, ctr_xyz, ctr_r, tgt_xyz, n_max=32, t_f=0.9, max_depth=40) -> Tree:
+    """Octree with target confinement (Algorithm 4 Stage 1). Inputs: CUDA float64 (3, N) / (N,)."""
+    s, c, r, t = (_dev(x, torch.float64) for x in (src_xyz, ctr_xyz, ctr_r, tgt_xyz))
+    opts = _TreeOpts(n_max, t_f, max_depth, 0)
+    h = C.c_void_p()
+    _check(lib().qbx_build_tree(_ptr(s), s.shape[1], _ptr(c), _ptr(r), c.shape[1], _ptr(t), t.shape[1],
+                                C.byref(opts), C.byref(h), _stream()))
+    return Tree(h)
+
+
+def qbx_build_lists(tree: Tree) -> Lists:
+    h = C.c_void_p()
+    _check(lib().qbx_build_lists(tree.handle, C.byref(h), _stream()))
+    return Lists(h, tree)
+
+
+def qbx_eval(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr, p_qbx, p_fmm, p_qbx_per_ctr=None,
+             p_fmm_per_box=None, precision=QBX_FP64, out=None):
+    """pot = S[sigma] + D[mu] at every target (Algorithm 4 Stages 2-9)."""
+    w = _dev(src_w, torch.float64)
+    sg, m, n = _dev(sigma, torch.float64), _dev(mu, torch.float64), _dev(src_n, torch.float64)
+    tc = _dev(tgt_ctr, torch.int32)
+    qc, pb = _dev(p_qbx_per_ctr, torch.int8), _dev(p_fmm_per_box, torch.int8)
+    if out is None:
+        out = torch.empty(tc.shape[0], dtype=torch.float64, device=tc.device)
+    opts = _EvalOpts(p_qbx, p_fmm, None if qc is None else qc.data_ptr(), None if pb is None else pb.data_ptr(),
+                     precision)
+    _check(lib().qbx_eval(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc), C.byref(opts),
+                          _ptr(out), _stream()))
+    return out
+
+
+def library_path() -> str:
+    return os.path.abspath(_build.LIB)

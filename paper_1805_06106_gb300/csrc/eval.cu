@@ -1,0 +1,907 @@
+// GIGAQBX FMM evaluation (Algorithm 4, Stages 2-9), FP64.
+//
+// Expansion forms (all coefficients m >= 0, tri layout, conjugate symmetry for m < 0):
+//   multipole of box b (center c, half width h):  Mu_n^m = sum_s q R_n^m((s-c)/h) (+ dipole)
+//       phi(t) = 1/(4 pi h) sum_{n,m} Mu_n^m conj S_n^m((t-c)/h)
+//   local of box b:                               phi(t) = 1/(4 pi) sum_{n,m} B_n^m R_n^m((c-t)/h)
+//   QBX local at center c with radius rho:        phi(t) = 1/(4 pi) sum_{k,l} A_k^l R_k^l((c-t)/rho)
+// which give the operators
+//   P2M   Mu_n^m += q R_n^m(x) + (d/h).grad R_n^m(x),                 x = (s-c)/h
+//   P2L   B_n^m  += conj[q S_n^m(x) - (d/h).grad S_n^m(x)] / h,      x = (c-s)/h   (also P2QBXL with h -> rho)
+//   M2M   Mu'_n^m = sum_{k,l} 2^-k Mu_k^l R_{n-k}^{m-l}((c_child - c_par)/h_par)
+//   M2L   B_k^l  += 1/h sum_{n,m} Mu_n^m conj S_{n+k}^{m+l}((c_b - c_d)/h)
+//   M2QBXL A_k^l += 1/h_d (rho/h_d)^k sum_{n,m} Mu_n^m conj S_{n+k}^{m+l}((c - c_d)/h_d)
+//   L2L   B'_k^l  = 2^-k sum_{n>=k,m} B_n^m R_{n-k}^{m-l}((c_par - c_child)/h_par)
+//   L2QBXL A_k^l += (rho/h)^k sum_{n>=k,m} B_n^m R_{n-k}^{m-l}((c_b - c)/h)
+// (Section 4.1 operators, written in these harmonics.)
+#include <algorithm>
+#include <cmath>
+
+#include <math_constants.h>
+
+#include "harmonics.cuh"
+
+namespace qbx {
+
+constexpr double INV4PI = 0.079577471545947667884;  // 1 / (4 pi)
+
+struct qbx_ws_impl;
+
+}  // namespace qbx
+
+struct qbx_workspace {
+    int PM = -1, QM = -1;          // orders the buffers were sized for
+    int64_t nb = 0, nc = 0, ns = 0;
+    double2 *Mu = nullptr, *B = nullptr, *A = nullptr;
+    double2 *m2l_tab = nullptr;    // 1331 offsets x ntri(2 PM): S_j^i(2 o)
+    double2 *oct_tab = nullptr;    // 8 octants x ntri(PM): R_j^i(delta_o)
+    double *sq = nullptr, *sd = nullptr;
+    signed char *qc = nullptr, *pb = nullptr;
+    int *flags = nullptr;
+    std::vector<int> lvl_first;    // host copies of level ranges
+};
+
+namespace qbx {
+
+void free_workspace(qbx_workspace *ws)
+{
+    if (!ws) return;
+    dfree(ws->Mu); dfree(ws->B); dfree(ws->A); dfree(ws->m2l_tab); dfree(ws->oct_tab);
+    dfree(ws->sq); dfree(ws->sd); dfree(ws->qc); dfree(ws->pb); dfree(ws->flags);
+    delete ws;
+}
+
+// ---------------------------------------------------------------- setup kernels
+
+__global__ void k_m2l_table(int pmax2, double2 *tab)
+{
+    int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= 1331) return;
+    int ox = o % 11 - 5, oy = (o / 11) % 11 - 5, oz = o / 121 - 5;
+    double2 *t = tab + (int64_t)o * ntri(pmax2);
+    if (ox == 0 && oy == 0 && oz == 0) {
+        for (int i = 0; i < ntri(pmax2); ++i) t[i] = make_double2(0.0, 0.0);
+        return;
+    }
+    irregular_table(pmax2, 2.0 * ox, 2.0 * oy, 2.0 * oz, 1.0, 1.0, t);
+}
+
+// R_j^i(delta_o) with delta_o = (+-1/2, +-1/2, +-1/2), sign + where octant bit d is set
+__global__ void k_oct_table(int p, double2 *tab)
+{
+    int o = threadIdx.x;
+    if (o >= 8) return;
+    regular_table(p, (o & 1) ? 0.5 : -0.5, (o & 2) ? 0.5 : -0.5, (o & 4) ? 0.5 : -0.5, tab + o * ntri(p));
+}
+
+// sorted charges q = w sigma and dipoles d = w mu n; flags[0] |= 1 on invalid input
+__global__ void k_prep_src(const int *perm, int64_t ns, const double *w, const double *sigma, const double *mu,
+                           const double *nrm, double *sq, double *sd, int *flags)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ns) return;
+    int j = perm[i];
+    double wj = w[j];
+    bool bad = !(wj > 0.0 && isfinite(wj));
+    double s = sigma ? sigma[j] : 0.0;
+    if (!isfinite(s)) bad = true;
+    sq[i] = wj * s;
+    if (mu) {
+        double m = mu[j];
+        double nx = nrm[j], ny = nrm[ns + j], nz = nrm[2 * ns + j];
+        if (!isfinite(m) || !isfinite(nx) || !isfinite(ny) || !isfinite(nz)) bad = true;
+        double a = wj * m;
+        sd[i] = a * nx;
+        sd[ns + i] = a * ny;
+        sd[2 * ns + i] = a * nz;
+    }
+    if (bad) atomicOr(flags, 1);
+}
+
+__global__ void k_prep_orders(const int *ctr_perm, int64_t nc, const signed char *qin, int qfix, int64_t nb,
+                              const signed char *pin, int pfix, signed char *qc, signed char *pb, int *flags)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nc) {
+        int q = qin ? qin[ctr_perm[i]] : qfix;
+        if (q < 0 || q > QMAX) atomicOr(flags, 2);
+        qc[i] = (signed char)min(max(q, 0), QMAX);  // clamped so that no kernel indexes past its tables
+    }
+    if (i < nb) {
+        int p = pin ? pin[i] : pfix;
+        if (p < 0 || p > PMAX) atomicOr(flags, 2);
+        pb[i] = (signed char)min(max(p, 0), PMAX);
+    }
+}
+
+__global__ void k_check_tgt(const int *tc, int64_t nt, int64_t nc, int *flags)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int c = tc[i];
+    if (c < -1 || c >= nc) atomicOr(flags, 4);
+}
+
+// ---------------------------------------------------------------- upward pass
+
+// P2M (Stage 2): one warp per box, lane m computes column m of R_n^m for each source in turn.
+template <int PM>
+__global__ void k_p2m(int64_t nb, const int *own_start, const double *sxyz, int64_t ns, const double *sq,
+                      const double *sd, const double *cen, const double *hw, const signed char *pb, double2 *Mu)
+{
+    int b = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    int m = threadIdx.x & 31;
+    if (b >= nb) return;
+    int s0 = own_start[b], s1 = own_start[b + 1];
+    if (s0 == s1) return;
+    const int P = pb[b];
+    double hinv = 1.0 / hw[b];
+    double cx = cen[3 * b], cy = cen[3 * b + 1], cz = cen[3 * b + 2];
+    double2 acc[PM + 1];
+#pragma unroll
+    for (int n = 0; n <= PM; ++n) acc[n] = make_double2(0.0, 0.0);
+    for (int s = s0; s < s1; ++s) {
+        double x = (sxyz[s] - cx) * hinv, y = (sxyz[ns + s] - cy) * hinv, z = (sxyz[2 * ns + s] - cz) * hinv;
+        double r2 = x * x + y * y + z * z;
+        double q = sq[s];
+        double2 dw = make_double2(0.0, 0.0), dwb = make_double2(0.0, 0.0);
+        double dz = 0.0;
+        if (sd) {
+            double dx = sd[s] * hinv, dy = sd[ns + s] * hinv;
+            dz = sd[2 * ns + s] * hinv;
+            dw = make_double2(0.5 * dx, 0.5 * dy);
+            dwb = make_double2(0.5 * dx, -0.5 * dy);
+        }
+        // diagonal R_m^m = w^m / (2^m m!)
+        double2 diag = make_double2(1.0, 0.0);
+        for (int j = 1; j <= m && j <= PM; ++j) diag = cscale(cmul(diag, make_double2(x, y)), 1.0 / (2.0 * j));
+        double2 p2 = make_double2(0.0, 0.0), p1 = make_double2(0.0, 0.0);
+#pragma unroll
+        for (int n = 0; n <= PM; ++n) {
+            double2 cur = make_double2(0.0, 0.0);
+            if (n == m) cur = diag;
+            else if (n > m) {
+                double inv = 1.0 / ((double)(n + m) * (double)(n - m));
+                cur = make_double2(((2 * n - 1) * z * p1.x - r2 * p2.x) * inv, ((2 * n - 1) * z * p1.y - r2 * p2.y) * inv);
+            }
+            // neighbor columns of the previous row: R_{n-1}^{m+1} and R_{n-1}^{m-1}
+            double2 up, dn;
+            up.x = __shfl_down_sync(0xffffffffu, p1.x, 1);
+            up.y = __shfl_down_sync(0xffffffffu, p1.y, 1);
+            dn.x = __shfl_up_sync(0xffffffffu, p1.x, 1);
+            dn.y = __shfl_up_sync(0xffffffffu, p1.y, 1);
+            if (m == 31) up = make_double2(0.0, 0.0);
+            if (m == 0) dn = make_double2(-up.x, up.y);  // R^{-1} = -conj R^1
+            if (n >= m && n <= P) {
+                double2 v = cscale(cur, q);
+                if (sd) {
+                    double2 t1 = cmul(dwb, up), t2 = cmul(dw, dn);
+                    v.x += -t1.x + t2.x + dz * p1.x;
+                    v.y += -t1.y + t2.y + dz * p1.y;
+                }
+                acc[n] = cadd(acc[n], v);
+            }
+            p2 = p1;
+            p1 = cur;
+        }
+    }
+    if (m <= P) {
+#pragma unroll
+        for (int n = 0; n <= PM; ++n)
+            if (n >= m && n <= P) Mu[(int64_t)b * ntri(PM) + tri(n, m)] = acc[n];
+    }
+}
+
+// M2M (Stage 2, postorder by level): one warp per parent, lanes over output coefficients.
+template <int PM>
+__global__ void k_m2m(int b0, int b1, const int *child, const int *nsrc_sub, const signed char *pb,
+                      const double2 *oct, double2 *Mu)
+{
+    int b = b0 + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (b >= b1 || nsrc_sub[b] == 0) return;
+    const int P = pb[b];
+    bool any = false;
+    for (int o = 0; o < 8; ++o) any |= child[8 * b + o] >= 0;
+    if (!any) return;
+    for (int out = lane; out < ntri(P); out += 32) {
+        int n = 0;
+        while (tri(n + 1, 0) <= out) ++n;
+        int m = out - tri(n, 0);
+        double2 acc = Mu[(int64_t)b * ntri(PM) + out];  // the box's own sources (none for non-leaves)
+        for (int o = 0; o < 8; ++o) {
+            int c = child[8 * b + o];
+            if (c < 0 || nsrc_sub[c] == 0) continue;
+            const int Pc = pb[c];
+            const double2 *Mc = Mu + (int64_t)c * ntri(PM);
+            // child center - parent center = -(parent - child); delta = (c_child - c_par)/h_par
+            const double2 *R = oct + o * ntri(PM);
+            double sk = 1.0;
+            for (int k = 0; k <= n && k <= Pc; ++k, sk *= 0.5) {
+                int j = n - k;
+                int lmin = max(-k, m - j), lmax = min(k, m + j);
+                for (int l = lmin; l <= lmax; ++l) {
+                    double2 t = cmul(sym_get(Mc, k, l), sym_get(R, j, m - l));
+                    acc.x += sk * t.x;
+                    acc.y += sk * t.y;
+                }
+            }
+        }
+        Mu[(int64_t)b * ntri(PM) + out] = acc;
+    }
+}
+
+// ---------------------------------------------------------------- List 2 M2L (Stage 4), FP64
+
+template <int PM>
+__global__ void k_m2l(int64_t nb, const int *vstart, const int *vidx, const int64_t *ic, const double *hw,
+                      const signed char *pb, const double2 *Mu, const double2 *tab, double2 *B)
+{
+    extern __shared__ double2 sh[];
+    int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int b = blockIdx.x * (blockDim.x / 32) + wl;
+    if (b >= nb) return;
+    int e0 = vstart[b], e1 = vstart[b + 1];
+    if (e0 == e1) return;
+    const int P = pb[b];
+    double2 *Ms = sh + wl * ntri(PM);
+    constexpr int NO = (ntri(PM) + 31) / 32;
+    double2 acc[NO];
+#pragma unroll
+    for (int i = 0; i < NO; ++i) acc[i] = make_double2(0.0, 0.0);
+    for (int e = e0; e < e1; ++e) {
+        int d = vidx[e];
+        const int Pd = pb[d];
+        __syncwarp();
+        for (int i = lane; i < ntri(PM); i += 32) Ms[i] = i < ntri(Pd) ? Mu[(int64_t)d * ntri(PM) + i] : make_double2(0, 0);
+        __syncwarp();
+        int ox = (int)(ic[3 * b] - ic[3 * d]), oy = (int)(ic[3 * b + 1] - ic[3 * d + 1]),
+            oz = (int)(ic[3 * b + 2] - ic[3 * d + 2]);
+        if (ox < -5 || ox > 5 || oy < -5 || oy > 5 || oz < -5 || oz > 5) continue;  // not a List 2 offset
+        const double2 *S = tab + (int64_t)((ox + 5) + 11 * (oy + 5) + 121 * (oz + 5)) * ntri(2 * PM);
+#pragma unroll
+        for (int i = 0; i < NO; ++i) {
+            int out = lane + 32 * i;
+            if (out >= ntri(P)) continue;
+            int k = 0;
+            while (tri(k + 1, 0) <= out) ++k;
+            int l = out - tri(k, 0);
+            double2 a = acc[i];
+            for (int n = 0; n <= Pd; ++n)
+                for (int m = -n; m <= n; ++m) {
+                    double2 mv = sym_get(Ms, n, m);
+                    double2 sv = cconj(sym_get(S, n + k, m + l));
+                    a.x += mv.x * sv.x - mv.y * sv.y;
+                    a.y += mv.x * sv.y + mv.y * sv.x;
+                }
+            acc[i] = a;
+        }
+    }
+    double hinv = 1.0 / hw[b];
+#pragma unroll
+    for (int i = 0; i < NO; ++i) {
+        int out = lane + 32 * i;
+        if (out < ntri(P)) {
+            double2 v = B[(int64_t)b * ntri(PM) + out];
+            B[(int64_t)b * ntri(PM) + out] = make_double2(v.x + acc[i].x * hinv, v.y + acc[i].y * hinv);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- List 4 far P2L (Stage 6b)
+
+// One warp per box, lane m computes column m of S_n^m((c-s)/h), one source at a time.
+template <int PM>
+__global__ void k_p2l(int64_t nb, const int *xs, const int *xi, const int *own_start, const double *sxyz, int64_t ns,
+                      const double *sq, const double *sd, const double *cen, const double *hw, const signed char *pb,
+                      double2 *B)
+{
+    int b = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    int m = threadIdx.x & 31;
+    if (b >= nb) return;
+    int e0 = xs[b], e1 = xs[b + 1];
+    if (e0 == e1) return;
+    const int P = pb[b];
+    double h = hw[b], hinv = 1.0 / h;
+    double cx = cen[3 * b], cy = cen[3 * b + 1], cz = cen[3 * b + 2];
+    double2 acc[PM + 1];
+#pragma unroll
+    for (int n = 0; n <= PM; ++n) acc[n] = make_double2(0.0, 0.0);
+    for (int e = e0; e < e1; ++e) {
+        int d = xi[e];
+        for (int s = own_start[d]; s < own_start[d + 1]; ++s) {
+            double x = (cx - sxyz[s]) * hinv, y = (cy - sxyz[ns + s]) * hinv, z = (cz - sxyz[2 * ns + s]) * hinv;
+            double ir2 = 1.0 / (x * x + y * y + z * z);
+            double rinv = sqrt(ir2);
+            double q = sq[s];
+            double2 dw = make_double2(0.0, 0.0), dwb = make_double2(0.0, 0.0);
+            double dz = 0.0;
+            if (sd) {
+                double dx = sd[s] * hinv, dy = sd[ns + s] * hinv;
+                dz = sd[2 * ns + s] * hinv;
+                dw = make_double2(0.5 * dx, 0.5 * dy);
+                dwb = make_double2(0.5 * dx, -0.5 * dy);
+            }
+            double2 wr = make_double2(x * ir2, y * ir2);
+            double zz = z * ir2;
+            double2 diag = make_double2(rinv, 0.0);
+            for (int j = 1; j <= m && j <= PM + 1; ++j) diag = cscale(cmul(diag, wr), 2.0 * j - 1.0);
+            double2 p2 = make_double2(0.0, 0.0), p1 = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int n1 = 0; n1 <= PM + 1; ++n1) {  // row n1 = n + 1 closes output row n
+                double2 cur = make_double2(0.0, 0.0);
+                if (n1 == m) cur = diag;
+                else if (n1 > m) {
+                    double c1 = (2 * n1 - 1) * zz, c2 = (double)(n1 + m - 1) * (double)(n1 - m - 1) * ir2;
+                    cur = make_double2(c1 * p1.x - c2 * p2.x, c1 * p1.y - c2 * p2.y);
+                }
+                int n = n1 - 1;
+                double2 up, dn;  // S_{n+1}^{m+1}, S_{n+1}^{m-1}
+                up.x = __shfl_down_sync(0xffffffffu, cur.x, 1);
+                up.y = __shfl_down_sync(0xffffffffu, cur.y, 1);
+                dn.x = __shfl_up_sync(0xffffffffu, cur.x, 1);
+                dn.y = __shfl_up_sync(0xffffffffu, cur.y, 1);
+                if (m == 31) up = make_double2(0.0, 0.0);
+                if (m == 0) dn = make_double2(-up.x, up.y);
+                if (n >= m && n <= P) {
+                    // conj[q S_n^m + (dbar/2) S_{n+1}^{m+1} - (d/2) S_{n+1}^{m-1} + dz S_{n+1}^m]
+                    double2 v = cscale(p1, q);
+                    if (sd) {
+                        double2 t1 = cmul(dwb, up), t2 = cmul(dw, dn);
+                        v.x += t1.x - t2.x + dz * cur.x;
+                        v.y += t1.y - t2.y + dz * cur.y;
+                    }
+                    acc[n] = cadd(acc[n], cconj(v));
+                }
+                p2 = p1;
+                p1 = cur;
+            }
+        }
+    }
+    if (m <= P) {
+#pragma unroll
+        for (int n = 0; n <= PM; ++n)
+            if (n >= m && n <= P) {
+                double2 v = B[(int64_t)b * ntri(PM) + tri(n, m)];
+                B[(int64_t)b * ntri(PM) + tri(n, m)] = make_double2(v.x + acc[n].x * hinv, v.y + acc[n].y * hinv);
+            }
+    }
+}
+
+// ---------------------------------------------------------------- L2L (Stage 7), by level
+
+template <int PM>
+__global__ void k_l2l(int b0, int b1, const int *parent, const int *ntgt_sub, const int *child, const signed char *pb,
+                      const double2 *oct, double2 *B)
+{
+    int b = b0 + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    int lane = threadIdx.x & 31;
+    if (b >= b1 || ntgt_sub[b] == 0) return;
+    int pa = parent[b];
+    if (pa < 0) return;
+    int o = 0;
+    while (o < 8 && child[8 * pa + o] != b) ++o;
+    if (o == 8) return;
+    // delta = (c_par - c_child)/h_par: the opposite corner of octant o
+    const double2 *R = oct + (7 - o) * ntri(PM);
+    const int P = pb[b], Pp = pb[pa];
+    const double2 *Lp = B + (int64_t)pa * ntri(PM);
+    for (int out = lane; out < ntri(P); out += 32) {
+        int k = 0;
+        while (tri(k + 1, 0) <= out) ++k;
+        int l = out - tri(k, 0);
+        double2 acc = make_double2(0.0, 0.0);
+        for (int n = k; n <= Pp; ++n) {
+            int j = n - k;
+            for (int m = max(-n, l - j); m <= min(n, l + j); ++m) {
+                double2 t = cmul(sym_get(Lp, n, m), sym_get(R, j, m - l));
+                acc.x += t.x;
+                acc.y += t.y;
+            }
+        }
+        double sk = ldexp(1.0, -k);
+        double2 v = B[(int64_t)b * ntri(PM) + out];
+        B[(int64_t)b * ntri(PM) + out] = make_double2(v.x + sk * acc.x, v.y + sk * acc.y);
+    }
+}
+
+// ---------------------------------------------------------------- QBX centers (Stages 3, 5, 6a, 8)
+
+struct ListRef {
+    const int *start, *idx;
+};
+
+// Per-lane accumulation of q conj S_k^l((c-s)/rho)/rho (+ dipole) for one source.
+template <int QM>
+__device__ __forceinline__ void p2qbxl_accum(double bx, double by, double bz, double q, bool dip, double dx, double dy,
+                                             double dz, int Q, double *ar, double *ai)
+{
+    double ir2 = 1.0 / (bx * bx + by * by + bz * bz);
+    double rinv = sqrt(ir2);
+    double wr = bx * ir2, wi = by * ir2, zz = bz * ir2;
+    // rows n-2, n-1, n of S
+    double s2r[QM + 2], s2i[QM + 2], s1r[QM + 2], s1i[QM + 2], s0r[QM + 2], s0i[QM + 2];
+#pragma unroll
+    for (int m = 0; m < QM + 2; ++m) { s2r[m] = s2i[m] = s1r[m] = s1i[m] = s0r[m] = s0i[m] = 0.0; }
+    s1r[0] = rinv;  // row 0
+    if (!dip) {
+        ar[0] += q * rinv;
+    }
+    const double hdx = 0.5 * dx, hdy = 0.5 * dy;
+#pragma unroll
+    for (int n = 1; n <= QM + 1; ++n) {
+        if (n > Q + (dip ? 1 : 0)) break;
+        const double c1 = (2 * n - 1) * zz;
+#pragma unroll
+        for (int m = 0; m < n; ++m) {
+            if (m <= n - 2) {
+                double c2 = (double)(n + m - 1) * (double)(n - m - 1) * ir2;
+                s0r[m] = c1 * s1r[m] - c2 * s2r[m];
+                s0i[m] = c1 * s1i[m] - c2 * s2i[m];
+            } else {
+                s0r[m] = c1 * s1r[m];
+                s0i[m] = c1 * s1i[m];
+            }
+        }
+        {
+            double f = 2 * n - 1;
+            double pr = s1r[n - 1], pi = s1i[n - 1];
+            s0r[n] = f * (pr * wr - pi * wi);
+            s0i[n] = f * (pr * wi + pi * wr);
+        }
+        if (!dip) {
+            if (n <= QM) {
+#pragma unroll
+                for (int m = 0; m <= n && n <= QM; ++m) {
+                    ar[tri(n, m)] += q * s0r[m];
+                    ai[tri(n, m)] -= q * s0i[m];
+                }
+            }
+        } else {
+            // close row k = n - 1: q S_k^l + (dbar/2) S_n^{l+1} - (d/2) S_n^{l-1} + dz S_n^l, conjugated
+            const int k = n - 1;
+            if (k <= QM) {
+#pragma unroll
+                for (int l = 0; l <= k && k <= QM; ++l) {
+                    double vr = q * s1r[l] + dz * s0r[l];
+                    double vi = q * s1i[l] + dz * s0i[l];
+                    // (dbar/2) S^{l+1}: (hdx - i hdy)(ur + i ui)
+                    double ur = s0r[l + 1], ui = s0i[l + 1];
+                    vr += hdx * ur + hdy * ui;
+                    vi += hdx * ui - hdy * ur;
+                    // -(d/2) S^{l-1}, S^{-1} = -conj S^1
+                    double tr, ti;
+                    if (l >= 1) { tr = s0r[l - 1]; ti = s0i[l - 1]; }
+                    else { tr = -s0r[1]; ti = s0i[1]; }
+                    vr -= hdx * tr - hdy * ti;
+                    vi -= hdx * ti + hdy * tr;
+                    ar[tri(k, l)] += vr;
+                    ai[tri(k, l)] -= vi;
+                }
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < QM + 2; ++m) {
+            s2r[m] = s1r[m]; s2i[m] = s1i[m];
+            s1r[m] = s0r[m]; s1i[m] = s0i[m];
+        }
+    }
+}
+
+template <int QM, int PM>
+__global__ void __launch_bounds__(128) k_centers(
+    int64_t nc, const int *ctr_box, const double *cxyz, const double *cr, const signed char *qc, const signed char *pb,
+    ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf, const int *own_start, const double *sxyz, int64_t ns,
+    const double *sq, const double *sd, const double *cen, const double *hw, const double2 *Mu, const double2 *B,
+    double2 *A)
+{
+    extern __shared__ double2 sh[];
+    constexpr int NT = ntri(QM);
+    constexpr int TAB = ntri(PM + QM) + PM + 1;
+    int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t i = (int64_t)blockIdx.x * (blockDim.x / 32) + wl;
+    if (i >= nc) return;
+    double2 *tab = sh + wl * TAB;
+    const int b = ctr_box[i];
+    const int Q = min((int)qc[i], QM);
+    const double cx = cxyz[i], cy = cxyz[nc + i], cz = cxyz[2 * nc + i];
+    const double rho = cr[i], rinv_c = 1.0 / rho;
+    double ar[NT], ai[NT];
+#pragma unroll
+    for (int t = 0; t < NT; ++t) ar[t] = ai[t] = 0.0;
+
+    // Stage 8: L2QBXL from the box local (inputs split over lanes)
+    double *pw = reinterpret_cast<double *>(tab + TAB - (PM + 1));  // powers, at the end of the warp's table
+    {
+        const int P = min((int)pb[b], PM);
+        const double h = hw[b], hinv = 1.0 / h, ratio = rho * hinv;  // rho/h
+        __syncwarp();
+        // R_j^i((c_b - c)/h) (h/rho)^j, j <= P; pw[n] = (rho/h)^n
+        regular_table_warp(P, (cen[3 * b] - cx) * hinv, (cen[3 * b + 1] - cy) * hinv, (cen[3 * b + 2] - cz) * hinv,
+                           1.0 / ratio, tab, lane);
+        if (lane <= P) pw[lane] = pow(ratio, lane);
+        __syncwarp();
+        const double2 *Lb = B + (int64_t)b * ntri(PM);
+        for (int in = lane; in < (P + 1) * (P + 1); in += 32) {
+            int n = (int)sqrtf((float)in);
+            while (n * n > in) --n;
+            while ((n + 1) * (n + 1) <= in) ++n;
+            int m = in - n * n - n;
+            double2 bv = cscale(sym_get(Lb, n, m), pw[n]);
+#pragma unroll
+            for (int k = 0; k <= QM; ++k) {
+                if (k > Q || k > n) break;
+                int j = n - k;
+#pragma unroll
+                for (int l = 0; l <= k; ++l) {
+                    int mi = m - l;
+                    if (mi < -j || mi > j) continue;
+                    double2 rv = sym_get(tab, j, mi);
+                    ar[tri(k, l)] += bv.x * rv.x - bv.y * rv.y;
+                    ai[tri(k, l)] += bv.x * rv.y + bv.y * rv.x;
+                }
+            }
+        }
+    }
+
+    // Stage 5(b): List 3 far multipoles to the QBX local
+    for (int e = lwf.start[b]; e < lwf.start[b + 1]; ++e) {
+        const int d = lwf.idx[e];
+        const int Pd = min((int)pb[d], PM);
+        const double hd = hw[d], hdinv = 1.0 / hd, ratio = rho * hdinv;
+        __syncwarp();
+        // S_j^i((c - c_d)/h_d) (rho/h_d)^j / h_d, j <= Pd + Q; pw[n] = (h_d/rho)^n
+        irregular_table_warp(Pd + Q, (cx - cen[3 * d]) * hdinv, (cy - cen[3 * d + 1]) * hdinv,
+                             (cz - cen[3 * d + 2]) * hdinv, ratio, hdinv, tab, lane);
+        if (lane <= Pd) pw[lane] = pow(ratio, -lane);
+        __syncwarp();
+        const double2 *Md = Mu + (int64_t)d * ntri(PM);
+        for (int in = lane; in < (Pd + 1) * (Pd + 1); in += 32) {
+            int n = (int)sqrtf((float)in);
+            while (n * n > in) --n;
+            while ((n + 1) * (n + 1) <= in) ++n;
+            int m = in - n * n - n;
+            double2 mv = cscale(sym_get(Md, n, m), pw[n]);
+#pragma unroll
+            for (int k = 0; k <= QM; ++k) {
+                if (k > Q) break;
+#pragma unroll
+                for (int l = 0; l <= k; ++l) {
+                    double2 sv = cconj(sym_get(tab, n + k, m + l));
+                    ar[tri(k, l)] += mv.x * sv.x - mv.y * sv.y;
+                    ai[tri(k, l)] += mv.x * sv.y + mv.y * sv.x;
+                }
+            }
+        }
+    }
+
+    // Stages 3, 5(a), 6(a): direct P2QBXL from List 1, List 3 close and List 4 close sources
+    const ListRef lists[3] = {lu, lwc, lxc};
+    const bool dip = sd != nullptr;
+    for (int li = 0; li < 3; ++li) {
+        const int e0 = lists[li].start[b], e1 = lists[li].start[b + 1];
+        for (int base = e0; base < e1; base += 32) {
+            int e = base + lane;
+            int d = e < e1 ? lists[li].idx[e] : -1;
+            int s0 = d >= 0 ? own_start[d] : 0;
+            int cnt = d >= 0 ? own_start[d + 1] - s0 : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int k0 = 0; k0 < total; k0 += 32) {
+                int k = k0 + lane;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                    if (v <= k) j += step;
+                }
+                int sj = __shfl_sync(0xffffffffu, s0, j);
+                int ij = __shfl_sync(0xffffffffu, incl, j);
+                int cj = __shfl_sync(0xffffffffu, cnt, j);
+                if (k < total) {
+                    int s = sj + (k - (ij - cj));
+                    double bx = (cx - sxyz[s]) * rinv_c, by = (cy - sxyz[ns + s]) * rinv_c,
+                           bz = (cz - sxyz[2 * ns + s]) * rinv_c;
+                    double q = sq[s] * rinv_c;
+                    double dx = 0.0, dy = 0.0, dz = 0.0;
+                    if (dip) {
+                        double f = rinv_c * rinv_c;
+                        dx = sd[s] * f;
+                        dy = sd[ns + s] * f;
+                        dz = sd[2 * ns + s] * f;
+                    }
+                    p2qbxl_accum<QM>(bx, by, bz, q, dip, dx, dy, dz, Q, ar, ai);
+                }
+            }
+        }
+    }
+
+    // reduce over the warp and store
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+        double vr = ar[t], vi = ai[t];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            vr += __shfl_xor_sync(0xffffffffu, vr, off);
+            vi += __shfl_xor_sync(0xffffffffu, vi, off);
+        }
+        if ((t & 31) == lane) A[i * NT + t] = make_double2(vr, vi);
+    }
+}
+
+// ---------------------------------------------------------------- Stage 9
+
+// QBX targets: phi(t) = 1/(4 pi) sum A_k^l R_k^l((c - t)/rho), real part with conjugate symmetry.
+template <int QM>
+__global__ void k_qbxl2p(int64_t nt, const int *tperm, const double *txyz, const int *tgt_ctr, const int *ctr_rank,
+                         int64_t nc, const double *cxyz, const double *cr, const signed char *qc, const double2 *A,
+                         double *pot)
+{
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= nt) return;
+    int t = tperm[it];
+    int c = tgt_ctr[t];
+    if (c < 0 || c >= nc) {
+        if (c < -1 || c >= nc) pot[t] = CUDART_NAN;
+        return;
+    }
+    int i = ctr_rank[c];
+    int Q = min((int)qc[i], QM);
+    double rinv = 1.0 / cr[i];
+    double x = (cxyz[i] - txyz[it]) * rinv, y = (cxyz[nc + i] - txyz[nt + it]) * rinv,
+           z = (cxyz[2 * nc + i] - txyz[2 * nt + it]) * rinv;
+    double r2 = x * x + y * y + z * z;
+    const double2 *Ac = A + (int64_t)i * ntri(QM);
+    double acc = 0.0;
+    double2 diag = make_double2(1.0, 0.0);
+    for (int m = 0; m <= Q; ++m) {
+        if (m > 0) diag = cscale(cmul(diag, make_double2(x, y)), 1.0 / (2.0 * m));
+        double2 a2 = make_double2(0.0, 0.0), a1 = diag;
+        double wgt = m ? 2.0 : 1.0;
+        double2 cv = Ac[tri(m, m)];
+        acc += wgt * (cv.x * diag.x - cv.y * diag.y);
+        for (int n = m + 1; n <= Q; ++n) {
+            double inv = 1.0 / ((double)(n + m) * (double)(n - m));
+            double2 v = make_double2(((2 * n - 1) * z * a1.x - r2 * a2.x) * inv, ((2 * n - 1) * z * a1.y - r2 * a2.y) * inv);
+            double2 cc = Ac[tri(n, m)];
+            acc += wgt * (cc.x * v.x - cc.y * v.y);
+            a2 = a1;
+            a1 = v;
+        }
+    }
+    pot[t] = INV4PI * acc;
+}
+
+// Point targets: P2P from List 1 / 3 close / 4 close, M2P from List 3 far, L2P of the box local.
+template <int PM>
+__global__ void k_points(int64_t nt, const int *tperm, const double *txyz, const int *tgt_ctr, const int *tgt_box,
+                         const signed char *pb, ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf,
+                         const int *own_start, const double *sxyz, int64_t ns, const double *sq, const double *sd,
+                         const double *cen, const double *hw, const double2 *Mu, const double2 *B, double *pot)
+{
+    int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + wl;
+    if (it >= nt) return;
+    int t = tperm[it];
+    if (tgt_ctr[t] >= 0) return;
+    int b = tgt_box[it];
+    double tx = txyz[it], ty = txyz[nt + it], tz = txyz[2 * nt + it];
+    double acc = 0.0;
+    // P2P
+    const ListRef lists[3] = {lu, lwc, lxc};
+    for (int li = 0; li < 3; ++li)
+        for (int e = lists[li].start[b]; e < lists[li].start[b + 1]; ++e) {
+            int d = lists[li].idx[e];
+            for (int s = own_start[d] + lane; s < own_start[d + 1]; s += 32) {
+                double rx = tx - sxyz[s], ry = ty - sxyz[ns + s], rz = tz - sxyz[2 * ns + s];
+                double r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 == 0.0) continue;
+                double ri = 1.0 / sqrt(r2);
+                double v = sq[s] * ri;
+                if (sd) v += (sd[s] * rx + sd[ns + s] * ry + sd[2 * ns + s] * rz) * ri * ri * ri;
+                acc += v;
+            }
+        }
+    // M2P: one List 3 far box per lane
+    for (int e = lwf.start[b] + lane; e < lwf.start[b + 1]; e += 32) {
+        int d = lwf.idx[e];
+        int P = pb[d];
+        double hinv = 1.0 / hw[d];
+        double x = (tx - cen[3 * d]) * hinv, y = (ty - cen[3 * d + 1]) * hinv, z = (tz - cen[3 * d + 2]) * hinv;
+        double ir2 = 1.0 / (x * x + y * y + z * z);
+        double2 wr = make_double2(x * ir2, y * ir2);
+        double zz = z * ir2;
+        const double2 *Md = Mu + (int64_t)d * ntri(PM);
+        double2 diag = make_double2(sqrt(ir2), 0.0);
+        double s = 0.0;
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) diag = cscale(cmul(diag, wr), 2.0 * m - 1.0);
+            double wgt = m ? 2.0 : 1.0;
+            double2 a2 = make_double2(0.0, 0.0), a1 = diag;
+            double2 mv = Md[tri(m, m)];
+            s += wgt * (mv.x * diag.x + mv.y * diag.y);
+            for (int n = m + 1; n <= P; ++n) {
+                double c1 = (2 * n - 1) * zz, c2 = (double)(n + m - 1) * (double)(n - m - 1) * ir2;
+                double2 v = make_double2(c1 * a1.x - c2 * a2.x, c1 * a1.y - c2 * a2.y);
+                double2 mm = Md[tri(n, m)];
+                s += wgt * (mm.x * v.x + mm.y * v.y);
+                a2 = a1;
+                a1 = v;
+            }
+        }
+        acc += s * hinv;
+    }
+    // L2P
+    if (lane == 0) {
+        int P = pb[b];
+        double hinv = 1.0 / hw[b];
+        double x = (cen[3 * b] - tx) * hinv, y = (cen[3 * b + 1] - ty) * hinv, z = (cen[3 * b + 2] - tz) * hinv;
+        double r2 = x * x + y * y + z * z;
+        const double2 *Lb = B + (int64_t)b * ntri(PM);
+        double2 diag = make_double2(1.0, 0.0);
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) diag = cscale(cmul(diag, make_double2(x, y)), 1.0 / (2.0 * m));
+            double wgt = m ? 2.0 : 1.0;
+            double2 a2 = make_double2(0.0, 0.0), a1 = diag;
+            double2 cv = Lb[tri(m, m)];
+            acc += wgt * (cv.x * diag.x - cv.y * diag.y);
+            for (int n = m + 1; n <= P; ++n) {
+                double inv = 1.0 / ((double)(n + m) * (double)(n - m));
+                double2 v = make_double2(((2 * n - 1) * z * a1.x - r2 * a2.x) * inv, ((2 * n - 1) * z * a1.y - r2 * a2.y) * inv);
+                double2 cc = Lb[tri(n, m)];
+                acc += wgt * (cc.x * v.x - cc.y * v.y);
+                a2 = a1;
+                a1 = v;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) pot[t] = INV4PI * acc;
+}
+
+// ---------------------------------------------------------------- driver
+
+static int read_flags(const int *f, cudaStream_t st)
+{
+    int v = 0;
+    QBX_CUDA_TRY(cudaMemcpyAsync(&v, f, sizeof(int), cudaMemcpyDeviceToHost, st));
+    QBX_CUDA_TRY(cudaStreamSynchronize(st));
+    return v;
+}
+
+constexpr int PM_T = 20;  // compile-time order bound of the box-expansion kernels
+constexpr int QB[] = {4, 8, 12, 16};
+
+template <int QM>
+static void launch_centers(const qbx_tree *T, const qbx_lists *L, qbx_workspace *ws, bool dip, const int *tgt_ctr,
+                           double *pot, cudaStream_t st)
+{
+    const int WPB = 4;
+    size_t smem = (size_t)WPB * (ntri(PM_T + QM) + PM_T + 1) * sizeof(double2);
+    static bool attr_set = false;
+    if (!attr_set) {
+        QBX_CUDA_TRY(cudaFuncSetAttribute(k_centers<QM, PM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    if (T->np[KCTR] > 0) {
+        k_centers<QM, PM_T><<<nblocks(T->np[KCTR], WPB), 32 * WPB, smem, st>>>(
+            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc, ws->pb, ListRef{L->start[LU], L->idx[LU]},
+            ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
+            ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,
+            dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A);
+        QBX_LAUNCH_CHECK();
+    }
+    if (T->np[KTGT] > 0) {
+        k_qbxl2p<QM><<<nblocks(T->np[KTGT], 128), 128, 0, st>>>(T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr,
+                                                                T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->qc,
+                                                                ws->A, pot);
+        QBX_LAUNCH_CHECK();
+    }
+}
+
+void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu, const double *nrm,
+          const int *tgt_ctr, const qbx_eval_opts *o, double *pot, cudaStream_t st)
+{
+    const int64_t nb = T->nb, ns = T->np[KSRC], nc = T->np[KCTR], nt = T->np[KTGT];
+    // orders: compile-time bucket for the QBX order, runtime orders per center / box
+    int qmax = o->p_qbx, pmax = o->p_fmm;
+    if (o->p_qbx_per_ctr) qmax = QMAX;
+    if (o->p_fmm_per_box) pmax = PMAX;
+    int QM = 0;
+    for (int qb : QB)
+        if (qmax <= qb) { QM = qb; break; }
+    qbx_workspace *ws = L->ws;
+    if (!ws || ws->QM < QM || ws->PM < 0) {
+        if (ws) free_workspace(ws);
+        ws = L->ws = new qbx_workspace();
+        ws->PM = PM_T;
+        ws->QM = QM;
+        ws->nb = nb; ws->nc = nc; ws->ns = ns;
+        ws->Mu = dalloc<double2>(nb * ntri(PM_T));
+        ws->B = dalloc<double2>(nb * ntri(PM_T));
+        ws->A = dalloc<double2>(std::max<int64_t>(nc, 1) * ntri(QM));
+        ws->m2l_tab = dalloc<double2>((int64_t)1331 * ntri(2 * PM_T));
+        ws->oct_tab = dalloc<double2>(8 * ntri(PM_T));
+        ws->sq = dalloc<double>(ns);
+        ws->sd = dalloc<double>(3 * ns);
+        ws->qc = dalloc<signed char>(nc);
+        ws->pb = dalloc<signed char>(nb);
+        ws->flags = dalloc<int>(1);
+        k_m2l_table<<<nblocks(1331, 64), 64, 0, st>>>(2 * PM_T, ws->m2l_tab);
+        k_oct_table<<<1, 32, 0, st>>>(PM_T, ws->oct_tab);
+        QBX_LAUNCH_CHECK();
+    }
+    (void)pmax;
+    (void)pot;
+    QBX_CUDA_TRY(cudaMemsetAsync(ws->flags, 0, sizeof(int), st));
+    k_prep_src<<<nblocks(ns, 256), 256, 0, st>>>(T->perm[KSRC], ns, w, sigma, mu, nrm, ws->sq, ws->sd, ws->flags);
+    k_prep_orders<<<nblocks(std::max(nb, nc), 256), 256, 0, st>>>(T->perm[KCTR], nc, o->p_qbx_per_ctr, o->p_qbx, nb,
+                                                                  o->p_fmm_per_box, o->p_fmm, ws->qc, ws->pb, ws->flags);
+    k_check_tgt<<<nblocks(nt, 256), 256, 0, st>>>(tgt_ctr, nt, nc, ws->flags);
+    QBX_LAUNCH_CHECK();
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    QBX_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusNone) {
+        int f = read_flags(ws->flags, st);
+        if (f & 1) throw Error{QBX_ERR_INVALID_ARG, "source weight <= 0 or non-finite density/normal"};
+        if (f & 2) throw Error{QBX_ERR_INVALID_ARG, "expansion order out of range"};
+        if (f & 4) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr entry out of range"};
+    }
+    QBX_CUDA_TRY(cudaMemsetAsync(ws->Mu, 0, nb * ntri(PM_T) * sizeof(double2), st));
+    QBX_CUDA_TRY(cudaMemsetAsync(ws->B, 0, nb * ntri(PM_T) * sizeof(double2), st));
+
+    const int WPB = 4;
+    const bool dip = mu != nullptr;
+    // Stage 2
+    k_p2m<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws->sq,
+                                                       dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->Mu);
+    QBX_LAUNCH_CHECK();
+    for (int l = (int)T->nlev - 2; l >= 0; --l) {
+        int b0 = T->level_start[l], b1 = T->level_start[l + 1];
+        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->child, T->nsrc_sub, ws->pb, ws->oct_tab,
+                                                                ws->Mu);
+        QBX_LAUNCH_CHECK();
+    }
+    // Stage 4
+    {
+        size_t smem = (size_t)WPB * ntri(PM_T) * sizeof(double2);
+        k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, smem, st>>>(nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws->pb,
+                                                              ws->Mu, ws->m2l_tab, ws->B);
+        QBX_LAUNCH_CHECK();
+    }
+    // Stage 6(b)
+    k_p2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], T->sxyz,
+                                                       ns, ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->B);
+    QBX_LAUNCH_CHECK();
+    // Stage 7
+    for (int l = 1; l < T->nlev; ++l) {
+        int b0 = T->level_start[l], b1 = T->level_start[l + 1];
+        k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->parent, T->ntgt_sub, T->child, ws->pb,
+                                                                ws->oct_tab, ws->B);
+        QBX_LAUNCH_CHECK();
+    }
+    // Stages 3, 5, 6(a), 8, 9 at QBX centers and their targets
+    switch (QM) {
+    case 4: launch_centers<4>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    case 8: launch_centers<8>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    case 12: launch_centers<12>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    default: launch_centers<16>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    }
+    // Stage 9 at point targets
+    if (nt > 0) {
+        k_points<PM_T><<<nblocks(nt, WPB), 32 * WPB, 0, st>>>(
+            nt, T->perm[KTGT], T->txyz, tgt_ctr, T->tgt_box, ws->pb, ListRef{L->start[LU], L->idx[LU]},
+            ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
+            ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, ns, ws->sq, dip ? ws->sd : nullptr,
+            T->cen, T->hw, ws->Mu, ws->B, pot);
+        QBX_LAUNCH_CHECK();
+    }
+}
+
+}  // namespace qbx

@@ -1,0 +1,198 @@
+// extern "C" entry points declared in include/qbx.h: argument checks, handle
+// lifetime and error reporting around the tree, list and evaluation drivers.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "qbx_internal.cuh"
+
+namespace qbx {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string &msg) { g_err = msg; }
+
+template <class F>
+static int guarded(F &&f)
+{
+    try {
+        g_err.clear();
+        return f();
+    } catch (const Error &e) {
+        g_err = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_err = "host allocation failed";
+        return QBX_ERR_OOM;
+    } catch (...) {
+        g_err = "unexpected exception";
+        return QBX_ERR_CUDA;
+    }
+}
+
+static void free_tree(qbx_tree *T)
+{
+    if (!T) return;
+    dfree(T->level); dfree(T->ic); dfree(T->cen); dfree(T->hw); dfree(T->parent); dfree(T->child);
+    dfree(T->nsrc_sub); dfree(T->ntgt_sub);
+    for (int k = 0; k < 3; ++k) { dfree(T->owner[k]); dfree(T->perm[k]); dfree(T->own_start[k]); }
+    dfree(T->sxyz); dfree(T->cxyz); dfree(T->cr); dfree(T->txyz);
+    dfree(T->ctr_box); dfree(T->tgt_box); dfree(T->ctr_rank);
+    delete T;
+}
+
+static void free_lists(qbx_lists *L)
+{
+    if (!L) return;
+    for (int l = 0; l < NLIST; ++l) { dfree(L->start[l]); dfree(L->idx[l]); }
+    free_workspace(L->ws);
+    delete L;
+}
+
+}  // namespace qbx
+
+using namespace qbx;
+
+extern "C" {
+
+int qbx_build_tree(const double *src_xyz_dev, int64_t n_src, const double *ctr_xyz_dev, const double *ctr_r_dev,
+                   int64_t n_ctr, const double *tgt_xyz_dev, int64_t n_tgt, const qbx_tree_opts *opts,
+                   qbx_tree **out, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!out) throw Error{QBX_ERR_INVALID_ARG, "out is NULL"};
+        *out = nullptr;
+        if (!opts) throw Error{QBX_ERR_INVALID_ARG, "opts is NULL"};
+        if (n_src < 0 || n_ctr < 0 || n_tgt < 0 || n_src + n_ctr + n_tgt < 1)
+            throw Error{QBX_ERR_INVALID_ARG, "particle counts must be >= 0 with at least one particle"};
+        if (n_src + n_ctr + n_tgt >= (int64_t(1) << 31)) throw Error{QBX_ERR_INVALID_ARG, "too many particles"};
+        if ((n_src && !src_xyz_dev) || (n_ctr && (!ctr_xyz_dev || !ctr_r_dev)) || (n_tgt && !tgt_xyz_dev))
+            throw Error{QBX_ERR_INVALID_ARG, "NULL particle array"};
+        if (opts->n_max < 1 || !(opts->t_f >= 0.0) || !std::isfinite(opts->t_f) || opts->flags != 0 ||
+            opts->max_depth < 1)
+            throw Error{QBX_ERR_INVALID_ARG, "bad tree options"};
+        if (opts->max_depth > 50) throw Error{QBX_ERR_DEPTH, "max_depth > 50"};
+        qbx_tree *T = new qbx_tree();
+        T->np[0] = n_src;
+        T->np[1] = n_ctr;
+        T->np[2] = n_tgt;
+        T->n_max = opts->n_max;
+        T->max_depth = opts->max_depth;
+        T->tf = opts->t_f;
+        try {
+            build_tree(T, src_xyz_dev, ctr_xyz_dev, ctr_r_dev, tgt_xyz_dev, (cudaStream_t)stream);
+        } catch (...) {
+            free_tree(T);
+            throw;
+        }
+        *out = T;
+        return QBX_OK;
+    });
+}
+
+int qbx_tree_query(const qbx_tree *T, qbx_tree_info *info)
+{
+    return guarded([&]() -> int {
+        if (!T || !info) throw Error{QBX_ERR_INVALID_ARG, "NULL argument"};
+        info->n_boxes = T->nb;
+        info->n_levels = T->nlev;
+        info->n_src = T->np[0];
+        info->n_ctr = T->np[1];
+        info->n_tgt = T->np[2];
+        info->n_overfull = T->n_overfull;
+        for (int d = 0; d < 3; ++d) info->root_center[d] = T->root_c[d];
+        info->root_radius = T->root_h;
+        return QBX_OK;
+    });
+}
+
+int qbx_tree_export(const qbx_tree *T, int32_t *level, int64_t *coords, int32_t *parent, int32_t *child,
+                    int32_t *src_owner, int32_t *ctr_owner, int32_t *tgt_owner, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!T) throw Error{QBX_ERR_INVALID_ARG, "tree is NULL"};
+        cudaStream_t st = (cudaStream_t)stream;
+        auto cp = [&](void *dst, const void *src, size_t bytes) {
+            if (dst && bytes) QBX_CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+        };
+        cp(level, T->level, T->nb * sizeof(int));
+        cp(coords, T->ic, 3 * T->nb * sizeof(int64_t));
+        cp(parent, T->parent, T->nb * sizeof(int));
+        cp(child, T->child, 8 * T->nb * sizeof(int));
+        cp(src_owner, T->owner[0], T->np[0] * sizeof(int));
+        cp(ctr_owner, T->owner[1], T->np[1] * sizeof(int));
+        cp(tgt_owner, T->owner[2], T->np[2] * sizeof(int));
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+        return QBX_OK;
+    });
+}
+
+void qbx_tree_free(qbx_tree *T) { free_tree(T); }
+
+int qbx_build_lists(const qbx_tree *T, qbx_lists **out, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!T || !out) throw Error{QBX_ERR_INVALID_ARG, "NULL argument"};
+        *out = nullptr;
+        qbx_lists *L = new qbx_lists();
+        L->tree = T;
+        try {
+            build_lists(L, (cudaStream_t)stream);
+        } catch (...) {
+            free_lists(L);
+            throw;
+        }
+        *out = L;
+        return QBX_OK;
+    });
+}
+
+int qbx_lists_nnz(const qbx_lists *L, int which, int64_t *nnz)
+{
+    return guarded([&]() -> int {
+        if (!L || !nnz || which < 0 || which >= NLIST) throw Error{QBX_ERR_INVALID_ARG, "bad argument"};
+        *nnz = L->nnz[which];
+        return QBX_OK;
+    });
+}
+
+int qbx_lists_export(const qbx_lists *L, int which, int32_t *start, int32_t *idx, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!L || which < 0 || which >= NLIST) throw Error{QBX_ERR_INVALID_ARG, "bad argument"};
+        cudaStream_t st = (cudaStream_t)stream;
+        if (start)
+            QBX_CUDA_TRY(cudaMemcpyAsync(start, L->start[which], (L->tree->nb + 1) * sizeof(int),
+                                         cudaMemcpyDeviceToDevice, st));
+        if (idx && L->nnz[which])
+            QBX_CUDA_TRY(cudaMemcpyAsync(idx, L->idx[which], L->nnz[which] * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+        return QBX_OK;
+    });
+}
+
+void qbx_lists_free(qbx_lists *L) { free_lists(L); }
+
+int qbx_eval(const qbx_tree *T, const qbx_lists *L, const double *w, const double *sigma, const double *mu,
+             const double *nrm, const int32_t *tgt_ctr, const qbx_eval_opts *o, double *pot, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!T || !L || !o || L->tree != T) throw Error{QBX_ERR_INVALID_ARG, "tree/lists/opts mismatch or NULL"};
+        if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
+        if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
+        if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
+        if (o->precision != QBX_FP64) throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
+        if (!o->p_qbx_per_ctr && (o->p_qbx < 0 || o->p_qbx > QMAX))
+            throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
+        if (!o->p_fmm_per_box && (o->p_fmm < 0 || o->p_fmm > PMAX))
+            throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
+        if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
+            throw Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
+        eval(T, const_cast<qbx_lists *>(L), w, sigma, mu, nrm, tgt_ctr, o, pot, (cudaStream_t)stream);
+        return QBX_OK;
+    });
+}
+
+const char *qbx_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

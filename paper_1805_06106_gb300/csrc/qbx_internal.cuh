@@ -1,0 +1,112 @@
+// Internal declarations shared by the translation units of libqbx.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "qbx.h"
+
+namespace qbx {
+
+// ---------------------------------------------------------------- errors
+
+void set_error(const std::string &msg);
+
+struct Error {
+    int code;
+    std::string msg;
+};
+
+#define QBX_CUDA_TRY(expr)                                                                    \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            throw ::qbx::Error{e_ == cudaErrorMemoryAllocation ? QBX_ERR_OOM : QBX_ERR_CUDA,  \
+                               std::string(#expr) + ": " + cudaGetErrorString(e_)};           \
+    } while (0)
+
+#define QBX_LAUNCH_CHECK() QBX_CUDA_TRY(cudaGetLastError())
+
+template <class T>
+T *dalloc(size_t n)
+{
+    void *p = nullptr;
+    if (n == 0) n = 1;
+    QBX_CUDA_TRY(cudaMalloc(&p, n * sizeof(T)));
+    return static_cast<T *>(p);
+}
+
+inline void dfree(void *p)
+{
+    if (p) cudaFree(p);
+}
+
+inline unsigned nblocks(int64_t n, int threads)
+{
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------- kinds and constants
+
+enum { KSRC = 0, KCTR = 1, KTGT = 2 };
+enum { LU = 0, LV = 1, LWC = 2, LWF = 3, LXC = 4, LXF = 5, NLIST = 6 };
+
+constexpr int PMAX = 20;   // highest FMM order
+constexpr int QMAX = 16;   // highest QBX order
+
+__host__ __device__ constexpr int ntri(int p) { return (p + 1) * (p + 2) / 2; }
+__host__ __device__ constexpr int tri(int n, int m) { return n * (n + 1) / 2 + m; }
+
+}  // namespace qbx
+
+// ---------------------------------------------------------------- handles
+
+struct qbx_tree {
+    int64_t nb = 0, nlev = 0, np[3] = {0, 0, 0}, n_overfull = 0;
+    int n_max = 0, max_depth = 0;
+    double tf = 0.0;
+    double root_c[3] = {0, 0, 0}, root_h = 0.0;
+    std::vector<int> level_start;  // host copy, nlev + 1
+    // device box arrays
+    int *level = nullptr;
+    int64_t *ic = nullptr;   // 3 per box
+    double *cen = nullptr;   // 3 per box
+    double *hw = nullptr;    // |b|
+    int *parent = nullptr;
+    int *child = nullptr;    // 8 per box
+    int *nsrc_sub = nullptr, *ntgt_sub = nullptr;
+    // particles: owner in input order, perm (sorted position -> input index), CSR over boxes
+    int *owner[3] = {nullptr, nullptr, nullptr};
+    int *perm[3] = {nullptr, nullptr, nullptr};
+    int *own_start[3] = {nullptr, nullptr, nullptr};
+    // geometry in sorted order, SoA
+    double *sxyz = nullptr, *cxyz = nullptr, *cr = nullptr, *txyz = nullptr;
+    int *ctr_box = nullptr;   // owning box of each sorted center
+    int *tgt_box = nullptr;   // owning box of each sorted target
+    int *ctr_rank = nullptr;  // input center index -> sorted position
+};
+
+struct qbx_workspace;
+
+struct qbx_lists {
+    const qbx_tree *tree = nullptr;
+    int *start[qbx::NLIST] = {};
+    int *idx[qbx::NLIST] = {};
+    int64_t nnz[qbx::NLIST] = {};
+    qbx_workspace *ws = nullptr;
+};
+
+namespace qbx {
+void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const double *cr, const double *txyz,
+                cudaStream_t st);
+void build_lists(qbx_lists *L, cudaStream_t st);
+void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
+          const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *pot, cudaStream_t st);
+void free_workspace(qbx_workspace *ws);
+void exclusive_scan(const int *in, int *out, int64_t n, int base_offset, int *total_dev, cudaStream_t st);
+void sort_pairs_by_key(int *keys, int *vals, int64_t n, int key_bits, cudaStream_t st);
+}  // namespace qbx
