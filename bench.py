@@ -1,0 +1,418 @@
+"""Benchmark of the GB300 GIGAQBX evaluation (Algorithm 4, Stages 2-9).
+
+Workload (default): the star surface r = 1 + 0.3 Re Y_6^3 with 8,000 curved
+triangles x 15 nodes (120,000 sources), two QBX centers per node at radius
+eta_k/2 (240,000 centers, one on-surface target each) plus 10,000 volume points
+in [-2,2]^3 associated by Algorithm 3; densities sigma = d_n u and mu = -u for
+u = 1/|x - (3,1,2)| (Green's formula S(d_n u) - D(u)); p_qbx = 7, p_fmm = 15,
+t_f = 0.9.  A step is one qbx_eval (every stage of the evaluation) with the tree
+and lists built beforehand, as in repeated evaluation inside an iterative solver.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl {gpu,reference}]
+
+--impl reference times the FP64 CPU oracle (the reference arm) on a bounded
+sample of the same workload.  Under torchrun each rank evaluates its own replica
+(the path needs no exchange between GPUs).  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "QBX target evals/s at 1e-6 rel err: learned+mixed vs plain FP64 GIGAQBX"
+P_QBX, P_FMM, T_F = 7, 15, 0.9
+N_MAX = 256           # chosen by the n_max sweep recorded in profiles/ (same value for every precision mode)
+N_VOLUME = 10000
+FP64_PEAK_TFLOPS = 1.258  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (1.25 TFLOP/s nominal)
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_workload(n_sub=20):
+    from synth import greens_density, make_surface, star_radius, volume_targets
+    from synth.surfaces import STAR_Y63
+
+    s = make_surface(n_sub, star_radius(STAR_Y63))
+    u, dudn = greens_density(s)
+    vt, vc, vflag = volume_targets(s, N_VOLUME, seed=2)
+    t = np.concatenate([s.tgt_xyz, vt], axis=1)
+    tc = np.concatenate([s.tgt_ctr, vc]).astype(np.int32)
+    return s, u, dudn, t, tc, vflag
+
+
+# ------------------------------------------------------------------ algorithmic work model
+
+
+def _tri(p):
+    return (p + 1) * (p + 2) // 2
+
+
+def _l2qbxl_macs(P, Q):
+    n_mac = 0
+    for n in range(P + 1):
+        for m in range(-n, n + 1):
+            for k in range(min(n, Q) + 1):
+                j = n - k
+                n_mac += sum(1 for l in range(k + 1) if abs(m - l) <= j)
+    return n_mac
+
+
+def center_kernel_flops(P, Q, n_direct_pairs, n_wfar_pairs, n_centers, dipole=True):
+    """FP64 flops of the formulas the fused center kernel evaluates (mul, add = 1; fused mul-add = 2).
+
+    direct pair: 16 (geometry, 1/r^2, 1/r) + 8 per irregular harmonic entry up to order
+    K = Q + dipole + per output coefficient 4 (charge) or 22 (charge + dipole);
+    List 3 far pair: 8 per harmonic up to P+Q + 8 per complex MAC over (P+1)^2 x ntri(Q);
+    L2QBXL per center: 8 per harmonic up to P + 8 per complex MAC of the shift.
+    """
+    K = Q + (1 if dipole else 0)
+    f_pair = 16 + 8 * (_tri(K) - 1) + (22 if dipole else 4) * _tri(Q)
+    f_wfar = 8 * _tri(P + Q) + 8 * (P + 1) ** 2 * _tri(Q) + 2 * (P + 1) ** 2
+    f_l2q = 8 * _tri(P) + 8 * _l2qbxl_macs(P, Q)
+    return f_pair * n_direct_pairs + f_wfar * n_wfar_pairs + f_l2q * n_centers, f_pair
+
+
+def list_work(G, T, L):
+    """Per-launch work units of the center kernel and the paper's modeled operation counts."""
+    tr = {k: v.cpu().numpy() for k, v in T.export().items()}
+    ls = {k: (a.cpu().numpy(), b.cpu().numpy()) for k, (a, b) in L.export().items()}
+    nb = T.n_boxes
+    nsrc = np.bincount(tr["src_owner"], minlength=nb).astype(np.int64)
+    nctr = np.bincount(tr["ctr_owner"], minlength=nb).astype(np.int64)
+
+    def per_box_sum(name, weight):
+        st, ix = ls[name]
+        cs = np.concatenate([[0], np.cumsum(weight[ix])])
+        return cs[st[1:]] - cs[st[:-1]]
+
+    direct_src = per_box_sum("U", nsrc) + per_box_sum("Wclose", nsrc) + per_box_sum("Xclose", nsrc)
+    wfar = np.diff(ls["Wfar"][0]).astype(np.int64)
+    n_direct = int(np.sum(direct_src * nctr))
+    n_wfar = int(np.sum(wfar * nctr))
+    # modeled operation counts (Table ilist-operation-counts), n_t = centers of the target box
+    q2, p3, p2 = P_QBX ** 2, P_FMM ** 3, P_FMM ** 2
+    sub_src = np.zeros(nb, np.int64)
+    par = tr["parent"]
+    for b in range(nb - 1, -1, -1):
+        sub_src[b] += nsrc[b]
+        if par[b] >= 0:
+            sub_src[par[b]] += sub_src[b]
+    modeled = {
+        "U": q2 * float(np.sum(per_box_sum("U", nsrc) * nctr)),
+        "V": p3 * float(len(ls["V"][1])),
+        "Wclose": q2 * float(np.sum(per_box_sum("Wclose", nsrc) * nctr)),
+        "Wfar": p3 * float(n_wfar),
+        "Xclose": q2 * float(np.sum(per_box_sum("Xclose", nsrc) * nctr)),
+        "Xfar": p2 * float(np.sum(per_box_sum("Xfar", sub_src))),
+    }
+    return n_direct, n_wfar, modeled
+
+
+def kernel_traffic():
+    """DRAM bytes per launch of the center kernel from the committed ncu summary, or None when the
+    kernel source changed since those counters were taken."""
+    import hashlib
+
+    prof_path = os.path.join(ROOT, "profiles", "traffic_centers_star8k.json")
+    try:
+        rec = json.load(open(prof_path))
+        src = b"".join(open(os.path.join(ROOT, "paper_1805_06106_gb300", "csrc", f), "rb").read()
+                       for f in ("eval.cu", "harmonics.cuh"))
+        if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
+            return None
+        return rec.get("bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+# ------------------------------------------------------------------ clocks
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons, sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+
+
+def cpu_oracle_sample(n_sub=3):
+    """Oracle FMM (Algorithm 4, serial FP64) on a bounded sample: the same surface family,
+    densities and orders at 20 n_sub^2 elements (180 elements for the default n_sub = 3)."""
+    import oracle as O
+    from synth import greens_density, make_surface, star_radius
+    from synth.surfaces import STAR_Y63
+
+    s = make_surface(n_sub, star_radius(STAR_Y63))
+    u, dudn = greens_density(s)
+    t0 = time.perf_counter()
+    T = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, s.tgt_xyz, n_max=N_MAX, t_f=T_F)
+    L = O.build_lists(T)
+    t1 = time.perf_counter()
+    O.fmm_eval(T, L, s.src_xyz, s.src_w, dudn, -u, s.src_n, s.ctr_xyz, s.tgt_xyz, s.tgt_ctr, P_QBX, P_FMM)
+    t2 = time.perf_counter()
+    n = s.n_ctr
+    return {"value": n / (t2 - t1), "unit": "QBX target evals/s", "cores": 1, "kind": "oracle",
+            "sample": f"serial FP64 oracle Algorithm 4 (Stages 2-9) on the same star family at {s.n_elem} elements "
+                      f"({s.n_src} sources, {n} QBX targets), p_qbx={P_QBX}, p_fmm={P_FMM}, n_max={N_MAX}; "
+                      f"{t2 - t1:.1f} s eval + {t1 - t0:.2f} s tree/lists"}
+
+
+def run_reference(args):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(2)
+    for _ in range(args.steps):
+        vals.append(cpu_oracle_sample(2))
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[-1])
+    cb["value"] = v
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "QBX target evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "star r=1+0.3ReY63, 80 curved triangles x 15 nodes (oracle sample of configs[1])",
+                       "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": N_MAX, "t_f": T_F},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": "QBX target evals/s", "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GPU arm
+
+
+def run_gpu(args):
+    import torch
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_1805_06106_gb300 as G
+
+    s, u, dudn, t, tc, vflag = make_workload(args.n_sub)
+    n_qbx_tgt = int(np.sum(tc >= 0))
+    n_pt_tgt = int(np.sum(tc < 0))
+
+    def cu(a, dt=torch.float64):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
+
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        geo = [cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(t)]
+        torch.cuda.synchronize()
+        tb0 = time.perf_counter()
+        T = G.qbx_build_tree(*geo, n_max=N_MAX, t_f=T_F)
+        torch.cuda.synchronize()
+        tb1 = time.perf_counter()
+        L = G.qbx_build_lists(T)
+        torch.cuda.synchronize()
+        tb2 = time.perf_counter()
+        ev_in = (cu(s.src_w), cu(dudn), cu(-u), cu(s.src_n), cu(tc, torch.int32))
+        pot = torch.empty(t.shape[1], dtype=torch.float64, device=dev)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+
+        def step():
+            G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM, out=pot)
+
+        L.profile(True)
+        for _ in range(max(args.warmup, 3)):
+            step()
+        torch.cuda.synchronize()
+        ref_pot = pot.clone()
+
+        stage_tot = {k: 0.0 for k in G.STAGE_NAMES}
+        step_ms = []
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        with ClockSampler(local) as clk:
+            for _ in range(args.steps):
+                flush.fill_(1)  # L2 flush between timed iterations (outside the timed events)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                step()
+                e1.record(stream)
+                e1.synchronize()
+                step_ms.append(e0.elapsed_time(e1))
+                for k, v in L.stage_ms().items():
+                    stage_tot[k] += v
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        total_ms = float(sum(step_ms))
+        if ws > 1:
+            tt = torch.tensor([total_ms], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            total_ms = float(tt.item())
+        ms_per_step = total_ms / args.steps
+        value = ws * n_qbx_tgt * args.steps / (total_ms * 1e-3)
+        determinism = bool(torch.equal(pot, ref_pot))
+
+        # end to end through the public API: pinned host inputs in, potentials out
+        L.profile(False)
+        host_in = [x.cpu().pin_memory() for x in ev_in]
+        host_out = torch.empty_like(pot, device="cpu").pin_memory()
+        dev_in = [torch.empty_like(x) for x in ev_in]
+        h2d = sum(x.numel() * x.element_size() for x in host_in)
+        d2h = host_out.numel() * host_out.element_size()
+        n_e2e = max(1, min(args.steps, 5))
+        torch.cuda.synchronize()
+        e2e_ms = []
+        for _ in range(n_e2e):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for d, h in zip(dev_in, host_in):
+                d.copy_(h, non_blocking=True)
+            G.qbx_eval(T, L, *dev_in, P_QBX, P_FMM, out=pot)
+            host_out.copy_(pot, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e_ms.append(e0.elapsed_time(e1))
+        e2e_total = float(sum(e2e_ms))
+        if ws > 1:
+            tt = torch.tensor([e2e_total], device=dev)
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+            e2e_total = float(tt.item())
+        e2e_value = ws * n_qbx_tgt * n_e2e / (e2e_total * 1e-3)
+        e2e_ok = bool(torch.allclose(host_out.to(dev), ref_pot, rtol=0, atol=0))
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+
+    n_direct, n_wfar, modeled = list_work(G, T, L)
+    flops, f_pair = center_kernel_flops(P_FMM, P_QBX, n_direct, n_wfar, T.info.n_ctr)
+    centers_ms = stage_tot["centers"] / args.steps
+    achieved = flops / (centers_ms * 1e-3) / 1e12
+    nlev = int(T.info.n_levels)
+    launches = 3 + 1 + (nlev - 1) + 1 + 1 + (nlev - 1) + 3  # prep, P2M, M2M, M2L, P2L, L2L, centers/targets
+    traffic = kernel_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "QBX target evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"star r=1+0.3ReY63, {s.n_elem} curved triangles x 15 nodes: S[d_n u] - D[u] at "
+                               f"{s.n_ctr} on-surface QBX targets + {N_VOLUME} volume points",
+                   "mode": "plain FP64 GIGAQBX, fixed orders", "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": N_MAX,
+                   "t_f": T_F, "n_src": int(s.n_src), "n_ctr": int(s.n_ctr), "n_qbx_targets": n_qbx_tgt,
+                   "n_point_targets": n_pt_tgt, "n_flagged": int(vflag.sum()), "n_boxes": int(T.n_boxes),
+                   "n_levels": nlev, "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "tree_build_ms": 1e3 * (tb1 - tb0), "lists_build_ms": 1e3 * (tb2 - tb1)},
+        "stage_ms": {k: v / args.steps for k, v in stage_tot.items()},
+        "modeled_ops": modeled,
+        "deterministic": determinism,
+        "e2e": {"value": e2e_value, "unit": "QBX target evals/s", "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h), "matches_device_result": e2e_ok},
+        "gpu_launches": launches * args.steps,
+        "roofline": {"kernel": "k_centers (L2QBXL + List 3 far M2QBXL + direct P2QBXL, FP64)", "bound": "alu",
+                     "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "flops_per_launch": flops, "flops_per_direct_pair": f_pair, "direct_pairs": n_direct,
+                     "wfar_pairs": n_wfar, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz "
+                                                          "(nominal 1.25 TFLOP/s; 1.195 measured by an FMA-chain probe)"},
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_oracle_sample()
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--n-sub", type=int, default=20, help="icosahedron face subdivision (20 = 8,000 elements)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

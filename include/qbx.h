@@ -152,6 +152,20 @@ int qbx_eval(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_d
              const double *mu_dev, const double *src_n_dev, const int32_t *tgt_ctr_dev,
              const qbx_eval_opts *opts, double *pot_dev, void *stream);
 
+/*
+ * Per-stage timing (tracing aid; not a step of the paper's method).  While enabled,
+ * every qbx_eval on these lists records CUDA events on its stream around each of
+ * QBX_NSTAGES stages: 0 input preparation, 1 P2M + M2M (Stage 2), 2 List 2 M2L
+ * (Stage 4), 3 List 4 far P2L (Stage 6b), 4 L2L (Stage 7), 5 QBX centers (Stages
+ * 3, 5, 6a, 8: L2QBXL, List 3 far M2QBXL, direct P2QBXL), 6 QBX targets (Stage 9),
+ * 7 point targets (Stage 9).  qbx_profile_read waits for the last profiled
+ * evaluation and writes the stage durations in milliseconds to stage_ms_host.
+ * Profiling must be disabled while the stream is being captured into a graph.
+ */
+#define QBX_NSTAGES 8
+int qbx_profile(qbx_lists *lists, int enable);
+int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *qbx_last_error(void);
 

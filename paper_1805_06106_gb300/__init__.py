@@ -5,6 +5,7 @@ marshals PyTorch CUDA tensors into it.
 """
 from .binding import (  # noqa: F401
     LIST_NAMES,
+    STAGE_NAMES,
     QBX_FP64,
     QBX_M2L_3XTF32,
     QBX_M2L_FP32,

@@ -16,6 +16,7 @@ from . import build as _build
 
 QBX_FP64, QBX_M2L_FP32, QBX_M2L_3XTF32 = 0, 1, 2
 LIST_NAMES = ("U", "V", "Wclose", "Wfar", "Xclose", "Xfar")
+STAGE_NAMES = ("prep", "p2m_m2m", "m2l", "p2l", "l2l", "centers", "qbx_targets", "point_targets")
 
 
 class QbxError(RuntimeError):
@@ -60,6 +61,8 @@ def lib():
         L.qbx_lists_free.argtypes = [P]
         L.qbx_lists_free.restype = None
         L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
+        L.qbx_profile.argtypes = [P, C.c_int]
+        L.qbx_profile_read.argtypes = [P, P]
         L.qbx_last_error.restype = C.c_char_p
         _lib = L
     return _lib
@@ -137,6 +140,18 @@ class Lists:
             _check(lib().qbx_lists_export(self.handle, k, _ptr(st), _ptr(ix), _stream()))
             out[name] = (st, ix[: self.nnz(k)])
         return out
+
+    def profile(self, enable=True):
+        """Turn per-stage CUDA-event timing of later qbx_eval calls on or off."""
+        _check(lib().qbx_profile(self.handle, 1 if enable else 0))
+
+    def stage_ms(self):
+        """Stage durations (ms) of the last profiled qbx_eval, keyed by STAGE_NAMES."""
+        import numpy as np
+
+        out = np.zeros(len(STAGE_NAMES))
+        _check(lib().qbx_profile_read(self.handle, C.c_void_p(out.ctypes.data)))
+        return dict(zip(STAGE_NAMES, out.tolist()))
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:

@@ -779,9 +779,10 @@ constexpr int PM_T = 20;  // compile-time order bound of the box-expansion kerne
 constexpr int QB[] = {4, 8, 12, 16};
 
 template <int QM>
-static void launch_centers(const qbx_tree *T, const qbx_lists *L, qbx_workspace *ws, bool dip, const int *tgt_ctr,
+static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, bool dip, const int *tgt_ctr,
                            double *pot, cudaStream_t st)
 {
+    stage_mark(L, 5, st);
     const int WPB = 4;
     size_t smem = (size_t)WPB * (ntri(PM_T + QM) + PM_T + 1) * sizeof(double2);
     static bool attr_set = false;
@@ -797,6 +798,7 @@ static void launch_centers(const qbx_tree *T, const qbx_lists *L, qbx_workspace 
             dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A);
         QBX_LAUNCH_CHECK();
     }
+    stage_mark(L, 6, st);
     if (T->np[KTGT] > 0) {
         k_qbxl2p<QM><<<nblocks(T->np[KTGT], 128), 128, 0, st>>>(T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr,
                                                                 T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->qc,
@@ -839,6 +841,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     }
     (void)pmax;
     (void)pot;
+    stage_mark(L, 0, st);
     QBX_CUDA_TRY(cudaMemsetAsync(ws->flags, 0, sizeof(int), st));
     k_prep_src<<<nblocks(ns, 256), 256, 0, st>>>(T->perm[KSRC], ns, w, sigma, mu, nrm, ws->sq, ws->sd, ws->flags);
     k_prep_orders<<<nblocks(std::max(nb, nc), 256), 256, 0, st>>>(T->perm[KCTR], nc, o->p_qbx_per_ctr, o->p_qbx, nb,
@@ -859,6 +862,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     const int WPB = 4;
     const bool dip = mu != nullptr;
     // Stage 2
+    stage_mark(L, 1, st);
     k_p2m<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws->sq,
                                                        dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->Mu);
     QBX_LAUNCH_CHECK();
@@ -869,6 +873,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         QBX_LAUNCH_CHECK();
     }
     // Stage 4
+    stage_mark(L, 2, st);
     {
         size_t smem = (size_t)WPB * ntri(PM_T) * sizeof(double2);
         k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, smem, st>>>(nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws->pb,
@@ -876,10 +881,12 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         QBX_LAUNCH_CHECK();
     }
     // Stage 6(b)
+    stage_mark(L, 3, st);
     k_p2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], T->sxyz,
                                                        ns, ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->B);
     QBX_LAUNCH_CHECK();
     // Stage 7
+    stage_mark(L, 4, st);
     for (int l = 1; l < T->nlev; ++l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
         k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->parent, T->ntgt_sub, T->child, ws->pb,
@@ -894,6 +901,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     default: launch_centers<16>(T, L, ws, dip, tgt_ctr, pot, st); break;
     }
     // Stage 9 at point targets
+    stage_mark(L, 7, st);
     if (nt > 0) {
         k_points<PM_T><<<nblocks(nt, WPB), 32 * WPB, 0, st>>>(
             nt, T->perm[KTGT], T->txyz, tgt_ctr, T->tgt_box, ws->pb, ListRef{L->start[LU], L->idx[LU]},
@@ -902,6 +910,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
             T->cen, T->hw, ws->Mu, ws->B, pot);
         QBX_LAUNCH_CHECK();
     }
+    stage_mark(L, 8, st);
+    L->prof_valid = L->prof;
 }
 
 }  // namespace qbx

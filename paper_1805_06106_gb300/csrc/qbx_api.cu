@@ -45,6 +45,8 @@ static void free_lists(qbx_lists *L)
 {
     if (!L) return;
     for (int l = 0; l < NLIST; ++l) { dfree(L->start[l]); dfree(L->idx[l]); }
+    for (int i = 0; i <= QBX_NSTAGES; ++i)
+        if (L->ev[i]) cudaEventDestroy(L->ev[i]);
     free_workspace(L->ws);
     delete L;
 }
@@ -189,6 +191,33 @@ int qbx_eval(const qbx_tree *T, const qbx_lists *L, const double *w, const doubl
         if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
             throw Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
         eval(T, const_cast<qbx_lists *>(L), w, sigma, mu, nrm, tgt_ctr, o, pot, (cudaStream_t)stream);
+        return QBX_OK;
+    });
+}
+
+int qbx_profile(qbx_lists *L, int enable)
+{
+    return guarded([&]() -> int {
+        if (!L) throw Error{QBX_ERR_INVALID_ARG, "lists is NULL"};
+        if (enable && !L->ev[0])
+            for (int i = 0; i <= QBX_NSTAGES; ++i) QBX_CUDA_TRY(cudaEventCreate(&L->ev[i]));
+        L->prof = enable != 0;
+        L->prof_valid = false;
+        return QBX_OK;
+    });
+}
+
+int qbx_profile_read(const qbx_lists *L, double *ms)
+{
+    return guarded([&]() -> int {
+        if (!L || !ms) throw Error{QBX_ERR_INVALID_ARG, "NULL argument"};
+        if (!L->prof_valid) throw Error{QBX_ERR_INVALID_ARG, "no profiled evaluation to read"};
+        QBX_CUDA_TRY(cudaEventSynchronize(L->ev[QBX_NSTAGES]));
+        for (int i = 0; i < QBX_NSTAGES; ++i) {
+            float t = 0.f;
+            QBX_CUDA_TRY(cudaEventElapsedTime(&t, L->ev[i], L->ev[i + 1]));
+            ms[i] = t;
+        }
         return QBX_OK;
     });
 }

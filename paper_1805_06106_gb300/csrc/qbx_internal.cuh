@@ -98,7 +98,18 @@ struct qbx_lists {
     int *idx[qbx::NLIST] = {};
     int64_t nnz[qbx::NLIST] = {};
     qbx_workspace *ws = nullptr;
+    bool prof = false;                       // record stage events in qbx_eval
+    bool prof_valid = false;                 // the events hold a finished profiled evaluation
+    cudaEvent_t ev[QBX_NSTAGES + 1] = {};
 };
+
+namespace qbx {
+// records stage event i when profiling is on
+inline void stage_mark(qbx_lists *L, int i, cudaStream_t st)
+{
+    if (L->prof) QBX_CUDA_TRY(cudaEventRecord(L->ev[i], st));
+}
+}  // namespace qbx
 
 namespace qbx {
 void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const double *cr, const double *txyz,
