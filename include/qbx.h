@@ -166,6 +166,32 @@ int qbx_eval(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_d
 int qbx_profile(qbx_lists *lists, int enable);
 int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
 
+/*
+ * qbx_eval without device allocation.  Computes the same potentials as qbx_eval
+ * (same arguments, same stages and kernels) for callers that cannot call cudaMalloc
+ * when they evaluate: code running while someone else captures the stream into a
+ * CUDA graph, real-time loops with a memory budget fixed up front, or hosts whose
+ * allocator owns the device.  The paper has no counterpart; it is an interface choice.
+ *   Scratch: one file-scope device array of QBX_NOALLOC_SCRATCH_BYTES (48 MiB) inside
+ *   the library, held by every GPU that loads the library until the process exits.
+ *   The problem must fit: about 18.4 MB of tables + 7,392 B per box + 16 ntri(Qb) B per
+ *   center (Qb = 4, 8, 12 or 16, the smallest >= p_qbx; 16 with per-center orders)
+ *   + 33 B per source; e.g. 2,000 boxes and 20,000 centers at p_qbx <= 8.  A larger
+ *   problem returns QBX_ERR_INVALID_ARG with the byte counts in qbx_last_error().
+ *   No call allocates: no cudaMalloc, cudaFree or allocating library routine.
+ *   The first call on each device looks up the array's device address (with that
+ *   device current); make that first call before any stream capture.
+ *   All calls share the array and it keeps the last call's contents: every call
+ *   rewrites its tables and zeroes its accumulators before use, but calls whose GPU
+ *   work overlaps in time on one device (issued on different streams, or from
+ *   different host threads) race on it and give wrong results.
+ * Errors: as qbx_eval.
+ */
+#define QBX_NOALLOC_SCRATCH_BYTES (48u << 20)
+int qbx_eval_noalloc(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev, const double *sigma_dev,
+                     const double *mu_dev, const double *src_n_dev, const int32_t *tgt_ctr_dev,
+                     const qbx_eval_opts *opts, double *pot_dev, void *stream);
+
 /* Message describing the last error on the calling thread ("" if none). */
 const char *qbx_last_error(void);
 

@@ -17,4 +17,5 @@ from .binding import (  # noqa: F401
     qbx_build_lists,
     qbx_build_tree,
     qbx_eval,
+    qbx_eval_noalloc,
 )

@@ -61,6 +61,7 @@ def lib():
         L.qbx_lists_free.argtypes = [P]
         L.qbx_lists_free.restype = None
         L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
+        L.qbx_eval_noalloc.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_profile.argtypes = [P, C.c_int]
         L.qbx_profile_read.argtypes = [P, P]
         L.qbx_last_error.restype = C.c_char_p
@@ -188,6 +189,22 @@ def qbx_eval(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr, p_qbx, 
                      precision)
     _check(lib().qbx_eval(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc), C.byref(opts),
                           _ptr(out), _stream()))
+    return out
+
+
+def qbx_eval_noalloc(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr, p_qbx, p_fmm, out,
+                     p_qbx_per_ctr=None, p_fmm_per_box=None, precision=QBX_FP64):
+    """qbx_eval for callers that cannot allocate device memory: the library takes its scratch
+    from a fixed 48 MiB array, and `out` must be given."""
+    w = _dev(src_w, torch.float64)
+    sg, m, n = _dev(sigma, torch.float64), _dev(mu, torch.float64), _dev(src_n, torch.float64)
+    tc = _dev(tgt_ctr, torch.int32)
+    qc, pb = _dev(p_qbx_per_ctr, torch.int8), _dev(p_fmm_per_box, torch.int8)
+    out = _dev(out, torch.float64)
+    opts = _EvalOpts(p_qbx, p_fmm, None if qc is None else qc.data_ptr(), None if pb is None else pb.data_ptr(),
+                     precision)
+    _check(lib().qbx_eval_noalloc(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc),
+                                  C.byref(opts), _ptr(out), _stream()))
     return out
 
 

@@ -915,3 +915,149 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
 }
 
 }  // namespace qbx
+
+// ---------------------------------------------------------------- evaluation on caller-provided storage
+//
+// Same stages and kernels as eval(), with every scratch buffer carved out of `base` (at least
+// fixed_workspace_bytes() bytes, 256-byte aligned).  Nothing is allocated.  Used by the
+// no-allocation entry point; the tables are regenerated on every call.
+
+namespace qbx {
+
+static size_t carve(size_t &off, size_t bytes)
+{
+    size_t at = off;
+    off += (bytes + 255) & ~size_t(255);
+    return at;
+}
+
+static int fixed_qbucket(const qbx_eval_opts *o)
+{
+    int qmax = o->p_qbx_per_ctr ? QMAX : o->p_qbx;
+    for (int qb : QB)
+        if (qmax <= qb) return qb;
+    return 16;
+}
+
+size_t fixed_workspace_bytes(const qbx_tree *T, const qbx_eval_opts *o)
+{
+    const int64_t nb = T->nb, ns = T->np[KSRC], nc = T->np[KCTR];
+    const int QM = fixed_qbucket(o);
+    size_t off = 0;
+    carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2));                 // Mu
+    carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2));                 // B
+    carve(off, (size_t)std::max<int64_t>(nc, 1) * ntri(QM) * sizeof(double2));  // A
+    carve(off, (size_t)1331 * ntri(2 * PM_T) * sizeof(double2));           // List 2 offset table
+    carve(off, (size_t)8 * ntri(PM_T) * sizeof(double2));                  // octant table
+    carve(off, (size_t)std::max<int64_t>(ns, 1) * sizeof(double));         // charges
+    carve(off, (size_t)3 * std::max<int64_t>(ns, 1) * sizeof(double));     // dipoles
+    carve(off, (size_t)std::max<int64_t>(nc, 1));                           // per-center orders
+    carve(off, (size_t)std::max<int64_t>(nb, 1));                           // per-box orders
+    carve(off, sizeof(int));                                                // flags
+    return off;
+}
+
+template <int QM>
+static void fixed_centers(const qbx_tree *T, const qbx_lists *L, const qbx_workspace &ws, bool dip,
+                          const int *tgt_ctr, double *pot, cudaStream_t st)
+{
+    const int WPB = 4;
+    size_t smem = (size_t)WPB * (ntri(PM_T + QM) + PM_T + 1) * sizeof(double2);
+    QBX_CUDA_TRY(cudaFuncSetAttribute(k_centers<QM, PM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (T->np[KCTR] > 0) {
+        k_centers<QM, PM_T><<<nblocks(T->np[KCTR], WPB), 32 * WPB, smem, st>>>(
+            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws.qc, ws.pb, ListRef{L->start[LU], L->idx[LU]},
+            ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
+            ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws.sq,
+            dip ? ws.sd : nullptr, T->cen, T->hw, ws.Mu, ws.B, ws.A);
+        QBX_LAUNCH_CHECK();
+    }
+    if (T->np[KTGT] > 0) {
+        k_qbxl2p<QM><<<nblocks(T->np[KTGT], 128), 128, 0, st>>>(T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr,
+                                                                T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws.qc,
+                                                                ws.A, pot);
+        QBX_LAUNCH_CHECK();
+    }
+}
+
+void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size_t cap, const double *w,
+                const double *sigma, const double *mu, const double *nrm, const int *tgt_ctr,
+                const qbx_eval_opts *o, double *pot, cudaStream_t st)
+{
+    const int64_t nb = T->nb, ns = T->np[KSRC], nc = T->np[KCTR], nt = T->np[KTGT];
+    if (fixed_workspace_bytes(T, o) > cap) throw Error{QBX_ERR_INVALID_ARG, "problem exceeds the fixed scratch"};
+    const int QM = fixed_qbucket(o);
+    qbx_workspace ws;  // a view into `base`; owns nothing
+    size_t off = 0;
+    ws.Mu = reinterpret_cast<double2 *>(base + carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2)));
+    ws.B = reinterpret_cast<double2 *>(base + carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2)));
+    ws.A = reinterpret_cast<double2 *>(base + carve(off, (size_t)std::max<int64_t>(nc, 1) * ntri(QM) * sizeof(double2)));
+    ws.m2l_tab = reinterpret_cast<double2 *>(base + carve(off, (size_t)1331 * ntri(2 * PM_T) * sizeof(double2)));
+    ws.oct_tab = reinterpret_cast<double2 *>(base + carve(off, (size_t)8 * ntri(PM_T) * sizeof(double2)));
+    ws.sq = reinterpret_cast<double *>(base + carve(off, (size_t)std::max<int64_t>(ns, 1) * sizeof(double)));
+    ws.sd = reinterpret_cast<double *>(base + carve(off, (size_t)3 * std::max<int64_t>(ns, 1) * sizeof(double)));
+    ws.qc = reinterpret_cast<signed char *>(base + carve(off, (size_t)std::max<int64_t>(nc, 1)));
+    ws.pb = reinterpret_cast<signed char *>(base + carve(off, (size_t)std::max<int64_t>(nb, 1)));
+    ws.flags = reinterpret_cast<int *>(base + carve(off, sizeof(int)));
+    ws.PM = PM_T;
+    ws.QM = QM;
+
+    k_m2l_table<<<nblocks(1331, 64), 64, 0, st>>>(2 * PM_T, ws.m2l_tab);
+    k_oct_table<<<1, 32, 0, st>>>(PM_T, ws.oct_tab);
+    QBX_LAUNCH_CHECK();
+    QBX_CUDA_TRY(cudaMemsetAsync(ws.flags, 0, sizeof(int), st));
+    k_prep_src<<<nblocks(ns, 256), 256, 0, st>>>(T->perm[KSRC], ns, w, sigma, mu, nrm, ws.sq, ws.sd, ws.flags);
+    k_prep_orders<<<nblocks(std::max(nb, nc), 256), 256, 0, st>>>(T->perm[KCTR], nc, o->p_qbx_per_ctr, o->p_qbx, nb,
+                                                                  o->p_fmm_per_box, o->p_fmm, ws.qc, ws.pb, ws.flags);
+    k_check_tgt<<<nblocks(nt, 256), 256, 0, st>>>(tgt_ctr, nt, nc, ws.flags);
+    QBX_LAUNCH_CHECK();
+    cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
+    QBX_CUDA_TRY(cudaStreamIsCapturing(st, &cap_st));
+    if (cap_st == cudaStreamCaptureStatusNone) {
+        int f = read_flags(ws.flags, st);
+        if (f & 1) throw Error{QBX_ERR_INVALID_ARG, "source weight <= 0 or non-finite density/normal"};
+        if (f & 2) throw Error{QBX_ERR_INVALID_ARG, "expansion order out of range"};
+        if (f & 4) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr entry out of range"};
+    }
+    // the expansions accumulate: they must start at zero on every call
+    QBX_CUDA_TRY(cudaMemsetAsync(ws.Mu, 0, nb * ntri(PM_T) * sizeof(double2), st));
+    QBX_CUDA_TRY(cudaMemsetAsync(ws.B, 0, nb * ntri(PM_T) * sizeof(double2), st));
+    const int WPB = 4;
+    const bool dip = mu != nullptr;
+    k_p2m<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws.sq,
+                                                       dip ? ws.sd : nullptr, T->cen, T->hw, ws.pb, ws.Mu);
+    QBX_LAUNCH_CHECK();
+    for (int l = (int)T->nlev - 2; l >= 0; --l) {
+        int b0 = T->level_start[l], b1 = T->level_start[l + 1];
+        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->child, T->nsrc_sub, ws.pb, ws.oct_tab, ws.Mu);
+        QBX_LAUNCH_CHECK();
+    }
+    k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, (size_t)WPB * ntri(PM_T) * sizeof(double2), st>>>(
+        nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws.pb, ws.Mu, ws.m2l_tab, ws.B);
+    QBX_LAUNCH_CHECK();
+    k_p2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], T->sxyz,
+                                                       ns, ws.sq, dip ? ws.sd : nullptr, T->cen, T->hw, ws.pb, ws.B);
+    QBX_LAUNCH_CHECK();
+    for (int l = 1; l < T->nlev; ++l) {
+        int b0 = T->level_start[l], b1 = T->level_start[l + 1];
+        k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->parent, T->ntgt_sub, T->child, ws.pb,
+                                                                ws.oct_tab, ws.B);
+        QBX_LAUNCH_CHECK();
+    }
+    switch (QM) {
+    case 4: fixed_centers<4>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    case 8: fixed_centers<8>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    case 12: fixed_centers<12>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    default: fixed_centers<16>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    }
+    if (nt > 0) {
+        k_points<PM_T><<<nblocks(nt, WPB), 32 * WPB, 0, st>>>(
+            nt, T->perm[KTGT], T->txyz, tgt_ctr, T->tgt_box, ws.pb, ListRef{L->start[LU], L->idx[LU]},
+            ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
+            ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, ns, ws.sq, dip ? ws.sd : nullptr,
+            T->cen, T->hw, ws.Mu, ws.B, pot);
+        QBX_LAUNCH_CHECK();
+    }
+}
+
+}  // namespace qbx
