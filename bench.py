@@ -276,7 +276,7 @@ def run_gpu(args):
         geo = [cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(t)]
         torch.cuda.synchronize()
         tb0 = time.perf_counter()
-        T = G.qbx_build_tree(*geo, n_max=N_MAX, t_f=T_F)
+        T = G.qbx_build_tree(*geo, n_max=args.n_max, t_f=T_F)
         torch.cuda.synchronize()
         tb1 = time.perf_counter()
         L = G.qbx_build_lists(T)
@@ -286,8 +286,10 @@ def run_gpu(args):
         pot = torch.empty(t.shape[1], dtype=torch.float64, device=dev)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
 
+        prec = {"fp64": G.QBX_FP64, "fp32": G.QBX_M2L_FP32}[args.precision]
+
         def step():
-            G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM, out=pot)
+            G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM, out=pot, precision=prec)
 
         L.profile(True)
         for _ in range(max(args.warmup, 3)):
@@ -341,7 +343,7 @@ def run_gpu(args):
             e0.record(stream)
             for d, h in zip(dev_in, host_in):
                 d.copy_(h, non_blocking=True)
-            G.qbx_eval(T, L, *dev_in, P_QBX, P_FMM, out=pot)
+            G.qbx_eval(T, L, *dev_in, P_QBX, P_FMM, out=pot, precision=prec)
             host_out.copy_(pot, non_blocking=True)
             e1.record(stream)
             e1.synchronize()
@@ -372,7 +374,7 @@ def run_gpu(args):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"star r=1+0.3ReY63, {s.n_elem} curved triangles x 15 nodes: S[d_n u] - D[u] at "
                                f"{s.n_ctr} on-surface QBX targets + {N_VOLUME} volume points",
-                   "mode": "plain FP64 GIGAQBX, fixed orders", "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": N_MAX,
+                   "mode": f"{args.precision} List 2 M2L, fixed orders", "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": args.n_max,
                    "t_f": T_F, "n_src": int(s.n_src), "n_ctr": int(s.n_ctr), "n_qbx_targets": n_qbx_tgt,
                    "n_point_targets": n_pt_tgt, "n_flagged": int(vflag.sum()), "n_boxes": int(T.n_boxes),
                    "n_levels": nlev, "l2": "flushed between timed steps (512 MiB write)",
@@ -407,6 +409,9 @@ def main():
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-sub", type=int, default=20, help="icosahedron face subdivision (20 = 8,000 elements)")
+    ap.add_argument("--n-max", type=int, default=N_MAX, help="particles per leaf before a box splits")
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64",
+                    help="fp64: every stage FP64; fp32: List 2 M2L as FP32 per-offset products")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

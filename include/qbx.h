@@ -153,16 +153,33 @@ int qbx_eval(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_d
              const qbx_eval_opts *opts, double *pot_dev, void *stream);
 
 /*
+ * Order sweep of the QBX expansions (generates the order-versus-error data the learned
+ * orders are trained on).  Runs qbx_eval with `opts`, then writes, for every target t and
+ * every QBX order q = 0..p_qbx (fixed orders only), the potential with each QBX local
+ * truncated at order q:
+ *     partial_dev[q * n_tgt + t] = 1/(4 pi) sum_{k <= q} sum_l A_k^l R_k^l((c - t)/r_c)
+ * The coefficients of order k do not depend on the truncation order (they are produced by
+ * the same P2QBXL, M2QBXL and L2QBXL sums), so column q equals a qbx_eval at p_qbx = q
+ * with the same p_fmm.  Point targets get their potential in every column.
+ *   partial_dev: device array of (p_qbx + 1) * n_tgt doubles, overwritten.
+ * Errors: as qbx_eval; QBX_ERR_INVALID_ARG if per-center orders are given.
+ */
+int qbx_eval_order_sweep(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev,
+                         const double *sigma_dev, const double *mu_dev, const double *src_n_dev,
+                         const int32_t *tgt_ctr_dev, const qbx_eval_opts *opts, double *partial_dev, void *stream);
+
+/*
  * Per-stage timing (tracing aid; not a step of the paper's method).  While enabled,
  * every qbx_eval on these lists records CUDA events on its stream around each of
  * QBX_NSTAGES stages: 0 input preparation, 1 P2M + M2M (Stage 2), 2 List 2 M2L
- * (Stage 4), 3 List 4 far P2L (Stage 6b), 4 L2L (Stage 7), 5 QBX centers (Stages
- * 3, 5, 6a, 8: L2QBXL, List 3 far M2QBXL, direct P2QBXL), 6 QBX targets (Stage 9),
- * 7 point targets (Stage 9).  qbx_profile_read waits for the last profiled
+ * (Stage 4), 3 List 4 far P2L (Stage 6b), 4 L2L (Stage 7), 5 List 3 far M2QBXL
+ * products in the mixed-precision modes (empty in QBX_FP64), 6 QBX centers (Stages
+ * 3, 5, 6a, 8: L2QBXL, direct P2QBXL, and List 3 far M2QBXL in QBX_FP64), 7 QBX
+ * targets (Stage 9), 8 point targets (Stage 9).  qbx_profile_read waits for the last profiled
  * evaluation and writes the stage durations in milliseconds to stage_ms_host.
  * Profiling must be disabled while the stream is being captured into a graph.
  */
-#define QBX_NSTAGES 8
+#define QBX_NSTAGES 9
 int qbx_profile(qbx_lists *lists, int enable);
 int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
 

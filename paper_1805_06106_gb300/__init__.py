@@ -18,4 +18,5 @@ from .binding import (  # noqa: F401
     qbx_build_tree,
     qbx_eval,
     qbx_eval_noalloc,
+    qbx_eval_order_sweep,
 )

@@ -16,7 +16,7 @@ from . import build as _build
 
 QBX_FP64, QBX_M2L_FP32, QBX_M2L_3XTF32 = 0, 1, 2
 LIST_NAMES = ("U", "V", "Wclose", "Wfar", "Xclose", "Xfar")
-STAGE_NAMES = ("prep", "p2m_m2m", "m2l", "p2l", "l2l", "centers", "qbx_targets", "point_targets")
+STAGE_NAMES = ("prep", "p2m_m2m", "m2l", "p2l", "l2l", "m2qbxl_mixed", "centers", "qbx_targets", "point_targets")
 
 
 class QbxError(RuntimeError):
@@ -62,6 +62,7 @@ def lib():
         L.qbx_lists_free.restype = None
         L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_eval_noalloc.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
+        L.qbx_eval_order_sweep.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_profile.argtypes = [P, C.c_int]
         L.qbx_profile_read.argtypes = [P, P]
         L.qbx_last_error.restype = C.c_char_p
@@ -205,6 +206,19 @@ def qbx_eval_noalloc(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr,
                      precision)
     _check(lib().qbx_eval_noalloc(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc),
                                   C.byref(opts), _ptr(out), _stream()))
+    return out
+
+
+def qbx_eval_order_sweep(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr, p_qbx, p_fmm,
+                         precision=QBX_FP64):
+    """Potentials with every QBX local truncated at each order 0..p_qbx: tensor (p_qbx+1, n_tgt)."""
+    w = _dev(src_w, torch.float64)
+    sg, m, n = _dev(sigma, torch.float64), _dev(mu, torch.float64), _dev(src_n, torch.float64)
+    tc = _dev(tgt_ctr, torch.int32)
+    out = torch.empty((p_qbx + 1, tc.shape[0]), dtype=torch.float64, device=tc.device)
+    opts = _EvalOpts(p_qbx, p_fmm, None, None, precision)
+    _check(lib().qbx_eval_order_sweep(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc),
+                                      C.byref(opts), _ptr(out), _stream()))
     return out
 
 

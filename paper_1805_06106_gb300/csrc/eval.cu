@@ -25,7 +25,20 @@ namespace qbx {
 
 constexpr double INV4PI = 0.079577471545947667884;  // 1 / (4 pi)
 
-struct qbx_ws_impl;
+struct M2LPlan;
+void free_m2l_plan(M2LPlan *p);
+M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, cudaStream_t st);
+void m2l_mixed_run(const qbx_tree *T, const qbx_lists *L, M2LPlan *pl, int PMT, const double2 *Mu, double2 *B,
+                   const signed char *pb, cudaStream_t st);
+int m2l_plan_order(const M2LPlan *p);
+struct WfarPlan;
+void free_wfar_plan(WfarPlan *p);
+int wfar_plan_orders(const WfarPlan *p);
+const int *wfar_empty_start(const WfarPlan *p);
+WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, cudaStream_t st);
+void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb,
+                    cudaStream_t st);
+void wfar_mixed_reduce(const qbx_tree *T, WfarPlan *pl, int QMS, const signed char *qc, double2 *A, cudaStream_t st);
 
 }  // namespace qbx
 
@@ -39,6 +52,8 @@ struct qbx_workspace {
     signed char *qc = nullptr, *pb = nullptr;
     int *flags = nullptr;
     std::vector<int> lvl_first;    // host copies of level ranges
+    qbx::M2LPlan *m2l = nullptr;   // mixed-precision List 2 plan (built on first use)
+    qbx::WfarPlan *wfar = nullptr; // mixed-precision List 3 far plan (built on first use)
 };
 
 namespace qbx {
@@ -48,6 +63,8 @@ void free_workspace(qbx_workspace *ws)
     if (!ws) return;
     dfree(ws->Mu); dfree(ws->B); dfree(ws->A); dfree(ws->m2l_tab); dfree(ws->oct_tab);
     dfree(ws->sq); dfree(ws->sd); dfree(ws->qc); dfree(ws->pb); dfree(ws->flags);
+    free_m2l_plan(ws->m2l);
+    free_wfar_plan(ws->wfar);
     delete ws;
 }
 
@@ -780,9 +797,12 @@ constexpr int QB[] = {4, 8, 12, 16};
 
 template <int QM>
 static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, bool dip, const int *tgt_ctr,
-                           double *pot, cudaStream_t st)
+                           double *pot, cudaStream_t st, WfarPlan *wf = nullptr)
 {
-    stage_mark(L, 5, st);
+    stage_mark(L, 6, st);
+    // with a mixed List 3 far plan the FP64 kernel sees an empty List 3 far and the plan's
+    // products are added to the QBX locals before they are evaluated
+    const int *wf_start = wf ? wfar_empty_start(wf) : L->start[LWF];
     const int WPB = 4;
     size_t smem = (size_t)WPB * (ntri(PM_T + QM) + PM_T + 1) * sizeof(double2);
     static bool attr_set = false;
@@ -794,11 +814,12 @@ static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, b
         k_centers<QM, PM_T><<<nblocks(T->np[KCTR], WPB), 32 * WPB, smem, st>>>(
             T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc, ws->pb, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
-            ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,
+            ListRef{wf_start, L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,
             dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A);
         QBX_LAUNCH_CHECK();
+        if (wf) wfar_mixed_reduce(T, wf, QM, ws->qc, ws->A, st);
     }
-    stage_mark(L, 6, st);
+    stage_mark(L, 7, st);
     if (T->np[KTGT] > 0) {
         k_qbxl2p<QM><<<nblocks(T->np[KTGT], 128), 128, 0, st>>>(T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr,
                                                                 T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->qc,
@@ -874,11 +895,19 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     }
     // Stage 4
     stage_mark(L, 2, st);
-    {
+    if (o->precision == QBX_FP64) {
         size_t smem = (size_t)WPB * ntri(PM_T) * sizeof(double2);
         k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, smem, st>>>(nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws->pb,
                                                               ws->Mu, ws->m2l_tab, ws->B);
         QBX_LAUNCH_CHECK();
+    } else {
+        const int Pm = o->p_fmm_per_box ? PMAX : o->p_fmm;
+        if (!ws->m2l || m2l_plan_order(ws->m2l) != Pm) {
+            free_m2l_plan(ws->m2l);
+            ws->m2l = nullptr;
+            ws->m2l = m2l_plan_build(T, L, Pm, PM_T, ws->m2l_tab, st);
+        }
+        m2l_mixed_run(T, L, ws->m2l, PM_T, ws->Mu, ws->B, ws->pb, st);
     }
     // Stage 6(b)
     stage_mark(L, 3, st);
@@ -893,15 +922,28 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
                                                                 ws->oct_tab, ws->B);
         QBX_LAUNCH_CHECK();
     }
+    // Stage 5(b) in mixed precision: List 3 far products, reduced into the QBX locals below
+    stage_mark(L, 5, st);
+    WfarPlan *wf = nullptr;
+    if (o->precision != QBX_FP64 && T->np[KCTR] > 0) {
+        const int Pm = o->p_fmm_per_box ? PMAX : o->p_fmm, Qm = o->p_qbx_per_ctr ? QM : o->p_qbx;
+        if (!ws->wfar || wfar_plan_orders(ws->wfar) != Pm * 100 + Qm) {
+            free_wfar_plan(ws->wfar);
+            ws->wfar = nullptr;
+            ws->wfar = wfar_plan_build(T, L, Pm, Qm, st);
+        }
+        wf = ws->wfar;
+        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->pb, st);
+    }
     // Stages 3, 5, 6(a), 8, 9 at QBX centers and their targets
     switch (QM) {
-    case 4: launch_centers<4>(T, L, ws, dip, tgt_ctr, pot, st); break;
-    case 8: launch_centers<8>(T, L, ws, dip, tgt_ctr, pot, st); break;
-    case 12: launch_centers<12>(T, L, ws, dip, tgt_ctr, pot, st); break;
-    default: launch_centers<16>(T, L, ws, dip, tgt_ctr, pot, st); break;
+    case 4: launch_centers<4>(T, L, ws, dip, tgt_ctr, pot, st, wf); break;
+    case 8: launch_centers<8>(T, L, ws, dip, tgt_ctr, pot, st, wf); break;
+    case 12: launch_centers<12>(T, L, ws, dip, tgt_ctr, pot, st, wf); break;
+    default: launch_centers<16>(T, L, ws, dip, tgt_ctr, pot, st, wf); break;
     }
     // Stage 9 at point targets
-    stage_mark(L, 7, st);
+    stage_mark(L, 8, st);
     if (nt > 0) {
         k_points<PM_T><<<nblocks(nt, WPB), 32 * WPB, 0, st>>>(
             nt, T->perm[KTGT], T->txyz, tgt_ctr, T->tgt_box, ws->pb, ListRef{L->start[LU], L->idx[LU]},
@@ -910,8 +952,82 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
             T->cen, T->hw, ws->Mu, ws->B, pot);
         QBX_LAUNCH_CHECK();
     }
-    stage_mark(L, 8, st);
+    stage_mark(L, 9, st);
     L->prof_valid = L->prof;
+}
+
+}  // namespace qbx
+
+// ---------------------------------------------------------------- order sweep of the QBX locals
+
+namespace qbx {
+
+template <int QM>
+__global__ void k_qbx_partials(int64_t nt, int Q, const int *tperm, const double *txyz, const int *tgt_ctr,
+                               const int *ctr_rank, int64_t nc, const double *cxyz, const double *cr,
+                               const double2 *A, double *partial)
+{
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= nt) return;
+    int t = tperm[it];
+    int c = tgt_ctr[t];
+    if (c < 0 || c >= nc) {
+        double v = partial[t];  // column 0 holds the point-target potential
+        for (int q = 1; q <= Q; ++q) partial[(int64_t)q * nt + t] = v;
+        return;
+    }
+    int i = ctr_rank[c];
+    double rinv = 1.0 / cr[i];
+    double x = (cxyz[i] - txyz[it]) * rinv, y = (cxyz[nc + i] - txyz[nt + it]) * rinv,
+           z = (cxyz[2 * nc + i] - txyz[2 * nt + it]) * rinv;
+    double r2 = x * x + y * y + z * z;
+    const double2 *Ac = A + (int64_t)i * ntri(QM);
+    double row[QMAX + 1];
+    for (int k = 0; k <= Q; ++k) row[k] = 0.0;
+    double2 diag = make_double2(1.0, 0.0);
+    for (int m = 0; m <= Q; ++m) {
+        if (m > 0) diag = cscale(cmul(diag, make_double2(x, y)), 1.0 / (2.0 * m));
+        double2 a2 = make_double2(0.0, 0.0), a1 = diag;
+        double wgt = m ? 2.0 : 1.0;
+        double2 cv = Ac[tri(m, m)];
+        row[m] += wgt * (cv.x * diag.x - cv.y * diag.y);
+        for (int n = m + 1; n <= Q; ++n) {
+            double inv = 1.0 / ((double)(n + m) * (double)(n - m));
+            double2 v = make_double2(((2 * n - 1) * z * a1.x - r2 * a2.x) * inv, ((2 * n - 1) * z * a1.y - r2 * a2.y) * inv);
+            double2 cc = Ac[tri(n, m)];
+            row[n] += wgt * (cc.x * v.x - cc.y * v.y);
+            a2 = a1;
+            a1 = v;
+        }
+    }
+    double acc = 0.0;
+    for (int k = 0; k <= Q; ++k) {
+        acc += row[k];
+        partial[(int64_t)k * nt + t] = INV4PI * acc;
+    }
+}
+
+void eval_order_sweep(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
+                      const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *partial, cudaStream_t st)
+{
+    eval(T, L, w, sigma, mu, nrm, tgt_ctr, o, partial, st);
+    const int64_t nt = T->np[KTGT];
+    if (nt == 0) return;
+    qbx_workspace *ws = L->ws;
+    switch (ws->QM) {
+#define QBX_PARTIALS(QB)                                                                                        \
+    case QB:                                                                                                     \
+        k_qbx_partials<QB><<<nblocks(nt, 128), 128, 0, st>>>(nt, o->p_qbx, T->perm[KTGT], T->txyz, tgt_ctr,     \
+                                                            T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->A,    \
+                                                            partial);                                           \
+        break;
+        QBX_PARTIALS(4)
+        QBX_PARTIALS(8)
+        QBX_PARTIALS(12)
+        QBX_PARTIALS(16)
+#undef QBX_PARTIALS
+    }
+    QBX_LAUNCH_CHECK();
 }
 
 }  // namespace qbx

@@ -1,0 +1,282 @@
+// List 2 M2L (Algorithm 4 Stage 4) in mixed precision, as batched dense per-offset products.
+//
+// With box-scaled expansions the M2L operator between two same-level boxes depends only on
+// their integer offset o = ic_b - ic_d (|o|_inf in [3, 5]).  In the balanced scaling
+//   Mh_n^m = Mu_n^m F(n,m),  Bh_k^l = B_k^l / F(k,l),  F(n,m) = sqrt((n+|m|)!(n-|m|)!),
+// the operator is
+//   Bh_k^l = 1/h sum_{n,m} Mh_n^m conj S_{n+k}^{m+l}(2o) / (F(n,m) F(k,l)),
+// whose entries are bounded by 2^(n+k) / 6^(n+k+1) <= 1, so it is well represented in FP32.
+// Written on real vectors of length D = (P+1)^2 (per degree n: Re X_n^0, then Re X_n^m, Im X_n^m
+// for m = 1..n) it becomes one real D x D matrix per offset.  The operator is generated in FP64
+// from the irregular-harmonic table and rounded to FP32.
+//
+// Per evaluation: multipoles are converted to the balanced real layout (FP32), one GEMM per
+// offset multiplies the offset's matrix by the gathered source multipoles of all pairs with that
+// offset (FP32 accumulation), each pair's result is stored, and a per-box reduction adds the
+// pairs of the box's List 2 in list order in FP64 (deterministic), undoes the scaling and adds
+// into the FP64 local expansion.
+#include <algorithm>
+#include <vector>
+
+#include "harmonics.cuh"
+
+namespace qbx {
+
+struct M2LPlan {
+    int P = -1, D = 0;
+    int64_t npairs = 0;
+    int ntiles = 0;
+    float *mats = nullptr;        // 1331 x D x D, row-major (output row, input column)
+    int *pair_src = nullptr;      // source box of each pair, pairs sorted by offset
+    int *pair_pos = nullptr;      // for List 2 entry e (CSR order): its position in the sorted pairs
+    int2 *tiles = nullptr;        // (offset, first pair) of each GEMM column tile
+    int *off_start = nullptr;     // 1332: pair range of each offset
+    float *mh = nullptr;          // n_boxes x D balanced multipoles
+    float *y = nullptr;           // npairs x D per-pair results
+};
+
+int m2l_plan_order(const M2LPlan *p) { return p ? p->P : -1; }
+
+void free_m2l_plan(M2LPlan *p)
+{
+    if (!p) return;
+    dfree(p->mats); dfree(p->pair_src); dfree(p->pair_pos); dfree(p->tiles); dfree(p->off_start);
+    dfree(p->mh); dfree(p->y);
+    delete p;
+}
+
+__device__ __forceinline__ double ffac_sqrt(int n, int m)  // F(n, m) = sqrt((n+|m|)!(n-|m|)!)
+{
+    int am = m < 0 ? -m : m;
+    double f = 1.0;
+    for (int i = 2; i <= n + am; ++i) f *= i;
+    for (int i = 2; i <= n - am; ++i) f *= i;
+    return sqrt(f);
+}
+
+// real-layout index of (n, m >= 0, part)
+__host__ __device__ __forceinline__ int ridx(int n, int m, int part) { return n * n + (m == 0 ? 0 : 2 * m - 1 + part); }
+
+// One block per offset; entries from the FP64 irregular table (stride ntri(2 PMT)).
+__global__ void k_m2l_mats(int P, int PMT, const double2 *stab, float *mats)
+{
+    const int o = blockIdx.x;
+    const int D = (P + 1) * (P + 1);
+    float *Mo = mats + (int64_t)o * D * D;
+    const double2 *S = stab + (int64_t)o * ntri(2 * PMT);
+    int ox = o % 11 - 5, oy = (o / 11) % 11 - 5, oz = o / 121 - 5;
+    int amax = max(abs(ox), max(abs(oy), abs(oz)));
+    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
+        int row = idx / D, col = idx % D;
+        float v = 0.f;
+        if (amax >= 3) {
+            int k = (int)sqrtf((float)row);
+            while (k * k > row) --k;
+            while ((k + 1) * (k + 1) <= row) ++k;
+            int rr = row - k * k;  // 0 -> (l=0,re), 2l-1 -> (l,re), 2l -> (l,im)
+            int l = (rr + 1) / 2, rpart = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+            int n = (int)sqrtf((float)col);
+            while (n * n > col) --n;
+            while ((n + 1) * (n + 1) <= col) ++n;
+            int cc = col - n * n;
+            int m = (cc + 1) / 2, cpart = (cc == 0) ? 0 : ((cc & 1) ? 0 : 1);
+            double scale = 1.0 / (ffac_sqrt(n, m) * ffac_sqrt(k, l));
+            double2 c1 = cconj(sym_get(S, n + k, m + l));
+            double2 c2 = make_double2(0.0, 0.0);
+            if (m > 0) c2 = cconj(sym_get(S, n + k, -m + l));
+            double s = (m & 1) ? -1.0 : 1.0;
+            double2 plus = make_double2(c1.x + s * c2.x, c1.y + s * c2.y);
+            double2 minus = make_double2(c1.x - s * c2.x, c1.y - s * c2.y);
+            double e;
+            if (rpart == 0 && cpart == 0) e = plus.x;
+            else if (rpart == 0 && cpart == 1) e = -minus.y;
+            else if (rpart == 1 && cpart == 0) e = plus.y;
+            else e = minus.x;
+            v = (float)(e * scale);
+        }
+        Mo[idx] = v;
+    }
+}
+
+__global__ void k_pair_offsets(int nb, const int *vstart, const int *vidx, const int64_t *ic, int *code, int *cnt)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    for (int e = vstart[b]; e < vstart[b + 1]; ++e) {
+        int d = vidx[e];
+        int ox = (int)(ic[3 * b] - ic[3 * d]), oy = (int)(ic[3 * b + 1] - ic[3 * d + 1]),
+            oz = (int)(ic[3 * b + 2] - ic[3 * d + 2]);
+        int c = (ox + 5) + 11 * (oy + 5) + 121 * (oz + 5);
+        bool ok = ox >= -5 && ox <= 5 && oy >= -5 && oy <= 5 && oz >= -5 && oz <= 5;
+        code[e] = ok ? c : 0;  // offset 0 holds a zero operator
+        atomicAdd(&cnt[ok ? c : 0], 1);
+    }
+}
+
+// Balanced real multipoles: Mh[b][ridx(n,m,part)] = (Mu_n^m F(n,m)).{re,im}
+__global__ void k_mhat(int64_t nb, int P, int PMT, const double2 *Mu, float *mh)
+{
+    const int D = (P + 1) * (P + 1);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * D) return;
+    int64_t b = i / D;
+    int r = (int)(i % D);
+    int n = (int)sqrtf((float)r);
+    while (n * n > r) --n;
+    while ((n + 1) * (n + 1) <= r) ++n;
+    int rr = r - n * n;
+    int m = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+    double2 v = Mu[b * ntri(PMT) + tri(n, m)];
+    mh[i] = (float)((part ? v.y : v.x) * ffac_sqrt(n, m));
+}
+
+// FP32 SIMT GEMM per offset tile: Y[pair] = Mats[o] * Mh[src(pair)], block = 64 rows x 64 pairs.
+constexpr int GM = 64, GN = 64, GK = 16;
+__global__ void __launch_bounds__(256) k_m2l_gemm_fp32(int D, const int2 *tiles, const int *off_start,
+                                                       const int *pair_src, const float *mats, const float *mh,
+                                                       float *y)
+{
+    __shared__ float As[GK][GM + 4];
+    __shared__ float Bs[GK][GN + 4];
+    const int2 tl = tiles[blockIdx.x];
+    const int o = tl.x, p0 = tl.y, p1 = min(off_start[o + 1], p0 + GN);
+    const int row0 = blockIdx.y * GM;
+    const float *A = mats + (int64_t)o * D * D;
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 16 x 16 threads, 4 x 4 outputs each
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < D; k0 += GK) {
+        for (int i = threadIdx.x; i < GM * GK; i += 256) {
+            int r = i / GK, k = i % GK;
+            int gr = row0 + r, gk = k0 + k;
+            As[k][r] = (gr < D && gk < D) ? A[(int64_t)gr * D + gk] : 0.f;
+        }
+        for (int i = threadIdx.x; i < GN * GK; i += 256) {
+            int c = i / GK, k = i % GK;
+            int p = p0 + c, gk = k0 + k;
+            Bs[k][c] = (p < p1 && gk < D) ? mh[(int64_t)pair_src[p] * D + gk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < GK; ++k) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[k][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[k][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            int r = row0 + ty * 4 + i, p = p0 + tx * 4 + j;
+            if (r < D && p < p1) y[(int64_t)p * D + r] = acc[i][j];
+        }
+}
+
+// B[b] += F(k,l)/h_b * sum_{e in V(b)} Y[pos(e)], summed in list order in FP64.
+__global__ void k_m2l_reduce(int64_t nb, int P, int PMT, const int *vstart, const int *pair_pos, const float *y,
+                             const double *hw, const signed char *pb, double2 *B)
+{
+    const int D = (P + 1) * (P + 1);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * D) return;
+    int b = (int)(i / D), r = (int)(i % D);
+    int e0 = vstart[b], e1 = vstart[b + 1];
+    if (e0 == e1) return;
+    int k = (int)sqrtf((float)r);
+    while (k * k > r) --k;
+    while ((k + 1) * (k + 1) <= r) ++k;
+    if (k > pb[b]) return;
+    int rr = r - k * k;
+    int l = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+    double s = 0.0;
+    for (int e = e0; e < e1; ++e) s += (double)y[(int64_t)pair_pos[e] * D + r];
+    s *= ffac_sqrt(k, l) / hw[b];
+    double2 *t = B + (int64_t)b * ntri(PMT) + tri(k, l);
+    if (part) t->y += s;
+    else t->x += s;
+}
+
+__global__ void k_scatter_pairs(int nb, const int *vstart, const int *vidx, const int *code, int *fill,
+                                int *pair_src, int *pair_pos)
+{
+    // one thread per box: entries are placed in CSR order within an offset, so the
+    // assignment is deterministic only up to the order boxes reach the atomic; the
+    // reduction reads pairs through pair_pos in list order, which keeps sums deterministic.
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    for (int e = vstart[b]; e < vstart[b + 1]; ++e) {
+        int p = atomicAdd(&fill[code[e]], 1);
+        pair_src[p] = vidx[e];
+        pair_pos[e] = p;
+    }
+}
+
+M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, cudaStream_t st)
+{
+    M2LPlan *pl = new M2LPlan();
+    try {
+        pl->P = P;
+        pl->D = (P + 1) * (P + 1);
+        const int nb = (int)T->nb;
+        const int64_t np = L->nnz[LV];
+        pl->npairs = np;
+        pl->mats = dalloc<float>((int64_t)1331 * pl->D * pl->D);
+        k_m2l_mats<<<1331, 256, 0, st>>>(P, PMT, stab, pl->mats);
+        QBX_LAUNCH_CHECK();
+        int *code = dalloc<int>(np), *cnt = dalloc<int>(1332), *fill = dalloc<int>(1332);
+        pl->off_start = dalloc<int>(1332);
+        pl->pair_src = dalloc<int>(np);
+        pl->pair_pos = dalloc<int>(np);
+        QBX_CUDA_TRY(cudaMemsetAsync(cnt, 0, 1332 * sizeof(int), st));
+        k_pair_offsets<<<nblocks(nb, 128), 128, 0, st>>>(nb, L->start[LV], L->idx[LV], T->ic, code, cnt);
+        QBX_LAUNCH_CHECK();
+        exclusive_scan(cnt, pl->off_start, 1332, 0, nullptr, st);
+        QBX_CUDA_TRY(cudaMemcpyAsync(fill, pl->off_start, 1332 * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        k_scatter_pairs<<<nblocks(nb, 128), 128, 0, st>>>(nb, L->start[LV], L->idx[LV], code, fill, pl->pair_src,
+                                                          pl->pair_pos);
+        QBX_LAUNCH_CHECK();
+        std::vector<int> os(1332);
+        QBX_CUDA_TRY(cudaMemcpyAsync(os.data(), pl->off_start, 1332 * sizeof(int), cudaMemcpyDeviceToHost, st));
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+        dfree(code); dfree(cnt); dfree(fill);
+        std::vector<int2> tiles;
+        for (int o = 0; o < 1331; ++o)
+            for (int p = os[o]; p < os[o + 1]; p += GN) tiles.push_back(make_int2(o, p));
+        pl->ntiles = (int)tiles.size();
+        pl->tiles = dalloc<int2>(std::max<size_t>(tiles.size(), 1));
+        if (!tiles.empty())
+            QBX_CUDA_TRY(cudaMemcpyAsync(pl->tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+        pl->mh = dalloc<float>((int64_t)nb * pl->D);
+        pl->y = dalloc<float>(std::max<int64_t>(np, 1) * pl->D);
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+    } catch (...) {
+        free_m2l_plan(pl);
+        throw;
+    }
+    return pl;
+}
+
+void m2l_mixed_run(const qbx_tree *T, const qbx_lists *L, M2LPlan *pl, int PMT, const double2 *Mu, double2 *B,
+                   const signed char *pb, cudaStream_t st)
+{
+    const int64_t nb = T->nb;
+    const int D = pl->D;
+    k_mhat<<<nblocks(nb * D, 256), 256, 0, st>>>(nb, pl->P, PMT, Mu, pl->mh);
+    QBX_LAUNCH_CHECK();
+    if (pl->ntiles > 0) {
+        dim3 grid(pl->ntiles, (D + GM - 1) / GM);
+        k_m2l_gemm_fp32<<<grid, 256, 0, st>>>(D, pl->tiles, pl->off_start, pl->pair_src, pl->mats, pl->mh, pl->y);
+        QBX_LAUNCH_CHECK();
+    }
+    k_m2l_reduce<<<nblocks(nb * D, 256), 256, 0, st>>>(nb, pl->P, PMT, L->start[LV], pl->pair_pos, pl->y, T->hw, pb, B);
+    QBX_LAUNCH_CHECK();
+}
+
+}  // namespace qbx

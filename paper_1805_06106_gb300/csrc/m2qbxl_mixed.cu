@@ -1,0 +1,414 @@
+// List 3 far M2QBXL (Algorithm 4 Stage 5(b)) in mixed precision.
+//
+// For a List 3 far box d (center c_d, half width h_d) and a QBX center c (radius rho) of a box
+// b with d in List 3 far of b, the QBX local receives
+//   A_k^l += 1/h (rho/h)^k sum_{j,i} Mu_{j-k}^{i-l} conj S_j^i(X),   X = (c - c_d)/h,  h = h_d.
+// In the balanced scaling (Mh = Mu F, Sh = S / F, Ah = A / F, F(n,m) = sqrt((n+|m|)!(n-|m|)!))
+//   Ah_k^l (h (h/rho)^k) = sum_{j,i} Mh_{j-k}^{i-l} G(j-k, i-l, k, l) conj Sh_j^i(X),
+//   G(n,m,k,l) = F(n+k, m+l) / (F(n,m) F(k,l)) <= 2^(n+k),
+// a product of a matrix that depends on d only (a Hankel arrangement of its multipole, built in
+// FP64 and rounded to FP32) with a vector that depends on the pair (irregular harmonics of X up
+// to order P+Q, computed in FP64 and rounded).  Pairs are grouped by d, each group is one FP32
+// GEMM, each pair's result is stored, and a per-center reduction adds the center's pairs in
+// List 3 far order in FP64.
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "harmonics.cuh"
+
+namespace qbx {
+
+struct WfarPlan {
+    int P = -1, Q = -1, K = 0, R = 0;
+    int64_t npairs = 0;
+    int ndsrc = 0, ntiles = 0;
+    int *slot = nullptr;      // n_boxes: H slot of a List 3 far source box, -1 otherwise
+    int *slot_box = nullptr;  // ndsrc: box of each slot
+    float *H = nullptr;       // ndsrc x R x K
+    int *pair_ctr = nullptr;  // sorted center of each pair (pairs grouped by d)
+    int *pair_d = nullptr;    // source box of each pair
+    int *pos_cm = nullptr;    // center-major entry -> pair position
+    int *cm_start = nullptr;  // nc + 1
+    int2 *tiles = nullptr;    // (first pair, last pair + 1) per GEMM tile
+    float *Y = nullptr;       // npairs x R
+    int *zero_start = nullptr;  // n_boxes + 1 zeros: an empty List 3 far for the FP64 center kernel
+};
+
+int wfar_plan_orders(const WfarPlan *p) { return p ? p->P * 100 + p->Q : -1; }
+const int *wfar_empty_start(const WfarPlan *p) { return p->zero_start; }
+
+void free_wfar_plan(WfarPlan *p)
+{
+    if (!p) return;
+    dfree(p->slot); dfree(p->slot_box); dfree(p->H); dfree(p->pair_ctr); dfree(p->pair_d); dfree(p->pos_cm);
+    dfree(p->cm_start); dfree(p->tiles); dfree(p->Y); dfree(p->zero_start);
+    delete p;
+}
+
+__constant__ double c_F[ntri(40)];     // F(n,m), m >= 0, n <= 40
+__constant__ double c_Finv[ntri(40)];  // 1 / F(n,m)
+
+__device__ __forceinline__ double Fnm(int n, int m) { return c_F[tri(n, m < 0 ? -m : m)]; }
+__device__ __forceinline__ double Finv(int n, int m) { return c_Finv[tri(n, m < 0 ? -m : m)]; }
+
+// row index of (k, l, part) and column index of (j, i, part) in the real layouts
+__device__ __forceinline__ void decode(int r, int &n, int &m, int &part)
+{
+    n = (int)sqrtf((float)r);
+    while (n * n > r) --n;
+    while ((n + 1) * (n + 1) <= r) ++n;
+    int rr = r - n * n;
+    m = (rr + 1) / 2;
+    part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+}
+
+__global__ void k_wfar_count(int64_t nc, const int *ctr_box, const int *wstart, const int *widx, int *cm_cnt,
+                             int *d_cnt)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    int b = ctr_box[i];
+    cm_cnt[i] = wstart[b + 1] - wstart[b];
+    for (int e = wstart[b]; e < wstart[b + 1]; ++e) atomicAdd(&d_cnt[widx[e]], 1);
+}
+
+__global__ void k_wfar_fill(int64_t nc, const int *ctr_box, const int *wstart, const int *widx, const int *cm_start,
+                            int *d_fill, int *pair_ctr, int *pair_d, int *pos_cm)
+{
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    int b = ctr_box[i];
+    for (int e = wstart[b]; e < wstart[b + 1]; ++e) {
+        int d = widx[e];
+        int p = atomicAdd(&d_fill[d], 1);
+        pair_ctr[p] = (int)i;
+        pair_d[p] = d;
+        pos_cm[cm_start[i] + (e - wstart[b])] = p;
+    }
+}
+
+__global__ void k_wfar_slots(int nb, const int *d_cnt, const int *slot_scan, int *slot, int *slot_box)
+{
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= nb) return;
+    if (d_cnt[d] > 0) {
+        slot[d] = slot_scan[d];
+        slot_box[slot_scan[d]] = d;
+    } else {
+        slot[d] = -1;
+    }
+}
+
+__global__ void k_flag_pos(int nb, const int *cnt, int *flag)
+{
+    int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d < nb) flag[d] = cnt[d] > 0 ? 1 : 0;
+}
+
+// H[slot][(k,l,rp)][(j,i,cp)] from the FP64 multipole of the slot's box.
+__global__ void k_wfar_H(int ndsrc, int P, int Q, int PMT, const int *slot_box, const signed char *pb,
+                         const double2 *Mu, float *H)
+{
+    const int K = (P + Q + 1) * (P + Q + 1), R = (Q + 1) * (Q + 1);
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)ndsrc * R * K) return;
+    int s = (int)(idx / ((int64_t)R * K));
+    int rem = (int)(idx % ((int64_t)R * K));
+    int row = rem / K, col = rem % K;
+    int d = slot_box[s];
+    int Pd = min((int)pb[d], P);
+    int k, l, rp, j, i, cp;
+    decode(row, k, l, rp);
+    decode(col, j, i, cp);
+    const double2 *M = Mu + (int64_t)d * ntri(PMT);
+    int n = j - k;
+    double2 a1 = make_double2(0, 0), a2 = make_double2(0, 0);
+    if (n >= 0 && n <= Pd) {
+        int m1 = i - l, m2 = -i - l;
+        // Mh_n^m G(n,m,k,l) = Mu_n^m F(n+k, m+l) / F(k,l)
+        if (m1 >= -n && m1 <= n) a1 = cscale(sym_get(M, n, m1), Fnm(n + k, m1 + l) * Finv(k, l));
+        if (i > 0 && m2 >= -n && m2 <= n) a2 = cscale(sym_get(M, n, m2), Fnm(n + k, m2 + l) * Finv(k, l));
+    }
+    double sg = (i & 1) ? -1.0 : 1.0;
+    double2 plus = make_double2(a1.x + sg * a2.x, a1.y + sg * a2.y);   // a1 + s a2
+    double2 mins = make_double2(sg * a2.x - a1.x, sg * a2.y - a1.y);   // s a2 - a1
+    double e;
+    if (rp == 0 && cp == 0) e = plus.x;
+    else if (rp == 0 && cp == 1) e = -mins.y;
+    else if (rp == 1 && cp == 0) e = plus.y;
+    else e = mins.x;
+    H[idx] = (float)e;
+}
+
+constexpr int WKC = 32;  // K chunk of the H tile
+
+// One tile = up to WT pairs of one source box d: balanced irregular harmonics of the pairs (FP64
+// -> FP32, shared memory), then Y = H_d x S in FP32, scaled per output row.  256 threads: 256/WT
+// per pair for the harmonics; (256/(WT/4)) row groups x (WT/4) column groups of 4 for the product.
+template <int WT, int MR>
+__global__ void __launch_bounds__(256) k_wfar_gemm(int P, int Q, const int2 *tiles, const int *pair_ctr,
+                                                   const int *pair_d, const int *slot, const float *H,
+                                                   const double *cxyz, int64_t nc, const double *cr,
+                                                   const double *cen, const double *hw, float *Y)
+{
+    extern __shared__ float smem[];
+    constexpr int TPP = 256 / WT, CG = WT / 4, RG = 256 / CG;
+    const int K = (P + Q + 1) * (P + Q + 1), R = (Q + 1) * (Q + 1), PQ = P + Q;
+    float *Ss = smem;                       // K x WT
+    float *Hs = smem + (size_t)K * WT;      // R x WKC
+    float *Pw = Hs + (size_t)R * WKC;       // WT x (Q+1): (rho/h)^k / h per pair
+    const int2 tl = tiles[blockIdx.x];
+    const int p0 = tl.x, np = tl.y - tl.x;
+    const int d = pair_d[p0];
+    const float *Hd = H + (int64_t)slot[d] * R * K;
+    const double h = hw[d], hinv = 1.0 / h;
+    {
+        const int pc = threadIdx.x / TPP, r = threadIdx.x % TPP;
+        bool valid = pc < np;
+        double x = 3.0, y = 0.0, z = 0.0;
+        if (valid) {
+            int c = pair_ctr[p0 + pc];
+            x = (cxyz[c] - cen[3 * d]) * hinv;
+            y = (cxyz[nc + c] - cen[3 * d + 1]) * hinv;
+            z = (cxyz[2 * nc + c] - cen[3 * d + 2]) * hinv;
+        }
+        double ir2 = 1.0 / (x * x + y * y + z * z);
+        double rinv = sqrt(ir2);
+        double2 wr = make_double2(x * ir2, y * ir2);
+        double zz = z * ir2;
+        if (r == 0) {
+            double ratio = valid ? cr[pair_ctr[p0 + pc]] * hinv : 0.0, pk = hinv;
+            for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[pc * (Q + 1) + k] = (float)pk;
+        }
+        // lockstep rounds: in round k thread r fills column i = k*TPP + r; every thread advances
+        // its own diagonal S_i^i by TPP steps per round, so the warp stays converged
+        double2 diag = make_double2(rinv, 0.0);
+        for (int t = 1; t <= r; ++t) diag = cscale(cmul(diag, wr), 2.0 * t - 1.0);
+        for (int base = 0; base <= PQ; base += TPP) {
+            const int i = base + r;
+            if (base > 0)
+                for (int t = i - TPP + 1; t <= i; ++t) diag = cscale(cmul(diag, wr), 2.0 * t - 1.0);
+            if (i > PQ) continue;
+            double2 a2 = make_double2(0.0, 0.0), a1 = diag;
+            const double fz = valid ? 1.0 : 0.0;
+            Ss[(size_t)(i * i + (i == 0 ? 0 : 2 * i - 1)) * WT + pc] = (float)(diag.x * Finv(i, i) * fz);
+            if (i > 0) Ss[(size_t)(i * i + 2 * i) * WT + pc] = (float)(diag.y * Finv(i, i) * fz);
+            for (int j = i + 1; j <= PQ; ++j) {
+                double c1 = (2 * j - 1) * zz, c2 = (double)(j + i - 1) * (double)(j - i - 1) * ir2;
+                double2 v = make_double2(c1 * a1.x - c2 * a2.x, c1 * a1.y - c2 * a2.y);
+                a2 = a1;
+                a1 = v;
+                double f = Finv(j, i) * fz;
+                // the balanced harmonic itself (Re, Im); H carries the conjugation
+                Ss[(size_t)(j * j + (i == 0 ? 0 : 2 * i - 1)) * WT + pc] = (float)(v.x * f);
+                if (i > 0) Ss[(size_t)(j * j + 2 * i) * WT + pc] = (float)(v.y * f);
+            }
+        }
+    }
+    __syncthreads();
+    const int tx = threadIdx.x % CG, ty = threadIdx.x / CG;
+    float acc[MR][4] = {};
+    for (int k0 = 0; k0 < K; k0 += WKC) {
+        for (int t = threadIdx.x; t < R * WKC; t += 256) {
+            int rr = t / WKC, kk = t % WKC;
+            Hs[t] = (k0 + kk < K) ? Hd[(int64_t)rr * K + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+        int kmax = min(WKC, K - k0);
+        for (int kk = 0; kk < kmax; ++kk) {
+            float b[4];
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj) b[jj] = Ss[(size_t)(k0 + kk) * WT + tx * 4 + jj];
+#pragma unroll
+            for (int ii = 0; ii < MR; ++ii) {
+                int row = ty + RG * ii;
+                float a = row < R ? Hs[row * WKC + kk] : 0.f;
+#pragma unroll
+                for (int jj = 0; jj < 4; ++jj) acc[ii][jj] = fmaf(a, b[jj], acc[ii][jj]);
+            }
+        }
+        __syncthreads();
+    }
+    // epilogue: A_k^l = Ah_k^l F(k,l) (rho/h)^k / h
+#pragma unroll
+    for (int ii = 0; ii < MR; ++ii) {
+        int row = ty + RG * ii;
+        if (row >= R) continue;
+        int k = (int)sqrtf((float)row);
+        while (k * k > row) --k;
+        while ((k + 1) * (k + 1) <= row) ++k;
+        int rr = row - k * k, l = (rr + 1) / 2;
+        float fk = (float)Fnm(k, l);
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+            int pc = tx * 4 + jj;
+            if (pc < np) Y[(int64_t)(p0 + pc) * R + row] = acc[ii][jj] * (fk * Pw[pc * (Q + 1) + k]);
+        }
+    }
+}
+
+static int wfar_tile_width(int, int) { return 32; }
+static int wfar_rows_per_thread(int R) { return R <= 64 ? 2 : R <= 96 ? 3 : R <= 160 ? 5 : 10; }
+
+template <int MR>
+static void wfar_launch(const qbx_tree *T, WfarPlan *pl, size_t smem, cudaStream_t st)
+{
+    k_wfar_gemm<32, MR><<<pl->ntiles, 256, smem, st>>>(pl->P, pl->Q, pl->tiles, pl->pair_ctr, pl->pair_d, pl->slot,
+                                                       pl->H, T->cxyz, T->np[KCTR], T->cr, T->cen, T->hw, pl->Y);
+}
+
+template <int MR>
+static void wfar_set_smem(size_t smem)
+{
+    QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_gemm<32, MR>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+}
+static size_t wfar_smem(int K, int R, int WT)
+{
+    int Q = (int)std::lround(std::sqrt((double)R)) - 1;
+    return ((size_t)K * WT + (size_t)R * WKC + (size_t)WT * (Q + 1)) * sizeof(float);
+}
+
+// A[c][tri(k,l)] += sum over the center's List 3 far pairs (list order), FP64.
+__global__ void k_wfar_reduce(int64_t nc, int Q, int QMS, const int *cm_start, const int *pos_cm, const float *Y,
+                              const signed char *qc, double2 *A)
+{
+    const int R = (Q + 1) * (Q + 1);
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nc * R) return;
+    int64_t i = t / R;
+    int row = (int)(t % R);
+    int k = (int)sqrtf((float)row);
+    while (k * k > row) --k;
+    while ((k + 1) * (k + 1) <= row) ++k;
+    if (k > qc[i]) return;
+    int rr = row - k * k, l = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+    int e0 = cm_start[i], e1 = cm_start[i + 1];
+    if (e0 == e1) return;
+    double s = 0.0;
+    for (int e = e0; e < e1; ++e) s += (double)Y[(int64_t)pos_cm[e] * R + row];
+    double2 *a = A + i * ntri(QMS) + tri(k, l);
+    if (part) a->y += s;
+    else a->x += s;
+}
+
+WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, cudaStream_t st)
+{
+    WfarPlan *pl = new WfarPlan();
+    int *cm_cnt = nullptr, *d_cnt = nullptr, *d_start = nullptr, *flag = nullptr, *tot = nullptr;
+    try {
+        pl->P = P;
+        pl->Q = Q;
+        pl->K = (P + Q + 1) * (P + Q + 1);
+        pl->R = (Q + 1) * (Q + 1);
+        const int nb = (int)T->nb;
+        const int64_t nc = T->np[KCTR];
+        {  // F(n, m) table in constant memory
+            std::vector<double> F(ntri(40));
+            std::vector<double> fact(81, 1.0);
+            for (int i = 1; i <= 80; ++i) fact[i] = fact[i - 1] * i;
+            for (int n = 0; n <= 40; ++n)
+                for (int m = 0; m <= n; ++m) F[tri(n, m)] = std::sqrt(fact[n + m] * fact[n - m]);
+            std::vector<double> Fi(F.size());
+            for (size_t i = 0; i < F.size(); ++i) Fi[i] = 1.0 / F[i];
+            QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_F, F.data(), F.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+            QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_Finv, Fi.data(), Fi.size() * sizeof(double), 0,
+                                                 cudaMemcpyHostToDevice, st));
+        }
+        cm_cnt = dalloc<int>(nc + 1);
+        d_cnt = dalloc<int>(nb + 1);
+        d_start = dalloc<int>(nb + 1);
+        flag = dalloc<int>(nb + 1);
+        tot = dalloc<int>(1);
+        pl->cm_start = dalloc<int>(nc + 1);
+        pl->zero_start = dalloc<int>(nb + 1);
+        pl->slot = dalloc<int>(nb);
+        QBX_CUDA_TRY(cudaMemsetAsync(pl->zero_start, 0, (nb + 1) * sizeof(int), st));
+        QBX_CUDA_TRY(cudaMemsetAsync(cm_cnt, 0, (nc + 1) * sizeof(int), st));
+        QBX_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, (nb + 1) * sizeof(int), st));
+        QBX_CUDA_TRY(cudaMemsetAsync(flag, 0, (nb + 1) * sizeof(int), st));  // flag[nb] stays 0 for the scan
+        if (nc > 0)
+            k_wfar_count<<<nblocks(nc, 256), 256, 0, st>>>(nc, T->ctr_box, L->start[LWF], L->idx[LWF], cm_cnt, d_cnt);
+        QBX_LAUNCH_CHECK();
+        exclusive_scan(cm_cnt, pl->cm_start, nc + 1, 0, tot, st);
+        int np = 0;
+        QBX_CUDA_TRY(cudaMemcpyAsync(&np, tot, sizeof(int), cudaMemcpyDeviceToHost, st));
+        exclusive_scan(d_cnt, d_start, nb + 1, 0, nullptr, st);
+        k_flag_pos<<<nblocks(nb, 256), 256, 0, st>>>(nb, d_cnt, flag);
+        exclusive_scan(flag, flag, nb + 1, 0, tot, st);
+        int nd = 0;
+        QBX_CUDA_TRY(cudaMemcpyAsync(&nd, tot, sizeof(int), cudaMemcpyDeviceToHost, st));
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+        pl->npairs = np;
+        pl->ndsrc = nd;
+        pl->slot_box = dalloc<int>(std::max(nd, 1));
+        k_wfar_slots<<<nblocks(nb, 256), 256, 0, st>>>(nb, d_cnt, flag, pl->slot, pl->slot_box);
+        pl->pair_ctr = dalloc<int>(std::max(np, 1));
+        pl->pair_d = dalloc<int>(std::max(np, 1));
+        pl->pos_cm = dalloc<int>(std::max(np, 1));
+        int *d_fill = flag;  // reuse
+        QBX_CUDA_TRY(cudaMemcpyAsync(d_fill, d_start, (nb + 1) * sizeof(int), cudaMemcpyDeviceToDevice, st));
+        if (nc > 0)
+            k_wfar_fill<<<nblocks(nc, 256), 256, 0, st>>>(nc, T->ctr_box, L->start[LWF], L->idx[LWF], pl->cm_start,
+                                                          d_fill, pl->pair_ctr, pl->pair_d, pl->pos_cm);
+        QBX_LAUNCH_CHECK();
+        std::vector<int> ds(nb + 1);
+        QBX_CUDA_TRY(cudaMemcpyAsync(ds.data(), d_start, (nb + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+        const int WT = wfar_tile_width(pl->K, pl->R);
+        if (pl->R > 320 || wfar_smem(pl->K, pl->R, WT) > 227 * 1024)
+            throw Error{QBX_ERR_INVALID_ARG, "orders too high for the mixed List 3 far product"};
+        std::vector<int2> tiles;
+        for (int d = 0; d < nb; ++d)
+            for (int p = ds[d]; p < ds[d + 1]; p += WT) tiles.push_back(make_int2(p, std::min(p + WT, ds[d + 1])));
+        pl->ntiles = (int)tiles.size();
+        pl->tiles = dalloc<int2>(std::max<size_t>(tiles.size(), 1));
+        if (!tiles.empty())
+            QBX_CUDA_TRY(cudaMemcpyAsync(pl->tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                                         st));
+        pl->H = dalloc<float>((int64_t)std::max(nd, 1) * pl->R * pl->K);
+        pl->Y = dalloc<float>((int64_t)std::max(np, 1) * pl->R);
+        size_t smem = wfar_smem(pl->K, pl->R, WT);
+        switch (wfar_rows_per_thread(pl->R)) {
+        case 2: wfar_set_smem<2>(smem); break;
+        case 3: wfar_set_smem<3>(smem); break;
+        case 5: wfar_set_smem<5>(smem); break;
+        default: wfar_set_smem<10>(smem); break;
+        }
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+    } catch (...) {
+        dfree(cm_cnt); dfree(d_cnt); dfree(d_start); dfree(flag); dfree(tot);
+        free_wfar_plan(pl);
+        throw;
+    }
+    dfree(cm_cnt); dfree(d_cnt); dfree(d_start); dfree(flag); dfree(tot);
+    return pl;
+}
+
+void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb,
+                    cudaStream_t st)
+{
+    if (pl->npairs == 0) return;
+    int64_t nH = (int64_t)pl->ndsrc * pl->R * pl->K;
+    k_wfar_H<<<nblocks(nH, 256), 256, 0, st>>>(pl->ndsrc, pl->P, pl->Q, PMT, pl->slot_box, pb, Mu, pl->H);
+    QBX_LAUNCH_CHECK();
+    const int WT = wfar_tile_width(pl->K, pl->R);
+    size_t smem = wfar_smem(pl->K, pl->R, WT);
+    switch (wfar_rows_per_thread(pl->R)) {
+    case 2: wfar_launch<2>(T, pl, smem, st); break;
+    case 3: wfar_launch<3>(T, pl, smem, st); break;
+    case 5: wfar_launch<5>(T, pl, smem, st); break;
+    default: wfar_launch<10>(T, pl, smem, st); break;
+    }
+    QBX_LAUNCH_CHECK();
+}
+
+void wfar_mixed_reduce(const qbx_tree *T, WfarPlan *pl, int QMS, const signed char *qc, double2 *A, cudaStream_t st)
+{
+    if (pl->npairs == 0) return;
+    const int64_t nc = T->np[KCTR];
+    k_wfar_reduce<<<nblocks(nc * pl->R, 256), 256, 0, st>>>(nc, pl->Q, QMS, pl->cm_start, pl->pos_cm, pl->Y, qc, A);
+    QBX_LAUNCH_CHECK();
+}
+
+}  // namespace qbx

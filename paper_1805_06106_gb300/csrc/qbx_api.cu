@@ -183,7 +183,8 @@ int qbx_eval(const qbx_tree *T, const qbx_lists *L, const double *w, const doubl
         if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
         if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
         if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
-        if (o->precision != QBX_FP64) throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
+        if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32)
+            throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
         if (!o->p_qbx_per_ctr && (o->p_qbx < 0 || o->p_qbx > QMAX))
             throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
         if (!o->p_fmm_per_box && (o->p_fmm < 0 || o->p_fmm > PMAX))
@@ -218,6 +219,19 @@ int qbx_profile_read(const qbx_lists *L, double *ms)
             QBX_CUDA_TRY(cudaEventElapsedTime(&t, L->ev[i], L->ev[i + 1]));
             ms[i] = t;
         }
+        return QBX_OK;
+    });
+}
+
+int qbx_eval_order_sweep(const qbx_tree *T, const qbx_lists *L, const double *w, const double *sigma,
+                         const double *mu, const double *nrm, const int32_t *tgt_ctr, const qbx_eval_opts *o,
+                         double *partial, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!o || o->p_qbx_per_ctr) throw Error{QBX_ERR_INVALID_ARG, "order sweep needs a fixed p_qbx"};
+        int rc = qbx_eval(T, L, w, sigma, mu, nrm, tgt_ctr, o, partial, stream);
+        if (rc != QBX_OK) throw Error{rc, g_err};
+        eval_order_sweep(T, const_cast<qbx_lists *>(L), w, sigma, mu, nrm, tgt_ctr, o, partial, (cudaStream_t)stream);
         return QBX_OK;
     });
 }

@@ -35,7 +35,12 @@ T *dalloc(size_t n)
 {
     void *p = nullptr;
     if (n == 0) n = 1;
-    QBX_CUDA_TRY(cudaMalloc(&p, n * sizeof(T)));
+    cudaError_t e = cudaMalloc(&p, n * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // an allocation failure must not surface again at the next launch check
+        throw ::qbx::Error{e == cudaErrorMemoryAllocation ? QBX_ERR_OOM : QBX_ERR_CUDA,
+                           "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes: " + cudaGetErrorString(e)};
+    }
     return static_cast<T *>(p);
 }
 
@@ -118,6 +123,8 @@ void build_lists(qbx_lists *L, cudaStream_t st);
 void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
           const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *pot, cudaStream_t st);
 void free_workspace(qbx_workspace *ws);
+void eval_order_sweep(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
+                      const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *partial, cudaStream_t st);
 void exclusive_scan(const int *in, int *out, int64_t n, int base_offset, int *total_dev, cudaStream_t st);
 void sort_pairs_by_key(int *keys, int *vals, int64_t n, int key_bits, cudaStream_t st);
 }  // namespace qbx

@@ -30,6 +30,6 @@ def test_library_exports_every_declared_symbol():
     from paper_1805_06106_gb300 import build
 
     path = build.build()
-    lib = ctypes.CDLL(path)
+    lib = ctypes.CDLL(path, mode=os.RTLD_NOW)  # every symbol the library needs resolves at load
     missing = [n for n in sorted(_declared()) if not hasattr(lib, n)]
     assert not missing, missing
