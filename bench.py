@@ -33,7 +33,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QBX target evals/s at 1e-6 rel err: learned+mixed vs plain FP64 GIGAQBX"
 P_QBX, P_FMM, T_F = 7, 15, 0.9
-N_MAX = 256           # chosen by the n_max sweep recorded in profiles/ (same value for every precision mode)
+N_MAX = 256           # leaf size of plain FP64 (best of the n_max sweep in profiles/)
+N_MAX_MIXED = 64      # leaf size of the mixed-precision mode (best of the same sweep)
 N_VOLUME = 10000
 FP64_PEAK_TFLOPS = 1.258  # 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (1.25 TFLOP/s nominal)
 L2_FLUSH_BYTES = 512 << 20
@@ -215,7 +216,7 @@ def cpu_oracle_sample(n_sub=3):
     s = make_surface(n_sub, star_radius(STAR_Y63))
     u, dudn = greens_density(s)
     t0 = time.perf_counter()
-    T = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, s.tgt_xyz, n_max=N_MAX, t_f=T_F)
+    T = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, s.tgt_xyz, n_max=N_MAX_MIXED, t_f=T_F)
     L = O.build_lists(T)
     t1 = time.perf_counter()
     O.fmm_eval(T, L, s.src_xyz, s.src_w, dudn, -u, s.src_n, s.ctr_xyz, s.tgt_xyz, s.tgt_ctr, P_QBX, P_FMM)
@@ -223,7 +224,7 @@ def cpu_oracle_sample(n_sub=3):
     n = s.n_ctr
     return {"value": n / (t2 - t1), "unit": "QBX target evals/s", "cores": 1, "kind": "oracle",
             "sample": f"serial FP64 oracle Algorithm 4 (Stages 2-9) on the same star family at {s.n_elem} elements "
-                      f"({s.n_src} sources, {n} QBX targets), p_qbx={P_QBX}, p_fmm={P_FMM}, n_max={N_MAX}; "
+                      f"({s.n_src} sources, {n} QBX targets), p_qbx={P_QBX}, p_fmm={P_FMM}, n_max={N_MAX_MIXED}; "
                       f"{t2 - t1:.1f} s eval + {t1 - t0:.2f} s tree/lists"}
 
 
@@ -233,7 +234,7 @@ def run_reference(args):
         return
     vals = []
     for _ in range(args.warmup):
-        cpu_oracle_sample(2)
+        cpu_oracle_sample(1)  # untimed warm-up on the smallest member of the family
     for _ in range(args.steps):
         vals.append(cpu_oracle_sample(2))
     v = statistics.median([x["value"] for x in vals])
@@ -243,13 +244,70 @@ def run_reference(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "star r=1+0.3ReY63, 80 curved triangles x 15 nodes (oracle sample of configs[1])",
-                       "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": N_MAX, "t_f": T_F},
+                       "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": N_MAX_MIXED, "t_f": T_F},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "QBX target evals/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 # ------------------------------------------------------------------ GPU arm
+
+
+def _measure(G, torch, dev, stream, geo, ev_in, n_out, n_max, prec, steps, warmup, want_clock, local,
+             orders=None, rank_sync=None):
+    """Build tree and lists for n_max, warm up, then time `steps` evaluations (CUDA events on the
+    launching stream, L2 flushed between steps).  Returns timings, stage times and the result."""
+    torch.cuda.synchronize()
+    tb0 = time.perf_counter()
+    T = G.qbx_build_tree(*geo, n_max=n_max, t_f=T_F)
+    torch.cuda.synchronize()
+    tb1 = time.perf_counter()
+    L = G.qbx_build_lists(T)
+    torch.cuda.synchronize()
+    tb2 = time.perf_counter()
+    pot = torch.empty(n_out, dtype=torch.float64, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    kw = dict(out=pot, precision=prec)
+    if orders is not None:
+        kw.update(orders(T, L))
+
+    def step(inputs):
+        G.qbx_eval(T, L, *inputs, P_QBX, P_FMM, **kw)
+
+    L.profile(True)
+    for _ in range(max(warmup, 3)):
+        step(ev_in)
+    torch.cuda.synchronize()
+    ref = pot.clone()
+    stage_tot = {k: 0.0 for k in G.STAGE_NAMES}
+    step_ms = []
+    if rank_sync:
+        rank_sync()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local) if want_clock else None
+    if clk:
+        clk.__enter__()
+    try:
+        for _ in range(steps):
+            flush.fill_(1)  # L2 flush between timed iterations (outside the timed events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            step(ev_in)
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            for k, v in L.stage_ms().items():
+                stage_tot[k] += v
+    finally:
+        if clk:
+            clk.__exit__(None, None, None)
+    torch.cuda.synchronize()
+    det = bool(torch.equal(pot, ref))
+    L.profile(False)
+    return dict(T=T, L=L, pot=ref, step_ms=step_ms, stage_ms={k: v / steps for k, v in stage_tot.items()},
+                det=det, clk=clk, step=step, flush=flush, pot_buf=pot, tree_ms=1e3 * (tb1 - tb0),
+                lists_ms=1e3 * (tb2 - tb1))
 
 
 def run_gpu(args):
@@ -271,65 +329,31 @@ def run_gpu(args):
     def cu(a, dt=torch.float64):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
 
+    precs = {"fp64": G.QBX_FP64, "fp32": G.QBX_M2L_FP32}
+    mode = args.precision
+    n_max = args.n_max if args.n_max else (N_MAX_MIXED if mode != "fp64" else N_MAX)
+    sync = (lambda: torch.distributed.barrier()) if ws > 1 else None
+
+    def max_over_ranks(x):
+        if ws == 1:
+            return x
+        tt = torch.tensor([x], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        return float(tt.item())
+
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         geo = [cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(t)]
-        torch.cuda.synchronize()
-        tb0 = time.perf_counter()
-        T = G.qbx_build_tree(*geo, n_max=args.n_max, t_f=T_F)
-        torch.cuda.synchronize()
-        tb1 = time.perf_counter()
-        L = G.qbx_build_lists(T)
-        torch.cuda.synchronize()
-        tb2 = time.perf_counter()
         ev_in = (cu(s.src_w), cu(dudn), cu(-u), cu(s.src_n), cu(tc, torch.int32))
-        pot = torch.empty(t.shape[1], dtype=torch.float64, device=dev)
-        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-
-        prec = {"fp64": G.QBX_FP64, "fp32": G.QBX_M2L_FP32}[args.precision]
-
-        def step():
-            G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM, out=pot, precision=prec)
-
-        L.profile(True)
-        for _ in range(max(args.warmup, 3)):
-            step()
-        torch.cuda.synchronize()
-        ref_pot = pot.clone()
-
-        stage_tot = {k: 0.0 for k in G.STAGE_NAMES}
-        step_ms = []
-        if ws > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-        with ClockSampler(local) as clk:
-            for _ in range(args.steps):
-                flush.fill_(1)  # L2 flush between timed iterations (outside the timed events)
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-                step()
-                e1.record(stream)
-                e1.synchronize()
-                step_ms.append(e0.elapsed_time(e1))
-                for k, v in L.stage_ms().items():
-                    stage_tot[k] += v
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-        total_ms = float(sum(step_ms))
-        if ws > 1:
-            tt = torch.tensor([total_ms], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            total_ms = float(tt.item())
+        main = _measure(G, torch, dev, stream, geo, ev_in, t.shape[1], n_max, precs[mode], args.steps, args.warmup,
+                        True, local, rank_sync=sync)
+        total_ms = max_over_ranks(float(sum(main["step_ms"])))
         ms_per_step = total_ms / args.steps
         value = ws * n_qbx_tgt * args.steps / (total_ms * 1e-3)
-        determinism = bool(torch.equal(pot, ref_pot))
 
         # end to end through the public API: pinned host inputs in, potentials out
-        L.profile(False)
         host_in = [x.cpu().pin_memory() for x in ev_in]
-        host_out = torch.empty_like(pot, device="cpu").pin_memory()
+        host_out = torch.empty(t.shape[1], dtype=torch.float64).pin_memory()
         dev_in = [torch.empty_like(x) for x in ev_in]
         h2d = sum(x.numel() * x.element_size() for x in host_in)
         d2h = host_out.numel() * host_out.element_size()
@@ -337,63 +361,83 @@ def run_gpu(args):
         torch.cuda.synchronize()
         e2e_ms = []
         for _ in range(n_e2e):
-            flush.fill_(1)
+            main["flush"].fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for d, h in zip(dev_in, host_in):
                 d.copy_(h, non_blocking=True)
-            G.qbx_eval(T, L, *dev_in, P_QBX, P_FMM, out=pot, precision=prec)
-            host_out.copy_(pot, non_blocking=True)
+            main["step"](dev_in)
+            host_out.copy_(main["pot_buf"], non_blocking=True)
             e1.record(stream)
             e1.synchronize()
             e2e_ms.append(e0.elapsed_time(e1))
-        e2e_total = float(sum(e2e_ms))
-        if ws > 1:
-            tt = torch.tensor([e2e_total], device=dev)
-            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-            e2e_total = float(tt.item())
-        e2e_value = ws * n_qbx_tgt * n_e2e / (e2e_total * 1e-3)
-        e2e_ok = bool(torch.allclose(host_out.to(dev), ref_pot, rtol=0, atol=0))
+        e2e_value = ws * n_qbx_tgt * n_e2e / (max_over_ranks(float(sum(e2e_ms))) * 1e-3)
+        e2e_ok = bool(torch.equal(host_out.to(dev), main["pot"]))
+
+        plain = None
+        err_vs_fp64 = None
+        if mode != "fp64" and not args.no_fp64_baseline:
+            # accuracy of the mixed result against FP64 on the same tree and lists (untimed)
+            T, L = main["T"], main["L"]
+            ref64 = G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM)
+            err_vs_fp64 = float((main["pot"] - ref64).abs().max() / ref64.abs().max())
+            # plain FP64 GIGAQBX at its own tuned leaf size, timed the same way
+            base = _measure(G, torch, dev, stream, geo, ev_in, t.shape[1], N_MAX, G.QBX_FP64, args.fp64_steps,
+                            args.warmup, False, local, rank_sync=sync)
+            b_total = max_over_ranks(float(sum(base["step_ms"])))
+            plain = {"value": ws * n_qbx_tgt * args.fp64_steps / (b_total * 1e-3), "ms_per_step": b_total / args.fp64_steps,
+                     "n_max": N_MAX, "steps": args.fp64_steps, "stage_ms": base["stage_ms"]}
 
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
         return
 
+    T, L = main["T"], main["L"]
     n_direct, n_wfar, modeled = list_work(G, T, L)
-    flops, f_pair = center_kernel_flops(P_FMM, P_QBX, n_direct, n_wfar, T.info.n_ctr)
-    centers_ms = stage_tot["centers"] / args.steps
+    flops, f_pair = center_kernel_flops(P_FMM, P_QBX, n_direct, 0 if mode != "fp64" else n_wfar, T.info.n_ctr)
+    centers_ms = main["stage_ms"]["centers"]
     achieved = flops / (centers_ms * 1e-3) / 1e12
     nlev = int(T.info.n_levels)
     launches = 3 + 1 + (nlev - 1) + 1 + 1 + (nlev - 1) + 3  # prep, P2M, M2M, M2L, P2L, L2L, centers/targets
-    traffic = kernel_traffic()
+    if mode != "fp64":
+        launches += 2 + 2 + 1  # mixed M2L (convert, GEMM, reduce counted as M2L + 2), M2QBXL (H, GEMM), reduce
     line = {
         "metric": METRIC, "value": value, "unit": "QBX target evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "vs_baseline": None,
+        "dtype": "f64" if mode == "fp64" else "f64 (List 2 M2L and List 3 far M2QBXL products in f32)",
+        "data": "synthetic",
         "config": {"workload": f"star r=1+0.3ReY63, {s.n_elem} curved triangles x 15 nodes: S[d_n u] - D[u] at "
                                f"{s.n_ctr} on-surface QBX targets + {N_VOLUME} volume points",
-                   "mode": f"{args.precision} List 2 M2L, fixed orders", "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": args.n_max,
-                   "t_f": T_F, "n_src": int(s.n_src), "n_ctr": int(s.n_ctr), "n_qbx_targets": n_qbx_tgt,
-                   "n_point_targets": n_pt_tgt, "n_flagged": int(vflag.sum()), "n_boxes": int(T.n_boxes),
-                   "n_levels": nlev, "l2": "flushed between timed steps (512 MiB write)",
+                   "mode": {"fp64": "plain FP64 GIGAQBX", "fp32": "mixed precision (FP32 translation products)"}[mode]
+                           + ", fixed orders",
+                   "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": n_max, "t_f": T_F, "n_src": int(s.n_src),
+                   "n_ctr": int(s.n_ctr), "n_qbx_targets": n_qbx_tgt, "n_point_targets": n_pt_tgt,
+                   "n_flagged": int(vflag.sum()), "n_boxes": int(T.n_boxes), "n_levels": nlev,
+                   "l2": "flushed between timed steps (512 MiB write)",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
-                   "tree_build_ms": 1e3 * (tb1 - tb0), "lists_build_ms": 1e3 * (tb2 - tb1)},
-        "stage_ms": {k: v / args.steps for k, v in stage_tot.items()},
+                   "tree_build_ms": main["tree_ms"], "lists_build_ms": main["lists_ms"]},
+        "stage_ms": main["stage_ms"],
         "modeled_ops": modeled,
-        "deterministic": determinism,
+        "deterministic": main["det"],
         "e2e": {"value": e2e_value, "unit": "QBX target evals/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "matches_device_result": e2e_ok},
         "gpu_launches": launches * args.steps,
-        "roofline": {"kernel": "k_centers (L2QBXL + List 3 far M2QBXL + direct P2QBXL, FP64)", "bound": "alu",
+        "roofline": {"kernel": "k_centers (L2QBXL + direct P2QBXL" + (", List 3 far M2QBXL" if mode == "fp64" else "")
+                               + ", FP64)", "bound": "alu",
                      "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                     "frac": achieved / FP64_PEAK_TFLOPS, "traffic": kernel_traffic(),
                      "flops_per_launch": flops, "flops_per_direct_pair": f_pair, "direct_pairs": n_direct,
                      "wfar_pairs": n_wfar, "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 x 2.07 GHz "
                                                           "(nominal 1.25 TFLOP/s; 1.195 measured by an FMA-chain probe)"},
-        "clocks": clk.summary(),
+        "clocks": main["clk"].summary(),
     }
+    if plain is not None:
+        line["plain_fp64"] = plain
+        line["speedup_vs_plain_fp64"] = value / plain["value"]
+        line["rel_err_vs_fp64_same_tree"] = err_vs_fp64
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample()
     print(json.dumps(line), flush=True)
@@ -409,9 +453,11 @@ def main():
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-sub", type=int, default=20, help="icosahedron face subdivision (20 = 8,000 elements)")
-    ap.add_argument("--n-max", type=int, default=N_MAX, help="particles per leaf before a box splits")
-    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64",
-                    help="fp64: every stage FP64; fp32: List 2 M2L as FP32 per-offset products")
+    ap.add_argument("--n-max", type=int, default=0, help="particles per leaf before a box splits (0: tuned value)")
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp32",
+                    help="fp64: every stage FP64; fp32: List 2 M2L and List 3 far M2QBXL as FP32 products")
+    ap.add_argument("--fp64-steps", type=int, default=5, help="timed steps of the plain FP64 comparison")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

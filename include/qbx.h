@@ -120,10 +120,10 @@ int qbx_lists_export(const qbx_lists *lists, int which, int32_t *start_dev, int3
 void qbx_lists_free(qbx_lists *lists);
 
 typedef struct {
-    int p_qbx;                    /* QBX order, 0 <= p_qbx <= 16 (ignored where p_qbx_per_ctr is given) */
-    int p_fmm;                    /* FMM order, 0 <= p_fmm <= 20 (ignored where p_fmm_per_box is given) */
-    const int8_t *p_qbx_per_ctr;  /* optional device array [n_ctr], per-center QBX order */
-    const int8_t *p_fmm_per_box;  /* optional device array [n_boxes], per-box FMM order */
+    int p_qbx;                    /* QBX order, 0 <= p_qbx <= 16; with p_qbx_per_ctr: the largest entry allowed */
+    int p_fmm;                    /* FMM order, 0 <= p_fmm <= 20; with p_fmm_per_box: the largest entry allowed */
+    const int8_t *p_qbx_per_ctr;  /* optional device array [n_ctr], per-center QBX order in [0, p_qbx] */
+    const int8_t *p_fmm_per_box;  /* optional device array [n_boxes], per-box FMM order in [0, p_fmm] */
     int precision;                /* QBX_FP64, QBX_M2L_FP32 or QBX_M2L_3XTF32 */
 } qbx_eval_opts;
 
@@ -168,6 +168,68 @@ int qbx_eval_order_sweep(const qbx_tree *tree, const qbx_lists *lists, const dou
                          const double *sigma_dev, const double *mu_dev, const double *src_n_dev,
                          const int32_t *tgt_ctr_dev, const qbx_eval_opts *opts, double *partial_dev, void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Learned expansion orders.  Not in the paper: a small network picks per-center QBX orders and
+ * per-box FMM orders that the fixed-order evaluation (its judge and fallback) would accept
+ * within a tolerance.  Training data are order sweeps of the method itself
+ * (qbx_eval_order_sweep and qbx_eval at several p_fmm); the network is trained by the kernels
+ * below.  All pointers are device pointers unless marked _host.
+ * ------------------------------------------------------------------------------------------ */
+
+/* Number of floats of the network's parameter vector: W1[64][4], b1[64], W2[64][64], b2[64],
+ * W3[2][64], b3[2] (4 -> 64 -> 64 -> 2, tanh hidden layers, linear output). */
+#define QBX_MLP_NPARAMS 4610
+
+/*
+ * Four features per QBX center, written to feat[4*c..4*c+3] in input center order:
+ * log2(r_c/|b|), level(b)/8, log2 of the smallest |c - c_d|/|d| over the List 3 far boxes d of b
+ * (log2 16 if none), log10 of the largest source strength |w sigma| + |w mu n| in List 1 of b
+ * relative to the largest over all sources (+1e-12); b is the box owning c.  Densities as in
+ * qbx_eval.  Errors: QBX_ERR_INVALID_ARG, QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_center_features(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev,
+                        const double *sigma_dev, const double *mu_dev, const double *src_n_dev, float *feat_dev,
+                        void *stream);
+
+/*
+ * Order labels from a sweep: values[k*n + t] holds target t's result at the k-th order of the
+ * sweep (increasing orders order_of_host[k], the last one the reference).  labels[t] =
+ * order_of_host[k*] for the smallest k* such that every column k >= k* is within tol of the
+ * reference (absolute).  n_orders <= 64.
+ */
+int qbx_order_labels(const double *values_dev, int n_orders, const int *order_of_host, int64_t n, double tol,
+                     int8_t *labels_dev, void *stream);
+
+/* Deterministic initialisation (uniform Glorot, SplitMix64 of (seed, index); zero biases). */
+int qbx_mlp_init(float *params_dev, uint64_t seed, void *stream);
+
+/* y[2*i..2*i+1] = network(x[4*i..4*i+3]) for i < n. */
+int qbx_mlp_forward(const float *params_dev, const float *x_dev, int64_t n, float *y_dev, void *stream);
+
+/* Gradient of L = 1/(2n) sum_i |network(x_i) - target_i|^2 into grad[0..QBX_MLP_NPARAMS), and L into
+ * grad[QBX_MLP_NPARAMS] (grad holds QBX_MLP_NPARAMS + 1 floats).  Summed in a fixed order. */
+int qbx_mlp_loss_grad(const float *params_dev, const float *x_dev, const float *target_dev, int64_t n,
+                      float *grad_dev, void *stream);
+
+/* `steps` full-batch Adam steps (beta 0.9/0.999, eps 1e-8, step counter starting at first_step >= 1)
+ * on params with moment buffers adam_m, adam_v (QBX_MLP_NPARAMS floats each, caller-owned, zero
+ * before the first step).  If loss_host is given it receives the loss after the last step. */
+int qbx_mlp_train(float *params_dev, float *adam_m_dev, float *adam_v_dev, const float *x_dev,
+                  const float *target_dev, int64_t n, int steps, int first_step, float lr, float *loss_host,
+                  void *stream);
+
+/*
+ * Orders from predictions pred[2*c..2*c+1] (input center order): p_qbx of center c =
+ * clamp(ceil(pred0 + margin_q), q_lo, q_hi); p_fmm of box b = the largest clamp(ceil(pred1 +
+ * margin_p), p_lo, p_hi) over the centers of b's subtree, then the largest such value over b
+ * and the boxes of b's six interaction lists (a box's order also truncates the expansions it
+ * sends); p_default where no center contributes.  Outputs are the per-center and per-box
+ * arrays qbx_eval_opts takes.
+ */
+int qbx_orders_from_mlp(const qbx_tree *tree, const qbx_lists *lists, const float *pred_dev, float margin_q,
+                        float margin_p, int q_lo, int q_hi, int p_lo, int p_hi, int p_default,
+                        int8_t *p_qbx_per_ctr_dev, int8_t *p_fmm_per_box_dev, void *stream);
+
 /*
  * Per-stage timing (tracing aid; not a step of the paper's method).  While enabled,
  * every qbx_eval on these lists records CUDA events on its stream around each of
@@ -192,7 +254,7 @@ int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
  *   Scratch: one file-scope device array of QBX_NOALLOC_SCRATCH_BYTES (48 MiB) inside
  *   the library, held by every GPU that loads the library until the process exits.
  *   The problem must fit: about 18.4 MB of tables + 7,392 B per box + 16 ntri(Qb) B per
- *   center (Qb = 4, 8, 12 or 16, the smallest >= p_qbx; 16 with per-center orders)
+ *   center (Qb = 4, 8, 12 or 16, the smallest >= p_qbx)
  *   + 33 B per source; e.g. 2,000 boxes and 20,000 centers at p_qbx <= 8.  A larger
  *   problem returns QBX_ERR_INVALID_ARG with the byte counts in qbx_last_error().
  *   No call allocates: no cudaMalloc, cudaFree or allocating library routine.

@@ -69,6 +69,7 @@ def lib():
         L.orc_fmm_eval.argtypes = [P, P, P, i, P, P, P, P, P, i, P, P, i, i, i, P, P, P, P, i]
         L.orc_direct_eval.argtypes = [P, i, P, P, P, P, P, i, P, P, i, i, P, P]
         L.orc_lists_cost.argtypes = [P, P, i, i, P]
+        L.orc_mlp_loss_grad.argtypes = [P, P, P, i, P]
         _lib = L
     return _lib
 
@@ -252,3 +253,16 @@ def direct_eval(src_xyz, src_w, sigma, mu, src_n, ctr_xyz, tgt_xyz, tgt_ctr, p_q
     lib().orc_direct_eval(_p(s), s.shape[1], _p(w), _p(sg), _p(m_), _p(n_), _p(c), c.shape[1], _p(t), _p(tc),
                           t.shape[1], p_qbx, _p(qc), _p(pot))
     return pot
+
+
+# ---------------------------------------------------------------- learned-order network
+
+
+def mlp_loss_grad(params, x, target):
+    """Gradient (4610 values) and loss of the 4-64-64-2 tanh network, FP64 chain rule."""
+    p = np.ascontiguousarray(params, np.float32)
+    xx = np.ascontiguousarray(x, np.float32)
+    tt = np.ascontiguousarray(target, np.float32)
+    out = np.zeros(p.size + 1)
+    lib().orc_mlp_loss_grad(_p(p), _p(xx), _p(tt), xx.shape[0], _p(out))
+    return out[:-1], out[-1]

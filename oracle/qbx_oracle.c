@@ -1340,3 +1340,65 @@ void orc_lists_cost(const otree *T, const olists *Ls, int p_qbx, int p_fmm, doub
             }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* reference for the learned-order network (not part of the paper's method)   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Network 4 -> 64 -> 64 -> 2 with tanh hidden layers and a linear output; parameters (float)
+ * W1[64][4], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].  Loss L = 1/(2n) sum_i |y_i - t_i|^2.
+ * Forward pass and gradient by the chain rule, in double precision, sample by sample.
+ * grad receives dL/dparams (4610 doubles) followed by L.
+ */
+int orc_mlp_loss_grad(const float *P, const float *x, const float *t, int n, double *grad)
+{
+    enum { NI = 4, A = 64, B = 64, NO = 2 };
+    const int oW1 = 0, ob1 = oW1 + A * NI, oW2 = ob1 + A, ob2 = oW2 + B * A, oW3 = ob2 + B, ob3 = oW3 + NO * B,
+              np = ob3 + NO;
+    for (int i = 0; i <= np; ++i) grad[i] = 0.0;
+    for (int s = 0; s < n; ++s) {
+        double h1[A], h2[B], y[NO], dy[NO], d2[B], d1[A];
+        for (int j = 0; j < A; ++j) {
+            double a = P[ob1 + j];
+            for (int k = 0; k < NI; ++k) a += (double)P[oW1 + j * NI + k] * x[NI * s + k];
+            h1[j] = tanh(a);
+        }
+        for (int j = 0; j < B; ++j) {
+            double a = P[ob2 + j];
+            for (int k = 0; k < A; ++k) a += (double)P[oW2 + j * A + k] * h1[k];
+            h2[j] = tanh(a);
+        }
+        for (int o = 0; o < NO; ++o) {
+            double a = P[ob3 + o];
+            for (int k = 0; k < B; ++k) a += (double)P[oW3 + o * B + k] * h2[k];
+            y[o] = a;
+            double r = y[o] - t[NO * s + o];
+            dy[o] = r / n;
+            grad[np] += 0.5 * r * r / n;
+        }
+        for (int j = 0; j < B; ++j) {
+            double g = 0.0;
+            for (int o = 0; o < NO; ++o) g += (double)P[oW3 + o * B + j] * dy[o];
+            d2[j] = g * (1.0 - h2[j] * h2[j]);
+        }
+        for (int k = 0; k < A; ++k) {
+            double g = 0.0;
+            for (int j = 0; j < B; ++j) g += (double)P[oW2 + j * A + k] * d2[j];
+            d1[k] = g * (1.0 - h1[k] * h1[k]);
+        }
+        for (int j = 0; j < A; ++j) {
+            for (int k = 0; k < NI; ++k) grad[oW1 + j * NI + k] += d1[j] * x[NI * s + k];
+            grad[ob1 + j] += d1[j];
+        }
+        for (int j = 0; j < B; ++j) {
+            for (int k = 0; k < A; ++k) grad[oW2 + j * A + k] += d2[j] * h1[k];
+            grad[ob2 + j] += d2[j];
+        }
+        for (int o = 0; o < NO; ++o) {
+            for (int k = 0; k < B; ++k) grad[oW3 + o * B + k] += dy[o] * h2[k];
+            grad[ob3 + o] += dy[o];
+        }
+    }
+    return 0;
+}

@@ -19,4 +19,12 @@ from .binding import (  # noqa: F401
     qbx_eval,
     qbx_eval_noalloc,
     qbx_eval_order_sweep,
+    MLP_NPARAMS,
+    qbx_center_features,
+    qbx_order_labels,
+    qbx_mlp_init,
+    qbx_mlp_forward,
+    qbx_mlp_loss_grad,
+    qbx_mlp_train,
+    qbx_orders_from_mlp,
 )

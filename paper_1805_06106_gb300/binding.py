@@ -63,6 +63,14 @@ def lib():
         L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_eval_noalloc.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_eval_order_sweep.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
+        L.qbx_center_features.argtypes = [P, P, P, P, P, P, P, P]
+        L.qbx_order_labels.argtypes = [P, C.c_int, P, I64, C.c_double, P, P]
+        L.qbx_mlp_init.argtypes = [P, C.c_uint64, P]
+        L.qbx_mlp_forward.argtypes = [P, P, I64, P, P]
+        L.qbx_mlp_loss_grad.argtypes = [P, P, P, I64, P, P]
+        L.qbx_mlp_train.argtypes = [P, P, P, P, P, I64, C.c_int, C.c_int, C.c_float, P, P]
+        L.qbx_orders_from_mlp.argtypes = [P, P, P, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                          P, P, P]
         L.qbx_profile.argtypes = [P, C.c_int]
         L.qbx_profile_read.argtypes = [P, P]
         L.qbx_last_error.restype = C.c_char_p
@@ -220,6 +228,69 @@ def qbx_eval_order_sweep(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_
     _check(lib().qbx_eval_order_sweep(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc),
                                       C.byref(opts), _ptr(out), _stream()))
     return out
+
+
+# ---------------------------------------------------------------- learned orders
+
+MLP_NPARAMS = 4610
+
+
+def qbx_center_features(tree: Tree, lists: Lists, src_w, sigma, mu, src_n):
+    """(n_ctr, 4) float32 features per center (input order)."""
+    w = _dev(src_w, torch.float64)
+    sg, m, n = _dev(sigma, torch.float64), _dev(mu, torch.float64), _dev(src_n, torch.float64)
+    out = torch.empty((tree.info.n_ctr, 4), dtype=torch.float32, device="cuda")
+    _check(lib().qbx_center_features(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(out),
+                                     _stream()))
+    return out
+
+
+def qbx_order_labels(values, orders, tol):
+    """values (K, n) float64 results at increasing orders (last = reference) -> (n,) int8 labels."""
+    v = _dev(values.contiguous(), torch.float64)
+    arr = (C.c_int * len(orders))(*orders)
+    out = torch.empty(v.shape[1], dtype=torch.int8, device=v.device)
+    _check(lib().qbx_order_labels(_ptr(v), len(orders), arr, v.shape[1], float(tol), _ptr(out), _stream()))
+    return out
+
+
+def qbx_mlp_init(seed=0):
+    p = torch.empty(MLP_NPARAMS, dtype=torch.float32, device="cuda")
+    _check(lib().qbx_mlp_init(_ptr(p), int(seed), _stream()))
+    return p
+
+
+def qbx_mlp_forward(params, x):
+    x = _dev(x.contiguous(), torch.float32)
+    y = torch.empty((x.shape[0], 2), dtype=torch.float32, device=x.device)
+    _check(lib().qbx_mlp_forward(_ptr(_dev(params, torch.float32)), _ptr(x), x.shape[0], _ptr(y), _stream()))
+    return y
+
+
+def qbx_mlp_loss_grad(params, x, target):
+    g = torch.empty(MLP_NPARAMS + 1, dtype=torch.float32, device="cuda")
+    _check(lib().qbx_mlp_loss_grad(_ptr(_dev(params, torch.float32)), _ptr(_dev(x.contiguous(), torch.float32)),
+                                   _ptr(_dev(target.contiguous(), torch.float32)), x.shape[0], _ptr(g), _stream()))
+    return g[:-1], float(g[-1])
+
+
+def qbx_mlp_train(params, adam_m, adam_v, x, target, steps, first_step, lr):
+    loss = C.c_float()
+    _check(lib().qbx_mlp_train(_ptr(_dev(params, torch.float32)), _ptr(_dev(adam_m, torch.float32)),
+                               _ptr(_dev(adam_v, torch.float32)), _ptr(_dev(x.contiguous(), torch.float32)),
+                               _ptr(_dev(target.contiguous(), torch.float32)), x.shape[0], steps, first_step,
+                               float(lr), C.byref(loss), _stream()))
+    return loss.value
+
+
+def qbx_orders_from_mlp(tree: Tree, lists: Lists, pred, margin_q, margin_p, q_lo, q_hi, p_lo, p_hi, p_default):
+    qc = torch.empty(tree.info.n_ctr, dtype=torch.int8, device="cuda")
+    pb = torch.empty(tree.n_boxes, dtype=torch.int8, device="cuda")
+    _check(lib().qbx_orders_from_mlp(tree.handle, lists.handle, _ptr(_dev(pred.contiguous(), torch.float32)),
+                                     float(margin_q),
+                                     float(margin_p), q_lo, q_hi, p_lo, p_hi, p_default, _ptr(qc), _ptr(pb),
+                                     _stream()))
+    return qc, pb
 
 
 def library_path() -> str:

@@ -115,19 +115,27 @@ __global__ void k_prep_src(const int *perm, int64_t ns, const double *w, const d
     if (bad) atomicOr(flags, 1);
 }
 
+void prep_sources(const int *perm, int64_t ns, const double *w, const double *sigma, const double *mu,
+                  const double *nrm, double *sq, double *sd, int *flags, cudaStream_t st)
+{
+    k_prep_src<<<nblocks(ns, 256), 256, 0, st>>>(perm, ns, w, sigma, mu, nrm, sq, sd, flags);
+    QBX_LAUNCH_CHECK();
+}
+
+// qfix / pfix are the fixed orders, or the bounds of the per-center / per-box arrays
 __global__ void k_prep_orders(const int *ctr_perm, int64_t nc, const signed char *qin, int qfix, int64_t nb,
                               const signed char *pin, int pfix, signed char *qc, signed char *pb, int *flags)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nc) {
         int q = qin ? qin[ctr_perm[i]] : qfix;
-        if (q < 0 || q > QMAX) atomicOr(flags, 2);
-        qc[i] = (signed char)min(max(q, 0), QMAX);  // clamped so that no kernel indexes past its tables
+        if (q < 0 || q > qfix) atomicOr(flags, 2);
+        qc[i] = (signed char)min(max(q, 0), qfix);  // clamped so that no kernel indexes past its tables
     }
     if (i < nb) {
         int p = pin ? pin[i] : pfix;
-        if (p < 0 || p > PMAX) atomicOr(flags, 2);
-        pb[i] = (signed char)min(max(p, 0), PMAX);
+        if (p < 0 || p > pfix) atomicOr(flags, 2);
+        pb[i] = (signed char)min(max(p, 0), pfix);
     }
 }
 
@@ -833,9 +841,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
 {
     const int64_t nb = T->nb, ns = T->np[KSRC], nc = T->np[KCTR], nt = T->np[KTGT];
     // orders: compile-time bucket for the QBX order, runtime orders per center / box
-    int qmax = o->p_qbx, pmax = o->p_fmm;
-    if (o->p_qbx_per_ctr) qmax = QMAX;
-    if (o->p_fmm_per_box) pmax = PMAX;
+    const int qmax = o->p_qbx, pmax = o->p_fmm;  // fixed orders, or bounds of the per-center / per-box arrays
     int QM = 0;
     for (int qb : QB)
         if (qmax <= qb) { QM = qb; break; }
@@ -901,7 +907,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
                                                               ws->Mu, ws->m2l_tab, ws->B);
         QBX_LAUNCH_CHECK();
     } else {
-        const int Pm = o->p_fmm_per_box ? PMAX : o->p_fmm;
+        const int Pm = o->p_fmm;
         if (!ws->m2l || m2l_plan_order(ws->m2l) != Pm) {
             free_m2l_plan(ws->m2l);
             ws->m2l = nullptr;
@@ -926,7 +932,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     stage_mark(L, 5, st);
     WfarPlan *wf = nullptr;
     if (o->precision != QBX_FP64 && T->np[KCTR] > 0) {
-        const int Pm = o->p_fmm_per_box ? PMAX : o->p_fmm, Qm = o->p_qbx_per_ctr ? QM : o->p_qbx;
+        const int Pm = o->p_fmm, Qm = o->p_qbx;
         if (!ws->wfar || wfar_plan_orders(ws->wfar) != Pm * 100 + Qm) {
             free_wfar_plan(ws->wfar);
             ws->wfar = nullptr;
@@ -1049,7 +1055,7 @@ static size_t carve(size_t &off, size_t bytes)
 
 static int fixed_qbucket(const qbx_eval_opts *o)
 {
-    int qmax = o->p_qbx_per_ctr ? QMAX : o->p_qbx;
+    int qmax = o->p_qbx;
     for (int qb : QB)
         if (qmax <= qb) return qb;
     return 16;

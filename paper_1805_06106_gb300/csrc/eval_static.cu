@@ -57,10 +57,8 @@ extern "C" int qbx_eval_noalloc(const qbx_tree *T, const qbx_lists *L, const dou
         if (mu && !nrm) throw qbx::Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
         if (T->np[2] && (!tgt_ctr || !pot)) throw qbx::Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
         if (o->precision != QBX_FP64) throw qbx::Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
-        if (!o->p_qbx_per_ctr && (o->p_qbx < 0 || o->p_qbx > qbx::QMAX))
-            throw qbx::Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
-        if (!o->p_fmm_per_box && (o->p_fmm < 0 || o->p_fmm > qbx::PMAX))
-            throw qbx::Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
+        if (o->p_qbx < 0 || o->p_qbx > qbx::QMAX) throw qbx::Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
+        if (o->p_fmm < 0 || o->p_fmm > qbx::PMAX) throw qbx::Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
         if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
             throw qbx::Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
         size_t need = qbx::fixed_workspace_bytes(T, o);

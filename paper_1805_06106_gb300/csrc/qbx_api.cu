@@ -185,10 +185,8 @@ int qbx_eval(const qbx_tree *T, const qbx_lists *L, const double *w, const doubl
         if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
         if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32)
             throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
-        if (!o->p_qbx_per_ctr && (o->p_qbx < 0 || o->p_qbx > QMAX))
-            throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
-        if (!o->p_fmm_per_box && (o->p_fmm < 0 || o->p_fmm > PMAX))
-            throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
+        if (o->p_qbx < 0 || o->p_qbx > QMAX) throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
+        if (o->p_fmm < 0 || o->p_fmm > PMAX) throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
         if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
             throw Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
         eval(T, const_cast<qbx_lists *>(L), w, sigma, mu, nrm, tgt_ctr, o, pot, (cudaStream_t)stream);

@@ -123,6 +123,8 @@ void build_lists(qbx_lists *L, cudaStream_t st);
 void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
           const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *pot, cudaStream_t st);
 void free_workspace(qbx_workspace *ws);
+void prep_sources(const int *perm, int64_t ns, const double *w, const double *sigma, const double *mu,
+                  const double *nrm, double *sq, double *sd, int *flags, cudaStream_t st);
 void eval_order_sweep(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
                       const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *partial, cudaStream_t st);
 void exclusive_scan(const int *in, int *out, int64_t n, int base_offset, int *total_dev, cudaStream_t st);
