@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "QBX target evals/s at 1e-6 rel err: learned+mixed vs plain FP64 GIGAQBX"
 P_QBX, P_FMM, T_F = 7, 15, 0.9
+TOL = 1e-6            # judge: normwise relative l-infinity distance to the fixed-order FP64 result
 N_MAX = 256           # leaf size of plain FP64 (best of the n_max sweep in profiles/)
 N_MAX_MIXED = 64      # leaf size of the mixed-precision mode (best of the same sweep)
 N_VOLUME = 10000
@@ -310,6 +311,30 @@ def _measure(G, torch, dev, stream, geo, ev_in, n_out, n_max, prec, steps, warmu
                 lists_ms=1e3 * (tb2 - tb1))
 
 
+def learned_setup(G, n_max):
+    """Train the order network on sweeps of configs 1-2 geometries (sphere and the Y_6^3 star at
+    small sizes; Re Y_2^1, Green's-formula and random-harmonic densities), calibrate its margins."""
+    from paper_1805_06106_gb300 import learned
+    from synth import greens_density, make_surface, random_harmonic_density, real_ylm, star_radius
+    from synth.surfaces import STAR_Y63
+
+    t0 = time.perf_counter()
+    samples = []
+    for n, shape, seed in ((3, None, 11), (3, STAR_Y63, 12), (4, None, 13), (4, STAR_Y63, 14)):
+        srf = make_surface(n) if shape is None else make_surface(n, star_radius(shape))
+        if shape is None:
+            samples.append(learned.sweep_samples(srf, real_ylm(2, 1, srf.src_xyz), None, P_QBX, P_FMM, n_max, TOL))
+        else:
+            uu, du = greens_density(srf)
+            samples.append(learned.sweep_samples(srf, du, -uu, P_QBX, P_FMM, n_max, TOL))
+        samples.append(learned.sweep_samples(srf, random_harmonic_density(srf, 10, seed), None, P_QBX, P_FMM, n_max,
+                                             TOL))
+    params, losses = learned.train(samples, steps=1000)
+    mq, mp = learned.calibrate(params, samples)
+    return params, (mq, mp), {"train_samples": int(sum(x.x.shape[0] for x in samples)), "final_loss": losses[-1],
+                              "margins": [mq, mp], "setup_s": time.perf_counter() - t0}
+
+
 def run_gpu(args):
     import torch
 
@@ -329,9 +354,26 @@ def run_gpu(args):
     def cu(a, dt=torch.float64):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
 
-    precs = {"fp64": G.QBX_FP64, "fp32": G.QBX_M2L_FP32}
+    precs = {"fp64": G.QBX_FP64, "fp32": G.QBX_M2L_FP32, "learned": G.QBX_M2L_FP32}
     mode = args.precision
     n_max = args.n_max if args.n_max else (N_MAX_MIXED if mode != "fp64" else N_MAX)
+    orders_fn, learned_info = None, None
+    if mode == "learned":
+        from paper_1805_06106_gb300 import learned
+
+        params, (mq, mp), learned_info = learned_setup(G, n_max)
+
+        def orders_fn(T, L):
+            w_, sg_, mu_, n_ = (cu(s.src_w), cu(dudn), cu(-u), cu(s.src_n))
+            qc, pb = learned.predict_orders(T, L, params, w_, sg_, mu_, n_, q_range=(2, P_QBX), p_range=(4, P_FMM),
+                                            margin_q=mq, margin_p=mp, p_default=P_FMM)
+            qn, pn = qc.cpu().numpy().astype(int), pb.cpu().numpy().astype(int)
+            learned_info["mean_p_qbx"] = float(qn.mean())
+            learned_info["mean_p_fmm_box"] = float(pn.mean())
+            learned_info["qbx_order_work_vs_fixed"] = float(np.sum((qn + 1) * (qn + 2)) /
+                                                            (qn.size * (P_QBX + 1) * (P_QBX + 2)))
+            learned_info["fmm_order_work_vs_fixed"] = float(np.sum((pn + 1) ** 3) / (pn.size * (P_FMM + 1) ** 3))
+            return dict(p_qbx_per_ctr=qc, p_fmm_per_box=pb)
     sync = (lambda: torch.distributed.barrier()) if ws > 1 else None
 
     def max_over_ranks(x):
@@ -346,7 +388,7 @@ def run_gpu(args):
         geo = [cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(t)]
         ev_in = (cu(s.src_w), cu(dudn), cu(-u), cu(s.src_n), cu(tc, torch.int32))
         main = _measure(G, torch, dev, stream, geo, ev_in, t.shape[1], n_max, precs[mode], args.steps, args.warmup,
-                        True, local, rank_sync=sync)
+                        True, local, orders=orders_fn, rank_sync=sync)
         total_ms = max_over_ranks(float(sum(main["step_ms"])))
         ms_per_step = total_ms / args.steps
         value = ws * n_qbx_tgt * args.steps / (total_ms * 1e-3)
@@ -382,6 +424,8 @@ def run_gpu(args):
             T, L = main["T"], main["L"]
             ref64 = G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM)
             err_vs_fp64 = float((main["pot"] - ref64).abs().max() / ref64.abs().max())
+            if learned_info is not None:
+                learned_info["judge_passed"] = err_vs_fp64 <= TOL
             # plain FP64 GIGAQBX at its own tuned leaf size, timed the same way
             base = _measure(G, torch, dev, stream, geo, ev_in, t.shape[1], N_MAX, G.QBX_FP64, args.fp64_steps,
                             args.warmup, False, local, rank_sync=sync)
@@ -411,8 +455,9 @@ def run_gpu(args):
         "data": "synthetic",
         "config": {"workload": f"star r=1+0.3ReY63, {s.n_elem} curved triangles x 15 nodes: S[d_n u] - D[u] at "
                                f"{s.n_ctr} on-surface QBX targets + {N_VOLUME} volume points",
-                   "mode": {"fp64": "plain FP64 GIGAQBX", "fp32": "mixed precision (FP32 translation products)"}[mode]
-                           + ", fixed orders",
+                   "mode": {"fp64": "plain FP64 GIGAQBX, fixed orders",
+                            "fp32": "mixed precision (FP32 translation products), fixed orders",
+                            "learned": "learned orders + mixed precision (FP32 translation products)"}[mode],
                    "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": n_max, "t_f": T_F, "n_src": int(s.n_src),
                    "n_ctr": int(s.n_ctr), "n_qbx_targets": n_qbx_tgt, "n_point_targets": n_pt_tgt,
                    "n_flagged": int(vflag.sum()), "n_boxes": int(T.n_boxes), "n_levels": nlev,
@@ -434,6 +479,8 @@ def run_gpu(args):
                                                           "(nominal 1.25 TFLOP/s; 1.195 measured by an FMA-chain probe)"},
         "clocks": main["clk"].summary(),
     }
+    if learned_info is not None:
+        line["learned_orders"] = learned_info
     if plain is not None:
         line["plain_fp64"] = plain
         line["speedup_vs_plain_fp64"] = value / plain["value"]
@@ -454,8 +501,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-sub", type=int, default=20, help="icosahedron face subdivision (20 = 8,000 elements)")
     ap.add_argument("--n-max", type=int, default=0, help="particles per leaf before a box splits (0: tuned value)")
-    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp32",
-                    help="fp64: every stage FP64; fp32: List 2 M2L and List 3 far M2QBXL as FP32 products")
+    ap.add_argument("--precision", choices=("fp64", "fp32", "learned"), default="learned",
+                    help="fp64: every stage FP64; fp32: List 2 M2L and List 3 far M2QBXL as FP32 products; "
+                         "learned: fp32 with per-center / per-box orders from the trained network")
     ap.add_argument("--fp64-steps", type=int, default=5, help="timed steps of the plain FP64 comparison")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     args = ap.parse_args()
