@@ -354,7 +354,8 @@ def run_gpu(args):
     def cu(a, dt=torch.float64):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
 
-    precs = {"fp64": G.QBX_FP64, "fp32": G.QBX_M2L_FP32, "learned": G.QBX_M2L_FP32}
+    precs = {"fp64": G.QBX_FP64, "fp32": G.QBX_M2L_FP32, "3xtf32": G.QBX_M2L_3XTF32,
+             "learned": G.QBX_M2L_3XTF32 if args.mixed_form == "3xtf32" else G.QBX_M2L_FP32}
     mode = args.precision
     n_max = args.n_max if args.n_max else (N_MAX_MIXED if mode != "fp64" else N_MAX)
     orders_fn, learned_info = None, None
@@ -451,13 +452,18 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": "QBX target evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f64" if mode == "fp64" else "f64 (List 2 M2L and List 3 far M2QBXL products in f32)",
+        "dtype": "f64" if mode == "fp64" else (
+            "f64 (List 2 M2L and List 3 far M2QBXL products in f32)" if precs[mode] == G.QBX_M2L_FP32 else
+            "f64 (List 2 M2L and List 3 far M2QBXL products as split-tf32 tensor-core MMAs, f32 accumulation)"),
         "data": "synthetic",
         "config": {"workload": f"star r=1+0.3ReY63, {s.n_elem} curved triangles x 15 nodes: S[d_n u] - D[u] at "
                                f"{s.n_ctr} on-surface QBX targets + {N_VOLUME} volume points",
                    "mode": {"fp64": "plain FP64 GIGAQBX, fixed orders",
                             "fp32": "mixed precision (FP32 translation products), fixed orders",
-                            "learned": "learned orders + mixed precision (FP32 translation products)"}[mode],
+                            "3xtf32": "mixed precision (split-TF32 tensor-core translation products), fixed orders",
+                            "learned": "learned orders + mixed precision (" + (
+                                "split-TF32 tensor-core" if args.mixed_form == "3xtf32" else "FP32")
+                            + " translation products)"}[mode],
                    "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": n_max, "t_f": T_F, "n_src": int(s.n_src),
                    "n_ctr": int(s.n_ctr), "n_qbx_targets": n_qbx_tgt, "n_point_targets": n_pt_tgt,
                    "n_flagged": int(vflag.sum()), "n_boxes": int(T.n_boxes), "n_levels": nlev,
@@ -501,7 +507,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--n-sub", type=int, default=20, help="icosahedron face subdivision (20 = 8,000 elements)")
     ap.add_argument("--n-max", type=int, default=0, help="particles per leaf before a box splits (0: tuned value)")
-    ap.add_argument("--precision", choices=("fp64", "fp32", "learned"), default="learned",
+    ap.add_argument("--mixed-form", choices=("fp32", "3xtf32"), default="3xtf32",
+                    help="translation products of the learned mode: FP32 SIMT or split-TF32 tensor cores")
+    ap.add_argument("--precision", choices=("fp64", "fp32", "3xtf32", "learned"), default="learned",
                     help="fp64: every stage FP64; fp32: List 2 M2L and List 3 far M2QBXL as FP32 products; "
                          "learned: fp32 with per-center / per-box orders from the trained network")
     ap.add_argument("--fp64-steps", type=int, default=5, help="timed steps of the plain FP64 comparison")

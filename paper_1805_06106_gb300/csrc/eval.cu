@@ -27,16 +27,17 @@ constexpr double INV4PI = 0.079577471545947667884;  // 1 / (4 pi)
 
 struct M2LPlan;
 void free_m2l_plan(M2LPlan *p);
-M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, cudaStream_t st);
+M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, bool tc,
+                        cudaStream_t st);
 void m2l_mixed_run(const qbx_tree *T, const qbx_lists *L, M2LPlan *pl, int PMT, const double2 *Mu, double2 *B,
-                   const signed char *pb, cudaStream_t st);
+                   const signed char *pb, int *err, cudaStream_t st);
 int m2l_plan_order(const M2LPlan *p);
 struct WfarPlan;
 void free_wfar_plan(WfarPlan *p);
 int wfar_plan_orders(const WfarPlan *p);
 const int *wfar_empty_start(const WfarPlan *p);
-WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, cudaStream_t st);
-void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb,
+WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, cudaStream_t st);
+void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, int *err,
                     cudaStream_t st);
 void wfar_mixed_reduce(const qbx_tree *T, WfarPlan *pl, int QMS, const signed char *qc, double2 *A, cudaStream_t st);
 
@@ -54,6 +55,7 @@ struct qbx_workspace {
     std::vector<int> lvl_first;    // host copies of level ranges
     qbx::M2LPlan *m2l = nullptr;   // mixed-precision List 2 plan (built on first use)
     qbx::WfarPlan *wfar = nullptr; // mixed-precision List 3 far plan (built on first use)
+    int wfar_key = -1;             // (orders, form) the List 3 far plan was built for
 };
 
 namespace qbx {
@@ -908,12 +910,13 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         QBX_LAUNCH_CHECK();
     } else {
         const int Pm = o->p_fmm;
-        if (!ws->m2l || m2l_plan_order(ws->m2l) != Pm) {
+        const bool tc = o->precision == QBX_M2L_3XTF32;
+        if (!ws->m2l || m2l_plan_order(ws->m2l) != Pm * 2 + (tc ? 1 : 0)) {
             free_m2l_plan(ws->m2l);
             ws->m2l = nullptr;
-            ws->m2l = m2l_plan_build(T, L, Pm, PM_T, ws->m2l_tab, st);
+            ws->m2l = m2l_plan_build(T, L, Pm, PM_T, ws->m2l_tab, tc, st);
         }
-        m2l_mixed_run(T, L, ws->m2l, PM_T, ws->Mu, ws->B, ws->pb, st);
+        m2l_mixed_run(T, L, ws->m2l, PM_T, ws->Mu, ws->B, ws->pb, ws->flags, st);
     }
     // Stage 6(b)
     stage_mark(L, 3, st);
@@ -933,13 +936,15 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     WfarPlan *wf = nullptr;
     if (o->precision != QBX_FP64 && T->np[KCTR] > 0) {
         const int Pm = o->p_fmm, Qm = o->p_qbx;
-        if (!ws->wfar || wfar_plan_orders(ws->wfar) != Pm * 100 + Qm) {
+        const bool tc = o->precision == QBX_M2L_3XTF32;
+        if (!ws->wfar || ws->wfar_key != (Pm * 100 + Qm) * 2 + (tc ? 1 : 0)) {
             free_wfar_plan(ws->wfar);
             ws->wfar = nullptr;
-            ws->wfar = wfar_plan_build(T, L, Pm, Qm, st);
+            ws->wfar = wfar_plan_build(T, L, Pm, Qm, tc, st);
+            ws->wfar_key = (Pm * 100 + Qm) * 2 + (tc ? 1 : 0);
         }
         wf = ws->wfar;
-        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->pb, st);
+        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->pb, ws->flags, st);
     }
     // Stages 3, 5, 6(a), 8, 9 at QBX centers and their targets
     switch (QM) {
@@ -960,6 +965,10 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     }
     stage_mark(L, 9, st);
     L->prof_valid = L->prof;
+    if (o->precision == QBX_M2L_3XTF32 && cap == cudaStreamCaptureStatusNone) {
+        // the tensor-core kernels report a wait that gave up through the flags word
+        if (read_flags(ws->flags, st) & 8) throw Error{QBX_ERR_TIMEOUT, "a tensor-core pipeline wait timed out"};
+    }
 }
 
 }  // namespace qbx

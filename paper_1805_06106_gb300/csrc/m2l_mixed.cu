@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "harmonics.cuh"
+#include "tc_common.cuh"
 
 namespace qbx {
 
@@ -33,15 +34,22 @@ struct M2LPlan {
     int *off_start = nullptr;     // 1332: pair range of each offset
     float *mh = nullptr;          // n_boxes x D balanced multipoles
     float *y = nullptr;           // npairs x D per-pair results
+    // split-TF32 tensor-core form (QBX_M2L_3XTF32)
+    bool tc = false;
+    int Np = 0, Dp = 0, KC = 0, nch = 0, ntc = 0;
+    float *mats_tc = nullptr;     // 1331 x nch x {hi, lo} x (Np x KC K-major tiles)
+    float *mh_hi = nullptr, *mh_lo = nullptr;  // n_boxes x Dp
+    int4 *tc_tiles = nullptr;     // (offset, first pair, last pair + 1) per 128-pair tile
 };
 
-int m2l_plan_order(const M2LPlan *p) { return p ? p->P : -1; }
+int m2l_plan_order(const M2LPlan *p) { return p ? p->P * 2 + (p->tc ? 1 : 0) : -1; }
 
 void free_m2l_plan(M2LPlan *p)
 {
     if (!p) return;
     dfree(p->mats); dfree(p->pair_src); dfree(p->pair_pos); dfree(p->tiles); dfree(p->off_start);
     dfree(p->mh); dfree(p->y);
+    dfree(p->mats_tc); dfree(p->mh_hi); dfree(p->mh_lo); dfree(p->tc_tiles);
     delete p;
 }
 
@@ -57,6 +65,40 @@ __device__ __forceinline__ double ffac_sqrt(int n, int m)  // F(n, m) = sqrt((n+
 // real-layout index of (n, m >= 0, part)
 __host__ __device__ __forceinline__ int ridx(int n, int m, int part) { return n * n + (m == 0 ? 0 : 2 * m - 1 + part); }
 
+// Entry (row, col) of the balanced real operator of List 2 offset with irregular table S (FP64).
+__device__ double m2l_entry(int D, const double2 *S, int row, int col)
+{
+    int k = (int)sqrtf((float)row);
+    while (k * k > row) --k;
+    while ((k + 1) * (k + 1) <= row) ++k;
+    int rr = row - k * k;  // 0 -> (l=0,re), 2l-1 -> (l,re), 2l -> (l,im)
+    int l = (rr + 1) / 2, rpart = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+    int n = (int)sqrtf((float)col);
+    while (n * n > col) --n;
+    while ((n + 1) * (n + 1) <= col) ++n;
+    int cc = col - n * n;
+    int m = (cc + 1) / 2, cpart = (cc == 0) ? 0 : ((cc & 1) ? 0 : 1);
+    double scale = 1.0 / (ffac_sqrt(n, m) * ffac_sqrt(k, l));
+    double2 c1 = cconj(sym_get(S, n + k, m + l));
+    double2 c2 = make_double2(0.0, 0.0);
+    if (m > 0) c2 = cconj(sym_get(S, n + k, -m + l));
+    double s = (m & 1) ? -1.0 : 1.0;
+    double2 plus = make_double2(c1.x + s * c2.x, c1.y + s * c2.y);
+    double2 minus = make_double2(c1.x - s * c2.x, c1.y - s * c2.y);
+    double e;
+    if (rpart == 0 && cpart == 0) e = plus.x;
+    else if (rpart == 0 && cpart == 1) e = -minus.y;
+    else if (rpart == 1 && cpart == 0) e = plus.y;
+    else e = minus.x;
+    return e * scale;
+}
+
+__device__ __forceinline__ bool m2l_offset_valid(int o)
+{
+    int ox = o % 11 - 5, oy = (o / 11) % 11 - 5, oz = o / 121 - 5;
+    return max(abs(ox), max(abs(oy), abs(oz))) >= 3;
+}
+
 // One block per offset; entries from the FP64 irregular table (stride ntri(2 PMT)).
 __global__ void k_m2l_mats(int P, int PMT, const double2 *stab, float *mats)
 {
@@ -64,38 +106,33 @@ __global__ void k_m2l_mats(int P, int PMT, const double2 *stab, float *mats)
     const int D = (P + 1) * (P + 1);
     float *Mo = mats + (int64_t)o * D * D;
     const double2 *S = stab + (int64_t)o * ntri(2 * PMT);
-    int ox = o % 11 - 5, oy = (o / 11) % 11 - 5, oz = o / 121 - 5;
-    int amax = max(abs(ox), max(abs(oy), abs(oz)));
-    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x) {
-        int row = idx / D, col = idx % D;
-        float v = 0.f;
-        if (amax >= 3) {
-            int k = (int)sqrtf((float)row);
-            while (k * k > row) --k;
-            while ((k + 1) * (k + 1) <= row) ++k;
-            int rr = row - k * k;  // 0 -> (l=0,re), 2l-1 -> (l,re), 2l -> (l,im)
-            int l = (rr + 1) / 2, rpart = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
-            int n = (int)sqrtf((float)col);
-            while (n * n > col) --n;
-            while ((n + 1) * (n + 1) <= col) ++n;
-            int cc = col - n * n;
-            int m = (cc + 1) / 2, cpart = (cc == 0) ? 0 : ((cc & 1) ? 0 : 1);
-            double scale = 1.0 / (ffac_sqrt(n, m) * ffac_sqrt(k, l));
-            double2 c1 = cconj(sym_get(S, n + k, m + l));
-            double2 c2 = make_double2(0.0, 0.0);
-            if (m > 0) c2 = cconj(sym_get(S, n + k, -m + l));
-            double s = (m & 1) ? -1.0 : 1.0;
-            double2 plus = make_double2(c1.x + s * c2.x, c1.y + s * c2.y);
-            double2 minus = make_double2(c1.x - s * c2.x, c1.y - s * c2.y);
-            double e;
-            if (rpart == 0 && cpart == 0) e = plus.x;
-            else if (rpart == 0 && cpart == 1) e = -minus.y;
-            else if (rpart == 1 && cpart == 0) e = plus.y;
-            else e = minus.x;
-            v = (float)(e * scale);
-        }
-        Mo[idx] = v;
+    const bool valid = m2l_offset_valid(o);
+    for (int idx = threadIdx.x; idx < D * D; idx += blockDim.x)
+        Mo[idx] = valid ? (float)m2l_entry(D, S, idx / D, idx % D) : 0.f;
+}
+
+// Split-TF32 operators in K-major tiles: for offset o and K chunk c (columns c KC .. c KC + KC - 1)
+// the hi tile (Np rows x KC) then the lo tile, each laid out as tc::kmajor_off with SBO = KC * 32.
+// Rows >= D and columns >= D are zero.
+__global__ void k_m2l_mats_tc(int P, int PMT, int Np, int Dp, int KC, const double2 *stab, float *mats)
+{
+    const int o = blockIdx.x;
+    const int D = (P + 1) * (P + 1), nch = Dp / KC;
+    const double2 *S = stab + (int64_t)o * ntri(2 * PMT);
+    const bool valid = m2l_offset_valid(o);
+    float *Mo = mats + (int64_t)o * Np * Dp * 2;
+    for (int idx = threadIdx.x; idx < Np * Dp; idx += blockDim.x) {
+        int row = idx / Dp, col = idx % Dp;
+        double e = (valid && row < D && col < D) ? m2l_entry(D, S, row, col) : 0.0;
+        float hi, lo;
+        tc::split_tf32(e, hi, lo);
+        int c = col / KC, kk = col % KC;
+        float *tile = Mo + (int64_t)c * 2 * Np * KC;
+        uint32_t off = tc::kmajor_off(row, kk, (uint32_t)KC * 32u) / 4u;
+        tile[off] = hi;
+        tile[(int64_t)Np * KC + off] = lo;
     }
+    (void)nch;
 }
 
 __global__ void k_pair_offsets(int nb, const int *vstart, const int *vidx, const int64_t *ic, int *code, int *cnt)
@@ -179,6 +216,159 @@ __global__ void __launch_bounds__(256) k_m2l_gemm_fp32(int D, const int2 *tiles,
         }
 }
 
+// Balanced real multipoles split into TF32 hi / lo parts, rows padded to Dp with zeros.
+__global__ void k_mhat_tc(int64_t nb, int P, int PMT, int Dp, const double2 *Mu, float *mh_hi, float *mh_lo)
+{
+    const int D = (P + 1) * (P + 1);
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb * Dp) return;
+    int64_t b = i / Dp;
+    int r = (int)(i % Dp);
+    double v = 0.0;
+    if (r < D) {
+        int n = (int)sqrtf((float)r);
+        while (n * n > r) --n;
+        while ((n + 1) * (n + 1) <= r) ++n;
+        int rr = r - n * n;
+        int m = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+        double2 c = Mu[b * ntri(PMT) + tri(n, m)];
+        v = (part ? c.y : c.x) * ffac_sqrt(n, m);
+    }
+    float hi, lo;
+    tc::split_tf32(v, hi, lo);
+    mh_hi[i] = hi;
+    mh_lo[i] = lo;
+}
+
+// Tensor-core List 2 products.  Persistent CTAs of 256 threads walk the 128-pair tiles; a tile
+// computes Y[pair][row] = sum_col Mats_o[row][col] Mh[src(pair)][col] as D = A B^T with
+// A = gathered multipoles (128 pairs x Dp, K-major) and B = the offset's operator (Np x Dp,
+// K-major), in K chunks of KC columns through a two-stage pipeline: the operator chunk arrives by
+// a bulk copy, the multipole chunk is gathered by the threads, one thread issues the split-TF32
+// MMAs (a_hi b_hi + a_lo b_hi + a_hi b_lo) into a 128 x Np FP32 accumulator in tensor memory.
+struct M2LTcArgs {
+    int ntiles, D, Dp, Np, KC, tmem_cols;
+    const int4 *tiles;
+    const int *pair_src;
+    const float *mh_hi, *mh_lo, *mats;
+    float *y;
+    int *err;
+};
+
+__global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    __shared__ uint64_t bar_b[2], bar_mma[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int KC = a.KC, Np = a.Np, nch = a.Dp / KC;
+    const uint32_t sboA = (uint32_t)KC * 32u + 16u, sboB = (uint32_t)KC * 32u;
+    const uint32_t bytesA = 16u * sboA, bytesB = (uint32_t)Np * KC * 4u;
+    unsigned char *Abuf[2][2], *Bbuf[2][2];
+    for (int s = 0; s < 2; ++s) {
+        Abuf[s][0] = smem_tc + (size_t)s * 2 * bytesA;
+        Abuf[s][1] = Abuf[s][0] + bytesA;
+        Bbuf[s][0] = smem_tc + (size_t)4 * bytesA + (size_t)s * 2 * bytesB;
+        Bbuf[s][1] = Bbuf[s][0] + bytesB;
+    }
+    if (tid == 0) {
+        for (int s = 0; s < 2; ++s) {
+            tc::mbar_init(&bar_b[s], 1);
+            tc::mbar_init(&bar_mma[s], 1);
+        }
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.tmem_cols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t nsplit = Np > 256 ? 2u : 1u;
+    const int N0 = Np > 256 ? 256 : Np, N1 = Np - N0;
+    const uint32_t id0 = tc::idesc_tf32(128, N0), id1 = tc::idesc_tf32(128, N1 > 0 ? N1 : 16);
+    bool ok = true;
+    uint32_t g = 0;  // chunks issued by this CTA (pipeline position)
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        const int4 tl = a.tiles[t];
+        const int o = tl.x, p0 = tl.y, np = tl.z - tl.y;
+        for (int c = 0; c < nch; ++c, ++g) {
+            const int s = g & 1;
+            const uint32_t use = g >> 1;
+            if (g >= 2) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, tc::WAIT_LIMIT);
+            if (__syncthreads_or(!ok)) { ok = false; break; }
+            if (tid == 0) {
+                tc::mbar_arrive_expect_tx(&bar_b[s], 2u * bytesB);
+                tc::bulk_g2s(Bbuf[s][0], a.mats + ((int64_t)o * nch + c) * 2 * Np * KC, 2u * bytesB, &bar_b[s]);
+            }
+            const int pieces = KC / 4;
+            for (int q = tid; q < 128 * pieces; q += 256) {
+                int row = q / pieces, pc = q % pieces;
+                float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
+                if (row < np) {
+                    int64_t src = (int64_t)a.pair_src[p0 + row] * a.Dp + c * KC + 4 * pc;
+                    h = *reinterpret_cast<const float4 *>(a.mh_hi + src);
+                    l = *reinterpret_cast<const float4 *>(a.mh_lo + src);
+                }
+                uint32_t off = tc::kmajor_off(row, 4 * pc, sboA);
+                *reinterpret_cast<float4 *>(Abuf[s][0] + off) = h;
+                *reinterpret_cast<float4 *>(Abuf[s][1] + off) = l;
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                bool got = tc::mbar_wait(&bar_b[s], use & 1, tc::WAIT_LIMIT);
+                if (got) {
+                    tc::tc_fence_after();
+                    const uint32_t a_hi = tc::smem_u32(Abuf[s][0]), a_lo = tc::smem_u32(Abuf[s][1]);
+                    const uint32_t b_hi = tc::smem_u32(Bbuf[s][0]), b_lo = tc::smem_u32(Bbuf[s][1]);
+                    for (int ks = 0; ks < KC / 8; ++ks) {
+                        for (uint32_t h = 0; h < nsplit; ++h) {
+                            const uint32_t boff = h * 32u * sboB + 256u * ks, aoff = 256u * ks;
+                            const uint32_t dcol = tmem + h * 256u, id = h ? id1 : id0;
+                            const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+                            tc::mma_tf32(dcol, tc::sdesc(a_hi + aoff, 128, sboA), tc::sdesc(b_hi + boff, 128, sboB), id, acc0);
+                            tc::mma_tf32(dcol, tc::sdesc(a_lo + aoff, 128, sboA), tc::sdesc(b_hi + boff, 128, sboB), id, 1u);
+                            tc::mma_tf32(dcol, tc::sdesc(a_hi + aoff, 128, sboA), tc::sdesc(b_lo + boff, 128, sboB), id, 1u);
+                        }
+                    }
+                } else {
+                    atomicOr(a.err, 8);
+                }
+                tc::mma_commit(&bar_mma[s]);  // also releases the stage when the MMAs were skipped
+            }
+        }
+        if (!ok) break;
+        // epilogue: lane quarter (warp & 3) holds pairs 32 q .. 32 q + 31; column groups of 16 split
+        // between warps w and w + 4
+        const int sl = (g - 1) & 1;
+        ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        tc::tc_fence_after();
+        const int qd = warp & 3, row = 32 * qd + lane;
+        for (int cg = warp >> 2; cg * 16 < Np; cg += 2) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(cg * 16), v);
+            if (row < np) {
+                float *dst = a.y + (int64_t)(p0 + row) * a.D + cg * 16;
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (cg * 16 + j < a.D) dst[j] = v[j];
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicOr(a.err, 8);
+    // wait for this CTA's last MMAs before releasing tensor memory
+    if (g > 0 && tid == 0) tc::mbar_wait(&bar_mma[(g - 1) & 1], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
+static size_t m2l_tc_smem(int Np, int KC) { return (size_t)4 * 16 * (KC * 32 + 16) + (size_t)4 * Np * KC * 4; }
+
 // B[b] += F(k,l)/h_b * sum_{e in V(b)} Y[pos(e)], summed in list order in FP64.
 __global__ void k_m2l_reduce(int64_t nb, int P, int PMT, const int *vstart, const int *pair_pos, const float *y,
                              const double *hw, const signed char *pb, double2 *B)
@@ -218,18 +408,34 @@ __global__ void k_scatter_pairs(int nb, const int *vstart, const int *vidx, cons
     }
 }
 
-M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, cudaStream_t st)
+M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, bool tc,
+                        cudaStream_t st)
 {
     M2LPlan *pl = new M2LPlan();
     try {
         pl->P = P;
         pl->D = (P + 1) * (P + 1);
+        pl->tc = tc;
         const int nb = (int)T->nb;
         const int64_t np = L->nnz[LV];
         pl->npairs = np;
-        pl->mats = dalloc<float>((int64_t)1331 * pl->D * pl->D);
-        k_m2l_mats<<<1331, 256, 0, st>>>(P, PMT, stab, pl->mats);
-        QBX_LAUNCH_CHECK();
+        if (tc) {
+            pl->Np = (pl->D + 15) / 16 * 16;
+            pl->KC = pl->Np > 256 ? 16 : 32;
+            pl->Dp = (pl->D + pl->KC - 1) / pl->KC * pl->KC;
+            pl->nch = pl->Dp / pl->KC;
+            pl->mats_tc = dalloc<float>((int64_t)1331 * pl->Np * pl->Dp * 2);
+            k_m2l_mats_tc<<<1331, 256, 0, st>>>(P, PMT, pl->Np, pl->Dp, pl->KC, stab, pl->mats_tc);
+            QBX_LAUNCH_CHECK();
+            pl->mh_hi = dalloc<float>((int64_t)nb * pl->Dp);
+            pl->mh_lo = dalloc<float>((int64_t)nb * pl->Dp);
+            QBX_CUDA_TRY(cudaFuncSetAttribute(k_m2l_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              (int)m2l_tc_smem(pl->Np, pl->KC)));
+        } else {
+            pl->mats = dalloc<float>((int64_t)1331 * pl->D * pl->D);
+            k_m2l_mats<<<1331, 256, 0, st>>>(P, PMT, stab, pl->mats);
+            QBX_LAUNCH_CHECK();
+        }
         int *code = dalloc<int>(np), *cnt = dalloc<int>(1332), *fill = dalloc<int>(1332);
         pl->off_start = dalloc<int>(1332);
         pl->pair_src = dalloc<int>(np);
@@ -247,13 +453,25 @@ M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, c
         QBX_CUDA_TRY(cudaStreamSynchronize(st));
         dfree(code); dfree(cnt); dfree(fill);
         std::vector<int2> tiles;
-        for (int o = 0; o < 1331; ++o)
+        std::vector<int4> tct;
+        for (int o = 0; o < 1331; ++o) {
             for (int p = os[o]; p < os[o + 1]; p += GN) tiles.push_back(make_int2(o, p));
-        pl->ntiles = (int)tiles.size();
-        pl->tiles = dalloc<int2>(std::max<size_t>(tiles.size(), 1));
-        if (!tiles.empty())
-            QBX_CUDA_TRY(cudaMemcpyAsync(pl->tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
-        pl->mh = dalloc<float>((int64_t)nb * pl->D);
+            for (int p = os[o]; p < os[o + 1]; p += 128) tct.push_back(make_int4(o, p, std::min(p + 128, os[o + 1]), 0));
+        }
+        if (tc) {
+            pl->ntc = (int)tct.size();
+            pl->tc_tiles = dalloc<int4>(std::max<size_t>(tct.size(), 1));
+            if (!tct.empty())
+                QBX_CUDA_TRY(cudaMemcpyAsync(pl->tc_tiles, tct.data(), tct.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                             st));
+        } else {
+            pl->ntiles = (int)tiles.size();
+            pl->tiles = dalloc<int2>(std::max<size_t>(tiles.size(), 1));
+            if (!tiles.empty())
+                QBX_CUDA_TRY(cudaMemcpyAsync(pl->tiles, tiles.data(), tiles.size() * sizeof(int2),
+                                             cudaMemcpyHostToDevice, st));
+            pl->mh = dalloc<float>((int64_t)nb * pl->D);
+        }
         pl->y = dalloc<float>(std::max<int64_t>(np, 1) * pl->D);
         QBX_CUDA_TRY(cudaStreamSynchronize(st));
     } catch (...) {
@@ -264,10 +482,29 @@ M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, c
 }
 
 void m2l_mixed_run(const qbx_tree *T, const qbx_lists *L, M2LPlan *pl, int PMT, const double2 *Mu, double2 *B,
-                   const signed char *pb, cudaStream_t st)
+                   const signed char *pb, int *err, cudaStream_t st)
 {
     const int64_t nb = T->nb;
     const int D = pl->D;
+    if (pl->tc) {
+        k_mhat_tc<<<nblocks(nb * pl->Dp, 256), 256, 0, st>>>(nb, pl->P, PMT, pl->Dp, Mu, pl->mh_hi, pl->mh_lo);
+        QBX_LAUNCH_CHECK();
+        if (pl->ntc > 0) {
+            int dev = 0, nsm = 0;
+            QBX_CUDA_TRY(cudaGetDevice(&dev));
+            QBX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            int cols = 32;
+            while (cols < pl->Np) cols <<= 1;
+            M2LTcArgs a{pl->ntc, D, pl->Dp, pl->Np, pl->KC, cols, pl->tc_tiles, pl->pair_src, pl->mh_hi, pl->mh_lo,
+                        pl->mats_tc, pl->y, err};
+            k_m2l_tc<<<std::min(pl->ntc, nsm), 256, m2l_tc_smem(pl->Np, pl->KC), st>>>(a);
+            QBX_LAUNCH_CHECK();
+        }
+        k_m2l_reduce<<<nblocks(nb * D, 256), 256, 0, st>>>(nb, pl->P, PMT, L->start[LV], pl->pair_pos, pl->y, T->hw, pb,
+                                                          B);
+        QBX_LAUNCH_CHECK();
+        return;
+    }
     k_mhat<<<nblocks(nb * D, 256), 256, 0, st>>>(nb, pl->P, PMT, Mu, pl->mh);
     QBX_LAUNCH_CHECK();
     if (pl->ntiles > 0) {

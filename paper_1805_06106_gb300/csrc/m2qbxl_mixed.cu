@@ -16,8 +16,11 @@
 #include <vector>
 
 #include "harmonics.cuh"
+#include "tc_common.cuh"
 
 namespace qbx {
+
+constexpr int WF_MAXCH = 48;  // K chunks of the tensor-core form
 
 struct WfarPlan {
     int P = -1, Q = -1, K = 0, R = 0;
@@ -33,9 +36,16 @@ struct WfarPlan {
     int2 *tiles = nullptr;    // (first pair, last pair + 1) per GEMM tile
     float *Y = nullptr;       // npairs x R
     int *zero_start = nullptr;  // n_boxes + 1 zeros: an empty List 3 far for the FP64 center kernel
+    // split-TF32 tensor-core form (QBX_M2L_3XTF32): K (the harmonic index) in chunks of whole
+    // degrees [cj0, cj1), each padded to a multiple of 8 columns; H in K-major tiles per chunk
+    bool tc = false;
+    int Rp = 0, Kp = 0, nch = 0, WMAX = 0, ntc = 0, NU = 0;
+    int cj0[WF_MAXCH] = {}, cj1[WF_MAXCH] = {}, ckoff[WF_MAXCH + 1] = {};
+    float *H_tc = nullptr;     // ndsrc x Rp x Kp
+    int4 *tc_tiles = nullptr;  // (source box, first pair, last pair + 1) per 128-pair tile
 };
 
-int wfar_plan_orders(const WfarPlan *p) { return p ? p->P * 100 + p->Q : -1; }
+int wfar_plan_orders(const WfarPlan *p) { return p ? (p->P * 100 + p->Q) * 2 + (p->tc ? 1 : 0) : -1; }
 const int *wfar_empty_start(const WfarPlan *p) { return p->zero_start; }
 
 void free_wfar_plan(WfarPlan *p)
@@ -43,6 +53,7 @@ void free_wfar_plan(WfarPlan *p)
     if (!p) return;
     dfree(p->slot); dfree(p->slot_box); dfree(p->H); dfree(p->pair_ctr); dfree(p->pair_d); dfree(p->pos_cm);
     dfree(p->cm_start); dfree(p->tiles); dfree(p->Y); dfree(p->zero_start);
+    dfree(p->H_tc); dfree(p->tc_tiles);
     delete p;
 }
 
@@ -106,6 +117,30 @@ __global__ void k_flag_pos(int nb, const int *cnt, int *flag)
     if (d < nb) flag[d] = cnt[d] > 0 ? 1 : 0;
 }
 
+// Entry (row = (k,l,rp), col = (j,i,cp)) of the Hankel operator of a source box with multipole M
+// (tri layout, stride PMT) truncated at order Pd.
+__device__ double wfar_H_entry(int row, int col, int Pd, const double2 *M)
+{
+    int k, l, rp, j, i, cp;
+    decode(row, k, l, rp);
+    decode(col, j, i, cp);
+    int n = j - k;
+    double2 a1 = make_double2(0, 0), a2 = make_double2(0, 0);
+    if (n >= 0 && n <= Pd) {
+        int m1 = i - l, m2 = -i - l;
+        // Mh_n^m G(n,m,k,l) = Mu_n^m F(n+k, m+l) / F(k,l)
+        if (m1 >= -n && m1 <= n) a1 = cscale(sym_get(M, n, m1), Fnm(n + k, m1 + l) * Finv(k, l));
+        if (i > 0 && m2 >= -n && m2 <= n) a2 = cscale(sym_get(M, n, m2), Fnm(n + k, m2 + l) * Finv(k, l));
+    }
+    double sg = (i & 1) ? -1.0 : 1.0;
+    double2 plus = make_double2(a1.x + sg * a2.x, a1.y + sg * a2.y);   // a1 + s a2
+    double2 mins = make_double2(sg * a2.x - a1.x, sg * a2.y - a1.y);   // s a2 - a1
+    if (rp == 0 && cp == 0) return plus.x;
+    if (rp == 0 && cp == 1) return -mins.y;
+    if (rp == 1 && cp == 0) return plus.y;
+    return mins.x;
+}
+
 // H[slot][(k,l,rp)][(j,i,cp)] from the FP64 multipole of the slot's box.
 __global__ void k_wfar_H(int ndsrc, int P, int Q, int PMT, const int *slot_box, const signed char *pb,
                          const double2 *Mu, float *H)
@@ -118,27 +153,256 @@ __global__ void k_wfar_H(int ndsrc, int P, int Q, int PMT, const int *slot_box, 
     int row = rem / K, col = rem % K;
     int d = slot_box[s];
     int Pd = min((int)pb[d], P);
-    int k, l, rp, j, i, cp;
-    decode(row, k, l, rp);
-    decode(col, j, i, cp);
-    const double2 *M = Mu + (int64_t)d * ntri(PMT);
-    int n = j - k;
-    double2 a1 = make_double2(0, 0), a2 = make_double2(0, 0);
-    if (n >= 0 && n <= Pd) {
-        int m1 = i - l, m2 = -i - l;
-        // Mh_n^m G(n,m,k,l) = Mu_n^m F(n+k, m+l) / F(k,l)
-        if (m1 >= -n && m1 <= n) a1 = cscale(sym_get(M, n, m1), Fnm(n + k, m1 + l) * Finv(k, l));
-        if (i > 0 && m2 >= -n && m2 <= n) a2 = cscale(sym_get(M, n, m2), Fnm(n + k, m2 + l) * Finv(k, l));
+    H[idx] = (float)wfar_H_entry(row, col, Pd, Mu + (int64_t)d * ntri(PMT));
+}
+
+struct WfarChunks {
+    int nch, R, Rp, Kp;
+    int cj0[WF_MAXCH], cj1[WF_MAXCH], ckoff[WF_MAXCH + 1];
+};
+
+// H of the tensor-core form: for each slot and chunk c, Rp rows x W_c columns (W_c = ckoff[c+1] -
+// ckoff[c]) as a K-major tile with SBO = 32 W_c, FP32 (split into TF32 parts when loaded).
+__global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, WfarChunks ch, const int *slot_box, const signed char *pb,
+                            const double2 *Mu, float *H)
+{
+    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t per = (int64_t)ch.Rp * ch.Kp;
+    if (idx >= (int64_t)ndsrc * per) return;
+    int s = (int)(idx / per);
+    int rem = (int)(idx % per);
+    int row = rem / ch.Kp, kp = rem % ch.Kp;
+    int c = 0;
+    while (c + 1 < ch.nch && ch.ckoff[c + 1] <= kp) ++c;
+    const int kk = kp - ch.ckoff[c], W = ch.ckoff[c + 1] - ch.ckoff[c];
+    const int nent = ch.cj1[c] * ch.cj1[c] - ch.cj0[c] * ch.cj0[c];
+    double v = 0.0;
+    if (row < ch.R && kk < nent) {
+        int d = slot_box[s];
+        v = wfar_H_entry(row, ch.cj0[c] * ch.cj0[c] + kk, min((int)pb[d], P), Mu + (int64_t)d * ntri(PMT));
     }
-    double sg = (i & 1) ? -1.0 : 1.0;
-    double2 plus = make_double2(a1.x + sg * a2.x, a1.y + sg * a2.y);   // a1 + s a2
-    double2 mins = make_double2(sg * a2.x - a1.x, sg * a2.y - a1.y);   // s a2 - a1
-    double e;
-    if (rp == 0 && cp == 0) e = plus.x;
-    else if (rp == 0 && cp == 1) e = -mins.y;
-    else if (rp == 1 && cp == 0) e = plus.y;
-    else e = mins.x;
-    H[idx] = (float)e;
+    float *tile = H + (int64_t)s * per + (int64_t)ch.ckoff[c] * ch.Rp;
+    tile[tc::kmajor_off(row, kk, (uint32_t)W * 32u) / 4u] = (float)v;
+}
+
+// Balanced-harmonic recurrence coefficients: Sh = S / F with F(n,m) = sqrt((n+m)!(n-m)!),
+//   Sh_i^i = sqrt((2i-1)/(2i)) (w/|x|^2) Sh_{i-1}^{i-1},
+//   Sh_j^i = a_j^i (z/|x|^2) Sh_{j-1}^i - b_j^i |x|^-2 Sh_{j-2}^i,
+//   a_j^i = (2j-1)/sqrt((j+i)(j-i)),  b_j^i = sqrt((j+i-1)(j-i-1)/((j+i)(j-i))).
+__constant__ double c_ra[ntri(40)], c_rb[ntri(40)], c_rg[41];
+
+struct WfarTcArgs {
+    int ntiles, P, Q, PQ, R, Rp, WMAX, tmem_cols;
+    WfarChunks ch;
+    const int4 *tiles;
+    const int *pair_ctr, *slot;
+    const float *H;
+    const double *cxyz, *cr, *cen, *hw;
+    int64_t nc;
+    float *Y;
+    int *err;
+};
+
+// Tensor-core List 3 far products.  Persistent CTAs of 256 threads walk 128-pair tiles of one
+// source box d: per K chunk the threads generate the balanced irregular harmonics of their pairs
+// in FP64 (two threads per pair, each carrying the recurrence of every other column i in
+// registers), split them into TF32 parts in shared memory, load and split the chunk of H_d; one
+// thread issues a_hi b_hi + a_lo b_hi + a_hi b_lo into a 128 x Rp FP32 accumulator in tensor
+// memory.  Epilogue: Y[pair][row] = acc F(k,l) (rho/h)^k / h.
+template <int NU>
+__global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_tc[];
+    __shared__ uint64_t bar_mma[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int Q = a.Q, PQ = a.PQ, Rp = a.Rp, WMAX = a.WMAX;
+    const uint32_t sboA = (uint32_t)WMAX * 32u + 16u;
+    const uint32_t bytesA = 16u * sboA, bytesB = (uint32_t)Rp * WMAX * 4u;
+    unsigned char *Abuf[2][2], *Bbuf[2][2];
+    for (int s = 0; s < 2; ++s) {
+        Abuf[s][0] = smem_tc + (size_t)s * 2 * bytesA;
+        Abuf[s][1] = Abuf[s][0] + bytesA;
+        Bbuf[s][0] = smem_tc + (size_t)4 * bytesA + (size_t)s * 2 * bytesB;
+        Bbuf[s][1] = Bbuf[s][0] + bytesB;
+    }
+    float *Pw = reinterpret_cast<float *>(smem_tc + (size_t)4 * bytesA + (size_t)4 * bytesB);  // 128 x (Q+1)
+    float *colF = Pw + 128 * (Q + 1);                                                     // Rp
+    int *colK = reinterpret_cast<int *>(colF + Rp);                                       // Rp
+    for (int r = tid; r < Rp; r += 256) {
+        int k = 0, l = 0, part = 0;
+        if (r < a.R) decode(r, k, l, part);
+        colF[r] = (float)Fnm(k, l);
+        colK[r] = k;
+    }
+    if (tid == 0) {
+        tc::mbar_init(&bar_mma[0], 1);
+        tc::mbar_init(&bar_mma[1], 1);
+        tc::fence_mbar_init();
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.tmem_cols);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    const uint32_t idesc = tc::idesc_tf32(128, Rp);
+    const int p = tid >> 1, par = tid & 1;
+    bool ok = true;
+    uint32_t g = 0;
+    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
+        const int4 tl = a.tiles[t];
+        const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
+        const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
+        const bool valid = p < np;
+        // pair geometry and the diagonal of the balanced irregular harmonics
+        double a1r[NU], a1i[NU], a2r[NU], a2i[NU];
+        double zz = 0.0, ir2 = 0.0;
+        {
+            const double h = a.hw[d], hinv = 1.0 / h;
+            double x = 3.0, y = 0.0, z = 0.0;
+            int c = 0;
+            if (valid) {
+                c = a.pair_ctr[p0 + p];
+                x = (a.cxyz[c] - a.cen[3 * d]) * hinv;
+                y = (a.cxyz[a.nc + c] - a.cen[3 * d + 1]) * hinv;
+                z = (a.cxyz[2 * a.nc + c] - a.cen[3 * d + 2]) * hinv;
+            }
+            ir2 = 1.0 / (x * x + y * y + z * z);
+            const double rinv = sqrt(ir2), wr = x * ir2, wi = y * ir2;
+            zz = z * ir2;
+            if (par == 0) {
+                const double ratio = valid ? a.cr[c] * hinv : 0.0;
+                double pk = hinv;
+                for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[p * (Q + 1) + k] = (float)pk;
+            }
+            double dr = rinv, di = 0.0;  // Sh_0^0
+            if (par == 1) {              // Sh_1^1
+                double g1 = c_rg[1];
+                dr = rinv * wr * g1;
+                di = rinv * wi * g1;
+            }
+#pragma unroll
+            for (int u = 0; u < NU; ++u) {
+                const int i = par + 2 * u;
+                a1r[u] = dr; a1i[u] = di; a2r[u] = 0.0; a2i[u] = 0.0;
+                // advance the diagonal by two columns: i -> i + 2
+                if (i + 2 <= 40) {
+                    double ga = c_rg[i + 1], gb = c_rg[i + 2];
+                    double tr = (dr * wr - di * wi) * ga, ti = (dr * wi + di * wr) * ga;
+                    dr = (tr * wr - ti * wi) * gb;
+                    di = (tr * wi + ti * wr) * gb;
+                }
+            }
+        }
+        for (int c = 0; c < a.ch.nch; ++c, ++g) {
+            const int s = g & 1;
+            const uint32_t use = g >> 1;
+            if (g >= 2) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, tc::WAIT_LIMIT);
+            if (__syncthreads_or(!ok)) { ok = false; break; }
+            const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
+            const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c], nent = j1 * j1 - j0 * j0;
+            // B: chunk of H_d, split into TF32 parts
+            {
+                const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[c] * Rp);
+                float4 *dh = reinterpret_cast<float4 *>(Bbuf[s][0]), *dl = reinterpret_cast<float4 *>(Bbuf[s][1]);
+                for (int q = tid; q < Rp * W / 4; q += 256) {
+                    float4 v = src[q], hi, lo;
+                    tc::split_tf32(v.x, hi.x, lo.x);
+                    tc::split_tf32(v.y, hi.y, lo.y);
+                    tc::split_tf32(v.z, hi.z, lo.z);
+                    tc::split_tf32(v.w, hi.w, lo.w);
+                    dh[q] = hi;
+                    dl[q] = lo;
+                }
+            }
+            // A: harmonics of degrees j0 .. j1-1 for this thread's columns
+            if (valid) {
+                unsigned char *Ah = Abuf[s][0], *Al = Abuf[s][1];
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    const int i = par + 2 * u;
+                    if (i <= PQ) {
+                        for (int j = max(i, j0); j < j1; ++j) {
+                            double vr = a1r[u], vi = a1i[u];
+                            if (j > i) {
+                                const double al = c_ra[tri(j, i)] * zz, be = c_rb[tri(j, i)] * ir2;
+                                vr = al * a1r[u] - be * a2r[u];
+                                vi = al * a1i[u] - be * a2i[u];
+                                a2r[u] = a1r[u]; a2i[u] = a1i[u];
+                                a1r[u] = vr; a1i[u] = vi;
+                            }
+                            const int kk = j * j - j0 * j0 + (i == 0 ? 0 : 2 * i - 1);
+                            float hi, lo;
+                            tc::split_tf32((float)vr, hi, lo);
+                            uint32_t off = tc::kmajor_off(p, kk, sboA);
+                            *reinterpret_cast<float *>(Ah + off) = hi;
+                            *reinterpret_cast<float *>(Al + off) = lo;
+                            if (i > 0) {
+                                tc::split_tf32((float)vi, hi, lo);
+                                off = tc::kmajor_off(p, kk + 1, sboA);
+                                *reinterpret_cast<float *>(Ah + off) = hi;
+                                *reinterpret_cast<float *>(Al + off) = lo;
+                            }
+                        }
+                    }
+                }
+                for (int kk = nent + par; kk < W; kk += 2) {
+                    uint32_t off = tc::kmajor_off(p, kk, sboA);
+                    *reinterpret_cast<float *>(Ah + off) = 0.f;
+                    *reinterpret_cast<float *>(Al + off) = 0.f;
+                }
+            }
+            tc::fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc::tc_fence_after();
+                const uint32_t a_hi = tc::smem_u32(Abuf[s][0]), a_lo = tc::smem_u32(Abuf[s][1]);
+                const uint32_t b_hi = tc::smem_u32(Bbuf[s][0]), b_lo = tc::smem_u32(Bbuf[s][1]);
+                const uint32_t sboB = (uint32_t)W * 32u;
+                for (int ks = 0; ks < W / 8; ++ks) {
+                    const uint32_t off = 256u * ks;
+                    const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+                    tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, acc0);
+                    tc::mma_tf32(tmem, tc::sdesc(a_lo + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, 1u);
+                    tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_lo + off, 128, sboB), idesc, 1u);
+                }
+                tc::mma_commit(&bar_mma[s]);
+            }
+        }
+        if (!ok) break;
+        const int sl = (g - 1) & 1;
+        ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
+        if (__syncthreads_or(!ok)) { ok = false; break; }
+        tc::tc_fence_after();
+        const int qd = warp & 3, row = 32 * qd + lane;
+        for (int cg = warp >> 2; cg * 16 < Rp; cg += 2) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(cg * 16), v);
+            if (row < np) {
+                float *dst = a.Y + (int64_t)(p0 + row) * a.R;
+                const float *pw = Pw + row * (Q + 1);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = cg * 16 + j;
+                    if (col < a.R) dst[col] = v[j] * (colF[col] * pw[colK[col]]);
+                }
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+    }
+    if (!ok && tid == 0) atomicOr(a.err, 8);
+    if (g > 0 && tid == 0) tc::mbar_wait(&bar_mma[(g - 1) & 1], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
+}
+
+static size_t wfar_tc_smem(int Rp, int WMAX, int Q)
+{
+    return (size_t)4 * 16 * (WMAX * 32 + 16) + (size_t)4 * Rp * WMAX * 4 + (size_t)128 * (Q + 1) * 4 +
+           (size_t)Rp * 8;
 }
 
 constexpr int WKC = 32;  // K chunk of the H tile
@@ -292,7 +556,51 @@ __global__ void k_wfar_reduce(int64_t nc, int Q, int QMS, const int *cm_start, c
     else a->x += s;
 }
 
-WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, cudaStream_t st)
+// Degree chunks of the tensor-core form and its shared-memory budget; false when the orders do not fit.
+static bool wfar_tc_layout(WfarPlan *pl)
+{
+    const int P = pl->P, Q = pl->Q, PQ = P + Q;
+    pl->Rp = (pl->R + 15) / 16 * 16;
+    if (pl->Rp > 256 || PQ > 35) return false;
+    pl->NU = PQ <= 23 ? 12 : 18;
+    const int wmin = (2 * PQ + 1 + 7) / 8 * 8;
+    int W = std::max(64, wmin);
+    while (W > wmin && wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) W -= 8;
+    if (wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) return false;
+    pl->WMAX = W;
+    int nch = 0, j = 0, koff = 0;
+    while (j <= PQ) {
+        int j1 = j + 1;
+        while (j1 <= PQ && j1 * j1 + 2 * j1 + 1 - j * j <= W) ++j1;  // add degree j1 while it fits
+        if (nch >= WF_MAXCH) return false;
+        pl->cj0[nch] = j;
+        pl->cj1[nch] = j1;
+        pl->ckoff[nch] = koff;
+        koff += (j1 * j1 - j * j + 7) / 8 * 8;
+        ++nch;
+        j = j1;
+    }
+    pl->ckoff[nch] = koff;
+    pl->nch = nch;
+    pl->Kp = koff;
+    return true;
+}
+
+static void set_recurrence_tables(cudaStream_t st)
+{
+    std::vector<double> ra(ntri(40), 0.0), rb(ntri(40), 0.0), rg(41, 0.0);
+    for (int j = 0; j <= 40; ++j)
+        for (int i = 0; i < j; ++i) {
+            ra[tri(j, i)] = (2.0 * j - 1.0) / std::sqrt((double)(j + i) * (double)(j - i));
+            rb[tri(j, i)] = std::sqrt((double)(j + i - 1) * (double)(j - i - 1) / ((double)(j + i) * (double)(j - i)));
+        }
+    for (int i = 1; i <= 40; ++i) rg[i] = std::sqrt((2.0 * i - 1.0) / (2.0 * i));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_ra, ra.data(), ra.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_rb, rb.data(), rb.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_rg, rg.data(), rg.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+}
+
+WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, cudaStream_t st)
 {
     WfarPlan *pl = new WfarPlan();
     int *cm_cnt = nullptr, *d_cnt = nullptr, *d_start = nullptr, *flag = nullptr, *tot = nullptr;
@@ -356,6 +664,28 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, c
         QBX_CUDA_TRY(cudaMemcpyAsync(ds.data(), d_start, (nb + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
         QBX_CUDA_TRY(cudaStreamSynchronize(st));
         const int WT = wfar_tile_width(pl->K, pl->R);
+        pl->tc = tc && wfar_tc_layout(pl);  // orders beyond the tensor-core layout use the FP32 form
+        if (pl->tc) {
+            set_recurrence_tables(st);
+            std::vector<int4> tct;
+            for (int d = 0; d < nb; ++d)
+                for (int p = ds[d]; p < ds[d + 1]; p += 128) tct.push_back(make_int4(d, p, std::min(p + 128, ds[d + 1]), 0));
+            pl->ntc = (int)tct.size();
+            pl->tc_tiles = dalloc<int4>(std::max<size_t>(tct.size(), 1));
+            if (!tct.empty())
+                QBX_CUDA_TRY(cudaMemcpyAsync(pl->tc_tiles, tct.data(), tct.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                             st));
+            pl->H_tc = dalloc<float>((int64_t)std::max(nd, 1) * pl->Rp * pl->Kp);
+            pl->Y = dalloc<float>((int64_t)std::max(np, 1) * pl->R);
+            const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, Q);
+            if (pl->NU == 12)
+                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            else
+                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            QBX_CUDA_TRY(cudaStreamSynchronize(st));
+            dfree(cm_cnt); dfree(d_cnt); dfree(d_start); dfree(flag); dfree(tot);
+            return pl;
+        }
         if (pl->R > 320 || wfar_smem(pl->K, pl->R, WT) > 227 * 1024)
             throw Error{QBX_ERR_INVALID_ARG, "orders too high for the mixed List 3 far product"};
         std::vector<int2> tiles;
@@ -385,10 +715,38 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, c
     return pl;
 }
 
-void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb,
+void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, int *err,
                     cudaStream_t st)
 {
     if (pl->npairs == 0) return;
+    if (pl->tc) {
+        WfarChunks ch;
+        ch.nch = pl->nch;
+        ch.R = pl->R;
+        ch.Rp = pl->Rp;
+        ch.Kp = pl->Kp;
+        for (int c = 0; c < WF_MAXCH; ++c) {
+            ch.cj0[c] = pl->cj0[c];
+            ch.cj1[c] = pl->cj1[c];
+        }
+        for (int c = 0; c <= WF_MAXCH; ++c) ch.ckoff[c] = pl->ckoff[c];
+        int64_t nH = (int64_t)pl->ndsrc * pl->Rp * pl->Kp;
+        k_wfar_H_tc<<<nblocks(nH, 256), 256, 0, st>>>(pl->ndsrc, pl->P, PMT, ch, pl->slot_box, pb, Mu, pl->H_tc);
+        QBX_LAUNCH_CHECK();
+        int dev = 0, nsm = 0;
+        QBX_CUDA_TRY(cudaGetDevice(&dev));
+        QBX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int cols = 32;
+        while (cols < pl->Rp) cols <<= 1;
+        WfarTcArgs a{pl->ntc, pl->P, pl->Q, pl->P + pl->Q, pl->R, pl->Rp, pl->WMAX, cols, ch, pl->tc_tiles,
+                     pl->pair_ctr, pl->slot, pl->H_tc, T->cxyz, T->cr, T->cen, T->hw, T->np[KCTR], pl->Y, err};
+        const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, pl->Q);
+        const int grid = std::min(pl->ntc, nsm);
+        if (pl->NU == 12) k_wfar_tc<12><<<grid, 256, sm, st>>>(a);
+        else k_wfar_tc<18><<<grid, 256, sm, st>>>(a);
+        QBX_LAUNCH_CHECK();
+        return;
+    }
     int64_t nH = (int64_t)pl->ndsrc * pl->R * pl->K;
     k_wfar_H<<<nblocks(nH, 256), 256, 0, st>>>(pl->ndsrc, pl->P, pl->Q, PMT, pl->slot_box, pb, Mu, pl->H);
     QBX_LAUNCH_CHECK();

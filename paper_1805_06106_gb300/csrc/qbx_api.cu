@@ -183,7 +183,7 @@ int qbx_eval(const qbx_tree *T, const qbx_lists *L, const double *w, const doubl
         if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
         if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
         if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
-        if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32)
+        if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32 && o->precision != QBX_M2L_3XTF32)
             throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
         if (o->p_qbx < 0 || o->p_qbx > QMAX) throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
         if (o->p_fmm < 0 || o->p_fmm > PMAX) throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
