@@ -498,6 +498,162 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
+def forest_inputs(G, torch, dev, surfs, dens, n_max, t_tgt=None):
+    """Trees, lists and the forest of many surfaces; concatenated evaluation inputs (single layer)."""
+    def cu(a, dt=torch.float64):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
+
+    trees, lists = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in surfs:
+        T = G.qbx_build_tree(cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(s.tgt_xyz), n_max=n_max, t_f=T_F)
+        trees.append(T)
+        lists.append(G.qbx_build_lists(T))
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    F, FL = G.qbx_build_forest(trees, lists)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    off = F.offsets
+    w = cu(np.concatenate([s.src_w for s in surfs]))
+    sg = cu(np.concatenate(dens))
+    nrm = cu(np.concatenate([s.src_n for s in surfs], axis=1))
+    tc = cu(np.concatenate([s.tgt_ctr + off["ctr"][i] for i, s in enumerate(surfs)]).astype(np.int32), torch.int32)
+    return dict(trees=trees, lists=lists, F=F, FL=FL, ev=(w, sg, None, nrm, tc), build_ms=1e3 * (t1 - t0),
+                forest_ms=1e3 * (t2 - t1))
+
+
+def run_batched(args):
+    """Many surfaces of uneven size in one forest: learned orders + split-TF32 tensor-core
+    translations replayed as one CUDA graph, against plain FP64 on the same surfaces."""
+    import torch
+
+    import paper_1805_06106_gb300 as G
+    from paper_1805_06106_gb300 import autotune, learned
+    from synth import batched_specs, make_surface, random_harmonic_density, star_radius
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    specs = batched_specs(args.batch, seed=5)
+    t0 = time.perf_counter()
+    surfs = [make_surface(n, star_radius(terms)) for n, terms, _ in specs]
+    dens = [random_harmonic_density(s, 10, seed) for s, (_, _, seed) in zip(surfs, specs)]
+    synth_s = time.perf_counter() - t0
+    n_qbx = int(sum(s.n_ctr for s in surfs))
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        tuned = autotune.tuned_n_max(G, surfs, dens, P_QBX, P_FMM, G.QBX_M2L_3XTF32, default=N_MAX_MIXED,
+                                     candidates=(32, 48, 64, 96), enabled=not args.no_tune)
+        n_max = args.n_max or tuned["n_max"]
+        fi = forest_inputs(G, torch, dev, surfs, dens, n_max)
+        F, FL, ev = fi["F"], fi["FL"], fi["ev"]
+        params, (mq, mp), info = learned_setup(G, n_max)
+        # features per surface (each normalised by its own densities), orders on the forest
+        preds = []
+        for i, (T, L) in enumerate(zip(fi["trees"], fi["lists"])):
+            o = F.offsets["src"]
+            sl = slice(o[i], o[i + 1])
+            feats = G.qbx_center_features(T, L, ev[0][sl].contiguous(), ev[1][sl].contiguous(), None,
+                                          ev[3][:, sl].contiguous())
+            preds.append(G.qbx_mlp_forward(params, feats))
+        qc, pb = G.qbx_orders_from_mlp(F, FL, torch.cat(preds), mq, mp, 2, P_QBX, 4, P_FMM, P_FMM)
+        pot = torch.empty(int(F.info.n_tgt), dtype=torch.float64, device=dev)
+        graph = G.qbx_graph_create(F, FL, *ev, P_QBX, P_FMM, pot, p_qbx_per_ctr=qc, p_fmm_per_box=pb,
+                                   precision=G.QBX_M2L_3XTF32)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        for _ in range(max(args.warmup, 3)):
+            graph.launch()
+        torch.cuda.synchronize()
+        res = pot.clone()
+        times = []
+        clk = ClockSampler(local)
+        clk.__enter__()
+        try:
+            for _ in range(args.steps):
+                flush.fill_(1)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                graph.launch()
+                e1.record(stream)
+                e1.synchronize()
+                times.append(e0.elapsed_time(e1))
+        finally:
+            clk.__exit__(None, None, None)
+        det = bool(torch.equal(pot, res))
+        # end to end: pinned host densities in, potentials out, around the graph replay
+        h_sig = ev[1].cpu().pin_memory()
+        h_out = torch.empty_like(pot, device="cpu").pin_memory()
+        e2e = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            ev[1].copy_(h_sig, non_blocking=True)
+            graph.launch()
+            h_out.copy_(pot, non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e2e.append(e0.elapsed_time(e1))
+        # plain FP64 on the same surfaces at its own leaf size, and FP64 at the learned run's tree
+        ref_same = G.qbx_eval(F, FL, *ev, P_QBX, P_FMM)
+        torch.cuda.synchronize()
+        errs = []
+        for i in range(len(surfs)):
+            o = F.offsets["tgt"]
+            a, b = res[o[i]:o[i + 1]], ref_same[o[i]:o[i + 1]]
+            errs.append(float((a - b).abs().max() / b.abs().max()))
+        build_ms, forest_ms = fi["build_ms"], fi["forest_ms"]
+        del fi
+        fp = forest_inputs(G, torch, dev, surfs, dens, N_MAX)
+        ptmp = torch.empty_like(pot)
+        G.qbx_eval(fp["F"], fp["FL"], *fp["ev"], P_QBX, P_FMM, out=ptmp)
+        torch.cuda.synchronize()
+        pt = []
+        for _ in range(args.fp64_steps):
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            G.qbx_eval(fp["F"], fp["FL"], *fp["ev"], P_QBX, P_FMM, out=ptmp)
+            e1.record(stream)
+            e1.synchronize()
+            pt.append(e0.elapsed_time(e1))
+    ms = statistics.mean(times)
+    value = ws * n_qbx / (ms * 1e-3)
+    plain = n_qbx / (statistics.mean(pt) * 1e-3)
+    qn, pn = qc.cpu().numpy().astype(int), pb.cpu().numpy().astype(int)
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "QBX target evals/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64 (List 2 M2L and List 3 far M2QBXL products as split-tf32 tensor-core MMAs, f32 accumulation)",
+        "data": "synthetic",
+        "config": {"workload": f"{len(surfs)} star surfaces r=1+a ReY_k^(k/2), k in 2..10, a in [0.1,0.4], "
+                               f"lognormal sizes ({int(sum(s.n_src for s in surfs))} sources, {n_qbx} QBX targets), "
+                               "random Y_n^m (n<=10) single-layer densities; one forest, one CUDA graph",
+                   "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": n_max, "n_max_source": tuned["source"], "t_f": T_F,
+                   "sizes_src": [int(s.n_src) for s in surfs], "n_boxes": int(F.n_boxes),
+                   "l2": "flushed between timed steps (512 MiB write)", "synth_s": synth_s,
+                   "tree_lists_build_ms": build_ms, "forest_build_ms": forest_ms},
+        "e2e": {"value": ws * n_qbx * len(e2e) / (sum(e2e) * 1e-3), "unit": "QBX target evals/s",
+                "h2d_bytes_per_step": int(h_sig.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8)},
+        "gpu_launches": None, "deterministic": det,
+        "rel_err_vs_fp64_same_tree_max": max(errs),
+        "plain_fp64": {"value": plain, "ms_per_step": statistics.mean(pt), "n_max": N_MAX, "steps": args.fp64_steps},
+        "speedup_vs_plain_fp64": value / plain,
+        "learned_orders": {**info, "mean_p_qbx": float(qn.mean()), "mean_p_fmm_box": float(pn.mean())},
+        "autotune": tuned, "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -513,10 +669,16 @@ def main():
                     help="fp64: every stage FP64; fp32: List 2 M2L and List 3 far M2QBXL as FP32 products; "
                          "learned: fp32 with per-center / per-box orders from the trained network")
     ap.add_argument("--fp64-steps", type=int, default=5, help="timed steps of the plain FP64 comparison")
+    ap.add_argument("--workload", choices=("star8k", "batched"), default="star8k",
+                    help="star8k: one 120k-source star surface; batched: many surfaces in one forest and graph")
+    ap.add_argument("--batch", type=int, default=64, help="surfaces of the batched workload")
+    ap.add_argument("--no-tune", action="store_true", help="batched: skip the leaf-size autotuner")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batched":
+        run_batched(args)
     else:
         run_gpu(args)
 

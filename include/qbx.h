@@ -50,6 +50,7 @@ extern "C" {
 
 typedef struct qbx_tree qbx_tree;
 typedef struct qbx_lists qbx_lists;
+typedef struct qbx_graph qbx_graph;
 
 typedef struct {
     int n_max;       /* split boxes owning more than n_max particles (Algorithm 4, Stage 1); >= 1 */
@@ -229,6 +230,63 @@ int qbx_mlp_train(float *params_dev, float *adam_m_dev, float *adam_v_dev, const
 int qbx_orders_from_mlp(const qbx_tree *tree, const qbx_lists *lists, const float *pred_dev, float margin_q,
                         float margin_p, int q_lo, int q_hi, int p_lo, int p_hi, int p_default,
                         int8_t *p_qbx_per_ctr_dev, int8_t *p_fmm_per_box_dev, void *stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Batched problems and captured evaluations.  Not steps of the paper's method: they run
+ * Algorithm 4 on many independent surfaces at once (each evaluation stage is one launch over
+ * every surface) and replay an evaluation as one CUDA graph, as repeated evaluation inside an
+ * iterative solver (Section 6.2 solves with GMRES) does with fixed geometry.
+ * ------------------------------------------------------------------------------------------ */
+
+/*
+ * Concatenates n_problems built trees and their lists into one forest.  Problem i's boxes,
+ * sources, centers and targets follow those of problems 0..i-1 (offsets from
+ * qbx_forest_offsets); its list entries are shifted accordingly, so no list crosses problems.
+ * The forest is a tree handle for qbx_eval, qbx_eval_order_sweep, the learned-order calls,
+ * qbx_graph_create and qbx_tree_export, with input arrays concatenated in problem order (point
+ * arrays as (3, total) structure of arrays) and tgt_ctr holding forest center indices (a
+ * problem's own center index plus its center offset, or -1).  qbx_build_lists rejects a forest.
+ *   trees_host, lists_host: host arrays of n_problems >= 1 handles, lists_host[i] built from
+ *   trees_host[i]; they are copied (the originals may be freed afterwards).
+ *   forest_out, lists_out: receive new handles (free the lists before the forest).
+ * Errors: QBX_ERR_INVALID_ARG (mismatched handles, a forest inside a forest, more than 2^31 - 1
+ * boxes, particles or list entries), QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_build_forest(int n_problems, const qbx_tree *const *trees_host, const qbx_lists *const *lists_host,
+                     qbx_tree **forest_out, qbx_lists **lists_out, void *stream);
+
+/* Number of problems of a forest (1 for a tree). */
+int qbx_forest_problems(const qbx_tree *forest, int *n_problems_host);
+
+/* Offsets of each problem: offsets_host[k * (n + 1) + i], k = 0 boxes, 1 sources, 2 centers,
+ * 3 targets, i = 0..n (entry n is the total); 4 (n + 1) int64 values. */
+int qbx_forest_offsets(const qbx_tree *forest, int64_t *offsets_host);
+
+/*
+ * Captures one qbx_eval with exactly these arguments into a CUDA graph.  Runs one evaluation
+ * eagerly first (argument checks, workspace and plans), then captures a second on `stream`
+ * (which must not be the legacy default stream) and instantiates it; pot holds a valid result
+ * on return.  qbx_graph_launch replays it on any stream: the pointers are baked in, so callers
+ * change densities by overwriting the same device arrays.  Profiling is off inside the graph.
+ * Errors: as qbx_eval, QBX_ERR_INVALID_ARG for a NULL stream.
+ */
+int qbx_graph_create(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev, const double *sigma_dev,
+                     const double *mu_dev, const double *src_n_dev, const int32_t *tgt_ctr_dev,
+                     const qbx_eval_opts *opts, double *pot_dev, qbx_graph **out, void *stream);
+int qbx_graph_launch(qbx_graph *graph, void *stream);
+void qbx_graph_free(qbx_graph *graph);
+
+/*
+ * Launch-shape hints of the tensor-core translation kernels (QBX_M2L_3XTF32), used by later
+ * evaluations on these lists (the plans are rebuilt when a hint changes); results do not depend
+ * on them beyond FP32 rounding of the chunked accumulation.  0 selects the library default.
+ *   m2l_kchunk:     K columns per pipeline stage of the List 2 products: 0, 16 or 32.
+ *   m2qbxl_kchunk:  cap on the K columns per stage of the List 3 far products: 0 or a multiple of
+ *                   8 in [16, 128]; raised to what one harmonic degree needs and lowered to what
+ *                   shared memory holds.
+ * Errors: QBX_ERR_INVALID_ARG.
+ */
+int qbx_lists_set_tiles(qbx_lists *lists, int m2l_kchunk, int m2qbxl_kchunk);
 
 /*
  * Per-stage timing (tracing aid; not a step of the paper's method).  While enabled,

@@ -27,4 +27,8 @@ from .binding import (  # noqa: F401
     qbx_mlp_loss_grad,
     qbx_mlp_train,
     qbx_orders_from_mlp,
+    Graph,
+    qbx_build_forest,
+    qbx_graph_create,
+    qbx_lists_set_tiles,
 )

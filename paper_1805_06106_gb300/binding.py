@@ -71,6 +71,14 @@ def lib():
         L.qbx_mlp_train.argtypes = [P, P, P, P, P, I64, C.c_int, C.c_int, C.c_float, P, P]
         L.qbx_orders_from_mlp.argtypes = [P, P, P, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                           P, P, P]
+        L.qbx_build_forest.argtypes = [C.c_int, P, P, C.POINTER(P), C.POINTER(P), P]
+        L.qbx_forest_problems.argtypes = [P, C.POINTER(C.c_int)]
+        L.qbx_forest_offsets.argtypes = [P, P]
+        L.qbx_graph_create.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, C.POINTER(P), P]
+        L.qbx_graph_launch.argtypes = [P, P]
+        L.qbx_graph_free.argtypes = [P]
+        L.qbx_graph_free.restype = None
+        L.qbx_lists_set_tiles.argtypes = [P, C.c_int, C.c_int]
         L.qbx_profile.argtypes = [P, C.c_int]
         L.qbx_profile_read.argtypes = [P, P]
         L.qbx_last_error.restype = C.c_char_p
@@ -291,6 +299,68 @@ def qbx_orders_from_mlp(tree: Tree, lists: Lists, pred, margin_q, margin_p, q_lo
                                      float(margin_p), q_lo, q_hi, p_lo, p_hi, p_default, _ptr(qc), _ptr(pb),
                                      _stream()))
     return qc, pb
+
+
+def qbx_lists_set_tiles(lists: Lists, m2l_kchunk=0, m2qbxl_kchunk=0):
+    """Launch-shape hints of the tensor-core translation kernels (0 = library default)."""
+    _check(lib().qbx_lists_set_tiles(lists.handle, int(m2l_kchunk), int(m2qbxl_kchunk)))
+
+
+# ---------------------------------------------------------------- batched problems and graphs
+
+
+def qbx_build_forest(trees, lists):
+    """Concatenate built trees and their lists into one forest: returns (Tree, Lists).
+
+    The returned Tree has `offsets` (dict of int64 prefix sums per problem: boxes, src, ctr, tgt)."""
+    n = len(trees)
+    if n != len(lists) or n == 0:
+        raise ValueError("need matching, non-empty lists of trees and lists")
+    th = (C.c_void_p * n)(*[t.handle for t in trees])
+    lh = (C.c_void_p * n)(*[x.handle for x in lists])
+    fh, flh = C.c_void_p(), C.c_void_p()
+    _check(lib().qbx_build_forest(n, th, lh, C.byref(fh), C.byref(flh), _stream()))
+    F = Tree(fh)
+    FL = Lists(flh, F)
+    off = (C.c_int64 * (4 * (n + 1)))()
+    _check(lib().qbx_forest_offsets(fh, off))
+    vals = list(off)
+    F.offsets = {k: vals[i * (n + 1):(i + 1) * (n + 1)] for i, k in enumerate(("boxes", "src", "ctr", "tgt"))}
+    F.n_problems = n
+    return F, FL
+
+
+class Graph:
+    """A captured qbx_eval (qbx_graph_create); launch() replays it on the current stream."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep  # tensors whose pointers are baked into the graph
+
+    def launch(self):
+        _check(lib().qbx_graph_launch(self.handle, _stream()))
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.qbx_graph_free(self.handle)
+            self.handle = None
+
+
+def qbx_graph_create(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr, p_qbx, p_fmm, out,
+                     p_qbx_per_ctr=None, p_fmm_per_box=None, precision=QBX_FP64) -> Graph:
+    """Capture one evaluation into a CUDA graph (needs a non-default current stream); `out` receives
+    the potentials of every replay.  The graph keeps references to every tensor it reads."""
+    w = _dev(src_w, torch.float64)
+    sg, m, n = _dev(sigma, torch.float64), _dev(mu, torch.float64), _dev(src_n, torch.float64)
+    tc = _dev(tgt_ctr, torch.int32)
+    qc, pb = _dev(p_qbx_per_ctr, torch.int8), _dev(p_fmm_per_box, torch.int8)
+    out = _dev(out, torch.float64)
+    opts = _EvalOpts(p_qbx, p_fmm, None if qc is None else qc.data_ptr(), None if pb is None else pb.data_ptr(),
+                     precision)
+    h = C.c_void_p()
+    _check(lib().qbx_graph_create(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc),
+                                  C.byref(opts), _ptr(out), C.byref(h), _stream()))
+    return Graph(h, (tree, lists, w, sg, m, n, tc, qc, pb, out))
 
 
 def library_path() -> str:

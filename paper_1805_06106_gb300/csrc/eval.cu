@@ -28,7 +28,7 @@ constexpr double INV4PI = 0.079577471545947667884;  // 1 / (4 pi)
 struct M2LPlan;
 void free_m2l_plan(M2LPlan *p);
 M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, bool tc,
-                        cudaStream_t st);
+                        int kc_hint, cudaStream_t st);
 void m2l_mixed_run(const qbx_tree *T, const qbx_lists *L, M2LPlan *pl, int PMT, const double2 *Mu, double2 *B,
                    const signed char *pb, int *err, cudaStream_t st);
 int m2l_plan_order(const M2LPlan *p);
@@ -36,7 +36,7 @@ struct WfarPlan;
 void free_wfar_plan(WfarPlan *p);
 int wfar_plan_orders(const WfarPlan *p);
 const int *wfar_empty_start(const WfarPlan *p);
-WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, cudaStream_t st);
+WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, int w_hint, cudaStream_t st);
 void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, int *err,
                     cudaStream_t st);
 void wfar_mixed_reduce(const qbx_tree *T, WfarPlan *pl, int QMS, const signed char *qc, double2 *A, cudaStream_t st);
@@ -55,7 +55,8 @@ struct qbx_workspace {
     std::vector<int> lvl_first;    // host copies of level ranges
     qbx::M2LPlan *m2l = nullptr;   // mixed-precision List 2 plan (built on first use)
     qbx::WfarPlan *wfar = nullptr; // mixed-precision List 3 far plan (built on first use)
-    int wfar_key = -1;             // (orders, form) the List 3 far plan was built for
+    int wfar_key = -1;             // (orders, form, tile) the List 3 far plan was built for
+    int m2l_key = -1;              // (order, form, tile) the List 2 plan was built for
 };
 
 namespace qbx {
@@ -221,12 +222,14 @@ __global__ void k_p2m(int64_t nb, const int *own_start, const double *sxyz, int6
 
 // M2M (Stage 2, postorder by level): one warp per parent, lanes over output coefficients.
 template <int PM>
-__global__ void k_m2m(int b0, int b1, const int *child, const int *nsrc_sub, const signed char *pb,
-                      const double2 *oct, double2 *Mu)
+__global__ void k_m2m(int b0, int b1, const int *lvl_boxes, const int *child, const int *nsrc_sub,
+                      const signed char *pb, const double2 *oct, double2 *Mu)
 {
     int b = b0 + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
-    if (b >= b1 || nsrc_sub[b] == 0) return;
+    if (b >= b1) return;
+    if (lvl_boxes) b = lvl_boxes[b];
+    if (nsrc_sub[b] == 0) return;
     const int P = pb[b];
     bool any = false;
     for (int o = 0; o < 8; ++o) any |= child[8 * b + o] >= 0;
@@ -398,12 +401,14 @@ __global__ void k_p2l(int64_t nb, const int *xs, const int *xi, const int *own_s
 // ---------------------------------------------------------------- L2L (Stage 7), by level
 
 template <int PM>
-__global__ void k_l2l(int b0, int b1, const int *parent, const int *ntgt_sub, const int *child, const signed char *pb,
-                      const double2 *oct, double2 *B)
+__global__ void k_l2l(int b0, int b1, const int *lvl_boxes, const int *parent, const int *ntgt_sub, const int *child,
+                      const signed char *pb, const double2 *oct, double2 *B)
 {
     int b = b0 + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
     int lane = threadIdx.x & 31;
-    if (b >= b1 || ntgt_sub[b] == 0) return;
+    if (b >= b1) return;
+    if (lvl_boxes) b = lvl_boxes[b];
+    if (ntgt_sub[b] == 0) return;
     int pa = parent[b];
     if (pa < 0) return;
     int o = 0;
@@ -455,6 +460,7 @@ __device__ __forceinline__ void p2qbxl_accum(double bx, double by, double bz, do
         ar[0] += q * rinv;
     }
     const double hdx = 0.5 * dx, hdy = 0.5 * dy;
+    const double nq = -q, ndz = -dz, nhdx = -hdx;
 #pragma unroll
     for (int n = 1; n <= QM + 1; ++n) {
         if (n > Q + (dip ? 1 : 0)) break;
@@ -490,20 +496,24 @@ __device__ __forceinline__ void p2qbxl_accum(double bx, double by, double bz, do
             if (k <= QM) {
 #pragma unroll
                 for (int l = 0; l <= k && k <= QM; ++l) {
-                    double vr = q * s1r[l] + dz * s0r[l];
-                    double vi = q * s1i[l] + dz * s0i[l];
-                    // (dbar/2) S^{l+1}: (hdx - i hdy)(ur + i ui)
-                    double ur = s0r[l + 1], ui = s0i[l + 1];
-                    vr += hdx * ur + hdy * ui;
-                    vi += hdx * ui - hdy * ur;
-                    // -(d/2) S^{l-1}, S^{-1} = -conj S^1
+                    // (dbar/2) S^{l+1} = (hdx - i hdy)(ur + i ui); -(d/2) S^{l-1} with S^{-1} = -conj S^1:
+                    //   Re: q S_k^l + dz S_n^l + hdx (ur - tr) + hdy (ui + ti)
+                    //   Im: q S_k^l + dz S_n^l + hdx (ui - ti) - hdy (ur + tr), accumulated conjugated
+                    const double ur = s0r[l + 1], ui = s0i[l + 1];
                     double tr, ti;
                     if (l >= 1) { tr = s0r[l - 1]; ti = s0i[l - 1]; }
                     else { tr = -s0r[1]; ti = s0i[1]; }
-                    vr -= hdx * tr - hdy * ti;
-                    vi -= hdx * ti + hdy * tr;
-                    ar[tri(k, l)] += vr;
-                    ai[tri(k, l)] -= vi;
+                    double xr = ar[tri(k, l)], xi = ai[tri(k, l)];
+                    xr = fma(q, s1r[l], xr);
+                    xr = fma(dz, s0r[l], xr);
+                    xr = fma(hdx, ur - tr, xr);
+                    xr = fma(hdy, ui + ti, xr);
+                    xi = fma(nq, s1i[l], xi);
+                    xi = fma(ndz, s0i[l], xi);
+                    xi = fma(nhdx, ui - ti, xi);
+                    xi = fma(hdy, ur + tr, xi);
+                    ar[tri(k, l)] = xr;
+                    ai[tri(k, l)] = xi;
                 }
             }
         }
@@ -555,6 +565,7 @@ __global__ void __launch_bounds__(128) k_centers(
             while ((n + 1) * (n + 1) <= in) ++n;
             int m = in - n * n - n;
             double2 bv = cscale(sym_get(Lb, n, m), pw[n]);
+            const double nby = -bv.y;
 #pragma unroll
             for (int k = 0; k <= QM; ++k) {
                 if (k > Q || k > n) break;
@@ -564,8 +575,8 @@ __global__ void __launch_bounds__(128) k_centers(
                     int mi = m - l;
                     if (mi < -j || mi > j) continue;
                     double2 rv = sym_get(tab, j, mi);
-                    ar[tri(k, l)] += bv.x * rv.x - bv.y * rv.y;
-                    ai[tri(k, l)] += bv.x * rv.y + bv.y * rv.x;
+                    ar[tri(k, l)] = fma(bv.x, rv.x, fma(nby, rv.y, ar[tri(k, l)]));
+                    ai[tri(k, l)] = fma(bv.x, rv.y, fma(bv.y, rv.x, ai[tri(k, l)]));
                 }
             }
         }
@@ -589,14 +600,15 @@ __global__ void __launch_bounds__(128) k_centers(
             while ((n + 1) * (n + 1) <= in) ++n;
             int m = in - n * n - n;
             double2 mv = cscale(sym_get(Md, n, m), pw[n]);
+            const double nmy = -mv.y;
 #pragma unroll
             for (int k = 0; k <= QM; ++k) {
                 if (k > Q) break;
 #pragma unroll
                 for (int l = 0; l <= k; ++l) {
                     double2 sv = cconj(sym_get(tab, n + k, m + l));
-                    ar[tri(k, l)] += mv.x * sv.x - mv.y * sv.y;
-                    ai[tri(k, l)] += mv.x * sv.y + mv.y * sv.x;
+                    ar[tri(k, l)] = fma(mv.x, sv.x, fma(nmy, sv.y, ar[tri(k, l)]));
+                    ai[tri(k, l)] = fma(mv.x, sv.y, fma(mv.y, sv.x, ai[tri(k, l)]));
                 }
             }
         }
@@ -897,7 +909,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     QBX_LAUNCH_CHECK();
     for (int l = (int)T->nlev - 2; l >= 0; --l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
-        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->child, T->nsrc_sub, ws->pb, ws->oct_tab,
+        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws->pb, ws->oct_tab,
                                                                 ws->Mu);
         QBX_LAUNCH_CHECK();
     }
@@ -911,10 +923,12 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     } else {
         const int Pm = o->p_fmm;
         const bool tc = o->precision == QBX_M2L_3XTF32;
-        if (!ws->m2l || m2l_plan_order(ws->m2l) != Pm * 2 + (tc ? 1 : 0)) {
+        const int mkey = (Pm * 2 + (tc ? 1 : 0)) * 64 + L->tile_m2l_kc;
+        if (!ws->m2l || ws->m2l_key != mkey) {
             free_m2l_plan(ws->m2l);
             ws->m2l = nullptr;
-            ws->m2l = m2l_plan_build(T, L, Pm, PM_T, ws->m2l_tab, tc, st);
+            ws->m2l = m2l_plan_build(T, L, Pm, PM_T, ws->m2l_tab, tc, L->tile_m2l_kc, st);
+            ws->m2l_key = mkey;
         }
         m2l_mixed_run(T, L, ws->m2l, PM_T, ws->Mu, ws->B, ws->pb, ws->flags, st);
     }
@@ -927,7 +941,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     stage_mark(L, 4, st);
     for (int l = 1; l < T->nlev; ++l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
-        k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->parent, T->ntgt_sub, T->child, ws->pb,
+        k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->parent, T->ntgt_sub, T->child, ws->pb,
                                                                 ws->oct_tab, ws->B);
         QBX_LAUNCH_CHECK();
     }
@@ -937,11 +951,12 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     if (o->precision != QBX_FP64 && T->np[KCTR] > 0) {
         const int Pm = o->p_fmm, Qm = o->p_qbx;
         const bool tc = o->precision == QBX_M2L_3XTF32;
-        if (!ws->wfar || ws->wfar_key != (Pm * 100 + Qm) * 2 + (tc ? 1 : 0)) {
+        const int wkey = ((Pm * 100 + Qm) * 2 + (tc ? 1 : 0)) * 256 + L->tile_wfar_w;
+        if (!ws->wfar || ws->wfar_key != wkey) {
             free_wfar_plan(ws->wfar);
             ws->wfar = nullptr;
-            ws->wfar = wfar_plan_build(T, L, Pm, Qm, tc, st);
-            ws->wfar_key = (Pm * 100 + Qm) * 2 + (tc ? 1 : 0);
+            ws->wfar = wfar_plan_build(T, L, Pm, Qm, tc, L->tile_wfar_w, st);
+            ws->wfar_key = wkey;
         }
         wf = ws->wfar;
         wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->pb, ws->flags, st);
@@ -1160,7 +1175,7 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     QBX_LAUNCH_CHECK();
     for (int l = (int)T->nlev - 2; l >= 0; --l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
-        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->child, T->nsrc_sub, ws.pb, ws.oct_tab, ws.Mu);
+        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws.pb, ws.oct_tab, ws.Mu);
         QBX_LAUNCH_CHECK();
     }
     k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, (size_t)WPB * ntri(PM_T) * sizeof(double2), st>>>(
@@ -1171,7 +1186,7 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     QBX_LAUNCH_CHECK();
     for (int l = 1; l < T->nlev; ++l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
-        k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->parent, T->ntgt_sub, T->child, ws.pb,
+        k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->parent, T->ntgt_sub, T->child, ws.pb,
                                                                 ws.oct_tab, ws.B);
         QBX_LAUNCH_CHECK();
     }

@@ -42,7 +42,7 @@ struct M2LPlan {
     int4 *tc_tiles = nullptr;     // (offset, first pair, last pair + 1) per 128-pair tile
 };
 
-int m2l_plan_order(const M2LPlan *p) { return p ? p->P * 2 + (p->tc ? 1 : 0) : -1; }
+int m2l_plan_order(const M2LPlan *p) { return p ? (p->P * 2 + (p->tc ? 1 : 0)) * 64 + (p->tc ? p->KC : 0) : -1; }
 
 void free_m2l_plan(M2LPlan *p)
 {
@@ -264,13 +264,9 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
     const int KC = a.KC, Np = a.Np, nch = a.Dp / KC;
     const uint32_t sboA = (uint32_t)KC * 32u + 16u, sboB = (uint32_t)KC * 32u;
     const uint32_t bytesA = 16u * sboA, bytesB = (uint32_t)Np * KC * 4u;
-    unsigned char *Abuf[2][2], *Bbuf[2][2];
-    for (int s = 0; s < 2; ++s) {
-        Abuf[s][0] = smem_tc + (size_t)s * 2 * bytesA;
-        Abuf[s][1] = Abuf[s][0] + bytesA;
-        Bbuf[s][0] = smem_tc + (size_t)4 * bytesA + (size_t)s * 2 * bytesB;
-        Bbuf[s][1] = Bbuf[s][0] + bytesB;
-    }
+    // stage s, part 0 (hi) / 1 (lo) of the A and B tiles
+    auto Abuf = [&](int s, int part) { return smem_tc + (size_t)(2 * s + part) * bytesA; };
+    auto Bbuf = [&](int s, int part) { return smem_tc + (size_t)4 * bytesA + (size_t)(2 * s + part) * bytesB; };
     if (tid == 0) {
         for (int s = 0; s < 2; ++s) {
             tc::mbar_init(&bar_b[s], 1);
@@ -298,20 +294,33 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
             if (__syncthreads_or(!ok)) { ok = false; break; }
             if (tid == 0) {
                 tc::mbar_arrive_expect_tx(&bar_b[s], 2u * bytesB);
-                tc::bulk_g2s(Bbuf[s][0], a.mats + ((int64_t)o * nch + c) * 2 * Np * KC, 2u * bytesB, &bar_b[s]);
+                tc::bulk_g2s(Bbuf(s, 0), a.mats + ((int64_t)o * nch + c) * 2 * Np * KC, 2u * bytesB, &bar_b[s]);
             }
-            const int pieces = KC / 4;
-            for (int q = tid; q < 128 * pieces; q += 256) {
-                int row = q / pieces, pc = q % pieces;
-                float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-                if (row < np) {
+            // eight consecutive threads fill one 128-byte core matrix (rows 8g..8g+7 of one 16-byte
+            // column piece): conflict-free stores, 64-byte row segments per warp in global memory;
+            // all loads of a thread are issued before its stores
+            const int pieces = KC / 4, nq = (128 * pieces) / 256;  // 4 (KC 32) or 2 (KC 16)
+            float4 hv[4], lv[4];
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                hv[it] = lv[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const int q = tid + 256 * it;
+                const int row = (q & 7) + 8 * (q / (8 * pieces)), pc = (q >> 3) % pieces;
+                if (it < nq && row < np) {
                     int64_t src = (int64_t)a.pair_src[p0 + row] * a.Dp + c * KC + 4 * pc;
-                    h = *reinterpret_cast<const float4 *>(a.mh_hi + src);
-                    l = *reinterpret_cast<const float4 *>(a.mh_lo + src);
+                    hv[it] = __ldg(reinterpret_cast<const float4 *>(a.mh_hi + src));
+                    lv[it] = __ldg(reinterpret_cast<const float4 *>(a.mh_lo + src));
                 }
-                uint32_t off = tc::kmajor_off(row, 4 * pc, sboA);
-                *reinterpret_cast<float4 *>(Abuf[s][0] + off) = h;
-                *reinterpret_cast<float4 *>(Abuf[s][1] + off) = l;
+            }
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                const int q = tid + 256 * it;
+                const int row = (q & 7) + 8 * (q / (8 * pieces)), pc = (q >> 3) % pieces;
+                if (it < nq) {
+                    uint32_t off = tc::kmajor_off(row, 4 * pc, sboA);
+                    *reinterpret_cast<float4 *>(Abuf(s, 0) + off) = hv[it];
+                    *reinterpret_cast<float4 *>(Abuf(s, 1) + off) = lv[it];
+                }
             }
             tc::fence_proxy_async();
             __syncthreads();
@@ -319,8 +328,8 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
                 bool got = tc::mbar_wait(&bar_b[s], use & 1, tc::WAIT_LIMIT);
                 if (got) {
                     tc::tc_fence_after();
-                    const uint32_t a_hi = tc::smem_u32(Abuf[s][0]), a_lo = tc::smem_u32(Abuf[s][1]);
-                    const uint32_t b_hi = tc::smem_u32(Bbuf[s][0]), b_lo = tc::smem_u32(Bbuf[s][1]);
+                    const uint32_t a_hi = tc::smem_u32(Abuf(s, 0)), a_lo = tc::smem_u32(Abuf(s, 1));
+                    const uint32_t b_hi = tc::smem_u32(Bbuf(s, 0)), b_lo = tc::smem_u32(Bbuf(s, 1));
                     for (int ks = 0; ks < KC / 8; ++ks) {
                         for (uint32_t h = 0; h < nsplit; ++h) {
                             const uint32_t boff = h * 32u * sboB + 256u * ks, aoff = 256u * ks;
@@ -409,7 +418,7 @@ __global__ void k_scatter_pairs(int nb, const int *vstart, const int *vidx, cons
 }
 
 M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, const double2 *stab, bool tc,
-                        cudaStream_t st)
+                        int kc_hint, cudaStream_t st)
 {
     M2LPlan *pl = new M2LPlan();
     try {
@@ -422,6 +431,7 @@ M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, c
         if (tc) {
             pl->Np = (pl->D + 15) / 16 * 16;
             pl->KC = pl->Np > 256 ? 16 : 32;
+            if (kc_hint == 16 || (kc_hint == 32 && m2l_tc_smem(pl->Np, 32) <= 220 * 1024)) pl->KC = kc_hint;
             pl->Dp = (pl->D + pl->KC - 1) / pl->KC * pl->KC;
             pl->nch = pl->Dp / pl->KC;
             pl->mats_tc = dalloc<float>((int64_t)1331 * pl->Np * pl->Dp * 2);

@@ -42,6 +42,7 @@ struct WfarPlan {
     int Rp = 0, Kp = 0, nch = 0, WMAX = 0, ntc = 0, NU = 0;
     int cj0[WF_MAXCH] = {}, cj1[WF_MAXCH] = {}, ckoff[WF_MAXCH + 1] = {};
     float *H_tc = nullptr;     // ndsrc x Rp x Kp
+    void *recipe = nullptr;    // Rp x Kp WfarRecipe records of the H block
     int4 *tc_tiles = nullptr;  // (source box, first pair, last pair + 1) per 128-pair tile
 };
 
@@ -53,7 +54,7 @@ void free_wfar_plan(WfarPlan *p)
     if (!p) return;
     dfree(p->slot); dfree(p->slot_box); dfree(p->H); dfree(p->pair_ctr); dfree(p->pair_d); dfree(p->pos_cm);
     dfree(p->cm_start); dfree(p->tiles); dfree(p->Y); dfree(p->zero_start);
-    dfree(p->H_tc); dfree(p->tc_tiles);
+    dfree(p->H_tc); dfree(p->tc_tiles); dfree(p->recipe);
     delete p;
 }
 
@@ -162,34 +163,60 @@ struct WfarChunks {
 };
 
 // H of the tensor-core form: for each slot and chunk c, Rp rows x W_c columns (W_c = ckoff[c+1] -
-// ckoff[c]) as a K-major tile with SBO = 32 W_c, FP32 (split into TF32 parts when loaded).
-__global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, WfarChunks ch, const int *slot_box, const signed char *pb,
-                            const double2 *Mu, float *H)
+// ckoff[c]) as a K-major tile with SBO = 32 W_c, FP32 (split into TF32 parts when loaded).  The
+// harmonics it multiplies are scaled per degree (A = S_j^i / D(j), D(j) = sqrt((2j)!)), so entry
+// (row, (j,i,cp)) is the balanced operator entry times D(j) / F(j,i).  Each entry is one or two
+// multipole coefficients times constants: the recipe table (one record per entry, in output order,
+// built once per plan) holds them, and the kernel only gathers and multiplies in FP64.
+struct WfarRecipe {
+    double f1, f2;   // factors of the two terms (signs and scales folded in)
+    int t1, t2;      // tri index of the multipole coefficient, -1 for none
+    int bits;        // bit 0: term 1 takes .y, bit 1: term 2 takes .y, bits 8..: degree n of both terms
+    int pad;
+};
+
+__global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, int64_t per, const WfarRecipe *rec, const int *slot_box,
+                            const signed char *pb, const double2 *Mu, float *H)
 {
     int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t per = (int64_t)ch.Rp * ch.Kp;
     if (idx >= (int64_t)ndsrc * per) return;
-    int s = (int)(idx / per);
-    int rem = (int)(idx % per);
-    int row = rem / ch.Kp, kp = rem % ch.Kp;
-    int c = 0;
-    while (c + 1 < ch.nch && ch.ckoff[c + 1] <= kp) ++c;
-    const int kk = kp - ch.ckoff[c], W = ch.ckoff[c + 1] - ch.ckoff[c];
-    const int nent = ch.cj1[c] * ch.cj1[c] - ch.cj0[c] * ch.cj0[c];
-    double v = 0.0;
-    if (row < ch.R && kk < nent) {
-        int d = slot_box[s];
-        v = wfar_H_entry(row, ch.cj0[c] * ch.cj0[c] + kk, min((int)pb[d], P), Mu + (int64_t)d * ntri(PMT));
+    const int s = (int)(idx / per);
+    const WfarRecipe r = rec[idx % per];
+    const int d = slot_box[s];
+    const int Pd = min((int)pb[d], P);
+    double e = 0.0;
+    if ((r.bits >> 8) <= Pd) {
+        const double2 *M = Mu + (int64_t)d * ntri(PMT);
+        if (r.t1 >= 0) {
+            double2 v = M[r.t1];
+            e = r.f1 * ((r.bits & 1) ? v.y : v.x);
+        }
+        if (r.t2 >= 0) {
+            double2 v = M[r.t2];
+            e = fma(r.f2, (r.bits & 2) ? v.y : v.x, e);
+        }
     }
-    float *tile = H + (int64_t)s * per + (int64_t)ch.ckoff[c] * ch.Rp;
-    tile[tc::kmajor_off(row, kk, (uint32_t)W * 32u) / 4u] = (float)v;
+    H[idx] = (float)e;
 }
 
-// Balanced-harmonic recurrence coefficients: Sh = S / F with F(n,m) = sqrt((n+m)!(n-m)!),
-//   Sh_i^i = sqrt((2i-1)/(2i)) (w/|x|^2) Sh_{i-1}^{i-1},
-//   Sh_j^i = a_j^i (z/|x|^2) Sh_{j-1}^i - b_j^i |x|^-2 Sh_{j-2}^i,
-//   a_j^i = (2j-1)/sqrt((j+i)(j-i)),  b_j^i = sqrt((j+i-1)(j-i-1)/((j+i)(j-i))).
-__constant__ double c_ra[ntri(40)], c_rb[ntri(40)], c_rg[41];
+// Unit-vector harmonics scaled per degree: Yh_j^i = |x|^{j+1} S_j^i(x) / D(j) obey
+//   Yh_0^0 = 1,  Yh_i^i = a_i (x + i y)/|x| Yh_{i-1}^{i-1},
+//   Yh_j^i = a_j (z/|x|) Yh_{j-1}^i - b_j^i Yh_{j-2}^i,
+//   a_j = sqrt((2j-1)/(2j)),  b_j^i = (j+i-1)(j-i-1) / sqrt(2j (2j-1) (2j-2) (2j-3)),
+// and |Yh_j^i| <= F(j,i)/F(j,j) <= 1.
+__constant__ double c_al[41], c_be[ntri(40)];
+
+// IEEE double -> float by truncation of the significand (values of magnitude below the float
+// normal range become 0); integer operations only, so the FP64 pipe is left to the recurrence.
+__device__ __forceinline__ float dbl_to_f32_trunc(double v)
+{
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int e = (hi >> 20) & 0x7ff;
+    if (e < 897) return 0.0f;
+    const unsigned mant = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);
+    return __uint_as_float(((unsigned)hi & 0x80000000u) | ((unsigned)(e - 896) << 23) | mant);
+}
 
 struct WfarTcArgs {
     int ntiles, P, Q, PQ, R, Rp, WMAX, tmem_cols;
@@ -219,13 +246,9 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
     const int Q = a.Q, PQ = a.PQ, Rp = a.Rp, WMAX = a.WMAX;
     const uint32_t sboA = (uint32_t)WMAX * 32u + 16u;
     const uint32_t bytesA = 16u * sboA, bytesB = (uint32_t)Rp * WMAX * 4u;
-    unsigned char *Abuf[2][2], *Bbuf[2][2];
-    for (int s = 0; s < 2; ++s) {
-        Abuf[s][0] = smem_tc + (size_t)s * 2 * bytesA;
-        Abuf[s][1] = Abuf[s][0] + bytesA;
-        Bbuf[s][0] = smem_tc + (size_t)4 * bytesA + (size_t)s * 2 * bytesB;
-        Bbuf[s][1] = Bbuf[s][0] + bytesB;
-    }
+    // stage s, part 0 (hi) / 1 (lo) of the A and B tiles
+    auto Abuf = [&](int s, int part) { return smem_tc + (size_t)(2 * s + part) * bytesA; };
+    auto Bbuf = [&](int s, int part) { return smem_tc + (size_t)4 * bytesA + (size_t)(2 * s + part) * bytesB; };
     float *Pw = reinterpret_cast<float *>(smem_tc + (size_t)4 * bytesA + (size_t)4 * bytesB);  // 128 x (Q+1)
     float *colF = Pw + 128 * (Q + 1);                                                     // Rp
     int *colK = reinterpret_cast<int *>(colF + Rp);                                       // Rp
@@ -254,9 +277,9 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
         const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
         const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
         const bool valid = p < np;
-        // pair geometry and the diagonal of the balanced irregular harmonics
+        // pair geometry and the diagonals of the scaled unit-vector harmonics of this thread's columns
         double a1r[NU], a1i[NU], a2r[NU], a2i[NU];
-        double zz = 0.0, ir2 = 0.0;
+        double zh = 0.0, rinv = 0.0, rpj = 0.0;
         {
             const double h = a.hw[d], hinv = 1.0 / h;
             double x = 3.0, y = 0.0, z = 0.0;
@@ -267,27 +290,26 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                 y = (a.cxyz[a.nc + c] - a.cen[3 * d + 1]) * hinv;
                 z = (a.cxyz[2 * a.nc + c] - a.cen[3 * d + 2]) * hinv;
             }
-            ir2 = 1.0 / (x * x + y * y + z * z);
-            const double rinv = sqrt(ir2), wr = x * ir2, wi = y * ir2;
-            zz = z * ir2;
+            rinv = 1.0 / sqrt(x * x + y * y + z * z);
+            const double wr = x * rinv, wi = y * rinv;
+            zh = z * rinv;
+            rpj = rinv;  // |x|^{-(j+1)} at the current degree j (starts at j = 0)
             if (par == 0) {
                 const double ratio = valid ? a.cr[c] * hinv : 0.0;
                 double pk = hinv;
                 for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[p * (Q + 1) + k] = (float)pk;
             }
-            double dr = rinv, di = 0.0;  // Sh_0^0
-            if (par == 1) {              // Sh_1^1
-                double g1 = c_rg[1];
-                dr = rinv * wr * g1;
-                di = rinv * wi * g1;
+            double dr = 1.0, di = 0.0;  // Yh_0^0
+            if (par == 1) {             // Yh_1^1
+                dr = c_al[1] * wr;
+                di = c_al[1] * wi;
             }
 #pragma unroll
             for (int u = 0; u < NU; ++u) {
                 const int i = par + 2 * u;
                 a1r[u] = dr; a1i[u] = di; a2r[u] = 0.0; a2i[u] = 0.0;
-                // advance the diagonal by two columns: i -> i + 2
-                if (i + 2 <= 40) {
-                    double ga = c_rg[i + 1], gb = c_rg[i + 2];
+                if (i + 2 <= 40) {  // advance the diagonal i -> i + 2
+                    double ga = c_al[i + 1], gb = c_al[i + 2];
                     double tr = (dr * wr - di * wi) * ga, ti = (dr * wi + di * wr) * ga;
                     dr = (tr * wr - ti * wi) * gb;
                     di = (tr * wi + ti * wr) * gb;
@@ -304,7 +326,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
             // B: chunk of H_d, split into TF32 parts
             {
                 const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[c] * Rp);
-                float4 *dh = reinterpret_cast<float4 *>(Bbuf[s][0]), *dl = reinterpret_cast<float4 *>(Bbuf[s][1]);
+                float4 *dh = reinterpret_cast<float4 *>(Bbuf(s, 0)), *dl = reinterpret_cast<float4 *>(Bbuf(s, 1));
                 for (int q = tid; q < Rp * W / 4; q += 256) {
                     float4 v = src[q], hi, lo;
                     tc::split_tf32(v.x, hi.x, lo.x);
@@ -315,30 +337,35 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                     dl[q] = lo;
                 }
             }
-            // A: harmonics of degrees j0 .. j1-1 for this thread's columns
+            // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's columns; the
+            // recurrence in FP64, the final scaling by |x|^{-(j+1)} in FP32 after the conversion
             if (valid) {
-                unsigned char *Ah = Abuf[s][0], *Al = Abuf[s][1];
+                unsigned char *Ah = Abuf(s, 0), *Al = Abuf(s, 1);
+                for (int j = j0; j < j1; ++j) {
+                    const double c1 = c_al[j] * zh;
+                    const float rf = dbl_to_f32_trunc(rpj);
+                    rpj *= rinv;
+                    const int kb = j * j - j0 * j0;
 #pragma unroll
-                for (int u = 0; u < NU; ++u) {
-                    const int i = par + 2 * u;
-                    if (i <= PQ) {
-                        for (int j = max(i, j0); j < j1; ++j) {
+                    for (int u = 0; u < NU; ++u) {
+                        const int i = par + 2 * u;
+                        if (i <= j && i <= PQ) {
                             double vr = a1r[u], vi = a1i[u];
                             if (j > i) {
-                                const double al = c_ra[tri(j, i)] * zz, be = c_rb[tri(j, i)] * ir2;
-                                vr = al * a1r[u] - be * a2r[u];
-                                vi = al * a1i[u] - be * a2i[u];
+                                const double bb = c_be[tri(j, i)];
+                                vr = fma(c1, a1r[u], -bb * a2r[u]);
+                                vi = fma(c1, a1i[u], -bb * a2i[u]);
                                 a2r[u] = a1r[u]; a2i[u] = a1i[u];
                                 a1r[u] = vr; a1i[u] = vi;
                             }
-                            const int kk = j * j - j0 * j0 + (i == 0 ? 0 : 2 * i - 1);
+                            const int kk = kb + (i == 0 ? 0 : 2 * i - 1);
                             float hi, lo;
-                            tc::split_tf32((float)vr, hi, lo);
+                            tc::split_tf32(dbl_to_f32_trunc(vr) * rf, hi, lo);
                             uint32_t off = tc::kmajor_off(p, kk, sboA);
                             *reinterpret_cast<float *>(Ah + off) = hi;
                             *reinterpret_cast<float *>(Al + off) = lo;
                             if (i > 0) {
-                                tc::split_tf32((float)vi, hi, lo);
+                                tc::split_tf32(dbl_to_f32_trunc(vi) * rf, hi, lo);
                                 off = tc::kmajor_off(p, kk + 1, sboA);
                                 *reinterpret_cast<float *>(Ah + off) = hi;
                                 *reinterpret_cast<float *>(Al + off) = lo;
@@ -356,8 +383,8 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
             __syncthreads();
             if (tid == 0) {
                 tc::tc_fence_after();
-                const uint32_t a_hi = tc::smem_u32(Abuf[s][0]), a_lo = tc::smem_u32(Abuf[s][1]);
-                const uint32_t b_hi = tc::smem_u32(Bbuf[s][0]), b_lo = tc::smem_u32(Bbuf[s][1]);
+                const uint32_t a_hi = tc::smem_u32(Abuf(s, 0)), a_lo = tc::smem_u32(Abuf(s, 1));
+                const uint32_t b_hi = tc::smem_u32(Bbuf(s, 0)), b_lo = tc::smem_u32(Bbuf(s, 1));
                 const uint32_t sboB = (uint32_t)W * 32u;
                 for (int ks = 0; ks < W / 8; ++ks) {
                     const uint32_t off = 256u * ks;
@@ -557,14 +584,14 @@ __global__ void k_wfar_reduce(int64_t nc, int Q, int QMS, const int *cm_start, c
 }
 
 // Degree chunks of the tensor-core form and its shared-memory budget; false when the orders do not fit.
-static bool wfar_tc_layout(WfarPlan *pl)
+static bool wfar_tc_layout(WfarPlan *pl, int w_hint)
 {
     const int P = pl->P, Q = pl->Q, PQ = P + Q;
     pl->Rp = (pl->R + 15) / 16 * 16;
     if (pl->Rp > 256 || PQ > 35) return false;
     pl->NU = PQ <= 23 ? 12 : 18;
     const int wmin = (2 * PQ + 1 + 7) / 8 * 8;
-    int W = std::max(64, wmin);
+    int W = std::max(w_hint > 0 ? w_hint / 8 * 8 : 64, wmin);
     while (W > wmin && wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) W -= 8;
     if (wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) return false;
     pl->WMAX = W;
@@ -588,19 +615,88 @@ static bool wfar_tc_layout(WfarPlan *pl)
 
 static void set_recurrence_tables(cudaStream_t st)
 {
-    std::vector<double> ra(ntri(40), 0.0), rb(ntri(40), 0.0), rg(41, 0.0);
-    for (int j = 0; j <= 40; ++j)
-        for (int i = 0; i < j; ++i) {
-            ra[tri(j, i)] = (2.0 * j - 1.0) / std::sqrt((double)(j + i) * (double)(j - i));
-            rb[tri(j, i)] = std::sqrt((double)(j + i - 1) * (double)(j - i - 1) / ((double)(j + i) * (double)(j - i)));
-        }
-    for (int i = 1; i <= 40; ++i) rg[i] = std::sqrt((2.0 * i - 1.0) / (2.0 * i));
-    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_ra, ra.data(), ra.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
-    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_rb, rb.data(), rb.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
-    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_rg, rg.data(), rg.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    std::vector<double> al(41, 0.0), be(ntri(40), 0.0);
+    for (int j = 1; j <= 40; ++j) al[j] = std::sqrt((2.0 * j - 1.0) / (2.0 * j));
+    for (int j = 2; j <= 40; ++j)
+        for (int i = 0; i < j; ++i)
+            be[tri(j, i)] = (double)(j + i - 1) * (double)(j - i - 1) /
+                            std::sqrt(2.0 * j * (2.0 * j - 1.0) * (2.0 * j - 2.0) * (2.0 * j - 3.0));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_al, al.data(), al.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_be, be.data(), be.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
 }
 
-WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, cudaStream_t st)
+// F(n, m) = sqrt((n+|m|)! (n-|m|)!) on the host
+static double host_F(int n, int m)
+{
+    m = m < 0 ? -m : m;
+    double f = 1.0;
+    for (int i = 2; i <= n + m; ++i) f *= i;
+    for (int i = 2; i <= n - m; ++i) f *= i;
+    return std::sqrt(f);
+}
+
+static void host_decode(int r, int &n, int &m, int &part)
+{
+    n = (int)std::sqrt((double)r);
+    while (n * n > r) --n;
+    while ((n + 1) * (n + 1) <= r) ++n;
+    int rr = r - n * n;
+    m = (rr + 1) / 2;
+    part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
+}
+
+// Recipe of every entry of the tensor-core H block of one slot, in output order (see k_wfar_H_tc):
+// the operator entry of row (k,l,rp), column (j,i,cp) is a1.c + s a2.c combinations of
+// a1 = M_n^{i-l} F(n+k, i)/F(k,l) and a2 = M_n^{-i-l} F(n+k, -i)/F(k,l) (n = j - k, s = (-1)^i,
+// M_n^{-m} = (-1)^m conj M_n^m), scaled by D(j)/F(j,i).
+static std::vector<WfarRecipe> wfar_recipe(const WfarPlan *pl)
+{
+    std::vector<WfarRecipe> out((size_t)pl->Rp * pl->Kp);
+    for (auto &r : out) r = WfarRecipe{0.0, 0.0, -1, -1, 0, 0};
+    for (int c = 0; c < pl->nch; ++c) {
+        const int W = pl->ckoff[c + 1] - pl->ckoff[c];
+        const int nent = pl->cj1[c] * pl->cj1[c] - pl->cj0[c] * pl->cj0[c];
+        for (int row = 0; row < pl->R; ++row)
+            for (int kk = 0; kk < nent; ++kk) {
+                int k, l, rp, j, i, cp;
+                host_decode(row, k, l, rp);
+                host_decode(pl->cj0[c] * pl->cj0[c] + kk, j, i, cp);
+                const int n = j - k;
+                WfarRecipe rc{0.0, 0.0, -1, -1, 0, 0};
+                if (n >= 0) {
+                    const double colscale = host_F(j, j) / host_F(j, i), inv_kl = 1.0 / host_F(k, l);
+                    const bool take_y = (rp != cp);  // (0,0), (1,1) read .x; (0,1), (1,0) read .y
+                    // sign applied to the chosen component of sym_get(M, n, m)
+                    auto sgn = [&](int m) {
+                        if (m >= 0) return 1.0;
+                        return take_y ? ((m & 1) ? 1.0 : -1.0) : ((m & 1) ? -1.0 : 1.0);
+                    };
+                    const double s = (i & 1) ? -1.0 : 1.0;
+                    // coefficient of a1.c and a2.c in the entry
+                    double w1, w2;
+                    if (rp == 0 && cp == 0) { w1 = 1.0; w2 = s; }
+                    else if (rp == 0 && cp == 1) { w1 = 1.0; w2 = -s; }
+                    else if (rp == 1 && cp == 0) { w1 = 1.0; w2 = s; }
+                    else { w1 = -1.0; w2 = s; }
+                    const int m1 = i - l, m2 = -i - l;
+                    if (m1 >= -n && m1 <= n) {
+                        rc.t1 = tri(n, m1 < 0 ? -m1 : m1);
+                        rc.f1 = w1 * sgn(m1) * host_F(n + k, m1 + l) * inv_kl * colscale;
+                    }
+                    if (i > 0 && m2 >= -n && m2 <= n) {
+                        rc.t2 = tri(n, m2 < 0 ? -m2 : m2);
+                        rc.f2 = w2 * sgn(m2) * host_F(n + k, m2 + l) * inv_kl * colscale;
+                    }
+                    rc.bits = (take_y ? 3 : 0) | (n << 8);
+                }
+                const size_t pos = (size_t)pl->ckoff[c] * pl->Rp + tc::kmajor_off(row, kk, (uint32_t)W * 32u) / 4u;
+                out[pos] = rc;
+            }
+    }
+    return out;
+}
+
+WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, int w_hint, cudaStream_t st)
 {
     WfarPlan *pl = new WfarPlan();
     int *cm_cnt = nullptr, *d_cnt = nullptr, *d_start = nullptr, *flag = nullptr, *tot = nullptr;
@@ -664,7 +760,7 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
         QBX_CUDA_TRY(cudaMemcpyAsync(ds.data(), d_start, (nb + 1) * sizeof(int), cudaMemcpyDeviceToHost, st));
         QBX_CUDA_TRY(cudaStreamSynchronize(st));
         const int WT = wfar_tile_width(pl->K, pl->R);
-        pl->tc = tc && wfar_tc_layout(pl);  // orders beyond the tensor-core layout use the FP32 form
+        pl->tc = tc && wfar_tc_layout(pl, w_hint);  // orders beyond the tensor-core layout use the FP32 form
         if (pl->tc) {
             set_recurrence_tables(st);
             std::vector<int4> tct;
@@ -676,6 +772,13 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
                 QBX_CUDA_TRY(cudaMemcpyAsync(pl->tc_tiles, tct.data(), tct.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                              st));
             pl->H_tc = dalloc<float>((int64_t)std::max(nd, 1) * pl->Rp * pl->Kp);
+            {
+                std::vector<WfarRecipe> rec = wfar_recipe(pl);
+                pl->recipe = dalloc<WfarRecipe>(rec.size());
+                QBX_CUDA_TRY(cudaMemcpyAsync(pl->recipe, rec.data(), rec.size() * sizeof(WfarRecipe),
+                                             cudaMemcpyHostToDevice, st));
+                QBX_CUDA_TRY(cudaStreamSynchronize(st));
+            }
             pl->Y = dalloc<float>((int64_t)std::max(np, 1) * pl->R);
             const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, Q);
             if (pl->NU == 12)
@@ -730,8 +833,10 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
             ch.cj1[c] = pl->cj1[c];
         }
         for (int c = 0; c <= WF_MAXCH; ++c) ch.ckoff[c] = pl->ckoff[c];
-        int64_t nH = (int64_t)pl->ndsrc * pl->Rp * pl->Kp;
-        k_wfar_H_tc<<<nblocks(nH, 256), 256, 0, st>>>(pl->ndsrc, pl->P, PMT, ch, pl->slot_box, pb, Mu, pl->H_tc);
+        const int64_t per = (int64_t)pl->Rp * pl->Kp, nH = (int64_t)pl->ndsrc * per;
+        k_wfar_H_tc<<<nblocks(nH, 256), 256, 0, st>>>(pl->ndsrc, pl->P, PMT, per,
+                                                       static_cast<const WfarRecipe *>(pl->recipe), pl->slot_box, pb,
+                                                       Mu, pl->H_tc);
         QBX_LAUNCH_CHECK();
         int dev = 0, nsm = 0;
         QBX_CUDA_TRY(cudaGetDevice(&dev));

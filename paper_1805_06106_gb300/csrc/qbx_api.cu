@@ -30,9 +30,10 @@ static int guarded(F &&f)
     }
 }
 
-static void free_tree(qbx_tree *T)
+void free_tree(qbx_tree *T)
 {
     if (!T) return;
+    dfree(T->lvl_boxes);
     dfree(T->level); dfree(T->ic); dfree(T->cen); dfree(T->hw); dfree(T->parent); dfree(T->child);
     dfree(T->nsrc_sub); dfree(T->ntgt_sub);
     for (int k = 0; k < 3; ++k) { dfree(T->owner[k]); dfree(T->perm[k]); dfree(T->own_start[k]); }
@@ -41,7 +42,7 @@ static void free_tree(qbx_tree *T)
     delete T;
 }
 
-static void free_lists(qbx_lists *L)
+void free_lists(qbx_lists *L)
 {
     if (!L) return;
     for (int l = 0; l < NLIST; ++l) { dfree(L->start[l]); dfree(L->idx[l]); }
@@ -136,6 +137,7 @@ int qbx_build_lists(const qbx_tree *T, qbx_lists **out, void *stream)
     return guarded([&]() -> int {
         if (!T || !out) throw Error{QBX_ERR_INVALID_ARG, "NULL argument"};
         *out = nullptr;
+        if (T->lvl_boxes) throw Error{QBX_ERR_INVALID_ARG, "a forest gets its lists from qbx_build_forest"};
         qbx_lists *L = new qbx_lists();
         L->tree = T;
         try {
@@ -175,21 +177,125 @@ int qbx_lists_export(const qbx_lists *L, int which, int32_t *start, int32_t *idx
 
 void qbx_lists_free(qbx_lists *L) { free_lists(L); }
 
+static void check_eval_args(const qbx_tree *T, const qbx_lists *L, const double *w, const double *mu,
+                            const double *nrm, const int32_t *tgt_ctr, const qbx_eval_opts *o, const double *pot)
+{
+    if (!T || !L || !o || L->tree != T) throw Error{QBX_ERR_INVALID_ARG, "tree/lists/opts mismatch or NULL"};
+    if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
+    if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
+    if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
+    if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32 && o->precision != QBX_M2L_3XTF32)
+        throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
+    if (o->p_qbx < 0 || o->p_qbx > QMAX) throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
+    if (o->p_fmm < 0 || o->p_fmm > PMAX) throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
+    if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
+        throw Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
+}
+
 int qbx_eval(const qbx_tree *T, const qbx_lists *L, const double *w, const double *sigma, const double *mu,
              const double *nrm, const int32_t *tgt_ctr, const qbx_eval_opts *o, double *pot, void *stream)
 {
     return guarded([&]() -> int {
-        if (!T || !L || !o || L->tree != T) throw Error{QBX_ERR_INVALID_ARG, "tree/lists/opts mismatch or NULL"};
-        if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
-        if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
-        if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
-        if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32 && o->precision != QBX_M2L_3XTF32)
-            throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
-        if (o->p_qbx < 0 || o->p_qbx > QMAX) throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
-        if (o->p_fmm < 0 || o->p_fmm > PMAX) throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
-        if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
-            throw Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
+        check_eval_args(T, L, w, mu, nrm, tgt_ctr, o, pot);
         eval(T, const_cast<qbx_lists *>(L), w, sigma, mu, nrm, tgt_ctr, o, pot, (cudaStream_t)stream);
+        return QBX_OK;
+    });
+}
+
+int qbx_build_forest(int n, const qbx_tree *const *trees, const qbx_lists *const *lists, qbx_tree **forest_out,
+                     qbx_lists **lists_out, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!forest_out || !lists_out || !trees || !lists || n < 1)
+            throw Error{QBX_ERR_INVALID_ARG, "bad forest arguments"};
+        *forest_out = nullptr;
+        *lists_out = nullptr;
+        for (int i = 0; i < n; ++i) {
+            if (!trees[i] || !lists[i] || lists[i]->tree != trees[i])
+                throw Error{QBX_ERR_INVALID_ARG, "tree/lists mismatch or NULL in the forest"};
+            if (trees[i]->lvl_boxes) throw Error{QBX_ERR_INVALID_ARG, "a forest cannot contain a forest"};
+        }
+        qbx_tree *F = new qbx_tree();
+        qbx_lists *FL = new qbx_lists();
+        FL->tree = F;
+        try {
+            build_forest(n, trees, lists, F, FL, (cudaStream_t)stream);
+        } catch (...) {
+            free_lists(FL);
+            free_tree(F);
+            throw;
+        }
+        *forest_out = F;
+        *lists_out = FL;
+        return QBX_OK;
+    });
+}
+
+int qbx_forest_problems(const qbx_tree *T, int *n_host)
+{
+    return guarded([&]() -> int {
+        if (!T || !n_host) throw Error{QBX_ERR_INVALID_ARG, "NULL argument"};
+        *n_host = T->nprob;
+        return QBX_OK;
+    });
+}
+
+int qbx_forest_offsets(const qbx_tree *T, int64_t *off_host)
+{
+    return guarded([&]() -> int {
+        if (!T || !off_host) throw Error{QBX_ERR_INVALID_ARG, "NULL argument"};
+        if (!T->lvl_boxes) {
+            const int64_t v[8] = {0, T->nb, 0, T->np[0], 0, T->np[1], 0, T->np[2]};
+            for (int i = 0; i < 8; ++i) off_host[i] = v[i];
+        } else {
+            for (size_t i = 0; i < T->prob_off.size(); ++i) off_host[i] = T->prob_off[i];
+        }
+        return QBX_OK;
+    });
+}
+
+int qbx_graph_create(const qbx_tree *T, const qbx_lists *L, const double *w, const double *sigma, const double *mu,
+                     const double *nrm, const int32_t *tgt_ctr, const qbx_eval_opts *o, double *pot, qbx_graph **out,
+                     void *stream)
+{
+    return guarded([&]() -> int {
+        if (!out) throw Error{QBX_ERR_INVALID_ARG, "out is NULL"};
+        *out = nullptr;
+        if (!stream) throw Error{QBX_ERR_INVALID_ARG, "graph capture needs a non-default stream"};
+        check_eval_args(T, L, w, mu, nrm, tgt_ctr, o, pot);
+        qbx_graph *g = new qbx_graph();
+        try {
+            capture_eval(T, const_cast<qbx_lists *>(L), w, sigma, mu, nrm, tgt_ctr, o, pot, (cudaStream_t)stream, g);
+        } catch (...) {
+            free_graph(g);
+            throw;
+        }
+        *out = g;
+        return QBX_OK;
+    });
+}
+
+int qbx_graph_launch(qbx_graph *g, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!g || !g->exec) throw Error{QBX_ERR_INVALID_ARG, "graph is NULL"};
+        QBX_CUDA_TRY(cudaGraphLaunch(g->exec, (cudaStream_t)stream));
+        return QBX_OK;
+    });
+}
+
+void qbx_graph_free(qbx_graph *g) { free_graph(g); }
+
+int qbx_lists_set_tiles(qbx_lists *L, int m2l_kchunk, int m2qbxl_kchunk)
+{
+    return guarded([&]() -> int {
+        if (!L) throw Error{QBX_ERR_INVALID_ARG, "lists is NULL"};
+        if (m2l_kchunk != 0 && m2l_kchunk != 16 && m2l_kchunk != 32)
+            throw Error{QBX_ERR_INVALID_ARG, "m2l_kchunk must be 0, 16 or 32"};
+        if (m2qbxl_kchunk != 0 && (m2qbxl_kchunk < 16 || m2qbxl_kchunk > 128 || m2qbxl_kchunk % 8))
+            throw Error{QBX_ERR_INVALID_ARG, "m2qbxl_kchunk must be 0 or a multiple of 8 in [16, 128]"};
+        L->tile_m2l_kc = m2l_kchunk;
+        L->tile_wfar_w = m2qbxl_kchunk;
         return QBX_OK;
     });
 }

@@ -93,9 +93,20 @@ struct qbx_tree {
     int *ctr_box = nullptr;   // owning box of each sorted center
     int *tgt_box = nullptr;   // owning box of each sorted target
     int *ctr_rank = nullptr;  // input center index -> sorted position
+    // forest of several problems (qbx_build_forest): the boxes of level l are
+    // lvl_boxes[level_start[l] .. level_start[l+1]); plain trees keep lvl_boxes == nullptr and
+    // number their boxes by level
+    int *lvl_boxes = nullptr;
+    int nprob = 1;
+    std::vector<int64_t> prob_off;  // 4 x (nprob + 1) prefix sums: boxes, sources, centers, targets
 };
 
 struct qbx_workspace;
+
+struct qbx_graph {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
 
 struct qbx_lists {
     const qbx_tree *tree = nullptr;
@@ -103,6 +114,8 @@ struct qbx_lists {
     int *idx[qbx::NLIST] = {};
     int64_t nnz[qbx::NLIST] = {};
     qbx_workspace *ws = nullptr;
+    int tile_m2l_kc = 0;                     // List 2 tensor-core K chunk (0: library default)
+    int tile_wfar_w = 0;                     // List 3 far tensor-core K chunk cap (0: library default)
     bool prof = false;                       // record stage events in qbx_eval
     bool prof_valid = false;                 // the events hold a finished profiled evaluation
     cudaEvent_t ev[QBX_NSTAGES + 1] = {};
@@ -128,5 +141,13 @@ void prep_sources(const int *perm, int64_t ns, const double *w, const double *si
 void eval_order_sweep(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
                       const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *partial, cudaStream_t st);
 void exclusive_scan(const int *in, int *out, int64_t n, int base_offset, int *total_dev, cudaStream_t st);
+void free_tree(qbx_tree *T);
+void free_lists(qbx_lists *L);
+void build_forest(int n, const qbx_tree *const *trees, const qbx_lists *const *lists, qbx_tree *F, qbx_lists *FL,
+                  cudaStream_t st);
+void free_graph(qbx_graph *g);
+void capture_eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma, const double *mu,
+                  const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *pot, cudaStream_t st,
+                  qbx_graph *g);
 void sort_pairs_by_key(int *keys, int *vals, int64_t n, int key_bits, cudaStream_t st);
 }  // namespace qbx

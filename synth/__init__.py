@@ -16,4 +16,5 @@ from .surfaces import (  # noqa: F401
     random_harmonic_density,
     volume_targets,
     config_surface,
+    batched_specs,
 )

@@ -354,6 +354,22 @@ STAR_Y63 = [(0.3, 6, 3)]
 STAR_Y84_Y52 = [(0.25, 8, 4), (0.15, 5, 2)]
 
 
+def batched_specs(count: int = 64, seed: int = 5):
+    """Specs of the many-surface workload: star surfaces r = 1 + a Re Y_k^{floor(k/2)} with
+    k ~ U{2..10}, a ~ U[0.1, 0.4], and source counts N ~ lognormal(10.36, 0.941) clipped to
+    [5k, 200k], realised as 300 n^2 sources (n = round(sqrt(N / 300)) in [4, 26]).  Returns a list
+    of (n_sub, terms, density_seed) with density seeds 500 + i for random_harmonic_density."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        k = int(rng.integers(2, 11))
+        a = float(rng.uniform(0.1, 0.4))
+        n_target = float(np.clip(rng.lognormal(10.36, 0.941), 5000.0, 200000.0))
+        n = int(np.clip(round(math.sqrt(n_target / 300.0)), 4, 26))
+        out.append((n, [(a, k, k // 2)], 500 + i))
+    return out
+
+
 def config_surface(name: str) -> Surface:
     """Surfaces of the named workloads: sphere320, star8k, star40k, urchin79k."""
     if name == "sphere320":

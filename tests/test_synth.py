@@ -37,3 +37,18 @@ def test_volume_target_association():
     assert np.all(d <= s.ctr_r[ctr[assoc]] * 1.05 + 1e-15)
     far = np.linalg.norm(t, axis=0) > 1.6
     assert not np.any(assoc & far)
+
+
+def test_batched_specs_follow_the_recipe():
+    from synth import batched_specs
+
+    a = batched_specs(64, seed=5)
+    assert a == batched_specs(64, seed=5)  # seeded
+    assert len(a) == 64
+    for n, terms, dseed in a:
+        assert 4 <= n <= 26  # 300 n^2 sources: 4,800 .. 202,800
+        (amp, k, m), = terms
+        assert 2 <= k <= 10 and m == k // 2 and 0.1 <= amp <= 0.4
+    assert [d for _, _, d in a] == list(range(500, 564))
+    total = sum(300 * n * n for n, _, _ in a)
+    assert 1_000_000 < total < 6_000_000
