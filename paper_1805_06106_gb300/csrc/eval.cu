@@ -153,7 +153,8 @@ __global__ void k_check_tgt(const int *tc, int64_t nt, int64_t nc, int *flags)
 // ---------------------------------------------------------------- upward pass
 
 // P2M (Stage 2): one warp per box, lane m computes column m of R_n^m for each source in turn.
-template <int PM>
+// PM bounds the orders (registers, unrolled rows); ST is the coefficient stride of the workspace.
+template <int PM, int ST = PM>
 __global__ void k_p2m(int64_t nb, const int *own_start, const double *sxyz, int64_t ns, const double *sq,
                       const double *sd, const double *cen, const double *hw, const signed char *pb, double2 *Mu)
 {
@@ -216,7 +217,7 @@ __global__ void k_p2m(int64_t nb, const int *own_start, const double *sxyz, int6
     if (m <= P) {
 #pragma unroll
         for (int n = 0; n <= PM; ++n)
-            if (n >= m && n <= P) Mu[(int64_t)b * ntri(PM) + tri(n, m)] = acc[n];
+            if (n >= m && n <= P) Mu[(int64_t)b * ntri(ST) + tri(n, m)] = acc[n];
     }
 }
 
@@ -321,7 +322,7 @@ __global__ void k_m2l(int64_t nb, const int *vstart, const int *vidx, const int6
 // ---------------------------------------------------------------- List 4 far P2L (Stage 6b)
 
 // One warp per box, lane m computes column m of S_n^m((c-s)/h), one source at a time.
-template <int PM>
+template <int PM, int ST = PM>
 __global__ void k_p2l(int64_t nb, const int *xs, const int *xi, const int *own_start, const double *sxyz, int64_t ns,
                       const double *sq, const double *sd, const double *cen, const double *hw, const signed char *pb,
                       double2 *B)
@@ -392,8 +393,8 @@ __global__ void k_p2l(int64_t nb, const int *xs, const int *xi, const int *own_s
 #pragma unroll
         for (int n = 0; n <= PM; ++n)
             if (n >= m && n <= P) {
-                double2 v = B[(int64_t)b * ntri(PM) + tri(n, m)];
-                B[(int64_t)b * ntri(PM) + tri(n, m)] = make_double2(v.x + acc[n].x * hinv, v.y + acc[n].y * hinv);
+                double2 v = B[(int64_t)b * ntri(ST) + tri(n, m)];
+                B[(int64_t)b * ntri(ST) + tri(n, m)] = make_double2(v.x + acc[n].x * hinv, v.y + acc[n].y * hinv);
             }
     }
 }
@@ -614,14 +615,20 @@ __global__ void __launch_bounds__(128) k_centers(
         }
     }
 
-    // Stages 3, 5(a), 6(a): direct P2QBXL from List 1, List 3 close and List 4 close sources
-    const ListRef lists[3] = {lu, lwc, lxc};
+    // Stages 3, 5(a), 6(a): direct P2QBXL from List 1, List 3 close and List 4 close sources, the three
+    // lists walked as one sequence of boxes so that partial batches of 32 sources are rare
     const bool dip = sd != nullptr;
-    for (int li = 0; li < 3; ++li) {
-        const int e0 = lists[li].start[b], e1 = lists[li].start[b + 1];
-        for (int base = e0; base < e1; base += 32) {
+    {
+        const int u0 = lu.start[b], n0 = lu.start[b + 1] - u0;
+        const int w0 = lwc.start[b], n1 = lwc.start[b + 1] - w0;
+        const int x0 = lxc.start[b], n2 = lxc.start[b + 1] - x0;
+        const int e1 = n0 + n1 + n2;
+        for (int base = 0; base < e1; base += 32) {
             int e = base + lane;
-            int d = e < e1 ? lists[li].idx[e] : -1;
+            int d = -1;
+            if (e < n0) d = lu.idx[u0 + e];
+            else if (e < n0 + n1) d = lwc.idx[w0 + e - n0];
+            else if (e < e1) d = lxc.idx[x0 + e - n0 - n1];
             int s0 = d >= 0 ? own_start[d] : 0;
             int cnt = d >= 0 ? own_start[d + 1] - s0 : 0;
             int incl = cnt;
@@ -880,7 +887,6 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         k_oct_table<<<1, 32, 0, st>>>(PM_T, ws->oct_tab);
         QBX_LAUNCH_CHECK();
     }
-    (void)pmax;
     (void)pot;
     stage_mark(L, 0, st);
     QBX_CUDA_TRY(cudaMemsetAsync(ws->flags, 0, sizeof(int), st));
@@ -904,8 +910,14 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     const bool dip = mu != nullptr;
     // Stage 2
     stage_mark(L, 1, st);
-    k_p2m<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws->sq,
-                                                       dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->Mu);
+    // the P2M and P2L kernels unroll their rows: instantiate them for the smallest order bound that covers p_fmm
+#define QBX_P2M(PB)                                                                                                 \
+    k_p2m<PB, PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws->sq,              \
+                                                           dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->Mu)
+    if (pmax <= 10) QBX_P2M(10);
+    else if (pmax <= 16) QBX_P2M(16);
+    else QBX_P2M(PM_T);
+#undef QBX_P2M
     QBX_LAUNCH_CHECK();
     for (int l = (int)T->nlev - 2; l >= 0; --l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
@@ -934,8 +946,14 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     }
     // Stage 6(b)
     stage_mark(L, 3, st);
-    k_p2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], T->sxyz,
-                                                       ns, ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->B);
+#define QBX_P2L(PB)                                                                                                 \
+    k_p2l<PB, PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC],        \
+                                                           T->sxyz, ns, ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, \
+                                                           ws->pb, ws->B)
+    if (pmax <= 10) QBX_P2L(10);
+    else if (pmax <= 16) QBX_P2L(16);
+    else QBX_P2L(PM_T);
+#undef QBX_P2L
     QBX_LAUNCH_CHECK();
     // Stage 7
     stage_mark(L, 4, st);

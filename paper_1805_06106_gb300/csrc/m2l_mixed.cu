@@ -353,16 +353,34 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
         ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
         if (__syncthreads_or(!ok)) { ok = false; break; }
         tc::tc_fence_after();
+        // Output rows of consecutive pairs are contiguous in Y: stage column blocks of 128 through
+        // shared memory (row stride 132 floats) and copy them out with coalesced 16-byte stores.
         const int qd = warp & 3, row = 32 * qd + lane;
-        for (int cg = warp >> 2; cg * 16 < Np; cg += 2) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(cg * 16), v);
-            if (row < np) {
-                float *dst = a.y + (int64_t)(p0 + row) * a.D + cg * 16;
+        float *stage = reinterpret_cast<float *>(smem_tc);  // 128 x 132 floats; the operand tiles are idle
+        for (int c0 = 0; c0 < a.D; c0 += 128) {
+            const int cw = min(128, a.D - c0);
+            for (int cg = warp >> 2; cg * 16 < cw; cg += 2) {
+                float v[16];
+                tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(c0 + cg * 16), v);
+                float4 *dst = reinterpret_cast<float4 *>(stage + row * 132 + cg * 16);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (cg * 16 + j < a.D) dst[j] = v[j];
+                for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
             }
+            __syncthreads();
+            const int c4 = cw / 4;  // D is a multiple of 4 only for odd P; copy scalars otherwise
+            if ((a.D & 3) == 0) {
+                for (int q = tid; q < np * c4; q += 256) {
+                    const int r = q / c4, cc = q % c4;
+                    *reinterpret_cast<float4 *>(a.y + (int64_t)(p0 + r) * a.D + c0 + 4 * cc) =
+                        *reinterpret_cast<const float4 *>(stage + r * 132 + 4 * cc);
+                }
+            } else {
+                for (int q = tid; q < np * cw; q += 256) {
+                    const int r = q / cw, cc = q % cw;
+                    a.y[(int64_t)(p0 + r) * a.D + c0 + cc] = stage[r * 132 + cc];
+                }
+            }
+            __syncthreads();
         }
         tc::tc_fence_before();
         __syncthreads();
@@ -376,7 +394,11 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
     if (warp == 0) tc::tmem_dealloc(tmem, (uint32_t)a.tmem_cols);
 }
 
-static size_t m2l_tc_smem(int Np, int KC) { return (size_t)4 * 16 * (KC * 32 + 16) + (size_t)4 * Np * KC * 4; }
+// operand stages, or the 128 x 132 float epilogue stage that reuses them, whichever is larger
+static size_t m2l_tc_smem(int Np, int KC)
+{
+    return std::max((size_t)4 * 16 * (KC * 32 + 16) + (size_t)4 * Np * KC * 4, (size_t)128 * 132 * 4);
+}
 
 // B[b] += F(k,l)/h_b * sum_{e in V(b)} Y[pos(e)], summed in list order in FP64.
 __global__ void k_m2l_reduce(int64_t nb, int P, int PMT, const int *vstart, const int *pair_pos, const float *y,

@@ -206,16 +206,17 @@ __global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, int64_t per, const WfarRe
 // and |Yh_j^i| <= F(j,i)/F(j,j) <= 1.
 __constant__ double c_al[41], c_be[ntri(40)];
 
-// IEEE double -> float by truncation of the significand (values of magnitude below the float
-// normal range become 0); integer operations only, so the FP64 pipe is left to the recurrence.
-__device__ __forceinline__ float dbl_to_f32_trunc(double v)
+// IEEE double -> float from the bit fields, rounding the 24-bit significand half away from zero
+// (a carry out of the significand moves into the exponent); magnitudes below the float normal
+// range become 0.  Integer operations only, so the FP64 pipe is left to the recurrence.
+__device__ __forceinline__ float dbl_to_f32_rn(double v)
 {
     const int hi = __double2hiint(v);
     const unsigned lo = (unsigned)__double2loint(v);
     const int e = (hi >> 20) & 0x7ff;
     if (e < 897) return 0.0f;
-    const unsigned mant = ((unsigned)(hi & 0xfffff) << 3) | (lo >> 29);
-    return __uint_as_float(((unsigned)hi & 0x80000000u) | ((unsigned)(e - 896) << 23) | mant);
+    const unsigned mant = (((unsigned)(hi & 0xfffff) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+    return __uint_as_float(((unsigned)hi & 0x80000000u) | (((unsigned)(e - 896) << 23) + mant));
 }
 
 struct WfarTcArgs {
@@ -249,7 +250,9 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
     // stage s, part 0 (hi) / 1 (lo) of the A and B tiles
     auto Abuf = [&](int s, int part) { return smem_tc + (size_t)(2 * s + part) * bytesA; };
     auto Bbuf = [&](int s, int part) { return smem_tc + (size_t)4 * bytesA + (size_t)(2 * s + part) * bytesB; };
-    float *Pw = reinterpret_cast<float *>(smem_tc + (size_t)4 * bytesA + (size_t)4 * bytesB);  // 128 x (Q+1)
+    // the epilogue stage (128 x (Rp + 4) floats) reuses the operand tiles; Pw and the column tables follow both
+    const size_t ops = std::max((size_t)4 * bytesA + (size_t)4 * bytesB, (size_t)128 * (Rp + 4) * 4);
+    float *Pw = reinterpret_cast<float *>(smem_tc + ops);  // 128 x (Q+1)
     float *colF = Pw + 128 * (Q + 1);                                                     // Rp
     int *colK = reinterpret_cast<int *>(colF + Rp);                                       // Rp
     for (int r = tid; r < Rp; r += 256) {
@@ -343,7 +346,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                 unsigned char *Ah = Abuf(s, 0), *Al = Abuf(s, 1);
                 for (int j = j0; j < j1; ++j) {
                     const double c1 = c_al[j] * zh;
-                    const float rf = dbl_to_f32_trunc(rpj);
+                    const float rf = dbl_to_f32_rn(rpj);
                     rpj *= rinv;
                     const int kb = j * j - j0 * j0;
 #pragma unroll
@@ -360,12 +363,12 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                             }
                             const int kk = kb + (i == 0 ? 0 : 2 * i - 1);
                             float hi, lo;
-                            tc::split_tf32(dbl_to_f32_trunc(vr) * rf, hi, lo);
+                            tc::split_tf32(dbl_to_f32_rn(vr) * rf, hi, lo);
                             uint32_t off = tc::kmajor_off(p, kk, sboA);
                             *reinterpret_cast<float *>(Ah + off) = hi;
                             *reinterpret_cast<float *>(Al + off) = lo;
                             if (i > 0) {
-                                tc::split_tf32(dbl_to_f32_trunc(vi) * rf, hi, lo);
+                                tc::split_tf32(dbl_to_f32_rn(vi) * rf, hi, lo);
                                 off = tc::kmajor_off(p, kk + 1, sboA);
                                 *reinterpret_cast<float *>(Ah + off) = hi;
                                 *reinterpret_cast<float *>(Al + off) = lo;
@@ -401,19 +404,27 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
         ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
         if (__syncthreads_or(!ok)) { ok = false; break; }
         tc::tc_fence_after();
-        const int qd = warp & 3, row = 32 * qd + lane;
+        // scaled rows staged in shared memory (row stride Rp + 4), then copied out coalesced: the
+        // tile's rows are contiguous in Y
+        const int qd = warp & 3, row = 32 * qd + lane, RS = Rp + 4;
+        float *stage = reinterpret_cast<float *>(smem_tc);  // 128 x (Rp + 4) floats
         for (int cg = warp >> 2; cg * 16 < Rp; cg += 2) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(cg * 16), v);
-            if (row < np) {
-                float *dst = a.Y + (int64_t)(p0 + row) * a.R;
-                const float *pw = Pw + row * (Q + 1);
+            const float *pw = Pw + row * (Q + 1);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = cg * 16 + j;
-                    if (col < a.R) dst[col] = v[j] * (colF[col] * pw[colK[col]]);
-                }
+            for (int j = 0; j < 16; ++j) {
+                const int col = cg * 16 + j;
+                v[j] *= colF[col] * pw[colK[col]];
             }
+            float4 *dst = reinterpret_cast<float4 *>(stage + row * RS + cg * 16);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        }
+        __syncthreads();
+        for (int q = tid; q < np * a.R; q += 256) {
+            const int r = q / a.R, cc = q % a.R;
+            a.Y[(int64_t)(p0 + r) * a.R + cc] = stage[r * RS + cc];
         }
         tc::tc_fence_before();
         __syncthreads();
@@ -428,8 +439,8 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
 
 static size_t wfar_tc_smem(int Rp, int WMAX, int Q)
 {
-    return (size_t)4 * 16 * (WMAX * 32 + 16) + (size_t)4 * Rp * WMAX * 4 + (size_t)128 * (Q + 1) * 4 +
-           (size_t)Rp * 8;
+    const size_t ops = std::max((size_t)4 * 16 * (WMAX * 32 + 16) + (size_t)4 * Rp * WMAX * 4, (size_t)128 * (Rp + 4) * 4);
+    return ops + (size_t)128 * (Q + 1) * 4 + (size_t)Rp * 8;
 }
 
 constexpr int WKC = 32;  // K chunk of the H tile

@@ -230,7 +230,34 @@ def _stretch(du: np.ndarray, dv: np.ndarray) -> np.ndarray:
     return 2.0 * np.sqrt(lam)
 
 
-def make_surface(n_sub: int, radius_fn=sphere_radius, scale: float = 1.0, offset=(0.0, 0.0, 0.0)) -> Surface:
+def _upsampled_rule(f: int):
+    """The 15-node rule on each of the f^2 congruent sub-triangles of the unit triangle (weights
+    scaled by the area ratio 1/f^2): nodes of a finer source quadrature on the same element."""
+    qu, qv, qw = triangle_rule()
+    us, vs, ws = [], [], []
+    for a in range(f):
+        for b in range(f - a):
+            # upright sub-triangle with corner (a, b)/f, and the inverted one above it
+            corners = [((a, b), (a + 1, b), (a, b + 1))]
+            if a + b < f - 1:
+                corners.append(((a + 1, b + 1), (a, b + 1), (a + 1, b)))
+            for (p0, p1, p2) in corners:
+                A = np.array(p0, float) / f
+                B = np.array(p1, float) / f
+                C = np.array(p2, float) / f
+                us.append(A[0] + qu * (B[0] - A[0]) + qv * (C[0] - A[0]))
+                vs.append(A[1] + qu * (B[1] - A[1]) + qv * (C[1] - A[1]))
+                ws.append(qw / (f * f))
+    return np.concatenate(us), np.concatenate(vs), np.concatenate(ws)
+
+
+def make_surface(n_sub: int, radius_fn=sphere_radius, scale: float = 1.0, offset=(0.0, 0.0, 0.0),
+                 upsample: int = 1) -> Surface:
+    """Curved triangles (icosahedron, n_sub^2 sub-triangles per face, degree-4 maps onto r(x_hat))
+    with 15 nodes each.  Centers and on-surface targets sit at the 15 nodes of every element; the
+    sources are those nodes too (upsample = 1), or the 15 f^2 nodes of the rule repeated on the
+    f^2 sub-triangles of every element (upsample = f), a finer source quadrature on the same
+    elements and expansion radii (the role of the paper's stage-2 quadrature, Section 3)."""
     flat = _flat_subtriangles(n_sub)  # (K, 3, 3)
     K = flat.shape[0]
     V0, V1, V2 = flat[:, 0], flat[:, 1], flat[:, 2]
@@ -257,16 +284,29 @@ def make_surface(n_sub: int, radius_fn=sphere_radius, scale: float = 1.0, offset
     dv_g = np.einsum("qb,kbd->kqd", gdv, geo)
     eta = np.maximum(_stretch(du, dv).max(axis=1), _stretch(du_g, dv_g).max(axis=1))
 
-    src_xyz = np.ascontiguousarray(x.reshape(-1, 3).T)
-    src_n = np.ascontiguousarray(nrm.reshape(-1, 3).T)
-    src_w = np.ascontiguousarray(w.reshape(-1))
-    src_elem = np.repeat(np.arange(K, dtype=np.int32), 15)
-    r = 0.5 * eta[src_elem]
-    N = src_xyz.shape[1]
-    ctr = np.concatenate([src_xyz + r * src_n, src_xyz - r * src_n], axis=1)
+    node_xyz = np.ascontiguousarray(x.reshape(-1, 3).T)
+    node_n = np.ascontiguousarray(nrm.reshape(-1, 3).T)
+    node_elem = np.repeat(np.arange(K, dtype=np.int32), 15)
+    if upsample > 1:
+        fu, fv, fw = _upsampled_rule(upsample)
+        fphi, fdu, fdv = _lagrange_eval(fu, fv)
+        xs = np.einsum("qb,kbd->kqd", fphi, geo)
+        crs = np.cross(np.einsum("qb,kbd->kqd", fdu, geo), np.einsum("qb,kbd->kqd", fdv, geo))
+        ars = np.linalg.norm(crs, axis=-1)
+        src_xyz = np.ascontiguousarray(xs.reshape(-1, 3).T)
+        src_n = np.ascontiguousarray((crs / ars[..., None]).reshape(-1, 3).T)
+        src_w = np.ascontiguousarray((fw[None, :] * ars).reshape(-1))
+        src_elem = np.repeat(np.arange(K, dtype=np.int32), fu.size)
+    else:
+        src_xyz, src_n = node_xyz, node_n
+        src_w = np.ascontiguousarray(w.reshape(-1))
+        src_elem = node_elem
+    r = 0.5 * eta[node_elem]
+    N = node_xyz.shape[1]
+    ctr = np.concatenate([node_xyz + r * node_n, node_xyz - r * node_n], axis=1)
     ctr_r = np.concatenate([r, r])
     side = np.concatenate([np.ones(N, np.int8), -np.ones(N, np.int8)])
-    tgt = np.concatenate([src_xyz, src_xyz], axis=1)
+    tgt = np.concatenate([node_xyz, node_xyz], axis=1)
     tctr = np.arange(2 * N, dtype=np.int32)
     return Surface(K, src_xyz, src_w, src_n, src_elem, eta, np.ascontiguousarray(ctr), ctr_r, side,
                    np.ascontiguousarray(tgt), tctr, radius_fn)

@@ -52,3 +52,14 @@ def test_batched_specs_follow_the_recipe():
     assert [d for _, _, d in a] == list(range(500, 564))
     total = sum(300 * n * n for n, _, _ in a)
     assert 1_000_000 < total < 6_000_000
+
+
+def test_upsampled_source_quadrature():
+    """f^2 copies of the rule on the sub-triangles: same area, same centers, finer sources."""
+    s1 = make_surface(2)
+    s3 = make_surface(2, upsample=3)
+    assert s3.n_src == 9 * s1.n_src and s3.n_ctr == s1.n_ctr
+    assert np.array_equal(s3.ctr_xyz, s1.ctr_xyz) and np.array_equal(s3.tgt_xyz, s1.tgt_xyz)
+    assert abs(s3.src_w.sum() - s1.src_w.sum()) < 1e-4 * s1.src_w.sum()
+    assert np.allclose(np.linalg.norm(s3.src_n, axis=0), 1.0)
+    assert np.allclose(np.linalg.norm(s3.src_xyz, axis=0), 1.0, atol=2e-3)  # on the (interpolated) sphere
