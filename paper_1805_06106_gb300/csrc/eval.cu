@@ -56,6 +56,10 @@ struct qbx_workspace {
     qbx::M2LPlan *m2l = nullptr;   // mixed-precision List 2 plan (built on first use)
     qbx::WfarPlan *wfar = nullptr; // mixed-precision List 3 far plan (built on first use)
     int wfar_key = -1;             // (orders, form, tile) the List 3 far plan was built for
+    // point targets: (target, List 3 far box) pairs, listed on every evaluation
+    int64_t pt_cap = -1;           // pairs if every target were a point target
+    int *pt_cnt = nullptr, *pt_off = nullptr, *pt_total = nullptr, *pt_it = nullptr, *pt_box = nullptr;
+    double *pt_part = nullptr;
     int m2l_key = -1;              // (order, form, tile) the List 2 plan was built for
 };
 
@@ -68,6 +72,8 @@ void free_workspace(qbx_workspace *ws)
     dfree(ws->sq); dfree(ws->sd); dfree(ws->qc); dfree(ws->pb); dfree(ws->flags);
     free_m2l_plan(ws->m2l);
     free_wfar_plan(ws->wfar);
+    dfree(ws->pt_cnt); dfree(ws->pt_off); dfree(ws->pt_total); dfree(ws->pt_it); dfree(ws->pt_box);
+    dfree(ws->pt_part);
     delete ws;
 }
 
@@ -259,6 +265,60 @@ __global__ void k_m2m(int b0, int b1, const int *lvl_boxes, const int *child, co
             }
         }
         Mu[(int64_t)b * ntri(PM) + out] = acc;
+    }
+}
+
+// M2M with one block of 8 warps per parent: warp o translates child octant o (lanes over the
+// outputs), the 8 contributions are added in octant order in shared memory, so the serial work per
+// parent is that of one child (the coarse levels hold few parents).
+template <int PM>
+__global__ void __launch_bounds__(256) k_m2m8(int b0, int b1, const int *lvl_boxes, const int *child,
+                                              const int *nsrc_sub, const signed char *pb, const double2 *oct,
+                                              double2 *Mu)
+{
+    __shared__ double2 part[8][ntri(PM)];
+    int b = b0 + blockIdx.x;
+    if (b >= b1) return;
+    if (lvl_boxes) b = lvl_boxes[b];
+    if (nsrc_sub[b] == 0) return;
+    const int o = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int P = pb[b];
+    const int c = child[8 * b + o];
+    const bool live = c >= 0 && nsrc_sub[c] > 0;
+    for (int out = lane; out < ntri(P); out += 32) {
+        double2 acc = make_double2(0.0, 0.0);
+        if (live) {
+            int n = 0;
+            while (tri(n + 1, 0) <= out) ++n;
+            const int m = out - tri(n, 0);
+            const int Pc = pb[c];
+            const double2 *Mc = Mu + (int64_t)c * ntri(PM);
+            const double2 *R = oct + o * ntri(PM);
+            double sk = 1.0;
+            for (int k = 0; k <= n && k <= Pc; ++k, sk *= 0.5) {
+                const int j = n - k;
+                const int lmin = max(-k, m - j), lmax = min(k, m + j);
+                double2 t = make_double2(0.0, 0.0);
+                for (int l = lmin; l <= lmax; ++l) {
+                    const double2 a = sym_get(Mc, k, l), r = sym_get(R, j, m - l);
+                    t.x = fma(a.x, r.x, fma(-a.y, r.y, t.x));
+                    t.y = fma(a.x, r.y, fma(a.y, r.x, t.y));
+                }
+                acc.x = fma(sk, t.x, acc.x);
+                acc.y = fma(sk, t.y, acc.y);
+            }
+        }
+        part[o][out] = acc;
+    }
+    __syncthreads();
+    for (int out = threadIdx.x; out < ntri(P); out += blockDim.x) {
+        double2 v = Mu[(int64_t)b * ntri(PM) + out];  // the box's own sources (none for non-leaves)
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            v.x += part[k][out].x;
+            v.y += part[k][out].y;
+        }
+        Mu[(int64_t)b * ntri(PM) + out] = v;
     }
 }
 
@@ -811,6 +871,136 @@ __global__ void k_points(int64_t nt, const int *tperm, const double *txyz, const
     if (lane == 0) pot[t] = INV4PI * acc;
 }
 
+// Point targets with the List 3 far M2P spread over (target, box) pairs: the lists of point targets
+// differ by orders of magnitude in length, so one thread per pair keeps the FP64 pipes busy.  The
+// pairs are listed on the device on every evaluation (targets change role with tgt_ctr), their
+// partial potentials are summed per target in list order (deterministic).
+// pairs of each sorted target (every target when tgt_ctr is NULL); cnt[nt] = 0 closes the scan
+__global__ void k_pt_count(int64_t nt, const int *tperm, const int *tgt_ctr, const int *tgt_box, const int *wfs,
+                           int *cnt)
+{
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it > nt) return;
+    int c = 0;
+    if (it < nt && (!tgt_ctr || tgt_ctr[tperm[it]] < 0)) {
+        const int b = tgt_box[it];
+        c = wfs[b + 1] - wfs[b];
+    }
+    cnt[it] = c;
+}
+
+__global__ void k_pt_fill(int64_t nt, const int *tgt_box, const int *wfs, const int *wfi, const int *off,
+                          int *pair_it, int *pair_box)
+{
+    int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (it >= nt) return;
+    const int o0 = off[it], n = off[it + 1] - o0;
+    if (n == 0) return;
+    const int b = tgt_box[it], e0 = wfs[b];
+    for (int j = 0; j < n; ++j) {
+        pair_it[o0 + j] = (int)it;
+        pair_box[o0 + j] = wfi[e0 + j];
+    }
+}
+
+// M2P of one (point target, List 3 far box) pair per thread: 1/h sum Mu_n^m conj S_n^m((t - c_d)/h).
+template <int PM>
+__global__ void k_m2p_pairs(int64_t cap, const int *total, const int *pair_it, const int *pair_box,
+                            const double *txyz, int64_t nt, const signed char *pb, const double *cen, const double *hw,
+                            const double2 *Mu, double *part)
+{
+    const int64_t np = *total;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < np && e < cap;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int it = pair_it[e], d = pair_box[e];
+        const int P = pb[d];
+        const double hinv = 1.0 / hw[d];
+        const double x = (txyz[it] - cen[3 * d]) * hinv, y = (txyz[nt + it] - cen[3 * d + 1]) * hinv,
+                     z = (txyz[2 * nt + it] - cen[3 * d + 2]) * hinv;
+        const double ir2 = 1.0 / (x * x + y * y + z * z);
+        const double2 wr = make_double2(x * ir2, y * ir2);
+        const double zz = z * ir2;
+        const double2 *Md = Mu + (int64_t)d * ntri(PM);
+        double2 diag = make_double2(sqrt(ir2), 0.0);
+        double s = 0.0;
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) diag = cscale(cmul(diag, wr), 2.0 * m - 1.0);
+            const double wgt = m ? 2.0 : 1.0;
+            double2 a2 = make_double2(0.0, 0.0), a1 = diag;
+            double2 mv = Md[tri(m, m)];
+            double sm = mv.x * diag.x + mv.y * diag.y;
+            for (int n = m + 1; n <= P; ++n) {
+                const double c1 = (2 * n - 1) * zz, c2 = (double)(n + m - 1) * (double)(n - m - 1) * ir2;
+                double2 v = make_double2(c1 * a1.x - c2 * a2.x, c1 * a1.y - c2 * a2.y);
+                double2 mm = Md[tri(n, m)];
+                sm = fma(mm.x, v.x, fma(mm.y, v.y, sm));
+                a2 = a1;
+                a1 = v;
+            }
+            s = fma(wgt, sm, s);
+        }
+        part[e] = s * hinv;
+    }
+}
+
+// Point targets: P2P from List 1 / 3 close / 4 close, the M2P partials of List 3 far, L2P.
+template <int PM>
+__global__ void k_points2(int64_t nt, const int *tperm, const double *txyz, const int *tgt_ctr, const int *tgt_box,
+                          const signed char *pb, ListRef lu, ListRef lwc, ListRef lxc, const int *pt_off,
+                          const double *part, const int *own_start, const double *sxyz, int64_t ns, const double *sq,
+                          const double *sd, const double *cen, const double *hw, const double2 *B, double *pot)
+{
+    int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int64_t it = (int64_t)blockIdx.x * (blockDim.x / 32) + wl;
+    if (it >= nt) return;
+    int t = tperm[it];
+    if (tgt_ctr[t] >= 0) return;
+    int b = tgt_box[it];
+    double tx = txyz[it], ty = txyz[nt + it], tz = txyz[2 * nt + it];
+    double acc = 0.0;
+    const ListRef lists[3] = {lu, lwc, lxc};
+    for (int li = 0; li < 3; ++li)
+        for (int e = lists[li].start[b]; e < lists[li].start[b + 1]; ++e) {
+            int d = lists[li].idx[e];
+            for (int s = own_start[d] + lane; s < own_start[d + 1]; s += 32) {
+                double rx = tx - sxyz[s], ry = ty - sxyz[ns + s], rz = tz - sxyz[2 * ns + s];
+                double r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 == 0.0) continue;
+                double ri = 1.0 / sqrt(r2);
+                double v = sq[s] * ri;
+                if (sd) v += (sd[s] * rx + sd[ns + s] * ry + sd[2 * ns + s] * rz) * ri * ri * ri;
+                acc += v;
+            }
+        }
+    for (int e = pt_off[it] + lane; e < pt_off[it + 1]; e += 32) acc += part[e];
+    if (lane == 0) {
+        int P = pb[b];
+        double hinv = 1.0 / hw[b];
+        double x = (cen[3 * b] - tx) * hinv, y = (cen[3 * b + 1] - ty) * hinv, z = (cen[3 * b + 2] - tz) * hinv;
+        double r2 = x * x + y * y + z * z;
+        const double2 *Lb = B + (int64_t)b * ntri(PM);
+        double2 diag = make_double2(1.0, 0.0);
+        for (int m = 0; m <= P; ++m) {
+            if (m > 0) diag = cscale(cmul(diag, make_double2(x, y)), 1.0 / (2.0 * m));
+            double wgt = m ? 2.0 : 1.0;
+            double2 a2 = make_double2(0.0, 0.0), a1 = diag;
+            double2 cv = Lb[tri(m, m)];
+            acc += wgt * (cv.x * diag.x - cv.y * diag.y);
+            for (int n = m + 1; n <= P; ++n) {
+                double inv = 1.0 / ((double)(n + m) * (double)(n - m));
+                double2 v = make_double2(((2 * n - 1) * z * a1.x - r2 * a2.x) * inv, ((2 * n - 1) * z * a1.y - r2 * a2.y) * inv);
+                double2 cc = Lb[tri(n, m)];
+                acc += wgt * (cc.x * v.x - cc.y * v.y);
+                a2 = a1;
+                a1 = v;
+            }
+        }
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) pot[t] = INV4PI * acc;
+}
+
 // ---------------------------------------------------------------- driver
 
 static int read_flags(const int *f, cudaStream_t st)
@@ -921,8 +1111,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     QBX_LAUNCH_CHECK();
     for (int l = (int)T->nlev - 2; l >= 0; --l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
-        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws->pb, ws->oct_tab,
-                                                                ws->Mu);
+        if (b1 > b0)
+            k_m2m8<PM_T><<<b1 - b0, 256, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws->pb, ws->oct_tab, ws->Mu);
         QBX_LAUNCH_CHECK();
     }
     // Stage 4
@@ -989,11 +1179,39 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     // Stage 9 at point targets
     stage_mark(L, 8, st);
     if (nt > 0) {
-        k_points<PM_T><<<nblocks(nt, WPB), 32 * WPB, 0, st>>>(
+        if (ws->pt_cap < 0) {  // first evaluation: size the pair buffers for any choice of point targets
+            ws->pt_cnt = dalloc<int>(nt + 1);
+            ws->pt_off = dalloc<int>(nt + 1);
+            ws->pt_total = dalloc<int>(1);
+            k_pt_count<<<nblocks(nt + 1, 256), 256, 0, st>>>(nt, T->perm[KTGT], nullptr, T->tgt_box, L->start[LWF],
+                                                             ws->pt_cnt);
+            QBX_LAUNCH_CHECK();
+            exclusive_scan(ws->pt_cnt, ws->pt_off, nt + 1, 0, ws->pt_total, st);
+            int cap = 0;
+            QBX_CUDA_TRY(cudaMemcpyAsync(&cap, ws->pt_total, sizeof(int), cudaMemcpyDeviceToHost, st));
+            QBX_CUDA_TRY(cudaStreamSynchronize(st));
+            ws->pt_cap = cap;
+            ws->pt_it = dalloc<int>(std::max(cap, 1));
+            ws->pt_box = dalloc<int>(std::max(cap, 1));
+            ws->pt_part = dalloc<double>(std::max(cap, 1));
+        }
+        k_pt_count<<<nblocks(nt + 1, 256), 256, 0, st>>>(nt, T->perm[KTGT], tgt_ctr, T->tgt_box, L->start[LWF],
+                                                         ws->pt_cnt);
+        QBX_LAUNCH_CHECK();
+        exclusive_scan(ws->pt_cnt, ws->pt_off, nt + 1, 0, ws->pt_total, st);
+        k_pt_fill<<<nblocks(nt, 256), 256, 0, st>>>(nt, T->tgt_box, L->start[LWF], L->idx[LWF], ws->pt_off, ws->pt_it,
+                                                    ws->pt_box);
+        QBX_LAUNCH_CHECK();
+        if (ws->pt_cap > 0) {
+            const unsigned grid = std::min<unsigned>(nblocks(ws->pt_cap, 128), 152 * 64);
+            k_m2p_pairs<PM_T><<<grid, 128, 0, st>>>(ws->pt_cap, ws->pt_total, ws->pt_it, ws->pt_box, T->txyz, nt, ws->pb,
+                                                     T->cen, T->hw, ws->Mu, ws->pt_part);
+            QBX_LAUNCH_CHECK();
+        }
+        k_points2<PM_T><<<nblocks(nt, WPB), 32 * WPB, 0, st>>>(
             nt, T->perm[KTGT], T->txyz, tgt_ctr, T->tgt_box, ws->pb, ListRef{L->start[LU], L->idx[LU]},
-            ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
-            ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, ns, ws->sq, dip ? ws->sd : nullptr,
-            T->cen, T->hw, ws->Mu, ws->B, pot);
+            ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]}, ws->pt_off, ws->pt_part,
+            T->own_start[KSRC], T->sxyz, ns, ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, ws->B, pot);
         QBX_LAUNCH_CHECK();
     }
     stage_mark(L, 9, st);

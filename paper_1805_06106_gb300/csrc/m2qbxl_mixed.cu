@@ -272,7 +272,9 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = tc::idesc_tf32(128, Rp);
-    const int p = tid >> 1, par = tid & 1;
+    // pair p = tid % 128; warps 0-3 take the even columns i, warps 4-7 the odd ones, so the column
+    // conditions are uniform within each warp
+    const int p = tid & 127, par = tid >> 7;
     bool ok = true;
     uint32_t g = 0;
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
