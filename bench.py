@@ -145,6 +145,13 @@ def kernel_traffic():
         return None
 
 
+def library_launches(nlev, mixed):
+    """Kernels of libqbx per evaluation: prep (3), P2M, M2M per level, M2L (1, or convert + GEMM +
+    reduce), P2L, L2L per level, M2QBXL (0, or operator + GEMM), centers (+ List 3 far reduce),
+    QBX targets, point targets (count, scan, fill, M2P pairs, P2P/L2P)."""
+    return 3 + 1 + (nlev - 1) + (3 if mixed else 1) + 1 + (nlev - 1) + (2 if mixed else 0) + (3 if mixed else 2) + 5
+
+
 # ------------------------------------------------------------------ clocks
 
 
@@ -445,9 +452,7 @@ def run_gpu(args):
     centers_ms = main["stage_ms"]["centers"]
     achieved = flops / (centers_ms * 1e-3) / 1e12
     nlev = int(T.info.n_levels)
-    launches = 3 + 1 + (nlev - 1) + 1 + 1 + (nlev - 1) + 3  # prep, P2M, M2M, M2L, P2L, L2L, centers/targets
-    if mode != "fp64":
-        launches += 2 + 2 + 1  # mixed M2L (convert, GEMM, reduce counted as M2L + 2), M2QBXL (H, GEMM), reduce
+    launches = library_launches(nlev, mode != "fp64")
     line = {
         "metric": METRIC, "value": value, "unit": "QBX target evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -644,7 +649,7 @@ def run_batched(args):
                    "tree_lists_build_ms": build_ms, "forest_build_ms": forest_ms},
         "e2e": {"value": ws * n_qbx * len(e2e) / (sum(e2e) * 1e-3), "unit": "QBX target evals/s",
                 "h2d_bytes_per_step": int(h_sig.numel() * 8), "d2h_bytes_per_step": int(h_out.numel() * 8)},
-        "gpu_launches": None, "deterministic": det,
+        "gpu_launches": library_launches(int(F.info.n_levels), True) * args.steps, "deterministic": det,
         "rel_err_vs_fp64_same_tree_max": max(errs),
         "plain_fp64": {"value": plain, "ms_per_step": statistics.mean(pt), "n_max": N_MAX, "steps": args.fp64_steps},
         "speedup_vs_plain_fp64": value / plain,

@@ -22,6 +22,11 @@ namespace qbx {
 
 constexpr int WF_MAXCH = 48;  // K chunks of the tensor-core form
 
+// K slots of harmonic degree j in the tensor-core layout: [Re S_j^0, 0, 0, 0] then, for each odd i,
+// [Re S_j^i, Im S_j^i, Re S_j^{i+1}, Im S_j^{i+1}] (zeros for i + 1 > j): 16-byte groups that one
+// thread writes with one store.
+__host__ __device__ __forceinline__ int wfar_degree_slots(int j) { return 4 + 4 * ((j + 1) / 2); }
+
 struct WfarPlan {
     int P = -1, Q = -1, K = 0, R = 0;
     int64_t npairs = 0;
@@ -232,11 +237,12 @@ struct WfarTcArgs {
 };
 
 // Tensor-core List 3 far products.  Persistent CTAs of 256 threads walk 128-pair tiles of one
-// source box d: per K chunk the threads generate the balanced irregular harmonics of their pairs
-// in FP64 (two threads per pair, each carrying the recurrence of every other column i in
-// registers), split them into TF32 parts in shared memory, load and split the chunk of H_d; one
-// thread issues a_hi b_hi + a_lo b_hi + a_hi b_lo into a 128 x Rp FP32 accumulator in tensor
-// memory.  Epilogue: Y[pair][row] = acc F(k,l) (rho/h)^k / h.
+// source box d: per K chunk (whole harmonic degrees) the threads generate the scaled irregular
+// harmonics of their pairs in FP64 (two threads per pair, warps 0-3 and 4-7, each carrying the
+// recurrences of every other 16-byte column group in registers), split them into TF32 parts in
+// shared memory, load and split the chunk of H_d; one thread issues a_hi b_hi + a_lo b_hi +
+// a_hi b_lo into a 128 x Rp FP32 accumulator in tensor memory.  Epilogue: Y[pair][row] =
+// acc F(k,l) (rho/h)^k / h.
 template <int NU>
 __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
 {
@@ -282,8 +288,9 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
         const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
         const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
         const bool valid = p < np;
-        // pair geometry and the diagonals of the scaled unit-vector harmonics of this thread's columns
-        double a1r[NU], a1i[NU], a2r[NU], a2i[NU];
+        // pair geometry and the diagonals of the scaled unit-vector harmonics of this thread's columns:
+        // 16-byte group g holds column 0 (g = 0) or columns 2g-1, 2g; this thread owns g = par + 2u
+        double a1r[NU][2], a1i[NU][2], a2r[NU][2], a2i[NU][2];
         double zh = 0.0, rinv = 0.0, rpj = 0.0;
         {
             const double h = a.hw[d], hinv = 1.0 / h;
@@ -304,20 +311,28 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                 double pk = hinv;
                 for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[p * (Q + 1) + k] = (float)pk;
             }
-            double dr = 1.0, di = 0.0;  // Yh_0^0
-            if (par == 1) {             // Yh_1^1
-                dr = c_al[1] * wr;
-                di = c_al[1] * wi;
-            }
+            // diagonal Yh_i^i for i = 0, 1, 2, ...; column i belongs to group (i + 1) / 2
+            double dr = 1.0, di = 0.0;
 #pragma unroll
-            for (int u = 0; u < NU; ++u) {
-                const int i = par + 2 * u;
-                a1r[u] = dr; a1i[u] = di; a2r[u] = 0.0; a2i[u] = 0.0;
-                if (i + 2 <= 40) {  // advance the diagonal i -> i + 2
-                    double ga = c_al[i + 1], gb = c_al[i + 2];
-                    double tr = (dr * wr - di * wi) * ga, ti = (dr * wi + di * wr) * ga;
-                    dr = (tr * wr - ti * wi) * gb;
-                    di = (tr * wi + ti * wr) * gb;
+            for (int u = 0; u < NU; ++u)
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) { a1r[u][h2] = a1i[u][h2] = a2r[u][h2] = a2i[u][h2] = 0.0; }
+            for (int i = 0; i <= PQ; ++i) {
+                if (i > 0) {
+                    const double ga = c_al[i];
+                    const double tr = (dr * wr - di * wi) * ga, ti = (dr * wi + di * wr) * ga;
+                    dr = tr;
+                    di = ti;
+                }
+                const int gi = (i + 1) >> 1;
+                const bool second = i > 0 && ((i - 1) & 1);  // column 2g of group g
+                if ((gi & 1) == par) {
+#pragma unroll
+                    for (int u = 0; u < NU; ++u)
+                        if (par + 2 * u == gi) {
+                            if (second) { a1r[u][1] = dr; a1i[u][1] = di; }
+                            else { a1r[u][0] = dr; a1i[u][0] = di; }
+                        }
                 }
             }
         }
@@ -327,7 +342,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
             if (g >= 2) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, tc::WAIT_LIMIT);
             if (__syncthreads_or(!ok)) { ok = false; break; }
             const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
-            const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c], nent = j1 * j1 - j0 * j0;
+            const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c];
             // B: chunk of H_d, split into TF32 parts
             {
                 const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[c] * Rp);
@@ -342,46 +357,53 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                     dl[q] = lo;
                 }
             }
-            // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's columns; the
-            // recurrence in FP64, the final scaling by |x|^{-(j+1)} in FP32 after the conversion
+            // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's column groups;
+            // the recurrence in FP64, the radial factor applied in FP32 after the conversion, one
+            // 16-byte store per group and TF32 part
             if (valid) {
                 unsigned char *Ah = Abuf(s, 0), *Al = Abuf(s, 1);
-                for (int j = j0; j < j1; ++j) {
+                const uint32_t rowoff = (uint32_t)(p >> 3) * sboA + (uint32_t)(p & 7) * 16u;
+                int kb = 0;
+                for (int j = j0; j < j1; kb += wfar_degree_slots(j), ++j) {
                     const double c1 = c_al[j] * zh;
                     const float rf = dbl_to_f32_rn(rpj);
                     rpj *= rinv;
-                    const int kb = j * j - j0 * j0;
 #pragma unroll
                     for (int u = 0; u < NU; ++u) {
-                        const int i = par + 2 * u;
-                        if (i <= j && i <= PQ) {
-                            double vr = a1r[u], vi = a1i[u];
+                        const int gg = par + 2 * u;
+                        const int i0 = gg == 0 ? 0 : 2 * gg - 1;  // first column of the group
+                        if (i0 > j || i0 > PQ) continue;
+                        float v[4];
+#pragma unroll
+                        for (int h2 = 0; h2 < 2; ++h2) {
+                            const int i = i0 + h2;
+                            v[2 * h2] = v[2 * h2 + 1] = 0.f;
+                            if ((gg == 0 && h2 == 1) || i > j) continue;
+                            double vr = a1r[u][h2], vi = a1i[u][h2];
                             if (j > i) {
                                 const double bb = c_be[tri(j, i)];
-                                vr = fma(c1, a1r[u], -bb * a2r[u]);
-                                vi = fma(c1, a1i[u], -bb * a2i[u]);
-                                a2r[u] = a1r[u]; a2i[u] = a1i[u];
-                                a1r[u] = vr; a1i[u] = vi;
+                                vr = fma(c1, a1r[u][h2], -bb * a2r[u][h2]);
+                                vi = fma(c1, a1i[u][h2], -bb * a2i[u][h2]);
+                                a2r[u][h2] = a1r[u][h2]; a2i[u][h2] = a1i[u][h2];
+                                a1r[u][h2] = vr; a1i[u][h2] = vi;
                             }
-                            const int kk = kb + (i == 0 ? 0 : 2 * i - 1);
-                            float hi, lo;
-                            tc::split_tf32(dbl_to_f32_rn(vr) * rf, hi, lo);
-                            uint32_t off = tc::kmajor_off(p, kk, sboA);
-                            *reinterpret_cast<float *>(Ah + off) = hi;
-                            *reinterpret_cast<float *>(Al + off) = lo;
-                            if (i > 0) {
-                                tc::split_tf32(dbl_to_f32_rn(vi) * rf, hi, lo);
-                                off = tc::kmajor_off(p, kk + 1, sboA);
-                                *reinterpret_cast<float *>(Ah + off) = hi;
-                                *reinterpret_cast<float *>(Al + off) = lo;
-                            }
+                            v[2 * h2] = dbl_to_f32_rn(vr) * rf;
+                            v[2 * h2 + 1] = (i == 0) ? 0.f : dbl_to_f32_rn(vi) * rf;
                         }
+                        float4 hv, lv;
+                        tc::split_tf32(v[0], hv.x, lv.x);
+                        tc::split_tf32(v[1], hv.y, lv.y);
+                        tc::split_tf32(v[2], hv.z, lv.z);
+                        tc::split_tf32(v[3], hv.w, lv.w);
+                        const uint32_t off = (uint32_t)((kb + 4 * gg) >> 2) * 128u + rowoff;
+                        *reinterpret_cast<float4 *>(Ah + off) = hv;
+                        *reinterpret_cast<float4 *>(Al + off) = lv;
                     }
                 }
-                for (int kk = nent + par; kk < W; kk += 2) {
-                    uint32_t off = tc::kmajor_off(p, kk, sboA);
-                    *reinterpret_cast<float *>(Ah + off) = 0.f;
-                    *reinterpret_cast<float *>(Al + off) = 0.f;
+                if (par == 0 && kb < W) {  // chunk padding to a multiple of 8 columns (one 16-byte group)
+                    const uint32_t off = (uint32_t)(kb >> 2) * 128u + rowoff;
+                    *reinterpret_cast<float4 *>(Ah + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    *reinterpret_cast<float4 *>(Al + off) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
             tc::fence_proxy_async();
@@ -597,26 +619,27 @@ __global__ void k_wfar_reduce(int64_t nc, int Q, int QMS, const int *cm_start, c
 }
 
 // Degree chunks of the tensor-core form and its shared-memory budget; false when the orders do not fit.
+
 static bool wfar_tc_layout(WfarPlan *pl, int w_hint)
 {
     const int P = pl->P, Q = pl->Q, PQ = P + Q;
     pl->Rp = (pl->R + 15) / 16 * 16;
     if (pl->Rp > 256 || PQ > 35) return false;
-    pl->NU = PQ <= 23 ? 12 : 18;
-    const int wmin = (2 * PQ + 1 + 7) / 8 * 8;
+    pl->NU = PQ <= 22 ? 6 : 10;  // 16-byte groups per thread: ceil((1 + ceil(PQ/2)) / 2)
+    const int wmin = (wfar_degree_slots(PQ) + 7) / 8 * 8;
     int W = std::max(w_hint > 0 ? w_hint / 8 * 8 : 64, wmin);
     while (W > wmin && wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) W -= 8;
     if (wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) return false;
     pl->WMAX = W;
     int nch = 0, j = 0, koff = 0;
     while (j <= PQ) {
-        int j1 = j + 1;
-        while (j1 <= PQ && j1 * j1 + 2 * j1 + 1 - j * j <= W) ++j1;  // add degree j1 while it fits
+        int j1 = j + 1, w = wfar_degree_slots(j);
+        while (j1 <= PQ && w + wfar_degree_slots(j1) <= W) w += wfar_degree_slots(j1++);  // add degree j1 while it fits
         if (nch >= WF_MAXCH) return false;
         pl->cj0[nch] = j;
         pl->cj1[nch] = j1;
         pl->ckoff[nch] = koff;
-        koff += (j1 * j1 - j * j + 7) / 8 * 8;
+        koff += (w + 7) / 8 * 8;
         ++nch;
         j = j1;
     }
@@ -668,42 +691,52 @@ static std::vector<WfarRecipe> wfar_recipe(const WfarPlan *pl)
     for (auto &r : out) r = WfarRecipe{0.0, 0.0, -1, -1, 0, 0};
     for (int c = 0; c < pl->nch; ++c) {
         const int W = pl->ckoff[c + 1] - pl->ckoff[c];
-        const int nent = pl->cj1[c] * pl->cj1[c] - pl->cj0[c] * pl->cj0[c];
-        for (int row = 0; row < pl->R; ++row)
-            for (int kk = 0; kk < nent; ++kk) {
-                int k, l, rp, j, i, cp;
-                host_decode(row, k, l, rp);
-                host_decode(pl->cj0[c] * pl->cj0[c] + kk, j, i, cp);
-                const int n = j - k;
-                WfarRecipe rc{0.0, 0.0, -1, -1, 0, 0};
-                if (n >= 0) {
-                    const double colscale = host_F(j, j) / host_F(j, i), inv_kl = 1.0 / host_F(k, l);
-                    const bool take_y = (rp != cp);  // (0,0), (1,1) read .x; (0,1), (1,0) read .y
-                    // sign applied to the chosen component of sym_get(M, n, m)
-                    auto sgn = [&](int m) {
-                        if (m >= 0) return 1.0;
-                        return take_y ? ((m & 1) ? 1.0 : -1.0) : ((m & 1) ? -1.0 : 1.0);
-                    };
-                    const double s = (i & 1) ? -1.0 : 1.0;
-                    // coefficient of a1.c and a2.c in the entry
-                    double w1, w2;
-                    if (rp == 0 && cp == 0) { w1 = 1.0; w2 = s; }
-                    else if (rp == 0 && cp == 1) { w1 = 1.0; w2 = -s; }
-                    else if (rp == 1 && cp == 0) { w1 = 1.0; w2 = s; }
-                    else { w1 = -1.0; w2 = s; }
-                    const int m1 = i - l, m2 = -i - l;
-                    if (m1 >= -n && m1 <= n) {
-                        rc.t1 = tri(n, m1 < 0 ? -m1 : m1);
-                        rc.f1 = w1 * sgn(m1) * host_F(n + k, m1 + l) * inv_kl * colscale;
-                    }
-                    if (i > 0 && m2 >= -n && m2 <= n) {
-                        rc.t2 = tri(n, m2 < 0 ? -m2 : m2);
-                        rc.f2 = w2 * sgn(m2) * host_F(n + k, m2 + l) * inv_kl * colscale;
-                    }
-                    rc.bits = (take_y ? 3 : 0) | (n << 8);
+        int kb = 0;  // first slot of degree j in the chunk
+        for (int j = pl->cj0[c]; j < pl->cj1[c]; kb += wfar_degree_slots(j), ++j)
+            for (int sl = 0; sl < wfar_degree_slots(j); ++sl) {
+                int i, cp;  // harmonic column and part held by this slot, or a padding slot
+                if (sl < 4) {
+                    if (sl != 0) continue;
+                    i = 0;
+                    cp = 0;
+                } else {
+                    i = 2 * ((sl - 4) / 4) + 1 + ((sl & 3) >> 1);
+                    cp = sl & 1;
+                    if (i > j) continue;
                 }
-                const size_t pos = (size_t)pl->ckoff[c] * pl->Rp + tc::kmajor_off(row, kk, (uint32_t)W * 32u) / 4u;
-                out[pos] = rc;
+                for (int row = 0; row < pl->R; ++row) {
+                    int k, l, rp;
+                    host_decode(row, k, l, rp);
+                    const int n = j - k;
+                    WfarRecipe rc{0.0, 0.0, -1, -1, 0, 0};
+                    if (n >= 0) {
+                        const double colscale = host_F(j, j) / host_F(j, i), inv_kl = 1.0 / host_F(k, l);
+                        const bool take_y = (rp != cp);  // (0,0), (1,1) read .x; (0,1), (1,0) read .y
+                        // sign applied to the chosen component of M_n^m for m < 0 (M_n^{-m} = (-1)^m conj M_n^m)
+                        auto sgn = [&](int m) {
+                            if (m >= 0) return 1.0;
+                            return take_y ? ((m & 1) ? 1.0 : -1.0) : ((m & 1) ? -1.0 : 1.0);
+                        };
+                        const double sg = (i & 1) ? -1.0 : 1.0;
+                        double w1, w2;  // coefficients of a1 and a2 in the entry
+                        if (rp == 0 && cp == 0) { w1 = 1.0; w2 = sg; }
+                        else if (rp == 0 && cp == 1) { w1 = 1.0; w2 = -sg; }
+                        else if (rp == 1 && cp == 0) { w1 = 1.0; w2 = sg; }
+                        else { w1 = -1.0; w2 = sg; }
+                        const int m1 = i - l, m2 = -i - l;
+                        if (m1 >= -n && m1 <= n) {
+                            rc.t1 = tri(n, m1 < 0 ? -m1 : m1);
+                            rc.f1 = w1 * sgn(m1) * host_F(n + k, m1 + l) * inv_kl * colscale;
+                        }
+                        if (i > 0 && m2 >= -n && m2 <= n) {
+                            rc.t2 = tri(n, m2 < 0 ? -m2 : m2);
+                            rc.f2 = w2 * sgn(m2) * host_F(n + k, m2 + l) * inv_kl * colscale;
+                        }
+                        rc.bits = (take_y ? 3 : 0) | (n << 8);
+                    }
+                    const size_t pos = (size_t)pl->ckoff[c] * pl->Rp + tc::kmajor_off(row, kb + sl, (uint32_t)W * 32u) / 4u;
+                    out[pos] = rc;
+                }
             }
     }
     return out;
@@ -794,10 +827,10 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
             }
             pl->Y = dalloc<float>((int64_t)std::max(np, 1) * pl->R);
             const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, Q);
-            if (pl->NU == 12)
-                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            if (pl->NU == 6)
+                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             else
-                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<18>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             QBX_CUDA_TRY(cudaStreamSynchronize(st));
             dfree(cm_cnt); dfree(d_cnt); dfree(d_start); dfree(flag); dfree(tot);
             return pl;
@@ -860,8 +893,8 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
                      pl->pair_ctr, pl->slot, pl->H_tc, T->cxyz, T->cr, T->cen, T->hw, T->np[KCTR], pl->Y, err};
         const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, pl->Q);
         const int grid = std::min(pl->ntc, nsm);
-        if (pl->NU == 12) k_wfar_tc<12><<<grid, 256, sm, st>>>(a);
-        else k_wfar_tc<18><<<grid, 256, sm, st>>>(a);
+        if (pl->NU == 6) k_wfar_tc<6><<<grid, 256, sm, st>>>(a);
+        else k_wfar_tc<10><<<grid, 256, sm, st>>>(a);
         QBX_LAUNCH_CHECK();
         return;
     }
