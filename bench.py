@@ -48,16 +48,35 @@ def _dist_env():
     return ws, rank, local
 
 
-def make_workload(n_sub=20):
-    from synth import greens_density, make_surface, star_radius, volume_targets
-    from synth.surfaces import STAR_Y63
+# Named single-surface workloads: (faces subdivided n x n, shape, density, (p_qbx, p_fmm), volume points)
+WORKLOADS = {
+    # 8,000 curved triangles (120,000 sources): S[d_n u] - D[u], Green's formula
+    "star8k": (20, "Y63", "greens", (7, 15), 10000),
+    # 40,500 curved triangles (607,500 sources): the precision variant of the same star
+    "star40k": (45, "Y63", "greens", (7, 15), 10000),
+    # 79,380 curved triangles (1,190,700 sources): the learned-order surface, random Y_n^m density
+    "star79k": (63, "Y84Y52", "random", (8, 16), 0),
+}
 
-    s = make_surface(n_sub, star_radius(STAR_Y63))
-    u, dudn = greens_density(s)
-    vt, vc, vflag = volume_targets(s, N_VOLUME, seed=2)
-    t = np.concatenate([s.tgt_xyz, vt], axis=1)
-    tc = np.concatenate([s.tgt_ctr, vc]).astype(np.int32)
-    return s, u, dudn, t, tc, vflag
+
+def make_workload(n_sub=20, name="star8k"):
+    from synth import greens_density, make_surface, random_harmonic_density, star_radius, volume_targets
+    from synth.surfaces import STAR_Y63, STAR_Y84_Y52
+
+    _, shape, dens, _, nvol = WORKLOADS[name]
+    s = make_surface(n_sub, star_radius(STAR_Y63 if shape == "Y63" else STAR_Y84_Y52))
+    if dens == "greens":
+        u, dudn = greens_density(s)
+        sigma, mu = dudn, -u
+    else:
+        sigma, mu = random_harmonic_density(s, 10, 4), None
+    if nvol:
+        vt, vc, vflag = volume_targets(s, nvol, seed=2)
+        t = np.concatenate([s.tgt_xyz, vt], axis=1)
+        tc = np.concatenate([s.tgt_ctr, vc]).astype(np.int32)
+    else:
+        t, tc, vflag = s.tgt_xyz, s.tgt_ctr.astype(np.int32), np.zeros(0, bool)
+    return s, sigma, mu, t, tc, vflag
 
 
 # ------------------------------------------------------------------ algorithmic work model
@@ -354,7 +373,7 @@ def run_gpu(args):
     dev = torch.device("cuda", local)
     import paper_1805_06106_gb300 as G
 
-    s, u, dudn, t, tc, vflag = make_workload(args.n_sub)
+    s, sigma, mu, t, tc, vflag = make_workload(args.n_sub, args.workload)
     n_qbx_tgt = int(np.sum(tc >= 0))
     n_pt_tgt = int(np.sum(tc < 0))
 
@@ -372,9 +391,10 @@ def run_gpu(args):
         params, (mq, mp), learned_info = learned_setup(G, n_max)
 
         def orders_fn(T, L):
-            w_, sg_, mu_, n_ = (cu(s.src_w), cu(dudn), cu(-u), cu(s.src_n))
+            w_, sg_, mu_, n_ = (cu(s.src_w), cu(sigma), None if mu is None else cu(mu), cu(s.src_n))
             qc, pb = learned.predict_orders(T, L, params, w_, sg_, mu_, n_, q_range=(2, P_QBX), p_range=(4, P_FMM),
-                                            margin_q=mq, margin_p=mp, p_default=P_FMM)
+                                            margin_q=mq, margin_p=mp, p_default=P_FMM,
+                                            tgt_ctr=cu(tc, torch.int32))
             qn, pn = qc.cpu().numpy().astype(int), pb.cpu().numpy().astype(int)
             learned_info["mean_p_qbx"] = float(qn.mean())
             learned_info["mean_p_fmm_box"] = float(pn.mean())
@@ -394,7 +414,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         geo = [cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(t)]
-        ev_in = (cu(s.src_w), cu(dudn), cu(-u), cu(s.src_n), cu(tc, torch.int32))
+        ev_in = (cu(s.src_w), cu(sigma), None if mu is None else cu(mu), cu(s.src_n), cu(tc, torch.int32))
         main = _measure(G, torch, dev, stream, geo, ev_in, t.shape[1], n_max, precs[mode], args.steps, args.warmup,
                         True, local, orders=orders_fn, rank_sync=sync)
         total_ms = max_over_ranks(float(sum(main["step_ms"])))
@@ -402,10 +422,10 @@ def run_gpu(args):
         value = ws * n_qbx_tgt * args.steps / (total_ms * 1e-3)
 
         # end to end through the public API: pinned host inputs in, potentials out
-        host_in = [x.cpu().pin_memory() for x in ev_in]
+        host_in = [None if x is None else x.cpu().pin_memory() for x in ev_in]
         host_out = torch.empty(t.shape[1], dtype=torch.float64).pin_memory()
-        dev_in = [torch.empty_like(x) for x in ev_in]
-        h2d = sum(x.numel() * x.element_size() for x in host_in)
+        dev_in = [None if x is None else torch.empty_like(x) for x in ev_in]
+        h2d = sum(x.numel() * x.element_size() for x in host_in if x is not None)
         d2h = host_out.numel() * host_out.element_size()
         n_e2e = max(1, min(args.steps, 5))
         torch.cuda.synchronize()
@@ -416,7 +436,8 @@ def run_gpu(args):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for d, h in zip(dev_in, host_in):
-                d.copy_(h, non_blocking=True)
+                if d is not None:
+                    d.copy_(h, non_blocking=True)
             main["step"](dev_in)
             host_out.copy_(main["pot_buf"], non_blocking=True)
             e1.record(stream)
@@ -427,13 +448,14 @@ def run_gpu(args):
 
         plain = None
         err_vs_fp64 = None
-        if mode != "fp64" and not args.no_fp64_baseline:
+        if mode != "fp64":
             # accuracy of the mixed result against FP64 on the same tree and lists (untimed)
             T, L = main["T"], main["L"]
             ref64 = G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM)
             err_vs_fp64 = float((main["pot"] - ref64).abs().max() / ref64.abs().max())
             if learned_info is not None:
                 learned_info["judge_passed"] = err_vs_fp64 <= TOL
+        if mode != "fp64" and not args.no_fp64_baseline:
             # plain FP64 GIGAQBX at its own tuned leaf size, timed the same way
             base = _measure(G, torch, dev, stream, geo, ev_in, t.shape[1], N_MAX, G.QBX_FP64, args.fp64_steps,
                             args.warmup, False, local, rank_sync=sync)
@@ -461,8 +483,12 @@ def run_gpu(args):
             "f64 (List 2 M2L and List 3 far M2QBXL products in f32)" if precs[mode] == G.QBX_M2L_FP32 else
             "f64 (List 2 M2L and List 3 far M2QBXL products as split-tf32 tensor-core MMAs, f32 accumulation)"),
         "data": "synthetic",
-        "config": {"workload": f"star r=1+0.3ReY63, {s.n_elem} curved triangles x 15 nodes: S[d_n u] - D[u] at "
-                               f"{s.n_ctr} on-surface QBX targets + {N_VOLUME} volume points",
+        "config": {"workload": (f"{args.workload}: star r=1+0.3ReY63, {s.n_elem} curved triangles x 15 nodes: "
+                                f"S[d_n u] - D[u] at {s.n_ctr} on-surface QBX targets + {n_pt_tgt} volume points"
+                                if WORKLOADS[args.workload][1] == "Y63" else
+                                f"{args.workload}: star r=1+0.25ReY84+0.15ReY52, {s.n_elem} curved triangles x 15 "
+                                f"nodes: S[sigma], sigma = sum of N(0,1) Y_n^m (n<=10), at {s.n_ctr} on-surface QBX "
+                                f"targets"),
                    "mode": {"fp64": "plain FP64 GIGAQBX, fixed orders",
                             "fp32": "mixed precision (FP32 translation products), fixed orders",
                             "3xtf32": "mixed precision (split-TF32 tensor-core translation products), fixed orders",
@@ -492,10 +518,11 @@ def run_gpu(args):
     }
     if learned_info is not None:
         line["learned_orders"] = learned_info
+    if err_vs_fp64 is not None:
+        line["rel_err_vs_fp64_same_tree"] = err_vs_fp64
     if plain is not None:
         line["plain_fp64"] = plain
         line["speedup_vs_plain_fp64"] = value / plain["value"]
-        line["rel_err_vs_fp64_same_tree"] = err_vs_fp64
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_oracle_sample()
     print(json.dumps(line), flush=True)
@@ -567,7 +594,7 @@ def run_batched(args):
             feats = G.qbx_center_features(T, L, ev[0][sl].contiguous(), ev[1][sl].contiguous(), None,
                                           ev[3][:, sl].contiguous())
             preds.append(G.qbx_mlp_forward(params, feats))
-        qc, pb = G.qbx_orders_from_mlp(F, FL, torch.cat(preds), mq, mp, 2, P_QBX, 4, P_FMM, P_FMM)
+        qc, pb = G.qbx_orders_from_mlp(F, FL, torch.cat(preds), mq, mp, 2, P_QBX, 4, P_FMM, P_FMM, tgt_ctr=ev[4])
         pot = torch.empty(int(F.info.n_tgt), dtype=torch.float64, device=dev)
         graph = G.qbx_graph_create(F, FL, *ev, P_QBX, P_FMM, pot, p_qbx_per_ctr=qc, p_fmm_per_box=pb,
                                    precision=G.QBX_M2L_3XTF32)
@@ -666,7 +693,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--n-sub", type=int, default=20, help="icosahedron face subdivision (20 = 8,000 elements)")
+    ap.add_argument("--n-sub", type=int, default=None,
+                    help="icosahedron face subdivision (default: the workload's; 20 = 8,000 elements)")
     ap.add_argument("--n-max", type=int, default=0, help="particles per leaf before a box splits (0: tuned value)")
     ap.add_argument("--mixed-form", choices=("fp32", "3xtf32"), default="3xtf32",
                     help="translation products of the learned mode: FP32 SIMT or split-TF32 tensor cores")
@@ -674,12 +702,20 @@ def main():
                     help="fp64: every stage FP64; fp32: List 2 M2L and List 3 far M2QBXL as FP32 products; "
                          "learned: fp32 with per-center / per-box orders from the trained network")
     ap.add_argument("--fp64-steps", type=int, default=5, help="timed steps of the plain FP64 comparison")
-    ap.add_argument("--workload", choices=("star8k", "batched"), default="star8k",
-                    help="star8k: one 120k-source star surface; batched: many surfaces in one forest and graph")
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched",), default="star8k",
+                    help="star8k (120k sources, default), star40k (607k), star79k (1.19M, random density, orders "
+                         "8/16), or batched: many surfaces in one forest and graph")
     ap.add_argument("--batch", type=int, default=64, help="surfaces of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the leaf-size autotuner")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     args = ap.parse_args()
+    global P_QBX, P_FMM
+    if args.workload in WORKLOADS:
+        n_sub, _, _, (P_QBX, P_FMM), _ = WORKLOADS[args.workload]
+        if args.n_sub is None:
+            args.n_sub = n_sub
+    elif args.n_sub is None:
+        args.n_sub = 20
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batched":

@@ -122,9 +122,12 @@ void qbx_lists_free(qbx_lists *lists);
 
 typedef struct {
     int p_qbx;                    /* QBX order, 0 <= p_qbx <= 16; with p_qbx_per_ctr: the largest entry allowed */
-    int p_fmm;                    /* FMM order, 0 <= p_fmm <= 20; with p_fmm_per_box: the largest entry allowed */
+    int p_fmm;                    /* FMM order, 0 <= p_fmm <= 20: the order of every multipole expansion, and of
+                                     every box's local expansion unless p_fmm_per_box is given */
     const int8_t *p_qbx_per_ctr;  /* optional device array [n_ctr], per-center QBX order in [0, p_qbx] */
-    const int8_t *p_fmm_per_box;  /* optional device array [n_boxes], per-box FMM order in [0, p_fmm] */
+    const int8_t *p_fmm_per_box;  /* optional device array [n_boxes], order in [0, p_fmm] of each box's local
+                                     expansion (List 2 M2L and List 4 far P2L outputs, L2L, L2QBXL, L2P);
+                                     multipoles always have the order p_fmm */
     int precision;                /* QBX_FP64, QBX_M2L_FP32 or QBX_M2L_3XTF32 */
 } qbx_eval_opts;
 
@@ -221,15 +224,16 @@ int qbx_mlp_train(float *params_dev, float *adam_m_dev, float *adam_v_dev, const
 
 /*
  * Orders from predictions pred[2*c..2*c+1] (input center order): p_qbx of center c =
- * clamp(ceil(pred0 + margin_q), q_lo, q_hi); p_fmm of box b = the largest clamp(ceil(pred1 +
- * margin_p), p_lo, p_hi) over the centers of b's subtree, then the largest such value over b
- * and the boxes of b's six interaction lists (a box's order also truncates the expansions it
- * sends); p_default where no center contributes.  Outputs are the per-center and per-box
+ * clamp(ceil(pred0 + margin_q), q_lo, q_hi); the order of box b's local expansion = the largest
+ * clamp(ceil(pred1 + margin_p), p_lo, p_hi) over the centers of b's subtree (a parent's local is
+ * translated to its children), p_hi for boxes holding point targets (tgt_ctr[t] = -1; they read
+ * the box local directly) and their ancestors, p_default where no center or point target
+ * contributes.  tgt_ctr may be NULL (no point targets).  Outputs are the per-center and per-box
  * arrays qbx_eval_opts takes.
  */
-int qbx_orders_from_mlp(const qbx_tree *tree, const qbx_lists *lists, const float *pred_dev, float margin_q,
-                        float margin_p, int q_lo, int q_hi, int p_lo, int p_hi, int p_default,
-                        int8_t *p_qbx_per_ctr_dev, int8_t *p_fmm_per_box_dev, void *stream);
+int qbx_orders_from_mlp(const qbx_tree *tree, const qbx_lists *lists, const float *pred_dev,
+                        const int32_t *tgt_ctr_dev, float margin_q, float margin_p, int q_lo, int q_hi, int p_lo,
+                        int p_hi, int p_default, int8_t *p_qbx_per_ctr_dev, int8_t *p_fmm_per_box_dev, void *stream);
 
 /* ------------------------------------------------------------------------------------------
  * Batched problems and captured evaluations.  Not steps of the paper's method: they run
@@ -311,7 +315,7 @@ int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
  * allocator owns the device.  The paper has no counterpart; it is an interface choice.
  *   Scratch: one file-scope device array of QBX_NOALLOC_SCRATCH_BYTES (48 MiB) inside
  *   the library, held by every GPU that loads the library until the process exits.
- *   The problem must fit: about 18.4 MB of tables + 7,392 B per box + 16 ntri(Qb) B per
+ *   The problem must fit: about 18.4 MB of tables + 7,394 B per box + 16 ntri(Qb) B per
  *   center (Qb = 4, 8, 12 or 16, the smallest >= p_qbx)
  *   + 33 B per source; e.g. 2,000 boxes and 20,000 centers at p_qbx <= 8.  A larger
  *   problem returns QBX_ERR_INVALID_ARG with the byte counts in qbx_last_error().

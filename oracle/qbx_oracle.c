@@ -1142,8 +1142,9 @@ static void setup_sources(srcset *S, const double *sxyz, int ns, const double *w
  * GIGAQBX FMM (Algorithm 4, Stages 2-9).  pot[t] = S[sigma](t) + D[mu](t) at every target.
  * Charges are w sigma, dipoles w mu n.  tgt_ctr[t] >= 0: t is evaluated through the QBX
  * local of that center (Stage 9, second loop); tgt_ctr[t] < 0: t is a conventional
- * (point) target.  Orders: per box p_fmm[b] (or the fixed p_fmm), per center p_qbx[c]
- * (or the fixed p_qbx); a translation between different orders truncates or pads.
+ * (point) target.  Orders: every multipole expansion has the order p_fmm; the local
+ * expansion of box b has the order pbox[b] (or p_fmm); the QBX local of center c has
+ * p_qbx[c] (or p_qbx); a translation between different orders truncates or pads.
  * If qbx_out is given it receives each center's QBX local, (qmax+1)^2 complex per center.
  */
 int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, const double *w, const double *sigma,
@@ -1157,7 +1158,7 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
     setup_sources(&S, sxyz, ns, w, sigma, mu, nrm);
     int nb = T->nb;
     int pmax = p_fmm;
-    if (pbox) { pmax = 0; for (int b = 0; b < nb; ++b) if (pbox[b] > pmax) pmax = pbox[b]; }
+    if (pbox) for (int b = 0; b < nb; ++b) if (pbox[b] > pmax) pmax = pbox[b];
     int qm = p_qbx;
     if (qctr) { qm = 0; for (int c = 0; c < nc; ++c) if (qctr[c] > qm) qm = qctr[c]; }
     int nP = sq(pmax), nQ = sq(qm);
@@ -1167,18 +1168,19 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
     double *pnear = calloc(nt > 0 ? nt : 1, sizeof(double));
     double s[3], d[3], c[3], t[3], qq;
     int hd;
-#define PB(b) (pbox ? (int)pbox[b] : p_fmm)
+#define PB(b) (pbox ? (int)pbox[b] : p_fmm) /* order of the local expansion of box b */
+#define PM p_fmm                            /* order of every multipole expansion */
 #define QC(cc) (qctr ? (int)qctr[cc] : p_qbx)
 
     /* Stage 2: multipoles of leaves, then upward pass in postorder */
     for (int b = 0; b < nb; ++b)
         for (int k = T->own_start[KSRC][b]; k < T->own_start[KSRC][b + 1]; ++k) {
             src_q_d(&S, T->own_idx[KSRC][k], s, &qq, d, &hd);
-            p2m(PB(b), &T->cen[3 * b], s, qq, hd ? d : NULL, &M[(size_t)b * nP]);
+            p2m(PM, &T->cen[3 * b], s, qq, hd ? d : NULL, &M[(size_t)b * nP]);
         }
     for (int b = nb - 1; b >= 1; --b) {
         int pa = T->parent[b];
-        if (T->nsrc_sub[b] > 0) m2m(PB(b), &T->cen[3 * b], &M[(size_t)b * nP], PB(pa), &T->cen[3 * pa], &M[(size_t)pa * nP]);
+        if (T->nsrc_sub[b] > 0) m2m(PM, &T->cen[3 * b], &M[(size_t)b * nP], PM, &T->cen[3 * pa], &M[(size_t)pa * nP]);
     }
 
     /* Stages 3, 5(a), 6(a): direct interactions from U, W-close, X-close */
@@ -1207,7 +1209,7 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
     for (int b = 0; b < nb; ++b)
         for (int i = Ls->start[L_V][b]; i < Ls->start[L_V][b + 1]; ++i) {
             int dd = Ls->idx[L_V][i];
-            m2l(PB(dd), &T->cen[3 * dd], &M[(size_t)dd * nP], PB(b), &T->cen[3 * b], &L[(size_t)b * nP]);
+            m2l(PM, &T->cen[3 * dd], &M[(size_t)dd * nP], PB(b), &T->cen[3 * b], &L[(size_t)b * nP]);
         }
 
     /* Stage 5(b): List 3 far multipoles at point targets and QBX centers */
@@ -1218,12 +1220,12 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
                 int ti = T->own_idx[KTGT][k];
                 if (tgt_ctr[ti] >= 0) continue;
                 get_pt(txyz, nt, ti, t);
-                pnear[ti] += m2p(PB(dd), &T->cen[3 * dd], &M[(size_t)dd * nP], t);
+                pnear[ti] += m2p(PM, &T->cen[3 * dd], &M[(size_t)dd * nP], t);
             }
             for (int k = T->own_start[KCTR][b]; k < T->own_start[KCTR][b + 1]; ++k) {
                 int ci = T->own_idx[KCTR][k];
                 get_pt(cxyz, nc, ci, c);
-                m2l(PB(dd), &T->cen[3 * dd], &M[(size_t)dd * nP], QC(ci), c, &Lq[(size_t)ci * nQ]);
+                m2l(PM, &T->cen[3 * dd], &M[(size_t)dd * nP], QC(ci), c, &Lq[(size_t)ci * nQ]);
             }
         }
 
@@ -1272,6 +1274,7 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
                 qbx_out[2 * ((size_t)ci * sq(qmax) + i) + 1] = cimag(v);
             }
 #undef PB
+#undef PM
 #undef QC
     free(M); free(L); free(Lq); free(pnear); free(S.q); free(S.dip);
     return 0;

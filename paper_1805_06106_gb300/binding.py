@@ -69,8 +69,8 @@ def lib():
         L.qbx_mlp_forward.argtypes = [P, P, I64, P, P]
         L.qbx_mlp_loss_grad.argtypes = [P, P, P, I64, P, P]
         L.qbx_mlp_train.argtypes = [P, P, P, P, P, I64, C.c_int, C.c_int, C.c_float, P, P]
-        L.qbx_orders_from_mlp.argtypes = [P, P, P, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
-                                          P, P, P]
+        L.qbx_orders_from_mlp.argtypes = [P, P, P, P, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int, C.c_int,
+                                          C.c_int, P, P, P]
         L.qbx_build_forest.argtypes = [C.c_int, P, P, C.POINTER(P), C.POINTER(P), P]
         L.qbx_forest_problems.argtypes = [P, C.POINTER(C.c_int)]
         L.qbx_forest_offsets.argtypes = [P, P]
@@ -291,13 +291,16 @@ def qbx_mlp_train(params, adam_m, adam_v, x, target, steps, first_step, lr):
     return loss.value
 
 
-def qbx_orders_from_mlp(tree: Tree, lists: Lists, pred, margin_q, margin_p, q_lo, q_hi, p_lo, p_hi, p_default):
+def qbx_orders_from_mlp(tree: Tree, lists: Lists, pred, margin_q, margin_p, q_lo, q_hi, p_lo, p_hi, p_default,
+                        tgt_ctr=None):
+    """Per-center QBX orders and per-box local-expansion orders from network predictions; tgt_ctr
+    (optional) marks point targets, whose boxes keep p_hi."""
     qc = torch.empty(tree.info.n_ctr, dtype=torch.int8, device="cuda")
     pb = torch.empty(tree.n_boxes, dtype=torch.int8, device="cuda")
+    tc = _dev(tgt_ctr, torch.int32)
     _check(lib().qbx_orders_from_mlp(tree.handle, lists.handle, _ptr(_dev(pred.contiguous(), torch.float32)),
-                                     float(margin_q),
-                                     float(margin_p), q_lo, q_hi, p_lo, p_hi, p_default, _ptr(qc), _ptr(pb),
-                                     _stream()))
+                                     _ptr(tc), float(margin_q), float(margin_p), q_lo, q_hi, p_lo, p_hi, p_default,
+                                     _ptr(qc), _ptr(pb), _stream()))
     return qc, pb
 
 

@@ -50,7 +50,7 @@ struct qbx_workspace {
     double2 *m2l_tab = nullptr;    // 1331 offsets x ntri(2 PM): S_j^i(2 o)
     double2 *oct_tab = nullptr;    // 8 octants x ntri(PM): R_j^i(delta_o)
     double *sq = nullptr, *sd = nullptr;
-    signed char *qc = nullptr, *pb = nullptr;
+    signed char *qc = nullptr, *pb = nullptr, *ps = nullptr;  // per-center QBX, per-box local and multipole orders
     int *flags = nullptr;
     std::vector<int> lvl_first;    // host copies of level ranges
     qbx::M2LPlan *m2l = nullptr;   // mixed-precision List 2 plan (built on first use)
@@ -69,7 +69,7 @@ void free_workspace(qbx_workspace *ws)
 {
     if (!ws) return;
     dfree(ws->Mu); dfree(ws->B); dfree(ws->A); dfree(ws->m2l_tab); dfree(ws->oct_tab);
-    dfree(ws->sq); dfree(ws->sd); dfree(ws->qc); dfree(ws->pb); dfree(ws->flags);
+    dfree(ws->sq); dfree(ws->sd); dfree(ws->qc); dfree(ws->pb); dfree(ws->ps); dfree(ws->flags);
     free_m2l_plan(ws->m2l);
     free_wfar_plan(ws->wfar);
     dfree(ws->pt_cnt); dfree(ws->pt_off); dfree(ws->pt_total); dfree(ws->pt_it); dfree(ws->pt_box);
@@ -132,8 +132,11 @@ void prep_sources(const int *perm, int64_t ns, const double *w, const double *si
 }
 
 // qfix / pfix are the fixed orders, or the bounds of the per-center / per-box arrays
+// qc: per-center QBX order; pb: per-box order of the local expansions a box receives; ps: order of
+// the multipole expansions every box sends (the fixed bound p_fmm)
 __global__ void k_prep_orders(const int *ctr_perm, int64_t nc, const signed char *qin, int qfix, int64_t nb,
-                              const signed char *pin, int pfix, signed char *qc, signed char *pb, int *flags)
+                              const signed char *pin, int pfix, signed char *qc, signed char *pb, signed char *ps,
+                              int *flags)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < nc) {
@@ -145,6 +148,7 @@ __global__ void k_prep_orders(const int *ctr_perm, int64_t nc, const signed char
         int p = pin ? pin[i] : pfix;
         if (p < 0 || p > pfix) atomicOr(flags, 2);
         pb[i] = (signed char)min(max(p, 0), pfix);
+        ps[i] = (signed char)pfix;
     }
 }
 
@@ -326,7 +330,7 @@ __global__ void __launch_bounds__(256) k_m2m8(int b0, int b1, const int *lvl_box
 
 template <int PM>
 __global__ void k_m2l(int64_t nb, const int *vstart, const int *vidx, const int64_t *ic, const double *hw,
-                      const signed char *pb, const double2 *Mu, const double2 *tab, double2 *B)
+                      const signed char *pb, const signed char *ps, const double2 *Mu, const double2 *tab, double2 *B)
 {
     extern __shared__ double2 sh[];
     int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -342,7 +346,7 @@ __global__ void k_m2l(int64_t nb, const int *vstart, const int *vidx, const int6
     for (int i = 0; i < NO; ++i) acc[i] = make_double2(0.0, 0.0);
     for (int e = e0; e < e1; ++e) {
         int d = vidx[e];
-        const int Pd = pb[d];
+        const int Pd = ps[d];
         __syncwarp();
         for (int i = lane; i < ntri(PM); i += 32) Ms[i] = i < ntri(Pd) ? Mu[(int64_t)d * ntri(PM) + i] : make_double2(0, 0);
         __syncwarp();
@@ -589,9 +593,9 @@ __device__ __forceinline__ void p2qbxl_accum(double bx, double by, double bz, do
 template <int QM, int PM>
 __global__ void __launch_bounds__(128) k_centers(
     int64_t nc, const int *ctr_box, const double *cxyz, const double *cr, const signed char *qc, const signed char *pb,
-    ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf, const int *own_start, const double *sxyz, int64_t ns,
-    const double *sq, const double *sd, const double *cen, const double *hw, const double2 *Mu, const double2 *B,
-    double2 *A)
+    const signed char *ps, ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf, const int *own_start, const double *sxyz,
+    int64_t ns, const double *sq, const double *sd, const double *cen, const double *hw, const double2 *Mu,
+    const double2 *B, double2 *A)
 {
     extern __shared__ double2 sh[];
     constexpr int NT = ntri(QM);
@@ -646,7 +650,7 @@ __global__ void __launch_bounds__(128) k_centers(
     // Stage 5(b): List 3 far multipoles to the QBX local
     for (int e = lwf.start[b]; e < lwf.start[b + 1]; ++e) {
         const int d = lwf.idx[e];
-        const int Pd = min((int)pb[d], PM);
+        const int Pd = min((int)ps[d], PM);
         const double hd = hw[d], hdinv = 1.0 / hd, ratio = rho * hdinv;
         __syncwarp();
         // S_j^i((c - c_d)/h_d) (rho/h_d)^j / h_d, j <= Pd + Q; pw[n] = (h_d/rho)^n
@@ -786,7 +790,7 @@ __global__ void k_qbxl2p(int64_t nt, const int *tperm, const double *txyz, const
 // Point targets: P2P from List 1 / 3 close / 4 close, M2P from List 3 far, L2P of the box local.
 template <int PM>
 __global__ void k_points(int64_t nt, const int *tperm, const double *txyz, const int *tgt_ctr, const int *tgt_box,
-                         const signed char *pb, ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf,
+                         const signed char *pb, const signed char *ps, ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf,
                          const int *own_start, const double *sxyz, int64_t ns, const double *sq, const double *sd,
                          const double *cen, const double *hw, const double2 *Mu, const double2 *B, double *pot)
 {
@@ -816,7 +820,7 @@ __global__ void k_points(int64_t nt, const int *tperm, const double *txyz, const
     // M2P: one List 3 far box per lane
     for (int e = lwf.start[b] + lane; e < lwf.start[b + 1]; e += 32) {
         int d = lwf.idx[e];
-        int P = pb[d];
+        int P = ps[d];
         double hinv = 1.0 / hw[d];
         double x = (tx - cen[3 * d]) * hinv, y = (ty - cen[3 * d + 1]) * hinv, z = (tz - cen[3 * d + 2]) * hinv;
         double ir2 = 1.0 / (x * x + y * y + z * z);
@@ -1031,7 +1035,7 @@ static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, b
     }
     if (T->np[KCTR] > 0) {
         k_centers<QM, PM_T><<<nblocks(T->np[KCTR], WPB), 32 * WPB, smem, st>>>(
-            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc, ws->pb, ListRef{L->start[LU], L->idx[LU]},
+            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc, ws->pb, ws->ps, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
             ListRef{wf_start, L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,
             dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A);
@@ -1072,6 +1076,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         ws->sd = dalloc<double>(3 * ns);
         ws->qc = dalloc<signed char>(nc);
         ws->pb = dalloc<signed char>(nb);
+        ws->ps = dalloc<signed char>(nb);
         ws->flags = dalloc<int>(1);
         k_m2l_table<<<nblocks(1331, 64), 64, 0, st>>>(2 * PM_T, ws->m2l_tab);
         k_oct_table<<<1, 32, 0, st>>>(PM_T, ws->oct_tab);
@@ -1082,7 +1087,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     QBX_CUDA_TRY(cudaMemsetAsync(ws->flags, 0, sizeof(int), st));
     k_prep_src<<<nblocks(ns, 256), 256, 0, st>>>(T->perm[KSRC], ns, w, sigma, mu, nrm, ws->sq, ws->sd, ws->flags);
     k_prep_orders<<<nblocks(std::max(nb, nc), 256), 256, 0, st>>>(T->perm[KCTR], nc, o->p_qbx_per_ctr, o->p_qbx, nb,
-                                                                  o->p_fmm_per_box, o->p_fmm, ws->qc, ws->pb, ws->flags);
+                                                                  o->p_fmm_per_box, o->p_fmm, ws->qc, ws->pb, ws->ps,
+                                                                  ws->flags);
     k_check_tgt<<<nblocks(nt, 256), 256, 0, st>>>(tgt_ctr, nt, nc, ws->flags);
     QBX_LAUNCH_CHECK();
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
@@ -1103,7 +1109,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     // the P2M and P2L kernels unroll their rows: instantiate them for the smallest order bound that covers p_fmm
 #define QBX_P2M(PB)                                                                                                 \
     k_p2m<PB, PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws->sq,              \
-                                                           dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->Mu)
+                                                           dip ? ws->sd : nullptr, T->cen, T->hw, ws->ps, ws->Mu)
     if (pmax <= 10) QBX_P2M(10);
     else if (pmax <= 16) QBX_P2M(16);
     else QBX_P2M(PM_T);
@@ -1112,7 +1118,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     for (int l = (int)T->nlev - 2; l >= 0; --l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
         if (b1 > b0)
-            k_m2m8<PM_T><<<b1 - b0, 256, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws->pb, ws->oct_tab, ws->Mu);
+            k_m2m8<PM_T><<<b1 - b0, 256, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws->ps, ws->oct_tab, ws->Mu);
         QBX_LAUNCH_CHECK();
     }
     // Stage 4
@@ -1120,7 +1126,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     if (o->precision == QBX_FP64) {
         size_t smem = (size_t)WPB * ntri(PM_T) * sizeof(double2);
         k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, smem, st>>>(nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws->pb,
-                                                              ws->Mu, ws->m2l_tab, ws->B);
+                                                              ws->ps, ws->Mu, ws->m2l_tab, ws->B);
         QBX_LAUNCH_CHECK();
     } else {
         const int Pm = o->p_fmm;
@@ -1167,7 +1173,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
             ws->wfar_key = wkey;
         }
         wf = ws->wfar;
-        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->pb, ws->flags, st);
+        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->ps, ws->flags, st);
     }
     // Stages 3, 5, 6(a), 8, 9 at QBX centers and their targets
     switch (QM) {
@@ -1204,7 +1210,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         QBX_LAUNCH_CHECK();
         if (ws->pt_cap > 0) {
             const unsigned grid = std::min<unsigned>(nblocks(ws->pt_cap, 128), 152 * 64);
-            k_m2p_pairs<PM_T><<<grid, 128, 0, st>>>(ws->pt_cap, ws->pt_total, ws->pt_it, ws->pt_box, T->txyz, nt, ws->pb,
+            k_m2p_pairs<PM_T><<<grid, 128, 0, st>>>(ws->pt_cap, ws->pt_total, ws->pt_it, ws->pt_box, T->txyz, nt, ws->ps,
                                                      T->cen, T->hw, ws->Mu, ws->pt_part);
             QBX_LAUNCH_CHECK();
         }
@@ -1334,7 +1340,8 @@ size_t fixed_workspace_bytes(const qbx_tree *T, const qbx_eval_opts *o)
     carve(off, (size_t)std::max<int64_t>(ns, 1) * sizeof(double));         // charges
     carve(off, (size_t)3 * std::max<int64_t>(ns, 1) * sizeof(double));     // dipoles
     carve(off, (size_t)std::max<int64_t>(nc, 1));                           // per-center orders
-    carve(off, (size_t)std::max<int64_t>(nb, 1));                           // per-box orders
+    carve(off, (size_t)std::max<int64_t>(nb, 1));                           // per-box local orders
+    carve(off, (size_t)std::max<int64_t>(nb, 1));                           // per-box multipole orders
     carve(off, sizeof(int));                                                // flags
     return off;
 }
@@ -1348,7 +1355,7 @@ static void fixed_centers(const qbx_tree *T, const qbx_lists *L, const qbx_works
     QBX_CUDA_TRY(cudaFuncSetAttribute(k_centers<QM, PM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (T->np[KCTR] > 0) {
         k_centers<QM, PM_T><<<nblocks(T->np[KCTR], WPB), 32 * WPB, smem, st>>>(
-            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws.qc, ws.pb, ListRef{L->start[LU], L->idx[LU]},
+            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws.qc, ws.pb, ws.ps, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
             ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws.sq,
             dip ? ws.sd : nullptr, T->cen, T->hw, ws.Mu, ws.B, ws.A);
@@ -1380,6 +1387,7 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     ws.sd = reinterpret_cast<double *>(base + carve(off, (size_t)3 * std::max<int64_t>(ns, 1) * sizeof(double)));
     ws.qc = reinterpret_cast<signed char *>(base + carve(off, (size_t)std::max<int64_t>(nc, 1)));
     ws.pb = reinterpret_cast<signed char *>(base + carve(off, (size_t)std::max<int64_t>(nb, 1)));
+    ws.ps = reinterpret_cast<signed char *>(base + carve(off, (size_t)std::max<int64_t>(nb, 1)));
     ws.flags = reinterpret_cast<int *>(base + carve(off, sizeof(int)));
     ws.PM = PM_T;
     ws.QM = QM;
@@ -1390,7 +1398,8 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     QBX_CUDA_TRY(cudaMemsetAsync(ws.flags, 0, sizeof(int), st));
     k_prep_src<<<nblocks(ns, 256), 256, 0, st>>>(T->perm[KSRC], ns, w, sigma, mu, nrm, ws.sq, ws.sd, ws.flags);
     k_prep_orders<<<nblocks(std::max(nb, nc), 256), 256, 0, st>>>(T->perm[KCTR], nc, o->p_qbx_per_ctr, o->p_qbx, nb,
-                                                                  o->p_fmm_per_box, o->p_fmm, ws.qc, ws.pb, ws.flags);
+                                                                  o->p_fmm_per_box, o->p_fmm, ws.qc, ws.pb, ws.ps,
+                                                                  ws.flags);
     k_check_tgt<<<nblocks(nt, 256), 256, 0, st>>>(tgt_ctr, nt, nc, ws.flags);
     QBX_LAUNCH_CHECK();
     cudaStreamCaptureStatus cap_st = cudaStreamCaptureStatusNone;
@@ -1407,15 +1416,15 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     const int WPB = 4;
     const bool dip = mu != nullptr;
     k_p2m<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws.sq,
-                                                       dip ? ws.sd : nullptr, T->cen, T->hw, ws.pb, ws.Mu);
+                                                       dip ? ws.sd : nullptr, T->cen, T->hw, ws.ps, ws.Mu);
     QBX_LAUNCH_CHECK();
     for (int l = (int)T->nlev - 2; l >= 0; --l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
-        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws.pb, ws.oct_tab, ws.Mu);
+        k_m2m<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws.ps, ws.oct_tab, ws.Mu);
         QBX_LAUNCH_CHECK();
     }
     k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, (size_t)WPB * ntri(PM_T) * sizeof(double2), st>>>(
-        nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws.pb, ws.Mu, ws.m2l_tab, ws.B);
+        nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws.pb, ws.ps, ws.Mu, ws.m2l_tab, ws.B);
     QBX_LAUNCH_CHECK();
     k_p2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], T->sxyz,
                                                        ns, ws.sq, dip ? ws.sd : nullptr, T->cen, T->hw, ws.pb, ws.B);
@@ -1434,7 +1443,7 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     }
     if (nt > 0) {
         k_points<PM_T><<<nblocks(nt, WPB), 32 * WPB, 0, st>>>(
-            nt, T->perm[KTGT], T->txyz, tgt_ctr, T->tgt_box, ws.pb, ListRef{L->start[LU], L->idx[LU]},
+            nt, T->perm[KTGT], T->txyz, tgt_ctr, T->tgt_box, ws.pb, ws.ps, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
             ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, ns, ws.sq, dip ? ws.sd : nullptr,
             T->cen, T->hw, ws.Mu, ws.B, pot);

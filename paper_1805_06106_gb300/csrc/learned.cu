@@ -225,13 +225,9 @@ __global__ void k_mlp_init(float *P, uint64_t seed)
 
 // ---------------------------------------------------------------- orders
 
-struct ListStarts {
-    const int *start[NLIST];
-    const int *idx[NLIST];
-};
-
-// q_out[c] (input order) = clamp(ceil(y0 + mq), qlo, qhi); per box: max over the centers of its
-// subtree of clamp(ceil(y1 + mp), plo, phi) (atomicMax up the parent chain), p_default elsewhere.
+// q_out[c] (input order) = clamp(ceil(y0 + mq), qlo, qhi); per box (the order of its local
+// expansion): max over the centers of its subtree of clamp(ceil(y1 + mp), plo, phi) (atomicMax up
+// the parent chain), p_default elsewhere.
 __global__ void k_orders_centers(int64_t nc, const int *ctr_perm, const int *ctr_box, const int *parent, const float *y,
                                  float mq, float mp, int qlo, int qhi, int plo, int phi, int8_t *q_out, int *pbox)
 {
@@ -248,17 +244,14 @@ __global__ void k_orders_centers(int64_t nc, const int *ctr_perm, const int *ctr
     for (int b = ctr_box[i]; b >= 0; b = parent[b]) atomicMax(&pbox[b], p);
 }
 
-// A box's order also truncates the expansions it sends: each box takes the largest order among
-// itself and the boxes of its six interaction lists (a box reaches the receivers of its field
-// through the partners of its lists).
-__global__ void k_orders_dilate(int64_t nb, const int *pin, ListStarts ls, int *pout)
+// Point targets read their box's local expansion directly: their boxes and all ancestors keep the
+// highest order.
+__global__ void k_orders_points(int64_t nt, const int *tgt_ctr, const int *tgt_owner, const int *parent, int phi,
+                                int *pbox)
 {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= nb) return;
-    int p = pin[b];
-    for (int l = 0; l < NLIST; ++l)
-        for (int e = ls.start[l][b]; e < ls.start[l][b + 1]; ++e) p = max(p, pin[ls.idx[l][e]]);
-    pout[b] = p;
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt || tgt_ctr[t] >= 0) return;
+    for (int b = tgt_owner[t]; b >= 0; b = parent[b]) atomicMax(&pbox[b], phi);
 }
 
 __global__ void k_orders_boxes(int64_t nb, const int *pbox, int p_default, int8_t *p_out)
@@ -420,9 +413,9 @@ int qbx_mlp_train(float *params, float *adam_m, float *adam_v, const float *x, c
     });
 }
 
-int qbx_orders_from_mlp(const qbx_tree *T, const qbx_lists *L, const float *pred, float margin_q, float margin_p,
-                        int q_lo, int q_hi, int p_lo, int p_hi, int p_default, int8_t *p_qbx_per_ctr,
-                        int8_t *p_fmm_per_box, void *stream)
+int qbx_orders_from_mlp(const qbx_tree *T, const qbx_lists *L, const float *pred, const int32_t *tgt_ctr,
+                        float margin_q, float margin_p, int q_lo, int q_hi, int p_lo, int p_hi, int p_default,
+                        int8_t *p_qbx_per_ctr, int8_t *p_fmm_per_box, void *stream)
 {
     return learned_guard([&]() -> int {
         if (!T || !L || L->tree != T || !pred || !p_qbx_per_ctr || !p_fmm_per_box || q_lo < 0 || q_hi > QMAX ||
@@ -430,28 +423,24 @@ int qbx_orders_from_mlp(const qbx_tree *T, const qbx_lists *L, const float *pred
             throw Error{QBX_ERR_INVALID_ARG, "bad argument"};
         cudaStream_t st = (cudaStream_t)stream;
         const int64_t nb = T->nb, nc = T->np[KCTR];
-        int *pbox = dalloc<int>(nb), *pdil = nullptr;
+        int *pbox = dalloc<int>(nb);
         try {
-            pdil = dalloc<int>(nb);
             QBX_CUDA_TRY(cudaMemsetAsync(pbox, 0, nb * sizeof(int), st));
             if (nc)
                 k_orders_centers<<<nblocks(nc, 256), 256, 0, st>>>(nc, T->perm[KCTR], T->ctr_box, T->parent, pred,
                                                                    margin_q, margin_p, q_lo, q_hi, p_lo, p_hi,
                                                                    p_qbx_per_ctr, pbox);
-            ListStarts ls;
-            for (int l = 0; l < NLIST; ++l) {
-                ls.start[l] = L->start[l];
-                ls.idx[l] = L->idx[l];
-            }
-            k_orders_dilate<<<nblocks(nb, 256), 256, 0, st>>>(nb, pbox, ls, pdil);
-            k_orders_boxes<<<nblocks(nb, 256), 256, 0, st>>>(nb, pdil, p_default, p_fmm_per_box);
+            if (tgt_ctr && T->np[KTGT])
+                k_orders_points<<<nblocks(T->np[KTGT], 256), 256, 0, st>>>(T->np[KTGT], tgt_ctr, T->owner[KTGT],
+                                                                           T->parent, p_hi, pbox);
+            k_orders_boxes<<<nblocks(nb, 256), 256, 0, st>>>(nb, pbox, p_default, p_fmm_per_box);
             QBX_LAUNCH_CHECK();
             QBX_CUDA_TRY(cudaStreamSynchronize(st));
         } catch (...) {
-            dfree(pbox); dfree(pdil);
+            dfree(pbox);
             throw;
         }
-        dfree(pbox); dfree(pdil);
+        dfree(pbox);
         return QBX_OK;
     });
 }

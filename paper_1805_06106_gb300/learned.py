@@ -75,11 +75,13 @@ def calibrate(params, samples, quantile=0.999):
 
 
 def predict_orders(tree, lists, params, src_w, sigma, mu, src_n, q_range=(2, 12), p_range=(4, 20),
-                   margin_q=0.5, margin_p=1.0, p_default=16):
+                   margin_q=0.5, margin_p=1.0, p_default=16, tgt_ctr=None):
+    """Per-center QBX orders and per-box local-expansion orders for one surface (tgt_ctr marks its
+    point targets, whose boxes keep the highest order)."""
     feats = B.qbx_center_features(tree, lists, src_w, sigma, mu, src_n)
     pred = B.qbx_mlp_forward(params, feats)
     return B.qbx_orders_from_mlp(tree, lists, pred, margin_q, margin_p, q_range[0], q_range[1], p_range[0],
-                                 p_range[1], p_default)
+                                 p_range[1], p_default, tgt_ctr=tgt_ctr)
 
 
 def save(params, path):
