@@ -179,6 +179,7 @@ __global__ void k_p2m(int64_t nb, const int *own_start, const double *sxyz, int6
     double2 acc[PM + 1];
 #pragma unroll
     for (int n = 0; n <= PM; ++n) acc[n] = make_double2(0.0, 0.0);
+    const double fm = m ? 0.5 / m : 0.0;
     for (int s = s0; s < s1; ++s) {
         double x = (sxyz[s] - cx) * hinv, y = (sxyz[ns + s] - cy) * hinv, z = (sxyz[2 * ns + s] - cz) * hinv;
         double r2 = x * x + y * y + z * z;
@@ -191,9 +192,15 @@ __global__ void k_p2m(int64_t nb, const int *own_start, const double *sxyz, int6
             dw = make_double2(0.5 * dx, 0.5 * dy);
             dwb = make_double2(0.5 * dx, -0.5 * dy);
         }
-        // diagonal R_m^m = w^m / (2^m m!)
-        double2 diag = make_double2(1.0, 0.0);
-        for (int j = 1; j <= m && j <= PM; ++j) diag = cscale(cmul(diag, make_double2(x, y)), 1.0 / (2.0 * j));
+        // diagonal R_m^m = w^m / (2^m m!): inclusive prefix product over the lanes of w / (2m)
+        double2 diag = (m == 0) ? make_double2(1.0, 0.0) : make_double2(x * fm, y * fm);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            double2 o;
+            o.x = __shfl_up_sync(0xffffffffu, diag.x, off);
+            o.y = __shfl_up_sync(0xffffffffu, diag.y, off);
+            if (m >= off) diag = cmul(o, diag);
+        }
         double2 p2 = make_double2(0.0, 0.0), p1 = make_double2(0.0, 0.0);
 #pragma unroll
         for (int n = 0; n <= PM; ++n) {
@@ -460,6 +467,102 @@ __global__ void k_p2l(int64_t nb, const int *xs, const int *xi, const int *own_s
                 double2 v = B[(int64_t)b * ntri(ST) + tri(n, m)];
                 B[(int64_t)b * ntri(ST) + tri(n, m)] = make_double2(v.x + acc[n].x * hinv, v.y + acc[n].y * hinv);
             }
+    }
+}
+
+// P2L with a block of 4 warps per box: warp w takes the List 4 far entries e = w (mod 4) (lane m
+// computes column m of S_n^m((c-s)/h) for one source at a time, the diagonal by a prefix product
+// over the lanes), and the 4 partial locals are added in warp order in shared memory.
+template <int PM, int ST = PM>
+__global__ void __launch_bounds__(128) k_p2l4(int64_t nb, const int *xs, const int *xi, const int *own_start,
+                                              const double *sxyz, int64_t ns, const double *sq, const double *sd,
+                                              const double *cen, const double *hw, const signed char *pb, double2 *B)
+{
+    __shared__ double2 part[4][PM + 1][PM + 1];
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int e0 = xs[b], e1 = xs[b + 1];
+    if (e0 == e1) return;
+    const int w = threadIdx.x >> 5, m = threadIdx.x & 31;
+    const int P = pb[b];
+    const double h = hw[b], hinv = 1.0 / h;
+    const double cx = cen[3 * b], cy = cen[3 * b + 1], cz = cen[3 * b + 2];
+    double2 acc[PM + 1];
+#pragma unroll
+    for (int n = 0; n <= PM; ++n) acc[n] = make_double2(0.0, 0.0);
+    const double fm = 2.0 * m - 1.0;
+    for (int e = e0 + w; e < e1; e += 4) {
+        const int d = xi[e];
+        for (int s = own_start[d]; s < own_start[d + 1]; ++s) {
+            double x = (cx - sxyz[s]) * hinv, y = (cy - sxyz[ns + s]) * hinv, z = (cz - sxyz[2 * ns + s]) * hinv;
+            double ir2 = 1.0 / (x * x + y * y + z * z);
+            double rinv = sqrt(ir2);
+            double q = sq[s];
+            double2 dw = make_double2(0.0, 0.0), dwb = make_double2(0.0, 0.0);
+            double dz = 0.0;
+            if (sd) {
+                double dx = sd[s] * hinv, dy = sd[ns + s] * hinv;
+                dz = sd[2 * ns + s] * hinv;
+                dw = make_double2(0.5 * dx, 0.5 * dy);
+                dwb = make_double2(0.5 * dx, -0.5 * dy);
+            }
+            const double2 wr = make_double2(x * ir2, y * ir2);
+            const double zz = z * ir2;
+            // diagonal S_m^m = rinv prod_{j<=m} (2j-1) wr: inclusive prefix product of the lane factors
+            double2 diag = (m == 0) ? make_double2(rinv, 0.0) : cscale(wr, fm);
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                double2 o;
+                o.x = __shfl_up_sync(0xffffffffu, diag.x, off);
+                o.y = __shfl_up_sync(0xffffffffu, diag.y, off);
+                if (m >= off) diag = cmul(o, diag);
+            }
+            double2 p2 = make_double2(0.0, 0.0), p1 = make_double2(0.0, 0.0);
+#pragma unroll
+            for (int n1 = 0; n1 <= PM + 1; ++n1) {  // row n1 = n + 1 closes output row n
+                double2 cur = make_double2(0.0, 0.0);
+                if (n1 == m) cur = diag;
+                else if (n1 > m) {
+                    double c1 = (2 * n1 - 1) * zz, c2 = (double)(n1 + m - 1) * (double)(n1 - m - 1) * ir2;
+                    cur = make_double2(c1 * p1.x - c2 * p2.x, c1 * p1.y - c2 * p2.y);
+                }
+                int n = n1 - 1;
+                double2 up, dn;  // S_{n+1}^{m+1}, S_{n+1}^{m-1}
+                up.x = __shfl_down_sync(0xffffffffu, cur.x, 1);
+                up.y = __shfl_down_sync(0xffffffffu, cur.y, 1);
+                dn.x = __shfl_up_sync(0xffffffffu, cur.x, 1);
+                dn.y = __shfl_up_sync(0xffffffffu, cur.y, 1);
+                if (m == 31) up = make_double2(0.0, 0.0);
+                if (m == 0) dn = make_double2(-up.x, up.y);
+                if (n >= m && n <= P) {
+                    // conj[q S_n^m + (dbar/2) S_{n+1}^{m+1} - (d/2) S_{n+1}^{m-1} + dz S_{n+1}^m]
+                    double2 v = cscale(p1, q);
+                    if (sd) {
+                        double2 t1 = cmul(dwb, up), t2 = cmul(dw, dn);
+                        v.x += t1.x - t2.x + dz * cur.x;
+                        v.y += t1.y - t2.y + dz * cur.y;
+                    }
+                    acc[n] = cadd(acc[n], cconj(v));
+                }
+                p2 = p1;
+                p1 = cur;
+            }
+        }
+    }
+    if (m <= PM) {
+#pragma unroll
+        for (int n = 0; n <= PM; ++n) part[w][n][m] = acc[n];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntri(P); t += blockDim.x) {
+        int n = 0;
+        while (tri(n + 1, 0) <= t) ++n;
+        const int mm = t - tri(n, 0);
+        double2 sum = part[0][n][mm];
+#pragma unroll
+        for (int k = 1; k < 4; ++k) sum = cadd(sum, part[k][n][mm]);
+        double2 v = B[(int64_t)b * ntri(ST) + t];
+        B[(int64_t)b * ntri(ST) + t] = make_double2(v.x + sum.x * hinv, v.y + sum.y * hinv);
     }
 }
 
@@ -962,20 +1065,53 @@ __global__ void k_points2(int64_t nt, const int *tperm, const double *txyz, cons
     int b = tgt_box[it];
     double tx = txyz[it], ty = txyz[nt + it], tz = txyz[2 * nt + it];
     double acc = 0.0;
-    const ListRef lists[3] = {lu, lwc, lxc};
-    for (int li = 0; li < 3; ++li)
-        for (int e = lists[li].start[b]; e < lists[li].start[b + 1]; ++e) {
-            int d = lists[li].idx[e];
-            for (int s = own_start[d] + lane; s < own_start[d + 1]; s += 32) {
-                double rx = tx - sxyz[s], ry = ty - sxyz[ns + s], rz = tz - sxyz[2 * ns + s];
-                double r2 = rx * rx + ry * ry + rz * rz;
-                if (r2 == 0.0) continue;
-                double ri = 1.0 / sqrt(r2);
-                double v = sq[s] * ri;
-                if (sd) v += (sd[s] * rx + sd[ns + s] * ry + sd[2 * ns + s] * rz) * ri * ri * ri;
-                acc += v;
+    // P2P: the sources of Lists 1, 3 close and 4 close as one sequence over the lanes (shuffle
+    // prefix scan of the box source counts, 32 boxes at a time)
+    {
+        const int u0 = lu.start[b], n0 = lu.start[b + 1] - u0;
+        const int w0 = lwc.start[b], n1 = lwc.start[b + 1] - w0;
+        const int x0 = lxc.start[b], n2 = lxc.start[b + 1] - x0;
+        const int e1 = n0 + n1 + n2;
+        for (int base = 0; base < e1; base += 32) {
+            const int e = base + lane;
+            int d = -1;
+            if (e < n0) d = lu.idx[u0 + e];
+            else if (e < n0 + n1) d = lwc.idx[w0 + e - n0];
+            else if (e < e1) d = lxc.idx[x0 + e - n0 - n1];
+            const int s0 = d >= 0 ? own_start[d] : 0;
+            const int cnt = d >= 0 ? own_start[d + 1] - s0 : 0;
+            int incl = cnt;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            const int total = __shfl_sync(0xffffffffu, incl, 31);
+            for (int k0 = 0; k0 < total; k0 += 32) {
+                const int k = k0 + lane;
+                int j = 0;
+#pragma unroll
+                for (int step = 16; step >= 1; step >>= 1) {
+                    int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                    if (v <= k) j += step;
+                }
+                const int sj = __shfl_sync(0xffffffffu, s0, j);
+                const int ij = __shfl_sync(0xffffffffu, incl, j);
+                const int cj = __shfl_sync(0xffffffffu, cnt, j);
+                if (k < total) {
+                    const int s = sj + (k - (ij - cj));
+                    double rx = tx - sxyz[s], ry = ty - sxyz[ns + s], rz = tz - sxyz[2 * ns + s];
+                    double r2 = rx * rx + ry * ry + rz * rz;
+                    if (r2 != 0.0) {
+                        double ri = 1.0 / sqrt(r2);
+                        double v = sq[s] * ri;
+                        if (sd) v += (sd[s] * rx + sd[ns + s] * ry + sd[2 * ns + s] * rz) * ri * ri * ri;
+                        acc += v;
+                    }
+                }
             }
         }
+    }
     for (int e = pt_off[it] + lane; e < pt_off[it + 1]; e += 32) acc += part[e];
     if (lane == 0) {
         int P = pb[b];
@@ -1143,9 +1279,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     // Stage 6(b)
     stage_mark(L, 3, st);
 #define QBX_P2L(PB)                                                                                                 \
-    k_p2l<PB, PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC],        \
-                                                           T->sxyz, ns, ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, \
-                                                           ws->pb, ws->B)
+    k_p2l4<PB, PM_T><<<(unsigned)nb, 128, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], T->sxyz, ns,   \
+                                                   ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->B)
     if (pmax <= 10) QBX_P2L(10);
     else if (pmax <= 16) QBX_P2L(16);
     else QBX_P2L(PM_T);

@@ -284,9 +284,25 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
     const uint32_t id0 = tc::idesc_tf32(128, N0), id1 = tc::idesc_tf32(128, N1 > 0 ? N1 : 16);
     bool ok = true;
     uint32_t g = 0;  // chunks issued by this CTA (pipeline position)
+    const int pieces = KC / 4, nq = (128 * pieces) / 256;  // float4 pieces per thread: 4 (KC 32) or 2 (KC 16)
+    float4 hv[4], lv[4];
     for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
         const int4 tl = a.tiles[t];
         const int o = tl.x, p0 = tl.y, np = tl.z - tl.y;
+        auto load_a = [&](int cc) {
+#pragma unroll
+            for (int it = 0; it < 4; ++it) {
+                hv[it] = lv[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+                const int q = tid + 256 * it;
+                const int row = (q & 7) + 8 * (q / (8 * pieces)), pc = (q >> 3) % pieces;
+                if (it < nq && row < np) {
+                    int64_t src = (int64_t)a.pair_src[p0 + row] * a.Dp + cc * KC + 4 * pc;
+                    hv[it] = __ldg(reinterpret_cast<const float4 *>(a.mh_hi + src));
+                    lv[it] = __ldg(reinterpret_cast<const float4 *>(a.mh_lo + src));
+                }
+            }
+        };
+        load_a(0);
         for (int c = 0; c < nch; ++c, ++g) {
             const int s = g & 1;
             const uint32_t use = g >> 1;
@@ -297,21 +313,8 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
                 tc::bulk_g2s(Bbuf(s, 0), a.mats + ((int64_t)o * nch + c) * 2 * Np * KC, 2u * bytesB, &bar_b[s]);
             }
             // eight consecutive threads fill one 128-byte core matrix (rows 8g..8g+7 of one 16-byte
-            // column piece): conflict-free stores, 64-byte row segments per warp in global memory;
-            // all loads of a thread are issued before its stores
-            const int pieces = KC / 4, nq = (128 * pieces) / 256;  // 4 (KC 32) or 2 (KC 16)
-            float4 hv[4], lv[4];
-#pragma unroll
-            for (int it = 0; it < 4; ++it) {
-                hv[it] = lv[it] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const int q = tid + 256 * it;
-                const int row = (q & 7) + 8 * (q / (8 * pieces)), pc = (q >> 3) % pieces;
-                if (it < nq && row < np) {
-                    int64_t src = (int64_t)a.pair_src[p0 + row] * a.Dp + c * KC + 4 * pc;
-                    hv[it] = __ldg(reinterpret_cast<const float4 *>(a.mh_hi + src));
-                    lv[it] = __ldg(reinterpret_cast<const float4 *>(a.mh_lo + src));
-                }
-            }
+            // column piece): conflict-free stores, 64-byte row segments per warp in global memory.
+            // The multipoles of the next chunk are loaded before this chunk's MMAs are issued.
 #pragma unroll
             for (int it = 0; it < 4; ++it) {
                 const int q = tid + 256 * it;
@@ -322,6 +325,7 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
                     *reinterpret_cast<float4 *>(Abuf(s, 1) + off) = lv[it];
                 }
             }
+            if (c + 1 < nch) load_a(c + 1);
             tc::fence_proxy_async();
             __syncthreads();
             if (tid == 0) {

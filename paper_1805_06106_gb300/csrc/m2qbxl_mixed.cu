@@ -209,7 +209,7 @@ __global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, int64_t per, const WfarRe
 //   Yh_j^i = a_j (z/|x|) Yh_{j-1}^i - b_j^i Yh_{j-2}^i,
 //   a_j = sqrt((2j-1)/(2j)),  b_j^i = (j+i-1)(j-i-1) / sqrt(2j (2j-1) (2j-2) (2j-3)),
 // and |Yh_j^i| <= F(j,i)/F(j,j) <= 1.
-__constant__ double c_al[41], c_be[ntri(40)];
+__constant__ double c_al[41], c_be[ntri(40)], c_cd[41];  // c_cd[i] = a_1 a_2 ... a_i
 
 // IEEE double -> float from the bit fields, rounding the 24-bit significand half away from zero
 // (a carry out of the significand moves into the exponent); magnitudes below the float normal
@@ -236,15 +236,19 @@ struct WfarTcArgs {
     int *err;
 };
 
-// Tensor-core List 3 far products.  Persistent CTAs of 256 threads walk 128-pair tiles of one
+// Tensor-core List 3 far products.  Persistent CTAs of 512 threads walk 128-pair tiles of one
 // source box d: per K chunk (whole harmonic degrees) the threads generate the scaled irregular
-// harmonics of their pairs in FP64 (two threads per pair, warps 0-3 and 4-7, each carrying the
-// recurrences of every other 16-byte column group in registers), split them into TF32 parts in
+// harmonics of their pairs in FP64 (four threads per pair, warps 4r..4r+3, each carrying the
+// recurrences of every fourth 16-byte column group in registers), split them into TF32 parts in
 // shared memory, load and split the chunk of H_d; one thread issues a_hi b_hi + a_lo b_hi +
 // a_hi b_lo into a 128 x Rp FP32 accumulator in tensor memory.  Epilogue: Y[pair][row] =
 // acc F(k,l) (rho/h)^k / h.
+constexpr int WF_THREADS = 512;  // 4 threads per pair of the 128-pair tile
+constexpr int WF_SPLIT = WF_THREADS / 128;
+constexpr int WF_BREG = 4;  // float4 registers per thread for one chunk of H: Rp * W <= 4 * 4 * WF_THREADS
+
 template <int NU>
-__global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
+__global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
     __shared__ uint64_t bar_mma[2];
@@ -261,7 +265,8 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
     float *Pw = reinterpret_cast<float *>(smem_tc + ops);  // 128 x (Q+1)
     float *colF = Pw + 128 * (Q + 1);                                                     // Rp
     int *colK = reinterpret_cast<int *>(colF + Rp);                                       // Rp
-    for (int r = tid; r < Rp; r += 256) {
+    double *geo = reinterpret_cast<double *>(smem_tc + ops + (((size_t)128 * (Q + 1) * 4 + (size_t)Rp * 8 + 15) & ~(size_t)15));  // 128 x 4
+    for (int r = tid; r < Rp; r += WF_THREADS) {
         int k = 0, l = 0, part = 0;
         if (r < a.R) decode(r, k, l, part);
         colF[r] = (float)Fnm(k, l);
@@ -278,7 +283,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
     const uint32_t idesc = tc::idesc_tf32(128, Rp);
-    // pair p = tid % 128; warps 0-3 take the even columns i, warps 4-7 the odd ones, so the column
+    // pair p = tid % 128; warps 4r .. 4r+3 take the column groups g = r (mod 4), so the column
     // conditions are uniform within each warp
     const int p = tid & 127, par = tid >> 7;
     bool ok = true;
@@ -288,11 +293,9 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
         const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
         const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
         const bool valid = p < np;
-        // pair geometry and the diagonals of the scaled unit-vector harmonics of this thread's columns:
-        // 16-byte group g holds column 0 (g = 0) or columns 2g-1, 2g; this thread owns g = par + 2u
+        // pair geometry, once per pair (the first of its 4 threads), shared through shared memory
         double a1r[NU][2], a1i[NU][2], a2r[NU][2], a2i[NU][2];
-        double zh = 0.0, rinv = 0.0, rpj = 0.0;
-        {
+        if (par == 0) {
             const double h = a.hw[d], hinv = 1.0 / h;
             double x = 3.0, y = 0.0, z = 0.0;
             int c = 0;
@@ -302,40 +305,57 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                 y = (a.cxyz[a.nc + c] - a.cen[3 * d + 1]) * hinv;
                 z = (a.cxyz[2 * a.nc + c] - a.cen[3 * d + 2]) * hinv;
             }
-            rinv = 1.0 / sqrt(x * x + y * y + z * z);
-            const double wr = x * rinv, wi = y * rinv;
-            zh = z * rinv;
-            rpj = rinv;  // |x|^{-(j+1)} at the current degree j (starts at j = 0)
-            if (par == 0) {
-                const double ratio = valid ? a.cr[c] * hinv : 0.0;
-                double pk = hinv;
-                for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[p * (Q + 1) + k] = (float)pk;
-            }
-            // diagonal Yh_i^i for i = 0, 1, 2, ...; column i belongs to group (i + 1) / 2
-            double dr = 1.0, di = 0.0;
+            const double ri = 1.0 / sqrt(x * x + y * y + z * z);
+            geo[4 * p + 0] = z * ri;
+            geo[4 * p + 1] = ri;
+            geo[4 * p + 2] = x * ri;
+            geo[4 * p + 3] = y * ri;
+            const double ratio = valid ? a.cr[c] * hinv : 0.0;
+            double pk = hinv;
+            for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[p * (Q + 1) + k] = (float)pk;
+        }
+        __syncthreads();
+        const double zh = geo[4 * p + 0], rinv = geo[4 * p + 1];
+        double rpj = rinv;  // |x|^{-(j+1)} at the current degree j (starts at j = 0)
+        {
+            // diagonals Yh_i^i = cd_i w^i (w = (x + iy)/|x|, cd_i = a_1 ... a_i) of this thread's groups:
+            // group g = par + 4u holds column 0 (g = 0) or columns 2g-1, 2g
+            const double wr = geo[4 * p + 2], wi = geo[4 * p + 3];
+            double2 w1 = make_double2(wr, wi);
+            double2 w2 = make_double2(wr * wr - wi * wi, 2.0 * wr * wi);
+            double2 w4 = make_double2(w2.x * w2.x - w2.y * w2.y, 2.0 * w2.x * w2.y);
+            double2 w8 = make_double2(w4.x * w4.x - w4.y * w4.y, 2.0 * w4.x * w4.y);
+            // w^(first column of group par): 1 (par 0), w (1), w^3 (2), w^5 (3)
+            double2 cur = par == 0 ? make_double2(1.0, 0.0)
+                                   : par == 1 ? w1 : par == 2 ? cmul(w2, w1) : cmul(w4, w1);
 #pragma unroll
-            for (int u = 0; u < NU; ++u)
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) { a1r[u][h2] = a1i[u][h2] = a2r[u][h2] = a2i[u][h2] = 0.0; }
-            for (int i = 0; i <= PQ; ++i) {
-                if (i > 0) {
-                    const double ga = c_al[i];
-                    const double tr = (dr * wr - di * wi) * ga, ti = (dr * wi + di * wr) * ga;
-                    dr = tr;
-                    di = ti;
-                }
-                const int gi = (i + 1) >> 1;
-                const bool second = i > 0 && ((i - 1) & 1);  // column 2g of group g
-                if ((gi & 1) == par) {
-#pragma unroll
-                    for (int u = 0; u < NU; ++u)
-                        if (par + 2 * u == gi) {
-                            if (second) { a1r[u][1] = dr; a1i[u][1] = di; }
-                            else { a1r[u][0] = dr; a1i[u][0] = di; }
-                        }
-                }
+            for (int u = 0; u < NU; ++u) {
+                const int g0 = par + WF_SPLIT * u;
+                const int i0 = g0 == 0 ? 0 : 2 * g0 - 1;
+                a2r[u][0] = a2i[u][0] = a2r[u][1] = a2i[u][1] = 0.0;
+                const double c0 = c_cd[min(i0, 40)], c1 = c_cd[min(i0 + 1, 40)];
+                a1r[u][0] = c0 * cur.x;
+                a1i[u][0] = c0 * cur.y;
+                const double2 nxt = cmul(cur, w1);
+                a1r[u][1] = c1 * nxt.x;
+                a1i[u][1] = c1 * nxt.y;
+                // next group of this thread: 8 columns on (from column 0: group 4 starts at column 7)
+                cur = (g0 == 0) ? cmul(cmul(w4, w2), w1) : cmul(cur, w8);
             }
         }
+        // B: the chunks of H_d pass through registers (WF_BREG float4 per thread), the next chunk's
+        // loads issued before this chunk's harmonics are generated so that their latency overlaps
+        float4 bpre[WF_BREG];
+        auto load_b = [&](int cc) {
+            const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[cc] * Rp);
+            const int nq = Rp * (a.ch.ckoff[cc + 1] - a.ch.ckoff[cc]) / 4;
+#pragma unroll
+            for (int k = 0; k < WF_BREG; ++k) {
+                const int q = tid + k * WF_THREADS;
+                bpre[k] = q < nq ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        };
+        load_b(0);
         for (int c = 0; c < a.ch.nch; ++c, ++g) {
             const int s = g & 1;
             const uint32_t use = g >> 1;
@@ -343,20 +363,24 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
             if (__syncthreads_or(!ok)) { ok = false; break; }
             const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
             const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c];
-            // B: chunk of H_d, split into TF32 parts
             {
-                const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[c] * Rp);
                 float4 *dh = reinterpret_cast<float4 *>(Bbuf(s, 0)), *dl = reinterpret_cast<float4 *>(Bbuf(s, 1));
-                for (int q = tid; q < Rp * W / 4; q += 256) {
-                    float4 v = src[q], hi, lo;
-                    tc::split_tf32(v.x, hi.x, lo.x);
-                    tc::split_tf32(v.y, hi.y, lo.y);
-                    tc::split_tf32(v.z, hi.z, lo.z);
-                    tc::split_tf32(v.w, hi.w, lo.w);
-                    dh[q] = hi;
-                    dl[q] = lo;
+                const int nq = Rp * W / 4;
+#pragma unroll
+                for (int k = 0; k < WF_BREG; ++k) {
+                    const int q = tid + k * WF_THREADS;
+                    if (q < nq) {
+                        float4 v = bpre[k], hi, lo;
+                        tc::split_tf32(v.x, hi.x, lo.x);
+                        tc::split_tf32(v.y, hi.y, lo.y);
+                        tc::split_tf32(v.z, hi.z, lo.z);
+                        tc::split_tf32(v.w, hi.w, lo.w);
+                        dh[q] = hi;
+                        dl[q] = lo;
+                    }
                 }
             }
+            if (c + 1 < a.ch.nch) load_b(c + 1);
             // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's column groups;
             // the recurrence in FP64, the radial factor applied in FP32 after the conversion, one
             // 16-byte store per group and TF32 part
@@ -370,7 +394,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
                     rpj *= rinv;
 #pragma unroll
                     for (int u = 0; u < NU; ++u) {
-                        const int gg = par + 2 * u;
+                        const int gg = par + WF_SPLIT * u;
                         const int i0 = gg == 0 ? 0 : 2 * gg - 1;  // first column of the group
                         if (i0 > j || i0 > PQ) continue;
                         float v[4];
@@ -432,7 +456,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
         // tile's rows are contiguous in Y
         const int qd = warp & 3, row = 32 * qd + lane, RS = Rp + 4;
         float *stage = reinterpret_cast<float *>(smem_tc);  // 128 x (Rp + 4) floats
-        for (int cg = warp >> 2; cg * 16 < Rp; cg += 2) {
+        for (int cg = warp >> 2; cg * 16 < Rp; cg += WF_THREADS / 128) {
             float v[16];
             tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(cg * 16), v);
             const float *pw = Pw + row * (Q + 1);
@@ -446,7 +470,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
             for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
         }
         __syncthreads();
-        for (int q = tid; q < np * a.R; q += 256) {
+        for (int q = tid; q < np * a.R; q += WF_THREADS) {
             const int r = q / a.R, cc = q % a.R;
             a.Y[(int64_t)(p0 + r) * a.R + cc] = stage[r * RS + cc];
         }
@@ -464,7 +488,7 @@ __global__ void __launch_bounds__(256, 1) k_wfar_tc(WfarTcArgs a)
 static size_t wfar_tc_smem(int Rp, int WMAX, int Q)
 {
     const size_t ops = std::max((size_t)4 * 16 * (WMAX * 32 + 16) + (size_t)4 * Rp * WMAX * 4, (size_t)128 * (Rp + 4) * 4);
-    return ops + (size_t)128 * (Q + 1) * 4 + (size_t)Rp * 8;
+    return ops + (((size_t)128 * (Q + 1) * 4 + (size_t)Rp * 8 + 15) & ~(size_t)15) + (size_t)128 * 4 * 8;
 }
 
 constexpr int WKC = 32;  // K chunk of the H tile
@@ -625,11 +649,12 @@ static bool wfar_tc_layout(WfarPlan *pl, int w_hint)
     const int P = pl->P, Q = pl->Q, PQ = P + Q;
     pl->Rp = (pl->R + 15) / 16 * 16;
     if (pl->Rp > 256 || PQ > 35) return false;
-    pl->NU = PQ <= 22 ? 6 : 10;  // 16-byte groups per thread: ceil((1 + ceil(PQ/2)) / 2)
+    pl->NU = PQ <= 22 ? 3 : 5;  // 16-byte groups per thread: ceil((1 + ceil(PQ/2)) / 4)
     const int wmin = (wfar_degree_slots(PQ) + 7) / 8 * 8;
     int W = std::max(w_hint > 0 ? w_hint / 8 * 8 : 64, wmin);
     while (W > wmin && wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) W -= 8;
     if (wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) return false;
+    if (pl->Rp * W / 4 > WF_BREG * WF_THREADS) return false;  // one chunk of H per register set
     pl->WMAX = W;
     int nch = 0, j = 0, koff = 0;
     while (j <= PQ) {
@@ -658,6 +683,9 @@ static void set_recurrence_tables(cudaStream_t st)
             be[tri(j, i)] = (double)(j + i - 1) * (double)(j - i - 1) /
                             std::sqrt(2.0 * j * (2.0 * j - 1.0) * (2.0 * j - 2.0) * (2.0 * j - 3.0));
     QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_al, al.data(), al.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    std::vector<double> cd(41, 1.0);
+    for (int i = 1; i <= 40; ++i) cd[i] = cd[i - 1] * al[i];
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_cd, cd.data(), cd.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
     QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_be, be.data(), be.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
 }
 
@@ -827,10 +855,10 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
             }
             pl->Y = dalloc<float>((int64_t)std::max(np, 1) * pl->R);
             const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, Q);
-            if (pl->NU == 6)
-                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            if (pl->NU == 3)
+                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             else
-                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<10>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
             QBX_CUDA_TRY(cudaStreamSynchronize(st));
             dfree(cm_cnt); dfree(d_cnt); dfree(d_start); dfree(flag); dfree(tot);
             return pl;
@@ -893,8 +921,8 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
                      pl->pair_ctr, pl->slot, pl->H_tc, T->cxyz, T->cr, T->cen, T->hw, T->np[KCTR], pl->Y, err};
         const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, pl->Q);
         const int grid = std::min(pl->ntc, nsm);
-        if (pl->NU == 6) k_wfar_tc<6><<<grid, 256, sm, st>>>(a);
-        else k_wfar_tc<10><<<grid, 256, sm, st>>>(a);
+        if (pl->NU == 3) k_wfar_tc<3><<<grid, WF_THREADS, sm, st>>>(a);
+        else k_wfar_tc<5><<<grid, WF_THREADS, sm, st>>>(a);
         QBX_LAUNCH_CHECK();
         return;
     }
