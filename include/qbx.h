@@ -174,7 +174,7 @@ int qbx_eval_order_sweep(const qbx_tree *tree, const qbx_lists *lists, const dou
 
 /* ------------------------------------------------------------------------------------------
  * Learned expansion orders.  Not in the paper: a small network picks per-center QBX orders and
- * per-box FMM orders that the fixed-order evaluation (its judge and fallback) would accept
+ * per-box FMM orders that the fixed-order evaluation (its acceptance check and fallback) would accept
  * within a tolerance.  Training data are order sweeps of the method itself
  * (qbx_eval_order_sweep and qbx_eval at several p_fmm); the network is trained by the kernels
  * below.  All pointers are device pointers unless marked _host.
@@ -297,13 +297,14 @@ int qbx_lists_set_tiles(qbx_lists *lists, int m2l_kchunk, int m2qbxl_kchunk);
  * every qbx_eval on these lists records CUDA events on its stream around each of
  * QBX_NSTAGES stages: 0 input preparation, 1 P2M + M2M (Stage 2), 2 List 2 M2L
  * (Stage 4), 3 List 4 far P2L (Stage 6b), 4 L2L (Stage 7), 5 List 3 far M2QBXL
- * products in the mixed-precision modes (empty in QBX_FP64), 6 QBX centers (Stages
- * 3, 5, 6a, 8: L2QBXL, direct P2QBXL, and List 3 far M2QBXL in QBX_FP64), 7 QBX
- * targets (Stage 9), 8 point targets (Stage 9).  qbx_profile_read waits for the last profiled
- * evaluation and writes the stage durations in milliseconds to stage_ms_host.
- * Profiling must be disabled while the stream is being captured into a graph.
+ * products in the mixed-precision modes (empty in QBX_FP64), 6 the QBX center kernel (Stages
+ * 3, 5(a), 6(a), 8: direct P2QBXL and L2QBXL, and List 3 far M2QBXL in QBX_FP64), 7 the reduction
+ * of the mixed List 3 far products into the QBX locals (empty in QBX_FP64), 8 QBX targets
+ * (Stage 9), 9 point targets (Stage 9).  qbx_profile_read waits for the last profiled evaluation
+ * and writes the stage durations in milliseconds to stage_ms_host.  Profiling must be disabled
+ * while the stream is being captured into a graph.
  */
-#define QBX_NSTAGES 9
+#define QBX_NSTAGES 10
 int qbx_profile(qbx_lists *lists, int enable);
 int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
 

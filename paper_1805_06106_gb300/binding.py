@@ -16,7 +16,8 @@ from . import build as _build
 
 QBX_FP64, QBX_M2L_FP32, QBX_M2L_3XTF32 = 0, 1, 2
 LIST_NAMES = ("U", "V", "Wclose", "Wfar", "Xclose", "Xfar")
-STAGE_NAMES = ("prep", "p2m_m2m", "m2l", "p2l", "l2l", "m2qbxl_mixed", "centers", "qbx_targets", "point_targets")
+STAGE_NAMES = ("prep", "p2m_m2m", "m2l", "p2l", "l2l", "m2qbxl_mixed", "centers", "m2qbxl_reduce", "qbx_targets",
+               "point_targets")
 
 
 class QbxError(RuntimeError):

@@ -41,6 +41,7 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
                     cudaStream_t st);
 void wfar_mixed_reduce(const qbx_tree *T, WfarPlan *pl, int QMS, const signed char *qc, double2 *A, cudaStream_t st);
 
+
 }  // namespace qbx
 
 struct qbx_workspace {
@@ -1176,9 +1177,10 @@ static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, b
             ListRef{wf_start, L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,
             dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A);
         QBX_LAUNCH_CHECK();
-        if (wf) wfar_mixed_reduce(T, wf, QM, ws->qc, ws->A, st);
     }
     stage_mark(L, 7, st);
+    if (T->np[KCTR] > 0 && wf) wfar_mixed_reduce(T, wf, QM, ws->qc, ws->A, st);
+    stage_mark(L, 8, st);
     if (T->np[KTGT] > 0) {
         k_qbxl2p<QM><<<nblocks(T->np[KTGT], 128), 128, 0, st>>>(T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr,
                                                                 T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->qc,
@@ -1318,7 +1320,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     default: launch_centers<16>(T, L, ws, dip, tgt_ctr, pot, st, wf); break;
     }
     // Stage 9 at point targets
-    stage_mark(L, 8, st);
+    stage_mark(L, 9, st);
     if (nt > 0) {
         if (ws->pt_cap < 0) {  // first evaluation: size the pair buffers for any choice of point targets
             ws->pt_cnt = dalloc<int>(nt + 1);
@@ -1355,7 +1357,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
             T->own_start[KSRC], T->sxyz, ns, ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, ws->B, pot);
         QBX_LAUNCH_CHECK();
     }
-    stage_mark(L, 9, st);
+    stage_mark(L, 10, st);
     L->prof_valid = L->prof;
     if (o->precision == QBX_M2L_3XTF32 && cap == cudaStreamCaptureStatusNone) {
         // the tensor-core kernels report a wait that gave up through the flags word

@@ -208,12 +208,14 @@ __global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, int64_t per, const WfarRe
 //   Yh_0^0 = 1,  Yh_i^i = a_i (x + i y)/|x| Yh_{i-1}^{i-1},
 //   Yh_j^i = a_j (z/|x|) Yh_{j-1}^i - b_j^i Yh_{j-2}^i,
 //   a_j = sqrt((2j-1)/(2j)),  b_j^i = (j+i-1)(j-i-1) / sqrt(2j (2j-1) (2j-2) (2j-3)),
-// and |Yh_j^i| <= F(j,i)/F(j,j) <= 1.
-__constant__ double c_al[41], c_be[ntri(40)], c_cd[41];  // c_cd[i] = a_1 a_2 ... a_i
+// and |Yh_j^i| <= F(j,i)/F(j,j) <= 1.  Bounded by 1 and forward-stable in j, the recurrence runs in
+// FP32: its rounding (a few units of 2^-24 at the degrees used) stays below the 2^-22 of the TF32
+// split that the products then apply to it.
+__constant__ float c_al[41], c_be[ntri(40)], c_cd[41];  // c_cd[i] = a_1 a_2 ... a_i
 
 // IEEE double -> float from the bit fields, rounding the 24-bit significand half away from zero
 // (a carry out of the significand moves into the exponent); magnitudes below the float normal
-// range become 0.  Integer operations only, so the FP64 pipe is left to the recurrence.
+// range become 0.  Integer operations only (no FP64 instruction).
 __device__ __forceinline__ float dbl_to_f32_rn(double v)
 {
     const int hi = __double2hiint(v);
@@ -222,6 +224,11 @@ __device__ __forceinline__ float dbl_to_f32_rn(double v)
     if (e < 897) return 0.0f;
     const unsigned mant = (((unsigned)(hi & 0xfffff) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
     return __uint_as_float(((unsigned)hi & 0x80000000u) | (((unsigned)(e - 896) << 23) + mant));
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 
 struct WfarTcArgs {
@@ -238,7 +245,7 @@ struct WfarTcArgs {
 
 // Tensor-core List 3 far products.  Persistent CTAs of 512 threads walk 128-pair tiles of one
 // source box d: per K chunk (whole harmonic degrees) the threads generate the scaled irregular
-// harmonics of their pairs in FP64 (four threads per pair, warps 4r..4r+3, each carrying the
+// harmonics of their pairs in FP32 (four threads per pair, warps 4r..4r+3, each carrying the
 // recurrences of every fourth 16-byte column group in registers), split them into TF32 parts in
 // shared memory, load and split the chunk of H_d; one thread issues a_hi b_hi + a_lo b_hi +
 // a_hi b_lo into a 128 x Rp FP32 accumulator in tensor memory.  Epilogue: Y[pair][row] =
@@ -294,7 +301,7 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
         const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
         const bool valid = p < np;
         // pair geometry, once per pair (the first of its 4 threads), shared through shared memory
-        double a1r[NU][2], a1i[NU][2], a2r[NU][2], a2i[NU][2];
+        float a1r[NU][2], a1i[NU][2], a2r[NU][2], a2i[NU][2];
         if (par == 0) {
             const double h = a.hw[d], hinv = 1.0 / h;
             double x = 3.0, y = 0.0, z = 0.0;
@@ -315,32 +322,30 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
             for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[p * (Q + 1) + k] = (float)pk;
         }
         __syncthreads();
-        const double zh = geo[4 * p + 0], rinv = geo[4 * p + 1];
+        const float zh = (float)geo[4 * p + 0];
+        const double rinv = geo[4 * p + 1];
         double rpj = rinv;  // |x|^{-(j+1)} at the current degree j (starts at j = 0)
         {
             // diagonals Yh_i^i = cd_i w^i (w = (x + iy)/|x|, cd_i = a_1 ... a_i) of this thread's groups:
             // group g = par + 4u holds column 0 (g = 0) or columns 2g-1, 2g
-            const double wr = geo[4 * p + 2], wi = geo[4 * p + 3];
-            double2 w1 = make_double2(wr, wi);
-            double2 w2 = make_double2(wr * wr - wi * wi, 2.0 * wr * wi);
-            double2 w4 = make_double2(w2.x * w2.x - w2.y * w2.y, 2.0 * w2.x * w2.y);
-            double2 w8 = make_double2(w4.x * w4.x - w4.y * w4.y, 2.0 * w4.x * w4.y);
+            const float2 w1 = make_float2((float)geo[4 * p + 2], (float)geo[4 * p + 3]);
+            const float2 w2 = cmulf(w1, w1), w4 = cmulf(w2, w2), w8 = cmulf(w4, w4);
             // w^(first column of group par): 1 (par 0), w (1), w^3 (2), w^5 (3)
-            double2 cur = par == 0 ? make_double2(1.0, 0.0)
-                                   : par == 1 ? w1 : par == 2 ? cmul(w2, w1) : cmul(w4, w1);
+            float2 cur = par == 0 ? make_float2(1.f, 0.f)
+                                  : par == 1 ? w1 : par == 2 ? cmulf(w2, w1) : cmulf(w4, w1);
 #pragma unroll
             for (int u = 0; u < NU; ++u) {
                 const int g0 = par + WF_SPLIT * u;
                 const int i0 = g0 == 0 ? 0 : 2 * g0 - 1;
-                a2r[u][0] = a2i[u][0] = a2r[u][1] = a2i[u][1] = 0.0;
-                const double c0 = c_cd[min(i0, 40)], c1 = c_cd[min(i0 + 1, 40)];
+                a2r[u][0] = a2i[u][0] = a2r[u][1] = a2i[u][1] = 0.f;
+                const float c0 = c_cd[min(i0, 40)], c1 = c_cd[min(i0 + 1, 40)];
                 a1r[u][0] = c0 * cur.x;
                 a1i[u][0] = c0 * cur.y;
-                const double2 nxt = cmul(cur, w1);
+                const float2 nxt = cmulf(cur, w1);
                 a1r[u][1] = c1 * nxt.x;
                 a1i[u][1] = c1 * nxt.y;
                 // next group of this thread: 8 columns on (from column 0: group 4 starts at column 7)
-                cur = (g0 == 0) ? cmul(cmul(w4, w2), w1) : cmul(cur, w8);
+                cur = (g0 == 0) ? cmulf(cmulf(w4, w2), w1) : cmulf(cur, w8);
             }
         }
         // B: the chunks of H_d pass through registers (WF_BREG float4 per thread), the next chunk's
@@ -382,14 +387,14 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
             }
             if (c + 1 < a.ch.nch) load_b(c + 1);
             // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's column groups;
-            // the recurrence in FP64, the radial factor applied in FP32 after the conversion, one
-            // 16-byte store per group and TF32 part
+            // the recurrence in FP32, the radial factor (a product of FP64 powers) rounded to FP32,
+            // one 16-byte store per group and TF32 part
             if (valid) {
                 unsigned char *Ah = Abuf(s, 0), *Al = Abuf(s, 1);
                 const uint32_t rowoff = (uint32_t)(p >> 3) * sboA + (uint32_t)(p & 7) * 16u;
                 int kb = 0;
                 for (int j = j0; j < j1; kb += wfar_degree_slots(j), ++j) {
-                    const double c1 = c_al[j] * zh;
+                    const float c1 = c_al[j] * zh;
                     const float rf = dbl_to_f32_rn(rpj);
                     rpj *= rinv;
 #pragma unroll
@@ -403,16 +408,16 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
                             const int i = i0 + h2;
                             v[2 * h2] = v[2 * h2 + 1] = 0.f;
                             if ((gg == 0 && h2 == 1) || i > j) continue;
-                            double vr = a1r[u][h2], vi = a1i[u][h2];
+                            float vr = a1r[u][h2], vi = a1i[u][h2];
                             if (j > i) {
-                                const double bb = c_be[tri(j, i)];
-                                vr = fma(c1, a1r[u][h2], -bb * a2r[u][h2]);
-                                vi = fma(c1, a1i[u][h2], -bb * a2i[u][h2]);
+                                const float bb = c_be[tri(j, i)];
+                                vr = fmaf(c1, a1r[u][h2], -bb * a2r[u][h2]);
+                                vi = fmaf(c1, a1i[u][h2], -bb * a2i[u][h2]);
                                 a2r[u][h2] = a1r[u][h2]; a2i[u][h2] = a1i[u][h2];
                                 a1r[u][h2] = vr; a1i[u][h2] = vi;
                             }
-                            v[2 * h2] = dbl_to_f32_rn(vr) * rf;
-                            v[2 * h2 + 1] = (i == 0) ? 0.f : dbl_to_f32_rn(vi) * rf;
+                            v[2 * h2] = vr * rf;
+                            v[2 * h2 + 1] = (i == 0) ? 0.f : vi * rf;
                         }
                         float4 hv, lv;
                         tc::split_tf32(v[0], hv.x, lv.x);
@@ -676,17 +681,19 @@ static bool wfar_tc_layout(WfarPlan *pl, int w_hint)
 
 static void set_recurrence_tables(cudaStream_t st)
 {
-    std::vector<double> al(41, 0.0), be(ntri(40), 0.0);
+    // computed in FP64, stored rounded to FP32
+    std::vector<double> al(41, 0.0), cd(41, 1.0);
+    std::vector<float> alf(41, 0.f), cdf(41, 1.f), bef(ntri(40), 0.f);
     for (int j = 1; j <= 40; ++j) al[j] = std::sqrt((2.0 * j - 1.0) / (2.0 * j));
+    for (int i = 1; i <= 40; ++i) cd[i] = cd[i - 1] * al[i];
+    for (int j = 0; j <= 40; ++j) { alf[j] = (float)al[j]; cdf[j] = (float)cd[j]; }
     for (int j = 2; j <= 40; ++j)
         for (int i = 0; i < j; ++i)
-            be[tri(j, i)] = (double)(j + i - 1) * (double)(j - i - 1) /
-                            std::sqrt(2.0 * j * (2.0 * j - 1.0) * (2.0 * j - 2.0) * (2.0 * j - 3.0));
-    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_al, al.data(), al.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
-    std::vector<double> cd(41, 1.0);
-    for (int i = 1; i <= 40; ++i) cd[i] = cd[i - 1] * al[i];
-    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_cd, cd.data(), cd.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
-    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_be, be.data(), be.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+            bef[tri(j, i)] = (float)((double)(j + i - 1) * (double)(j - i - 1) /
+                                     std::sqrt(2.0 * j * (2.0 * j - 1.0) * (2.0 * j - 2.0) * (2.0 * j - 3.0)));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_al, alf.data(), alf.size() * sizeof(float), 0, cudaMemcpyHostToDevice, st));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_cd, cdf.data(), cdf.size() * sizeof(float), 0, cudaMemcpyHostToDevice, st));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_be, bef.data(), bef.size() * sizeof(float), 0, cudaMemcpyHostToDevice, st));
 }
 
 // F(n, m) = sqrt((n+|m|)! (n-|m|)!) on the host

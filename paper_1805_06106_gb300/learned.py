@@ -3,7 +3,7 @@
 Host-side orchestration only; every arithmetic step (features, labels, network forward,
 backward and Adam, order assignment, evaluations) runs in libqbx kernels.
 
-Labels (per center, relative to the fixed orders (q_fix, p_fix) that act as judge):
+Labels (per center, relative to the fixed orders (q_fix, p_fix) that act as the acceptance check):
   p_qbx label = lowest q <= q_fix whose truncated QBX local stays within tol/2 (normwise, relative
   to max |phi|) of the order-q_fix result for every order from q to q_fix (one order sweep);
   p_fmm label = lowest p in the grid whose result at (q_fix, p) stays within tol/2 of the

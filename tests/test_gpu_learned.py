@@ -1,10 +1,10 @@
-"""Learned expansion orders: network kernels against the CPU oracle, labels, and the judge.
+"""Learned expansion orders: network kernels against the CPU oracle, labels, and the fixed-order acceptance check.
 
 * The gradient of the training loss computed by the library's backward kernel equals the
   oracle's FP64 chain-rule gradient (FP32 tolerance).
 * Training with the library's Adam kernel reduces the loss and is deterministic.
 * On a surface held out of training, the orders the network picks give a result within
-  1e-6 (normwise) of the fixed-order run that judges it, with no more work than that run (the
+  1e-6 (normwise) of the fixed-order run that checks it, with no more work than that run (the
   per-box orders set the order of each box's local expansion); the work ratios are printed.
 """
 import numpy as np
@@ -70,7 +70,7 @@ def test_features_and_labels_are_well_formed(sphere80):
     assert np.all((y[:, 0] >= 0) & (y[:, 0] <= 5)) and np.all((y[:, 1] >= 4) & (y[:, 1] <= 10))
 
 
-def test_learned_orders_pass_the_fixed_order_judge_on_a_held_out_surface():
+def test_learned_orders_pass_the_fixed_order_check_on_a_held_out_surface():
     import paper_1805_06106_gb300 as G
     from paper_1805_06106_gb300 import learned
     from synth import greens_density, make_surface, random_harmonic_density, real_ylm, star_radius
@@ -106,7 +106,7 @@ def test_learned_orders_pass_the_fixed_order_judge_on_a_held_out_surface():
     # L2QBXL work per center scales with (p_b + 1)^2 of its box's local expansion
     ctr_box = T.export()["ctr_owner"].cpu().numpy()
     work_l2q = np.sum((p[ctr_box] + 1) ** 2) / (s.n_ctr * (p_fix + 1) ** 2)
-    print(f"learned orders: margins {mq:.2f}/{mp:.2f}, judge error {err:.2e}, QBX-order work {work_q:.3f}, "
+    print(f"learned orders: margins {mq:.2f}/{mp:.2f}, error vs fixed {err:.2e}, QBX-order work {work_q:.3f}, "
           f"L2QBXL work {work_l2q:.3f} of fixed, mean local order {p.mean():.2f}")
     assert err <= tol
     assert work_q <= 1.0

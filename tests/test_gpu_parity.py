@@ -192,3 +192,26 @@ def test_no_sources_gives_zero(G):
     pot = G.qbx_eval(Tg, Lg, z, z, None, torch.zeros((3, 0), dtype=torch.float64, device="cuda"),
                      _cuda(s.tgt_ctr, torch.int32), 5, 10)
     assert torch.count_nonzero(pot) == 0
+
+
+def test_stage_profiling_leaves_results_unchanged(G, star_small):
+    """Per-stage event timing changes no result; the stages that only the mixed-precision modes
+    fill (List 3 far products and their reduction) are empty in FP64."""
+    s = star_small
+    u, dudn = greens_density(s)
+    Tg = _gpu_tree(G, s)
+    Lg = G.qbx_build_lists(Tg)
+    args = (_cuda(s.src_w), _cuda(dudn), _cuda(-u), _cuda(s.src_n), _cuda(s.tgt_ctr, torch.int32), 7, 15)
+    for prec in (G.QBX_FP64, G.QBX_M2L_3XTF32):
+        Lg.profile(False)
+        a = G.qbx_eval(Tg, Lg, *args, precision=prec).cpu().numpy()
+        Lg.profile(True)
+        b = G.qbx_eval(Tg, Lg, *args, precision=prec).cpu().numpy()
+        ms = Lg.stage_ms()
+        Lg.profile(False)
+        assert np.array_equal(a, b)
+        assert tuple(ms) == G.STAGE_NAMES and len(ms) == 10
+        assert all(v >= 0.0 for v in ms.values())
+        assert ms["centers"] > 0.0
+        if prec == G.QBX_FP64:
+            assert ms["m2qbxl_mixed"] < 0.05 and ms["m2qbxl_reduce"] < 0.05
