@@ -13,8 +13,8 @@
 // Per evaluation: multipoles are converted to the balanced real layout (FP32), one GEMM per
 // offset multiplies the offset's matrix by the gathered source multipoles of all pairs with that
 // offset (FP32 accumulation), each pair's result is stored, and a per-box reduction adds the
-// pairs of the box's List 2 in list order in FP64 (deterministic), undoes the scaling and adds
-// into the FP64 local expansion.
+// pairs of the box's List 2 in list order in compensated FP32 (deterministic), undoes the scaling
+// and adds into the FP64 local expansion.
 #include <algorithm>
 #include <vector>
 
@@ -404,7 +404,7 @@ static size_t m2l_tc_smem(int Np, int KC)
     return std::max((size_t)4 * 16 * (KC * 32 + 16) + (size_t)4 * Np * KC * 4, (size_t)128 * 132 * 4);
 }
 
-// B[b] += F(k,l)/h_b * sum_{e in V(b)} Y[pos(e)], summed in list order in FP64.
+// B[b] += F(k,l)/h_b * sum_{e in V(b)} Y[pos(e)], summed in list order in compensated FP32.
 __global__ void k_m2l_reduce(int64_t nb, int P, int PMT, const int *vstart, const int *pair_pos, const float *y,
                              const double *hw, const signed char *pb, double2 *B)
 {
@@ -420,9 +420,22 @@ __global__ void k_m2l_reduce(int64_t nb, int P, int PMT, const int *vstart, cons
     if (k > pb[b]) return;
     int rr = r - k * k;
     int l = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
-    double s = 0.0;
-    for (int e = e0; e < e1; ++e) s += (double)y[(int64_t)pair_pos[e] * D + r];
-    s *= ffac_sqrt(k, l) / hw[b];
+    // list-order sum in compensated FP32 (FP64 adds of converted terms would occupy the FP64 pipe);
+    // eight independent loads in flight per step
+    float hi = 0.f, lo = 0.f;
+    int e = e0;
+    for (; e + 8 <= e1; e += 8) {
+        int q[8];
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = pair_pos[e + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(y + (int64_t)q[u] * D + r);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tc::df_add(hi, lo, v[u]);
+    }
+    for (; e < e1; ++e) tc::df_add(hi, lo, __ldg(y + (int64_t)pair_pos[e] * D + r));
+    double s = ((double)hi + (double)lo) * (ffac_sqrt(k, l) / hw[b]);
     double2 *t = B + (int64_t)b * ntri(PMT) + tri(k, l);
     if (part) t->y += s;
     else t->x += s;

@@ -167,14 +167,28 @@ struct WfarChunks {
     int cj0[WF_MAXCH], cj1[WF_MAXCH], ckoff[WF_MAXCH + 1];
 };
 
+// IEEE double -> float from the bit fields, rounding the 24-bit significand half away from zero
+// (a carry out of the significand moves into the exponent); magnitudes below the float normal
+// range become 0, beyond its range infinite.  Integer operations only (no FP64 instruction).
+__device__ __forceinline__ float dbl_to_f32_rn(double v)
+{
+    const int hi = __double2hiint(v);
+    const unsigned lo = (unsigned)__double2loint(v);
+    const int e = (hi >> 20) & 0x7ff;
+    if (e < 897) return 0.0f;
+    if (e > 1150) return __uint_as_float(((unsigned)hi & 0x80000000u) | 0x7f800000u);
+    const unsigned mant = (((unsigned)(hi & 0xfffff) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
+    return __uint_as_float(((unsigned)hi & 0x80000000u) | (((unsigned)(e - 896) << 23) + mant));
+}
+
 // H of the tensor-core form: for each slot and chunk c, Rp rows x W_c columns (W_c = ckoff[c+1] -
 // ckoff[c]) as a K-major tile with SBO = 32 W_c, FP32 (split into TF32 parts when loaded).  The
 // harmonics it multiplies are scaled per degree (A = S_j^i / D(j), D(j) = sqrt((2j)!)), so entry
 // (row, (j,i,cp)) is the balanced operator entry times D(j) / F(j,i).  Each entry is one or two
 // multipole coefficients times constants: the recipe table (one record per entry, in output order,
-// built once per plan) holds them, and the kernel only gathers and multiplies in FP64.
+// built once per plan) holds them, and the kernel only gathers and multiplies (in FP32).
 struct WfarRecipe {
-    double f1, f2;   // factors of the two terms (signs and scales folded in)
+    float f1, f2;    // factors of the two terms (signs and scales folded in; computed in FP64, rounded)
     int t1, t2;      // tri index of the multipole coefficient, -1 for none
     int bits;        // bit 0: term 1 takes .y, bit 1: term 2 takes .y, bits 8..: degree n of both terms
     int pad;
@@ -189,19 +203,22 @@ __global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, int64_t per, const WfarRe
     const WfarRecipe r = rec[idx % per];
     const int d = slot_box[s];
     const int Pd = min((int)pb[d], P);
-    double e = 0.0;
+    // in FP32 from the multipole coefficients rounded to nearest by integer operations: the entry is
+    // rounded to FP32 (and split into TF32 parts) anyway, and FP64 arithmetic on ~10^9 entries per
+    // evaluation would bound this kernel by the FP64 pipe
+    float e = 0.f;
     if ((r.bits >> 8) <= Pd) {
         const double2 *M = Mu + (int64_t)d * ntri(PMT);
         if (r.t1 >= 0) {
-            double2 v = M[r.t1];
-            e = r.f1 * ((r.bits & 1) ? v.y : v.x);
+            const double2 v = M[r.t1];
+            e = r.f1 * dbl_to_f32_rn((r.bits & 1) ? v.y : v.x);
         }
         if (r.t2 >= 0) {
-            double2 v = M[r.t2];
-            e = fma(r.f2, (r.bits & 2) ? v.y : v.x, e);
+            const double2 v = M[r.t2];
+            e = fmaf(r.f2, dbl_to_f32_rn((r.bits & 2) ? v.y : v.x), e);
         }
     }
-    H[idx] = (float)e;
+    H[idx] = e;
 }
 
 // Unit-vector harmonics scaled per degree: Yh_j^i = |x|^{j+1} S_j^i(x) / D(j) obey
@@ -212,19 +229,6 @@ __global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, int64_t per, const WfarRe
 // FP32: its rounding (a few units of 2^-24 at the degrees used) stays below the 2^-22 of the TF32
 // split that the products then apply to it.
 __constant__ float c_al[41], c_be[ntri(40)], c_cd[41];  // c_cd[i] = a_1 a_2 ... a_i
-
-// IEEE double -> float from the bit fields, rounding the 24-bit significand half away from zero
-// (a carry out of the significand moves into the exponent); magnitudes below the float normal
-// range become 0.  Integer operations only (no FP64 instruction).
-__device__ __forceinline__ float dbl_to_f32_rn(double v)
-{
-    const int hi = __double2hiint(v);
-    const unsigned lo = (unsigned)__double2loint(v);
-    const int e = (hi >> 20) & 0x7ff;
-    if (e < 897) return 0.0f;
-    const unsigned mant = (((unsigned)(hi & 0xfffff) << 3) | (lo >> 29)) + ((lo >> 28) & 1u);
-    return __uint_as_float(((unsigned)hi & 0x80000000u) | (((unsigned)(e - 896) << 23) + mant));
-}
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b)
 {
@@ -624,7 +628,7 @@ static size_t wfar_smem(int K, int R, int WT)
     return ((size_t)K * WT + (size_t)R * WKC + (size_t)WT * (Q + 1)) * sizeof(float);
 }
 
-// A[c][tri(k,l)] += sum over the center's List 3 far pairs (list order), FP64.
+// A[c][tri(k,l)] += sum over the center's List 3 far pairs (list order, compensated FP32).
 __global__ void k_wfar_reduce(int64_t nc, int Q, int QMS, const int *cm_start, const int *pos_cm, const float *Y,
                               const signed char *qc, double2 *A)
 {
@@ -640,8 +644,22 @@ __global__ void k_wfar_reduce(int64_t nc, int Q, int QMS, const int *cm_start, c
     int rr = row - k * k, l = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
     int e0 = cm_start[i], e1 = cm_start[i + 1];
     if (e0 == e1) return;
-    double s = 0.0;
-    for (int e = e0; e < e1; ++e) s += (double)Y[(int64_t)pos_cm[e] * R + row];
+    // list-order sum in compensated FP32 (FP64 adds of converted terms would occupy the FP64 pipe);
+    // eight independent loads in flight per step
+    float hi = 0.f, lo = 0.f;
+    int e = e0;
+    for (; e + 8 <= e1; e += 8) {
+        int q[8];
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) q[u] = pos_cm[e + u];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) v[u] = __ldg(Y + (int64_t)q[u] * R + row);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) tc::df_add(hi, lo, v[u]);
+    }
+    for (; e < e1; ++e) tc::df_add(hi, lo, __ldg(Y + (int64_t)pos_cm[e] * R + row));
+    const double s = (double)hi + (double)lo;
     double2 *a = A + i * ntri(QMS) + tri(k, l);
     if (part) a->y += s;
     else a->x += s;
@@ -723,7 +741,7 @@ static void host_decode(int r, int &n, int &m, int &part)
 static std::vector<WfarRecipe> wfar_recipe(const WfarPlan *pl)
 {
     std::vector<WfarRecipe> out((size_t)pl->Rp * pl->Kp);
-    for (auto &r : out) r = WfarRecipe{0.0, 0.0, -1, -1, 0, 0};
+    for (auto &r : out) r = WfarRecipe{0.f, 0.f, -1, -1, 0, 0};
     for (int c = 0; c < pl->nch; ++c) {
         const int W = pl->ckoff[c + 1] - pl->ckoff[c];
         int kb = 0;  // first slot of degree j in the chunk
@@ -743,7 +761,7 @@ static std::vector<WfarRecipe> wfar_recipe(const WfarPlan *pl)
                     int k, l, rp;
                     host_decode(row, k, l, rp);
                     const int n = j - k;
-                    WfarRecipe rc{0.0, 0.0, -1, -1, 0, 0};
+                    WfarRecipe rc{0.f, 0.f, -1, -1, 0, 0};
                     if (n >= 0) {
                         const double colscale = host_F(j, j) / host_F(j, i), inv_kl = 1.0 / host_F(k, l);
                         const bool take_y = (rp != cp);  // (0,0), (1,1) read .x; (0,1), (1,0) read .y
@@ -761,11 +779,11 @@ static std::vector<WfarRecipe> wfar_recipe(const WfarPlan *pl)
                         const int m1 = i - l, m2 = -i - l;
                         if (m1 >= -n && m1 <= n) {
                             rc.t1 = tri(n, m1 < 0 ? -m1 : m1);
-                            rc.f1 = w1 * sgn(m1) * host_F(n + k, m1 + l) * inv_kl * colscale;
+                            rc.f1 = (float)(w1 * sgn(m1) * host_F(n + k, m1 + l) * inv_kl * colscale);
                         }
                         if (i > 0 && m2 >= -n && m2 <= n) {
                             rc.t2 = tri(n, m2 < 0 ? -m2 : m2);
-                            rc.f2 = w2 * sgn(m2) * host_F(n + k, m2 + l) * inv_kl * colscale;
+                            rc.f2 = (float)(w2 * sgn(m2) * host_F(n + k, m2 + l) * inv_kl * colscale);
                         }
                         rc.bits = (take_y ? 3 : 0) | (n << 8);
                     }

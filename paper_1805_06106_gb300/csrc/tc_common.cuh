@@ -171,6 +171,18 @@ __host__ __device__ __forceinline__ uint32_t kmajor_off(int row, int col, uint32
            (uint32_t)(col & 3) * 4u;
 }
 
+// Compensated FP32 accumulation (a double-float sum): hi + lo carries the running sum of FP32 terms to
+// about 2^-44 of the sum of their magnitudes.  Each step is Knuth's TwoSum (t + err == hi + x exactly)
+// with the error added into lo; six FP32 operations, no FP64 instruction.
+__device__ __forceinline__ void df_add(float &hi, float &lo, float x)
+{
+    const float t = hi + x;
+    const float bp = t - hi;
+    const float err = (hi - (t - bp)) + (x - bp);
+    hi = t;
+    lo += err;
+}
+
 constexpr long long WAIT_LIMIT = 4000000000LL;  // clock cycles (about two seconds) before a wait gives up
 
 }  // namespace tc
