@@ -270,7 +270,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "QBX target evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": None, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "star r=1+0.3ReY63, 80 curved triangles x 15 nodes (oracle sample of configs[1])",
+            "config": {"workload": "star r=1+0.3ReY63, 80 curved triangles x 15 nodes (oracle sample of the 120k-source star family)",
                        "p_qbx": P_QBX, "p_fmm": P_FMM, "n_max": N_MAX_MIXED, "t_f": T_F},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": "QBX target evals/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
