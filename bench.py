@@ -470,7 +470,8 @@ def run_gpu(args):
 
     T, L = main["T"], main["L"]
     n_direct, n_wfar, modeled = list_work(G, T, L)
-    flops, f_pair = center_kernel_flops(P_FMM, P_QBX, n_direct, 0 if mode != "fp64" else n_wfar, T.info.n_ctr)
+    flops, f_pair = center_kernel_flops(P_FMM, P_QBX, n_direct, 0 if mode != "fp64" else n_wfar, T.info.n_ctr,
+                                        dipole=mu is not None)
     centers_ms = main["stage_ms"]["centers"]
     achieved = flops / (centers_ms * 1e-3) / 1e12
     nlev = int(T.info.n_levels)
