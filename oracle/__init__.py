@@ -69,7 +69,11 @@ def lib():
         L.orc_fmm_eval.argtypes = [P, P, P, i, P, P, P, P, P, i, P, P, i, i, i, P, P, P, P, i]
         L.orc_direct_eval.argtypes = [P, i, P, P, P, P, P, i, P, P, i, i, P, P]
         L.orc_lists_cost.argtypes = [P, P, i, i, P]
+        L.orc_lists_counts.argtypes = [P, P, P]
         L.orc_mlp_loss_grad.argtypes = [P, P, P, i, P]
+        L.orc_mlp_loss_grad_f64.argtypes = [P, P, P, i, P]
+        L.orc_order_labels.argtypes = [P, i, P, i, d, P]
+        L.orc_orders_from_pred.argtypes = [P, P, P, C.c_float, C.c_float, i, i, i, i, i, P, P]
         _lib = L
     return _lib
 
@@ -215,10 +219,20 @@ def build_lists(tree: Tree, slow: bool = False) -> Lists:
     return Lists(h, start, idx)
 
 
+def lists_counts(tree: Tree, lists: Lists) -> dict:
+    """Interaction counts per list: sum of n_s n_t (U, W-close, X-close), entries (V), sum of n_t
+    (W-far), sum of subtree n_s (X-far); n_t = QBX centers of the target box."""
+    out = np.zeros(6, np.int64)
+    lib().orc_lists_counts(tree.handle, lists.handle, _p(out))
+    return dict(zip(LIST_NAMES, (int(v) for v in out)))
+
+
 def lists_cost(tree: Tree, lists: Lists, p_qbx: int, p_fmm: int) -> dict:
-    out = np.zeros(6)
+    """Modeled operation counts: per list (Table ilist-operation-counts), the remaining stage
+    terms of Table complexity-analysis ("stages"), and their sum ("total")."""
+    out = np.zeros(8)
     lib().orc_lists_cost(tree.handle, lists.handle, p_qbx, p_fmm, _p(out))
-    return dict(zip(LIST_NAMES, out))
+    return dict(zip(LIST_NAMES + ("stages", "total"), out.tolist()))
 
 
 # ---------------------------------------------------------------- evaluation
@@ -266,3 +280,33 @@ def mlp_loss_grad(params, x, target):
     out = np.zeros(p.size + 1)
     lib().orc_mlp_loss_grad(_p(p), _p(xx), _p(tt), xx.shape[0], _p(out))
     return out[:-1], out[-1]
+
+
+def mlp_loss_grad_f64(params, x, target):
+    """The same gradient and loss with double-precision parameters, inputs and labels."""
+    p = np.ascontiguousarray(params, np.float64)
+    xx = np.ascontiguousarray(x, np.float64)
+    tt = np.ascontiguousarray(target, np.float64)
+    out = np.zeros(p.size + 1)
+    lib().orc_mlp_loss_grad_f64(_p(p), _p(xx), _p(tt), xx.shape[0], _p(out))
+    return out[:-1], out[-1]
+
+
+def order_labels(values, orders, tol):
+    """values (K, n) results at increasing orders (last = reference) -> (n,) labels."""
+    v = np.ascontiguousarray(values, np.float64)
+    o = np.ascontiguousarray(orders, np.int32)
+    out = np.zeros(v.shape[1], np.int32)
+    lib().orc_order_labels(_p(v), v.shape[0], _p(o), v.shape[1], float(tol), _p(out))
+    return out
+
+
+def orders_from_pred(tree: Tree, pred, margin_q, margin_p, q_lo, q_hi, p_lo, p_hi, p_default, tgt_ctr=None):
+    """Per-center QBX orders and per-box local-expansion orders from predictions (n_ctr, 2)."""
+    pr = np.ascontiguousarray(pred, np.float32)
+    tc = None if tgt_ctr is None else np.ascontiguousarray(tgt_ctr, np.int32)
+    q = np.zeros(pr.shape[0], np.int32)
+    pb = np.zeros(tree.n_boxes, np.int32)
+    lib().orc_orders_from_pred(tree.handle, _p(pr), _p(tc), float(margin_q), float(margin_p), q_lo, q_hi, p_lo, p_hi,
+                               p_default, _p(q), _p(pb))
+    return q, pb

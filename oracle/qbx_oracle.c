@@ -1323,25 +1323,52 @@ int orc_direct_eval(const double *sxyz, int ns, const double *w, const double *s
 }
 
 /*
- * Modeled operation counts per list (Table ilist-operation-counts), from the built lists:
- * out = [U, V, W-close, W-far, X-close, X-far] with n_t = QBX centers owned by the target box.
+ * Interaction counts per list, from the built lists (the quantities Table ilist-operation-counts
+ * multiplies by the per-entry cost), n_t = QBX centers owned by the target box, n_s = sources of the
+ * source box (owned sources; U, W-close and X-close entries are leaves) or of its subtree (X-far):
+ *   counts[U], counts[W-close], counts[X-close] = sum over entries of n_s n_t
+ *   counts[V] = number of entries,  counts[W-far] = sum over entries of n_t,
+ *   counts[X-far] = sum over entries of n_s.
+ */
+void orc_lists_counts(const otree *T, const olists *Ls, int64_t *counts)
+{
+    for (int l = 0; l < L_N; ++l) counts[l] = 0;
+    for (int b = 0; b < T->nb; ++b) {
+        int64_t nt = T->own_start[KCTR][b + 1] - T->own_start[KCTR][b];
+        for (int l = 0; l < L_N; ++l)
+            for (int i = Ls->start[l][b]; i < Ls->start[l][b + 1]; ++i) {
+                int d = Ls->idx[l][i];
+                int64_t nsd = T->own_start[KSRC][d + 1] - T->own_start[KSRC][d];
+                if (l == L_U || l == L_WCLOSE || l == L_XCLOSE) counts[l] += nsd * nt;
+                else if (l == L_V) counts[l] += 1;
+                else if (l == L_WFAR) counts[l] += nt;
+                else counts[l] += T->nsrc_sub[d];
+            }
+    }
+}
+
+/*
+ * Modeled operation counts (Section 6.3): out[0..5] = the per-list costs of Table
+ * ilist-operation-counts (U, W-close, X-close: p_qbx^2 n_s n_t; V: p_fmm^3; W-far: p_fmm^3 n_t;
+ * X-far: p_fmm^2 n_s) summed over the entries; out[6] = the stage terms of Table
+ * complexity-analysis that no list carries: N_S p_fmm^2 + N_B p_fmm^3 (Stage 2),
+ * 8 N_B p_fmm^3 (Stage 7), N_C p_fmm^3 (Stage 8), N_T p_qbx^2 (Stage 9); out[7] = the sum.
  */
 void orc_lists_cost(const otree *T, const olists *Ls, int p_qbx, int p_fmm, double *out)
 {
     double q2 = (double)p_qbx * p_qbx, p3 = (double)p_fmm * p_fmm * p_fmm, p2 = (double)p_fmm * p_fmm;
-    for (int l = 0; l < L_N; ++l) out[l] = 0.0;
-    for (int b = 0; b < T->nb; ++b) {
-        double nt = T->own_start[KCTR][b + 1] - T->own_start[KCTR][b];
-        for (int l = 0; l < L_N; ++l)
-            for (int i = Ls->start[l][b]; i < Ls->start[l][b + 1]; ++i) {
-                int d = Ls->idx[l][i];
-                double nsd = T->own_start[KSRC][d + 1] - T->own_start[KSRC][d];
-                if (l == L_U || l == L_WCLOSE || l == L_XCLOSE) out[l] += q2 * nsd * nt;
-                else if (l == L_V) out[l] += p3;
-                else if (l == L_WFAR) out[l] += p3 * nt;
-                else out[l] += p2 * T->nsrc_sub[d];
-            }
-    }
+    int64_t c[L_N];
+    orc_lists_counts(T, Ls, c);
+    out[L_U] = q2 * (double)c[L_U];
+    out[L_V] = p3 * (double)c[L_V];
+    out[L_WCLOSE] = q2 * (double)c[L_WCLOSE];
+    out[L_WFAR] = p3 * (double)c[L_WFAR];
+    out[L_XCLOSE] = q2 * (double)c[L_XCLOSE];
+    out[L_XFAR] = p2 * (double)c[L_XFAR];
+    out[6] = (double)T->np[KSRC] * p2 + (double)T->nb * p3 + 8.0 * (double)T->nb * p3 + (double)T->np[KCTR] * p3 +
+             (double)T->np[KTGT] * q2;
+    out[7] = 0.0;
+    for (int l = 0; l < 7; ++l) out[7] += out[l];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1349,12 +1376,13 @@ void orc_lists_cost(const otree *T, const olists *Ls, int p_qbx, int p_fmm, doub
 /* ------------------------------------------------------------------------ */
 
 /*
- * Network 4 -> 64 -> 64 -> 2 with tanh hidden layers and a linear output; parameters (float)
+ * Network 4 -> 64 -> 64 -> 2 with tanh hidden layers and a linear output; parameters
  * W1[64][4], b1[64], W2[64][64], b2[64], W3[2][64], b3[2].  Loss L = 1/(2n) sum_i |y_i - t_i|^2.
  * Forward pass and gradient by the chain rule, in double precision, sample by sample.
- * grad receives dL/dparams (4610 doubles) followed by L.
+ * grad receives dL/dparams (4610 doubles) followed by L.  This core takes double parameters,
+ * inputs and labels; orc_mlp_loss_grad below is the same computation on float arrays.
  */
-int orc_mlp_loss_grad(const float *P, const float *x, const float *t, int n, double *grad)
+void orc_mlp_loss_grad_f64(const double *P, const double *x, const double *t, int n, double *grad)
 {
     enum { NI = 4, A = 64, B = 64, NO = 2 };
     const int oW1 = 0, ob1 = oW1 + A * NI, oW2 = ob1 + A, ob2 = oW2 + B * A, oW3 = ob2 + B, ob3 = oW3 + NO * B,
@@ -1364,17 +1392,17 @@ int orc_mlp_loss_grad(const float *P, const float *x, const float *t, int n, dou
         double h1[A], h2[B], y[NO], dy[NO], d2[B], d1[A];
         for (int j = 0; j < A; ++j) {
             double a = P[ob1 + j];
-            for (int k = 0; k < NI; ++k) a += (double)P[oW1 + j * NI + k] * x[NI * s + k];
+            for (int k = 0; k < NI; ++k) a += P[oW1 + j * NI + k] * x[NI * s + k];
             h1[j] = tanh(a);
         }
         for (int j = 0; j < B; ++j) {
             double a = P[ob2 + j];
-            for (int k = 0; k < A; ++k) a += (double)P[oW2 + j * A + k] * h1[k];
+            for (int k = 0; k < A; ++k) a += P[oW2 + j * A + k] * h1[k];
             h2[j] = tanh(a);
         }
         for (int o = 0; o < NO; ++o) {
             double a = P[ob3 + o];
-            for (int k = 0; k < B; ++k) a += (double)P[oW3 + o * B + k] * h2[k];
+            for (int k = 0; k < B; ++k) a += P[oW3 + o * B + k] * h2[k];
             y[o] = a;
             double r = y[o] - t[NO * s + o];
             dy[o] = r / n;
@@ -1382,12 +1410,12 @@ int orc_mlp_loss_grad(const float *P, const float *x, const float *t, int n, dou
         }
         for (int j = 0; j < B; ++j) {
             double g = 0.0;
-            for (int o = 0; o < NO; ++o) g += (double)P[oW3 + o * B + j] * dy[o];
+            for (int o = 0; o < NO; ++o) g += P[oW3 + o * B + j] * dy[o];
             d2[j] = g * (1.0 - h2[j] * h2[j]);
         }
         for (int k = 0; k < A; ++k) {
             double g = 0.0;
-            for (int j = 0; j < B; ++j) g += (double)P[oW2 + j * A + k] * d2[j];
+            for (int j = 0; j < B; ++j) g += P[oW2 + j * A + k] * d2[j];
             d1[k] = g * (1.0 - h1[k] * h1[k]);
         }
         for (int j = 0; j < A; ++j) {
@@ -1403,5 +1431,82 @@ int orc_mlp_loss_grad(const float *P, const float *x, const float *t, int n, dou
             grad[ob3 + o] += dy[o];
         }
     }
+}
+
+int orc_mlp_loss_grad(const float *P, const float *x, const float *t, int n, double *grad)
+{
+    enum { NP = 4610 };
+    double *Pd = malloc(sizeof(double) * NP), *xd = malloc(sizeof(double) * 4 * (n > 0 ? n : 1)),
+           *td = malloc(sizeof(double) * 2 * (n > 0 ? n : 1));
+    for (int i = 0; i < NP; ++i) Pd[i] = P[i];
+    for (int i = 0; i < 4 * n; ++i) xd[i] = x[i];
+    for (int i = 0; i < 2 * n; ++i) td[i] = t[i];
+    orc_mlp_loss_grad_f64(Pd, xd, td, n, grad);
+    free(Pd); free(xd); free(td);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* learned orders: sweep labels and the map from predictions to orders       */
+/* (not part of the paper's method; the order network's inputs and outputs)  */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Labels from an order sweep.  values[k * n + t] is target t's result at the k-th order of the
+ * sweep (orders order_of[0] < ... < order_of[K-1], the last column the reference).  The label of
+ * t is order_of[k*] for the smallest k* such that every column k >= k* lies within tol of the
+ * reference: |values[k][t] - values[K-1][t]| <= tol.
+ */
+void orc_order_labels(const double *values, int K, const int *order_of, int n, double tol, int *labels)
+{
+    for (int t = 0; t < n; ++t) {
+        double ref = values[(size_t)(K - 1) * n + t];
+        int best = K - 1;
+        for (int ks = 0; ks < K; ++ks) {
+            int all_within = 1;
+            for (int k = ks; k < K; ++k)
+                if (!(fabs(values[(size_t)k * n + t] - ref) <= tol)) all_within = 0;
+            if (all_within) { best = ks; break; }
+        }
+        labels[t] = order_of[best];
+    }
+}
+
+/* clamp(ceil(y + margin), lo, hi) in single precision; a NaN prediction gives hi */
+static int order_from_pred(float y, float margin, int lo, int hi)
+{
+    if (y != y) return hi;
+    float v = ceilf(y + margin);
+    if (v < (float)lo) return lo;
+    if (v > (float)hi) return hi;
+    return (int)v;
+}
+
+/*
+ * Orders from network predictions pred[2c], pred[2c+1] (input center order).  The QBX order of
+ * center c is clamp(ceil(pred[2c] + margin_q), q_lo, q_hi).  The order of box b's local expansion is
+ * the largest clamp(ceil(pred[2c+1] + margin_p), p_lo, p_hi) over the centers c owned by b or by a
+ * box below b; a box owning a point target (tgt_ctr[t] < 0), and every box above it, gets p_hi; a box
+ * that neither holds a center nor a point target in its subtree gets p_default.  tgt_ctr may be
+ * NULL (no point targets).
+ */
+void orc_orders_from_pred(const otree *T, const float *pred, const int *tgt_ctr, float margin_q, float margin_p,
+                          int q_lo, int q_hi, int p_lo, int p_hi, int p_default, int *q_out, int *p_out)
+{
+    int nb = T->nb;
+    int *best = malloc(sizeof(int) * (nb > 0 ? nb : 1));
+    for (int b = 0; b < nb; ++b) best[b] = -1;
+    for (int c = 0; c < T->np[KCTR]; ++c) {
+        q_out[c] = order_from_pred(pred[2 * c], margin_q, q_lo, q_hi);
+        int p = order_from_pred(pred[2 * c + 1], margin_p, p_lo, p_hi);
+        for (int b = T->owner[KCTR][c]; b >= 0; b = T->parent[b])
+            if (p > best[b]) best[b] = p;
+    }
+    if (tgt_ctr)
+        for (int t = 0; t < T->np[KTGT]; ++t)
+            if (tgt_ctr[t] < 0)
+                for (int b = T->owner[KTGT][t]; b >= 0; b = T->parent[b])
+                    if (p_hi > best[b]) best[b] = p_hi;
+    for (int b = 0; b < nb; ++b) p_out[b] = best[b] >= 0 ? best[b] : p_default;
+    free(best);
 }
