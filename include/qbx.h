@@ -121,7 +121,30 @@ int qbx_lists_export(const qbx_lists *lists, int which, int32_t *start_dev, int3
 void qbx_lists_free(qbx_lists *lists);
 
 typedef struct {
-    int p_qbx;                    /* QBX order, 0 <= p_qbx <= 16; with p_qbx_per_ctr: the largest entry allowed */
+    /* interaction counts per list (index QBX_LIST_*), n_t = QBX centers owned by the target box,
+     * n_s = sources owned by the source box (its whole subtree for List 4 far):
+     * U, W-close, X-close: sum over entries of n_s n_t;  V: entries;  W-far: sum of n_t;
+     * X-far: sum of n_s.  Exact integers. */
+    int64_t count[6];
+    double ops[6];      /* modeled operations per list: count x p_qbx^2 (U, W-close, X-close),
+                           x p_fmm^3 (V, W-far), x p_fmm^2 (X-far) */
+    double ops_stages;  /* the stage terms no list carries: N_S p_fmm^2 + N_B p_fmm^3 (Stage 2),
+                           8 N_B p_fmm^3 (Stage 7), N_C p_fmm^3 (Stage 8), N_T p_qbx^2 (Stage 9) */
+    double ops_total;   /* ops[0] + ... + ops[5] + ops_stages, summed in that order */
+} qbx_cost;
+
+/*
+ * Modeled operation counts of one evaluation (Section 6.3): the per-entry costs of Table
+ * ilist-operation-counts over the built lists, plus the remaining stage costs of Table
+ * complexity-analysis, for orders p_qbx and p_fmm.  The counts are reduced on the device
+ * (integer sums); the call synchronizes `stream`.
+ *   cost_host: host struct, overwritten.
+ * Errors: QBX_ERR_INVALID_ARG (NULL handle or output, negative order), QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_lists_cost(const qbx_lists *lists, int p_qbx, int p_fmm, qbx_cost *cost_host, void *stream);
+
+typedef struct {
+    int p_qbx;                   /* QBX order, 0 <= p_qbx <= 16; with p_qbx_per_ctr: the largest entry allowed */
     int p_fmm;                    /* FMM order, 0 <= p_fmm <= 20: the order of every multipole expansion, and of
                                      every box's local expansion unless p_fmm_per_box is given */
     const int8_t *p_qbx_per_ctr;  /* optional device array [n_ctr], per-center QBX order in [0, p_qbx] */
@@ -185,11 +208,12 @@ int qbx_eval_order_sweep(const qbx_tree *tree, const qbx_lists *lists, const dou
 #define QBX_MLP_NPARAMS 4610
 
 /*
- * Four features per QBX center, written to feat[4*c..4*c+3] in input center order:
- * log2(r_c/|b|), level(b)/8, log2 of the smallest |c - c_d|/|d| over the List 3 far boxes d of b
- * (log2 16 if none), log10 of the largest source strength |w sigma| + |w mu n| in List 1 of b
- * relative to the largest over all sources (+1e-12); b is the box owning c.  Densities as in
- * qbx_eval.  Errors: QBX_ERR_INVALID_ARG, QBX_ERR_OOM, QBX_ERR_CUDA.
+ * Four features per QBX center, written to feat[4*c..4*c+3] in input center order, b the box owning c:
+ * log2(r_c/|b|), level(b)/8, (|c - c_b| + r_c)/|b| (how far the expansion ball reaches from the
+ * center of b, where b's local expansion is centered), and log10 of the largest source strength
+ * |w sigma| + |w mu n| over the sources of List 1 of b relative to the largest over all sources
+ * (+1e-12).  Computed in FP64, stored as float.  Densities as in qbx_eval.
+ * Errors: QBX_ERR_INVALID_ARG, QBX_ERR_OOM, QBX_ERR_CUDA.
  */
 int qbx_center_features(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev,
                         const double *sigma_dev, const double *mu_dev, const double *src_n_dev, float *feat_dev,
@@ -293,6 +317,22 @@ void qbx_graph_free(qbx_graph *graph);
 int qbx_lists_set_tiles(qbx_lists *lists, int m2l_kchunk, int m2qbxl_kchunk);
 
 /*
+ * Failure handling of the tensor-core pipelines (QBX_M2L_3XTF32; not a step of the paper's method).
+ * Every wait of those kernels is bounded; when one gives up, the kernel waits (again bounded) for the
+ * bulk copies and tensor-core products it has already issued, frees its tensor memory and returns, and
+ * qbx_eval returns QBX_ERR_TIMEOUT.  The next evaluation starts clean.
+ *   limit_cycles:  SM clock cycles a pipeline wait may take before it gives up; 0 restores the
+ *                  default (4e9 cycles, about two seconds).  The drain waits after a failure keep the
+ *                  default.
+ *   probe_step:    -1 (normal operation), or a pipeline step k >= 0 at which the issuing thread of every
+ *                  block of both tensor-core kernels also waits on a barrier that nothing ever arrives
+ *                  on, so that the wait runs out after limit_cycles and the failure path above runs
+ *                  (a test of that path; blocks with fewer than k + 1 steps are not affected).
+ * Settings apply to later evaluations on these lists.  Errors: QBX_ERR_INVALID_ARG.
+ */
+int qbx_lists_set_wait(qbx_lists *lists, long long limit_cycles, int probe_step);
+
+/*
  * Per-stage timing (tracing aid; not a step of the paper's method).  While enabled,
  * every qbx_eval on these lists records CUDA events on its stream around each of
  * QBX_NSTAGES stages: 0 input preparation, 1 P2M + M2M (Stage 2), 2 List 2 M2L
@@ -309,25 +349,27 @@ int qbx_profile(qbx_lists *lists, int enable);
 int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
 
 /*
- * qbx_eval without device allocation.  Computes the same potentials as qbx_eval
- * (same arguments, same stages and kernels) for callers that cannot call cudaMalloc
- * when they evaluate: code running while someone else captures the stream into a
- * CUDA graph, real-time loops with a memory budget fixed up front, or hosts whose
- * allocator owns the device.  The paper has no counterpart; it is an interface choice.
- *   Scratch: one file-scope device array of QBX_NOALLOC_SCRATCH_BYTES (48 MiB) inside
- *   the library, held by every GPU that loads the library until the process exits.
- *   The problem must fit: about 18.4 MB of tables + 7,394 B per box + 16 ntri(Qb) B per
- *   center (Qb = 4, 8, 12 or 16, the smallest >= p_qbx)
- *   + 33 B per source; e.g. 2,000 boxes and 20,000 centers at p_qbx <= 8.  A larger
- *   problem returns QBX_ERR_INVALID_ARG with the byte counts in qbx_last_error().
+ * qbx_eval without device allocation, for callers that cannot call cudaMalloc when they
+ * evaluate: real-time loops whose device-memory budget is fixed up front, or hosts whose
+ * allocator owns the whole device and forbids allocations from elsewhere.  The paper has no
+ * counterpart; it is an interface choice.  Same arguments and the same stages and formulas as
+ * qbx_eval, in QBX_FP64 only; the box-expansion passes run the library's per-warp kernels rather
+ * than qbx_eval's, so the two agree to rounding (about 1e-15 relative), not bit for bit.
+ *   Scratch: one file-scope device array of QBX_NOALLOC_SCRATCH_BYTES (48 MiB) inside the
+ *   library, held by every GPU that loads the library until the process exits.  The problem
+ *   must fit: roughly 18.4 MB of tables + 7.4 kB per box + 16 ntri(Qb) bytes per center (Qb =
+ *   4, 8, 12 or 16, the smallest >= p_qbx) + 33 bytes per source, each buffer rounded up to 256
+ *   bytes; e.g. 2,000 boxes and 20,000 centers at p_qbx <= 8.  A larger problem returns
+ *   QBX_ERR_INVALID_ARG with the exact byte counts in qbx_last_error().
  *   No call allocates: no cudaMalloc, cudaFree or allocating library routine.
- *   The first call on each device looks up the array's device address (with that
- *   device current); make that first call before any stream capture.
- *   All calls share the array and it keeps the last call's contents: every call
- *   rewrites its tables and zeroes its accumulators before use, but calls whose GPU
- *   work overlaps in time on one device (issued on different streams, or from
- *   different host threads) race on it and give wrong results.
- * Errors: as qbx_eval.
+ *   The first call on each device looks up the array's device address (with that device
+ *   current) and keeps it; make that first call before any stream capture.  The address stays
+ *   valid while the device's primary context lives: after a device reset, reload the library.
+ *   All calls share the array and it keeps the last call's contents: every call rewrites its
+ *   tables and zeroes its accumulators before use, but calls whose GPU work overlaps in time on
+ *   one device (issued on different streams, or from different host threads) race on it and
+ *   give wrong results.
+ * Errors: as qbx_eval; QBX_ERR_INVALID_ARG also for a precision other than QBX_FP64.
  */
 #define QBX_NOALLOC_SCRATCH_BYTES (48u << 20)
 int qbx_eval_noalloc(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev, const double *sigma_dev,

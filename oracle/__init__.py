@@ -20,20 +20,40 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "qbx_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liborc.so")
+_LIB_OMP = os.path.join(_HERE, "_build", "liborc_omp.so")  # the same source built with -fopenmp
 
 LIST_NAMES = ("U", "V", "Wclose", "Wfar", "Xclose", "Xfar")
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle (plain C, -O2 -ffp-contract=off, no target-specific flags)."""
+    """Compile the oracle (plain C, -O2 -ffp-contract=off, no target-specific flags): a serial library
+    and, where the compiler supports it, the same source with OpenMP (all-cores timing only)."""
     os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    base = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared"]
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", _LIB, _SRC, "-lm"]
-        subprocess.run(cmd, check=True)
+        subprocess.run(base + ["-o", _LIB, _SRC, "-lm"], check=True)
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        subprocess.run(base + ["-fopenmp", "-o", _LIB_OMP, _SRC, "-lm"], check=False)
     return _LIB
 
 
 _lib = None
+_lib_omp = None
+
+
+def lib_omp():
+    """The OpenMP build (same functions; orc_fmm_eval runs its box and center loops on all cores)."""
+    global _lib_omp
+    if _lib_omp is None:
+        lib()
+        if not os.path.exists(_LIB_OMP):
+            raise RuntimeError("the OpenMP build of the oracle is not available (gcc -fopenmp failed)")
+        L = C.CDLL(_LIB_OMP)
+        P = C.c_void_p
+        i = C.c_int
+        L.orc_fmm_eval.argtypes = [P, P, P, i, P, P, P, P, P, i, P, P, i, i, i, P, P, P, P, i]
+        _lib_omp = L
+    return _lib_omp
 
 
 def lib():
@@ -74,6 +94,7 @@ def lib():
         L.orc_mlp_loss_grad_f64.argtypes = [P, P, P, i, P]
         L.orc_order_labels.argtypes = [P, i, P, i, d, P]
         L.orc_orders_from_pred.argtypes = [P, P, P, C.c_float, C.c_float, i, i, i, i, i, P, P]
+        L.orc_center_features.argtypes = [P, P, P, P, P, P, P, P, P]
         _lib = L
     return _lib
 
@@ -239,8 +260,9 @@ def lists_cost(tree: Tree, lists: Lists, p_qbx: int, p_fmm: int) -> dict:
 
 
 def fmm_eval(tree: Tree, lists: Lists, src_xyz, src_w, sigma, mu, src_n, ctr_xyz, tgt_xyz, tgt_ctr,
-             p_qbx, p_fmm, p_qbx_ctr=None, p_fmm_box=None, return_qbx_locals=False, qmax=None):
-    """GIGAQBX FMM (Algorithm 4): pot = S[sigma] + D[mu] at every target."""
+             p_qbx, p_fmm, p_qbx_ctr=None, p_fmm_box=None, return_qbx_locals=False, qmax=None, omp=False):
+    """GIGAQBX FMM (Algorithm 4): pot = S[sigma] + D[mu] at every target.  omp=True runs the OpenMP
+    build of the same code (same results)."""
     s, w, sg, m_, n_ = _f64(src_xyz), _f64(src_w), _f64(sigma), _f64(mu), _f64(src_n)
     c, t = _f64(ctr_xyz), _f64(tgt_xyz)
     tc = np.ascontiguousarray(tgt_ctr, np.int32)
@@ -250,7 +272,7 @@ def fmm_eval(tree: Tree, lists: Lists, src_xyz, src_w, sigma, mu, src_n, ctr_xyz
     pot = np.zeros(nt)
     qm = qmax if qmax is not None else (p_qbx if qc is None else int(qc.max()))
     ql = np.zeros((c.shape[1], _ncoef(qm)), np.complex128) if return_qbx_locals else None
-    rc = lib().orc_fmm_eval(tree.handle, lists.handle, _p(s), s.shape[1], _p(w), _p(sg), _p(m_), _p(n_), _p(c),
+    rc = (lib_omp() if omp else lib()).orc_fmm_eval(tree.handle, lists.handle, _p(s), s.shape[1], _p(w), _p(sg), _p(m_), _p(n_), _p(c),
                             c.shape[1], _p(t), _p(tc), nt, p_qbx, p_fmm, _p(qc), _p(pb), _p(pot), _p(ql), qm)
     if rc != 0:
         raise ValueError("particle counts do not match the tree")
@@ -290,6 +312,15 @@ def mlp_loss_grad_f64(params, x, target):
     out = np.zeros(p.size + 1)
     lib().orc_mlp_loss_grad_f64(_p(p), _p(xx), _p(tt), xx.shape[0], _p(out))
     return out[:-1], out[-1]
+
+
+def center_features(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, ctr_xyz, ctr_r):
+    """(n_ctr, 4) float32 inputs of the order network per center (input order)."""
+    w, sg, m_, n_ = _f64(src_w), _f64(sigma), _f64(mu), _f64(src_n)
+    c, r = _f64(ctr_xyz), _f64(ctr_r)
+    out = np.zeros((c.shape[1], 4), np.float32)
+    lib().orc_center_features(tree.handle, lists.handle, _p(w), _p(sg), _p(m_), _p(n_), _p(c), _p(r), _p(out))
+    return out
 
 
 def order_labels(values, orders, tol):

@@ -1166,28 +1166,42 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
     cplx *L = calloc((size_t)nb * nP, sizeof(cplx));
     cplx *Lq = calloc((size_t)(nc > 0 ? nc : 1) * nQ, sizeof(cplx));
     double *pnear = calloc(nt > 0 ? nt : 1, sizeof(double));
-    double s[3], d[3], c[3], t[3], qq;
-    int hd;
 #define PB(b) (pbox ? (int)pbox[b] : p_fmm) /* order of the local expansion of box b */
 #define PM p_fmm                            /* order of every multipole expansion */
 #define QC(cc) (qctr ? (int)qctr[cc] : p_qbx)
 
-    /* Stage 2: multipoles of leaves, then upward pass in postorder */
-    for (int b = 0; b < nb; ++b)
+    /* Every loop below that is marked "omp parallel for" writes, per iteration, only the expansions
+     * and potentials of its own box, center or target; compiled with -fopenmp it runs on all cores,
+     * otherwise serially.  Each result is accumulated in the same order either way. */
+
+    /* Stage 2: multipoles of leaves, then the upward pass: level by level from the deepest, each
+     * parent adding its children from the highest box number down (postorder) */
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int b = 0; b < nb; ++b) {
+        double s[3], d[3], qq;
+        int hd;
         for (int k = T->own_start[KSRC][b]; k < T->own_start[KSRC][b + 1]; ++k) {
             src_q_d(&S, T->own_idx[KSRC][k], s, &qq, d, &hd);
             p2m(PM, &T->cen[3 * b], s, qq, hd ? d : NULL, &M[(size_t)b * nP]);
         }
-    for (int b = nb - 1; b >= 1; --b) {
-        int pa = T->parent[b];
-        if (T->nsrc_sub[b] > 0) m2m(PM, &T->cen[3 * b], &M[(size_t)b * nP], PM, &T->cen[3 * pa], &M[(size_t)pa * nP]);
+    }
+    for (int lev = T->nlev - 2; lev >= 0; --lev) {
+#pragma omp parallel for schedule(dynamic, 16)
+        for (int pa = T->level_start[lev]; pa < T->level_start[lev + 1]; ++pa)
+            for (int o = 7; o >= 0; --o) {
+                int b = T->child[8 * pa + o];
+                if (b >= 0 && T->nsrc_sub[b] > 0)
+                    m2m(PM, &T->cen[3 * b], &M[(size_t)b * nP], PM, &T->cen[3 * pa], &M[(size_t)pa * nP]);
+            }
     }
 
     /* Stages 3, 5(a), 6(a): direct interactions from U, W-close, X-close */
     const int direct_lists[3] = {L_U, L_WCLOSE, L_XCLOSE};
     for (int li = 0; li < 3; ++li) {
         int l = direct_lists[li];
+#pragma omp parallel for schedule(dynamic, 16)
         for (int b = 0; b < nb; ++b) {
+            double c[3], t[3];
             const int *lst = Ls->idx[l] + Ls->start[l][b];
             int n = Ls->start[l][b + 1] - Ls->start[l][b];
             if (n == 0) continue;
@@ -1206,6 +1220,7 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
     }
 
     /* Stage 4: List 2 multipole-to-local */
+#pragma omp parallel for schedule(dynamic, 16)
     for (int b = 0; b < nb; ++b)
         for (int i = Ls->start[L_V][b]; i < Ls->start[L_V][b + 1]; ++i) {
             int dd = Ls->idx[L_V][i];
@@ -1213,8 +1228,10 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
         }
 
     /* Stage 5(b): List 3 far multipoles at point targets and QBX centers */
+#pragma omp parallel for schedule(dynamic, 16)
     for (int b = 0; b < nb; ++b)
         for (int i = Ls->start[L_WFAR][b]; i < Ls->start[L_WFAR][b + 1]; ++i) {
+            double c[3], t[3];
             int dd = Ls->idx[L_WFAR][i];
             for (int k = T->own_start[KTGT][b]; k < T->own_start[KTGT][b + 1]; ++k) {
                 int ti = T->own_idx[KTGT][k];
@@ -1230,8 +1247,11 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
         }
 
     /* Stage 6(b): List 4 far sources to local expansions of the box */
+#pragma omp parallel for schedule(dynamic, 16)
     for (int b = 0; b < nb; ++b)
         for (int i = Ls->start[L_XFAR][b]; i < Ls->start[L_XFAR][b + 1]; ++i) {
+            double s[3], d[3], qq;
+            int hd;
             int dd = Ls->idx[L_XFAR][i];
             for (int k = T->own_start[KSRC][dd]; k < T->own_start[KSRC][dd + 1]; ++k) {
                 src_q_d(&S, T->own_idx[KSRC][k], s, &qq, d, &hd);
@@ -1239,23 +1259,31 @@ int orc_fmm_eval(const otree *T, const olists *Ls, const double *sxyz, int ns, c
             }
         }
 
-    /* Stage 7: downward pass in preorder */
-    for (int b = 1; b < nb; ++b) {
-        int pa = T->parent[b];
-        if (T->ntgt_sub[b] > 0) l2l(PB(pa), &T->cen[3 * pa], &L[(size_t)pa * nP], PB(b), &T->cen[3 * b], &L[(size_t)b * nP]);
+    /* Stage 7: downward pass in preorder (level by level) */
+    for (int lev = 1; lev < T->nlev; ++lev) {
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int b = T->level_start[lev]; b < T->level_start[lev + 1]; ++b) {
+            int pa = T->parent[b];
+            if (T->ntgt_sub[b] > 0)
+                l2l(PB(pa), &T->cen[3 * pa], &L[(size_t)pa * nP], PB(b), &T->cen[3 * b], &L[(size_t)b * nP]);
+        }
     }
 
     /* Stage 8: box locals to QBX centers */
+#pragma omp parallel for schedule(dynamic, 16)
     for (int b = 0; b < nb; ++b)
         for (int k = T->own_start[KCTR][b]; k < T->own_start[KCTR][b + 1]; ++k) {
+            double c[3];
             int ci = T->own_idx[KCTR][k];
             get_pt(cxyz, nc, ci, c);
             l2l(PB(b), &T->cen[3 * b], &L[(size_t)b * nP], QC(ci), c, &Lq[(size_t)ci * nQ]);
         }
 
     /* Stage 9: final potentials */
+#pragma omp parallel for schedule(dynamic, 64)
     for (int b = 0; b < nb; ++b)
         for (int k = T->own_start[KTGT][b]; k < T->own_start[KTGT][b + 1]; ++k) {
+            double c[3], t[3];
             int ti = T->own_idx[KTGT][k];
             get_pt(txyz, nt, ti, t);
             int ci = tgt_ctr[ti];
@@ -1509,4 +1537,51 @@ void orc_orders_from_pred(const otree *T, const float *pred, const int *tgt_ctr,
                     if (p_hi > best[b]) best[b] = p_hi;
     for (int b = 0; b < nb; ++b) p_out[b] = best[b] >= 0 ? best[b] : p_default;
     free(best);
+}
+
+/*
+ * Four inputs of the order network per QBX center c (input order), b the box owning c:
+ *   feat[4c]   = log2(r_c / |b|)                        (expansion radius relative to the box)
+ *   feat[4c+1] = level(b) / 8                           (box size: |b| = |root| 2^-level)
+ *   feat[4c+2] = (|c - c_b|_2 + r_c) / |b|              (how far the expansion ball reaches from the
+ *                                                        box center, where the box local is expanded)
+ *   feat[4c+3] = log10(s_near / s_max + 1e-12)          (near-field source strength)
+ * with the source strength |w sigma| + |w mu n|_2, s_near its largest value over the sources of the
+ * List 1 boxes of b and s_max its largest value over all sources (0 for a zero density).  Computed in
+ * double precision and rounded to float.  sigma or mu may be NULL.
+ */
+void orc_center_features(const otree *T, const olists *Ls, const double *w, const double *sigma, const double *mu,
+                         const double *nrm, const double *cxyz, const double *cr, float *feat)
+{
+    int ns = T->np[KSRC], nc = T->np[KCTR];
+    double *str = malloc(sizeof(double) * (ns > 0 ? ns : 1));
+    double smax = 0.0;
+    for (int j = 0; j < ns; ++j) {
+        double q = sigma ? w[j] * sigma[j] : 0.0, v = fabs(q);
+        if (mu) {
+            double a = w[j] * mu[j], dx = a * nrm[j], dy = a * nrm[ns + j], dz = a * nrm[2 * ns + j];
+            v += sqrt(dx * dx + dy * dy + dz * dz);
+        }
+        str[j] = v;
+        if (v > smax) smax = v;
+    }
+    for (int ci = 0; ci < nc; ++ci) {
+        int b = T->owner[KCTR][ci];
+        double x[3], r = cr[ci];
+        get_pt(cxyz, nc, ci, x);
+        double dx = x[0] - T->cen[3 * b], dy = x[1] - T->cen[3 * b + 1], dz = x[2] - T->cen[3 * b + 2];
+        double snear = 0.0;
+        for (int e = Ls->start[L_U][b]; e < Ls->start[L_U][b + 1]; ++e) {
+            int d = Ls->idx[L_U][e];
+            for (int k = T->own_start[KSRC][d]; k < T->own_start[KSRC][d + 1]; ++k) {
+                double v = str[T->own_idx[KSRC][k]];
+                if (v > snear) snear = v;
+            }
+        }
+        feat[4 * ci] = (float)log2(r / T->hw[b]);
+        feat[4 * ci + 1] = (float)(T->level[b] / 8.0);
+        feat[4 * ci + 2] = (float)((sqrt(dx * dx + dy * dy + dz * dz) + r) / T->hw[b]);
+        feat[4 * ci + 3] = (float)log10(snear / (smax > 0.0 ? smax : 1e-300) + 1e-12);
+    }
+    free(str);
 }

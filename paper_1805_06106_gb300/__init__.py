@@ -19,6 +19,7 @@ from .binding import (  # noqa: F401
     qbx_eval,
     qbx_eval_noalloc,
     qbx_eval_order_sweep,
+    qbx_lists_cost,
     MLP_NPARAMS,
     qbx_center_features,
     qbx_order_labels,
@@ -31,4 +32,8 @@ from .binding import (  # noqa: F401
     qbx_build_forest,
     qbx_graph_create,
     qbx_lists_set_tiles,
+    qbx_lists_set_wait,
+    qbx_peak_flops,
+    QBX_PEAK_FP64,
+    QBX_PEAK_FP32,
 )

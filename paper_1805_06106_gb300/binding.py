@@ -36,6 +36,11 @@ class _TreeInfo(C.Structure):
                 ("root_radius", C.c_double)]
 
 
+class _Cost(C.Structure):
+    _fields_ = [("count", C.c_int64 * 6), ("ops", C.c_double * 6), ("ops_stages", C.c_double),
+                ("ops_total", C.c_double)]
+
+
 class _EvalOpts(C.Structure):
     _fields_ = [("p_qbx", C.c_int), ("p_fmm", C.c_int), ("p_qbx_per_ctr", C.c_void_p),
                 ("p_fmm_per_box", C.c_void_p), ("precision", C.c_int)]
@@ -61,6 +66,7 @@ def lib():
         L.qbx_lists_export.argtypes = [P, C.c_int, P, P, P]
         L.qbx_lists_free.argtypes = [P]
         L.qbx_lists_free.restype = None
+        L.qbx_lists_cost.argtypes = [P, C.c_int, C.c_int, C.POINTER(_Cost), P]
         L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_eval_noalloc.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_eval_order_sweep.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
@@ -80,8 +86,10 @@ def lib():
         L.qbx_graph_free.argtypes = [P]
         L.qbx_graph_free.restype = None
         L.qbx_lists_set_tiles.argtypes = [P, C.c_int, C.c_int]
+        L.qbx_lists_set_wait.argtypes = [P, C.c_longlong, C.c_int]
         L.qbx_profile.argtypes = [P, C.c_int]
         L.qbx_profile_read.argtypes = [P, P]
+        L.qbx_peak_flops.argtypes = [C.c_int, C.c_int, C.POINTER(C.c_double), P]
         L.qbx_last_error.restype = C.c_char_p
         _lib = L
     return _lib
@@ -192,6 +200,15 @@ def qbx_build_lists(tree: Tree) -> Lists:
     h = C.c_void_p()
     _check(lib().qbx_build_lists(tree.handle, C.byref(h), _stream()))
     return Lists(h, tree)
+
+
+def qbx_lists_cost(lists: Lists, p_qbx, p_fmm) -> dict:
+    """Modeled operation counts (Section 6.3) of an evaluation on these lists: per-list integer
+    counts ("count"), per-list modeled operations ("ops"), the remaining stage terms and the total."""
+    c = _Cost()
+    _check(lib().qbx_lists_cost(lists.handle, int(p_qbx), int(p_fmm), C.byref(c), _stream()))
+    return {"count": dict(zip(LIST_NAMES, list(c.count))), "ops": dict(zip(LIST_NAMES, list(c.ops))),
+            "stages": c.ops_stages, "total": c.ops_total}
 
 
 def qbx_eval(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr, p_qbx, p_fmm, p_qbx_per_ctr=None,
@@ -310,6 +327,11 @@ def qbx_lists_set_tiles(lists: Lists, m2l_kchunk=0, m2qbxl_kchunk=0):
     _check(lib().qbx_lists_set_tiles(lists.handle, int(m2l_kchunk), int(m2qbxl_kchunk)))
 
 
+def qbx_lists_set_wait(lists: Lists, limit_cycles=0, probe_step=-1):
+    """Tensor-core pipeline wait limit (cycles; 0 = default) and failure-path probe step (-1 = off)."""
+    _check(lib().qbx_lists_set_wait(lists.handle, int(limit_cycles), int(probe_step)))
+
+
 # ---------------------------------------------------------------- batched problems and graphs
 
 
@@ -365,6 +387,16 @@ def qbx_graph_create(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, tgt_ctr,
     _check(lib().qbx_graph_create(tree.handle, lists.handle, _ptr(w), _ptr(sg), _ptr(m), _ptr(n), _ptr(tc),
                                   C.byref(opts), _ptr(out), C.byref(h), _stream()))
     return Graph(h, (tree, lists, w, sg, m, n, tc, qc, pb, out))
+
+
+QBX_PEAK_FP64, QBX_PEAK_FP32 = 0, 1
+
+
+def qbx_peak_flops(kind, reps=5):
+    """Measured FMA throughput of the device in flop/s (kind QBX_PEAK_FP64 or QBX_PEAK_FP32)."""
+    v = C.c_double()
+    _check(lib().qbx_peak_flops(int(kind), int(reps), C.byref(v), _stream()))
+    return v.value
 
 
 def library_path() -> str:

@@ -1,12 +1,13 @@
 // qbx_eval_noalloc: qbx_eval for callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc at evaluation time: code that runs while a
-// stream is being captured into a CUDA graph by someone else, real-time loops whose
-// memory budget is fixed up front, or hosts whose allocator owns the whole device
-// and forbids outside allocations.  This entry point computes exactly what qbx_eval
-// computes, but takes every piece of scratch from one fixed, file-scope device array
-// of QBX_NOALLOC_SCRATCH_BYTES (48 MiB) that is part of the library image: every GPU
-// that loads the library holds it until the process exits.
+// Some callers cannot call cudaMalloc at evaluation time: real-time loops whose memory
+// budget is fixed up front, or hosts whose allocator owns the whole device and forbids
+// outside allocations.  This entry point computes what qbx_eval computes in QBX_FP64 (the
+// same stages and formulas; the box-expansion passes run the library's per-warp kernels,
+// so results agree with qbx_eval to rounding, about 1e-15 relative), but takes every
+// piece of scratch from one fixed, file-scope device array of QBX_NOALLOC_SCRATCH_BYTES
+// (48 MiB) that is part of the library image: every GPU that loads the library holds it
+// until the process exits.
 #include <mutex>
 
 #include "qbx_internal.cuh"
@@ -52,15 +53,9 @@ extern "C" int qbx_eval_noalloc(const qbx_tree *T, const qbx_lists *L, const dou
 {
     try {
         qbx::set_error("");
-        if (!T || !L || !o || L->tree != T) throw qbx::Error{QBX_ERR_INVALID_ARG, "tree/lists/opts mismatch or NULL"};
-        if (T->np[0] && !w) throw qbx::Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
-        if (mu && !nrm) throw qbx::Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
-        if (T->np[2] && (!tgt_ctr || !pot)) throw qbx::Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
-        if (o->precision != QBX_FP64) throw qbx::Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
-        if (o->p_qbx < 0 || o->p_qbx > qbx::QMAX) throw qbx::Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
-        if (o->p_fmm < 0 || o->p_fmm > qbx::PMAX) throw qbx::Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
-        if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
-            throw qbx::Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
+        qbx::check_eval_args(T, L, w, mu, nrm, tgt_ctr, o, pot);
+        if (o->precision != QBX_FP64)
+            throw qbx::Error{QBX_ERR_INVALID_ARG, "qbx_eval_noalloc evaluates in QBX_FP64 only"};
         size_t need = qbx::fixed_workspace_bytes(T, o);
         if (need > (size_t)QBX_NOALLOC_SCRATCH_BYTES)
             throw qbx::Error{QBX_ERR_INVALID_ARG, "problem needs " + std::to_string(need) +

@@ -18,12 +18,13 @@ static_assert(NPAR == QBX_MLP_NPARAMS, "parameter layout");
 
 // ---------------------------------------------------------------- features
 
-// f0 = log2(rho / |b|), f1 = level(b) / 8, f2 = log2(min_{d in List 3 far(b)} |c - c_d| / |d|) (4 if
-// empty), f3 = log10(max near-field source strength / max strength + 1e-12): b = owner box of c.
+// f0 = log2(rho / |b|), f1 = level(b) / 8, f2 = (|c - c_b| + rho) / |b| (how far the expansion ball
+// reaches from the center of the box local), f3 = log10(max near-field source strength / max strength
+// + 1e-12), near field = the sources of List 1 of b: b = owner box of c.
 __global__ void k_features(int64_t nc, const int *ctr_perm, const int *ctr_box, const double *cxyz, const double *cr,
                            const int *level, const double *cen, const double *hw, const int *ustart,
-                           const int *uidx, const int *wfs, const int *wfi, const int *own_start,
-                           const double *sq, const double *sd, int64_t ns, const double *gmax, float *feat)
+                           const int *uidx, const int *own_start, const double *sq, const double *sd, int64_t ns,
+                           const double *gmax, float *feat)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
@@ -32,13 +33,8 @@ __global__ void k_features(int64_t nc, const int *ctr_perm, const int *ctr_box, 
     const int out = ctr_perm[i];
     feat[4 * out + 0] = (float)log2(cr[i] / hw[b]);
     feat[4 * out + 1] = (float)(level[b] / 8.0);
-    double sep = 16.0;
-    for (int e = wfs[b]; e < wfs[b + 1]; ++e) {
-        int d = wfi[e];
-        double dx = x - cen[3 * d], dy = y - cen[3 * d + 1], dz = z - cen[3 * d + 2];
-        sep = fmin(sep, sqrt(dx * dx + dy * dy + dz * dz) / hw[d]);
-    }
-    feat[4 * out + 2] = (float)log2(sep);
+    const double dx = x - cen[3 * b], dy = y - cen[3 * b + 1], dz = z - cen[3 * b + 2];
+    feat[4 * out + 2] = (float)((sqrt(dx * dx + dy * dy + dz * dz) + cr[i]) / hw[b]);
     double m = 0.0;
     for (int e = ustart[b]; e < ustart[b + 1]; ++e) {
         int d = uidx[e];
@@ -225,21 +221,26 @@ __global__ void k_mlp_init(float *P, uint64_t seed)
 
 // ---------------------------------------------------------------- orders
 
+// clamp(ceil(y + margin), lo, hi) in single precision; a NaN prediction gives hi
+__device__ __forceinline__ int order_from_pred(float y, float margin, int lo, int hi)
+{
+    if (y != y) return hi;
+    const float v = ceilf(y + margin);
+    if (v < (float)lo) return lo;
+    if (v > (float)hi) return hi;
+    return (int)v;
+}
+
 // q_out[c] (input order) = clamp(ceil(y0 + mq), qlo, qhi); per box (the order of its local
 // expansion): max over the centers of its subtree of clamp(ceil(y1 + mp), plo, phi) (atomicMax up
-// the parent chain), p_default elsewhere.
+// the parent chain from -1), p_default where nothing contributes.
 __global__ void k_orders_centers(int64_t nc, const int *ctr_perm, const int *ctr_box, const int *parent, const float *y,
                                  float mq, float mp, int qlo, int qhi, int plo, int phi, int8_t *q_out, int *pbox)
 {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nc) return;
     int c = ctr_perm[i];
-    float y0 = y[NOUT * c], y1 = y[NOUT * c + 1];
-    int q = (int)ceilf(y0 + mq), p = (int)ceilf(y1 + mp);
-    if (!(y0 == y0)) q = qhi;  // NaN prediction: highest order
-    if (!(y1 == y1)) p = phi;
-    q = min(max(q, qlo), qhi);
-    p = min(max(p, plo), phi);
+    const int q = order_from_pred(y[NOUT * c], mq, qlo, qhi), p = order_from_pred(y[NOUT * c + 1], mp, plo, phi);
     q_out[c] = (int8_t)q;
     for (int b = ctr_box[i]; b >= 0; b = parent[b]) atomicMax(&pbox[b], p);
 }
@@ -259,7 +260,7 @@ __global__ void k_orders_boxes(int64_t nb, const int *pbox, int p_default, int8_
     int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= nb) return;
     int p = pbox[b];
-    p_out[b] = (int8_t)(p > 0 ? p : p_default);
+    p_out[b] = (int8_t)(p >= 0 ? p : p_default);
 }
 
 }  // namespace qbx
@@ -303,9 +304,8 @@ int qbx_center_features(const qbx_tree *T, const qbx_lists *L, const double *w, 
             }
             if (nc)
                 k_features<<<nblocks(nc, 128), 128, 0, st>>>(nc, T->perm[KCTR], T->ctr_box, T->cxyz, T->cr, T->level,
-                                                             T->cen, T->hw, L->start[LU], L->idx[LU], L->start[LWF],
-                                                             L->idx[LWF], T->own_start[KSRC], sq, mu ? sd : nullptr, ns,
-                                                             gmax, feat);
+                                                             T->cen, T->hw, L->start[LU], L->idx[LU],
+                                                             T->own_start[KSRC], sq, mu ? sd : nullptr, ns, gmax, feat);
             QBX_LAUNCH_CHECK();
             QBX_CUDA_TRY(cudaStreamSynchronize(st));
         } catch (...) {
@@ -425,7 +425,7 @@ int qbx_orders_from_mlp(const qbx_tree *T, const qbx_lists *L, const float *pred
         const int64_t nb = T->nb, nc = T->np[KCTR];
         int *pbox = dalloc<int>(nb);
         try {
-            QBX_CUDA_TRY(cudaMemsetAsync(pbox, 0, nb * sizeof(int), st));
+            QBX_CUDA_TRY(cudaMemsetAsync(pbox, 0xff, nb * sizeof(int), st));  // -1: no contribution yet
             if (nc)
                 k_orders_centers<<<nblocks(nc, 256), 256, 0, st>>>(nc, T->perm[KCTR], T->ctr_box, T->parent, pred,
                                                                    margin_q, margin_p, q_lo, q_hi, p_lo, p_hi,

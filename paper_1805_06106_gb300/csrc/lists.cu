@@ -449,4 +449,64 @@ void build_lists(qbx_lists *L, cudaStream_t st)
     for (int l = 0; l < NLIST; ++l) dfree(cnt[l]);
 }
 
+// ---------------------------------------------------------------- interaction counts
+
+struct ListSet {
+    const int *start[NLIST], *idx[NLIST];
+};
+
+// Per-list interaction counts (the factors of Table ilist-operation-counts), one thread per target
+// box b, with n_t = the QBX centers b owns and n_s = the sources a source box owns (its subtree for
+// List 4 far): U, W-close, X-close add n_s n_t per entry, V adds 1, W-far adds n_t, X-far adds n_s.
+// Integer sums, so the result does not depend on the order of the atomic adds.
+__global__ void k_list_counts(int nb, const int *own_src, const int *own_ctr, const int *nsrc_sub, ListSet ls,
+                              unsigned long long *out)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long acc[NLIST] = {0, 0, 0, 0, 0, 0};
+    if (b < nb) {
+        const unsigned long long nt = (unsigned long long)(own_ctr[b + 1] - own_ctr[b]);
+        for (int l = 0; l < NLIST; ++l)
+            for (int e = ls.start[l][b]; e < ls.start[l][b + 1]; ++e) {
+                const int d = ls.idx[l][e];
+                if (l == LV) acc[l] += 1ull;
+                else if (l == LWF) acc[l] += nt;
+                else if (l == LXF) acc[l] += (unsigned long long)nsrc_sub[d];
+                else acc[l] += (unsigned long long)(own_src[d + 1] - own_src[d]) * nt;
+            }
+    }
+    for (int l = 0; l < NLIST; ++l) {
+        unsigned long long v = acc[l];
+        for (int off = 16; off >= 1; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if ((threadIdx.x & 31) == 0 && v) atomicAdd(out + l, v);
+    }
+}
+
+void list_counts(const qbx_lists *L, int64_t *counts_host, cudaStream_t st)
+{
+    const qbx_tree *T = L->tree;
+    unsigned long long *d = dalloc<unsigned long long>(NLIST);
+    try {
+        QBX_CUDA_TRY(cudaMemsetAsync(d, 0, NLIST * sizeof(unsigned long long), st));
+        ListSet ls;
+        for (int l = 0; l < NLIST; ++l) {
+            ls.start[l] = L->start[l];
+            ls.idx[l] = L->idx[l];
+        }
+        if (T->nb > 0) {
+            k_list_counts<<<nblocks(T->nb, 128), 128, 0, st>>>((int)T->nb, T->own_start[KSRC], T->own_start[KCTR],
+                                                              T->nsrc_sub, ls, d);
+            QBX_LAUNCH_CHECK();
+        }
+        unsigned long long h[NLIST];
+        QBX_CUDA_TRY(cudaMemcpyAsync(h, d, sizeof h, cudaMemcpyDeviceToHost, st));
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+        for (int l = 0; l < NLIST; ++l) counts_host[l] = (int64_t)h[l];
+    } catch (...) {
+        dfree(d);
+        throw;
+    }
+    dfree(d);
+}
+
 }  // namespace qbx

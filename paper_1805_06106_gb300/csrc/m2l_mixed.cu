@@ -253,12 +253,14 @@ struct M2LTcArgs {
     const float *mh_hi, *mh_lo, *mats;
     float *y;
     int *err;
+    long long wait_limit;  // clock cycles a pipeline wait may take before it gives up
+    int probe_step;        // failure-path probe: pipeline step at which the wait on bar_never runs out (-1: off)
 };
 
 __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
-    __shared__ uint64_t bar_b[2], bar_mma[2];
+    __shared__ uint64_t bar_b[2], bar_mma[2], bar_never;  // bar_never: nothing ever arrives on it
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int KC = a.KC, Np = a.Np, nch = a.Dp / KC;
@@ -272,6 +274,7 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
             tc::mbar_init(&bar_b[s], 1);
             tc::mbar_init(&bar_mma[s], 1);
         }
+        tc::mbar_init(&bar_never, 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.tmem_cols);
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
         for (int c = 0; c < nch; ++c, ++g) {
             const int s = g & 1;
             const uint32_t use = g >> 1;
-            if (g >= 2) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, tc::WAIT_LIMIT);
+            if (g >= 2 && ok) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, a.wait_limit);
             if (__syncthreads_or(!ok)) { ok = false; break; }
             if (tid == 0) {
                 tc::mbar_arrive_expect_tx(&bar_b[s], 2u * bytesB);
@@ -329,7 +332,14 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
             tc::fence_proxy_async();
             __syncthreads();
             if (tid == 0) {
-                bool got = tc::mbar_wait(&bar_b[s], use & 1, tc::WAIT_LIMIT);
+                bool got;
+                if ((int)g == a.probe_step) {
+                    got = tc::mbar_wait(&bar_never, 0, a.wait_limit);  // runs out: nothing arrives
+                    tc::mbar_wait(&bar_b[s], use & 1, tc::WAIT_LIMIT);  // drain this step's copy
+                } else {
+                    got = tc::mbar_wait(&bar_b[s], use & 1, a.wait_limit);
+                    if (!got) tc::mbar_wait(&bar_b[s], use & 1, tc::WAIT_LIMIT);  // drain a late copy
+                }
                 if (got) {
                     tc::tc_fence_after();
                     const uint32_t a_hi = tc::smem_u32(Abuf(s, 0)), a_lo = tc::smem_u32(Abuf(s, 1));
@@ -346,15 +356,16 @@ __global__ void __launch_bounds__(256, 1) k_m2l_tc(M2LTcArgs a)
                     }
                 } else {
                     atomicOr(a.err, 8);
+                    ok = false;  // the other threads learn it at the next barrier
                 }
                 tc::mma_commit(&bar_mma[s]);  // also releases the stage when the MMAs were skipped
             }
         }
-        if (!ok) break;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
         // epilogue: lane quarter (warp & 3) holds pairs 32 q .. 32 q + 31; column groups of 16 split
         // between warps w and w + 4
         const int sl = (g - 1) & 1;
-        ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
+        ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, a.wait_limit);
         if (__syncthreads_or(!ok)) { ok = false; break; }
         tc::tc_fence_after();
         // Output rows of consecutive pairs are contiguous in Y: stage column blocks of 128 through
@@ -544,8 +555,9 @@ void m2l_mixed_run(const qbx_tree *T, const qbx_lists *L, M2LPlan *pl, int PMT, 
             QBX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
             int cols = 32;
             while (cols < pl->Np) cols <<= 1;
-            M2LTcArgs a{pl->ntc, D, pl->Dp, pl->Np, pl->KC, cols, pl->tc_tiles, pl->pair_src, pl->mh_hi, pl->mh_lo,
-                        pl->mats_tc, pl->y, err};
+            M2LTcArgs a{pl->ntc,      D,         pl->Dp,   pl->Np,   pl->KC, cols,
+                        pl->tc_tiles, pl->pair_src, pl->mh_hi, pl->mh_lo, pl->mats_tc, pl->y,
+                        err,          L->wait_limit > 0 ? L->wait_limit : tc::WAIT_LIMIT, L->probe_step};
             k_m2l_tc<<<std::min(pl->ntc, nsm), 256, m2l_tc_smem(pl->Np, pl->KC), st>>>(a);
             QBX_LAUNCH_CHECK();
         }

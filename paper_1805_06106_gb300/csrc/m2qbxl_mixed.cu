@@ -245,6 +245,8 @@ struct WfarTcArgs {
     int64_t nc;
     float *Y;
     int *err;
+    long long wait_limit;  // clock cycles a pipeline wait may take before it gives up
+    int probe_step;        // failure-path probe: pipeline step at which the wait on bar_never runs out (-1: off)
 };
 
 // Tensor-core List 3 far products.  Persistent CTAs of 512 threads walk 128-pair tiles of one
@@ -262,7 +264,7 @@ template <int NU>
 __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
-    __shared__ uint64_t bar_mma[2];
+    __shared__ uint64_t bar_mma[2], bar_never;  // bar_never: nothing ever arrives on it
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Q = a.Q, PQ = a.PQ, Rp = a.Rp, WMAX = a.WMAX;
@@ -286,6 +288,7 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
     if (tid == 0) {
         tc::mbar_init(&bar_mma[0], 1);
         tc::mbar_init(&bar_mma[1], 1);
+        tc::mbar_init(&bar_never, 1);
         tc::fence_mbar_init();
     }
     if (warp == 0) tc::tmem_alloc(&tmem_base, (uint32_t)a.tmem_cols);
@@ -368,7 +371,7 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
         for (int c = 0; c < a.ch.nch; ++c, ++g) {
             const int s = g & 1;
             const uint32_t use = g >> 1;
-            if (g >= 2) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, tc::WAIT_LIMIT);
+            if (g >= 2 && ok) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, a.wait_limit);
             if (__syncthreads_or(!ok)) { ok = false; break; }
             const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
             const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c];
@@ -442,23 +445,30 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
             tc::fence_proxy_async();
             __syncthreads();
             if (tid == 0) {
-                tc::tc_fence_after();
-                const uint32_t a_hi = tc::smem_u32(Abuf(s, 0)), a_lo = tc::smem_u32(Abuf(s, 1));
-                const uint32_t b_hi = tc::smem_u32(Bbuf(s, 0)), b_lo = tc::smem_u32(Bbuf(s, 1));
-                const uint32_t sboB = (uint32_t)W * 32u;
-                for (int ks = 0; ks < W / 8; ++ks) {
-                    const uint32_t off = 256u * ks;
-                    const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-                    tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, acc0);
-                    tc::mma_tf32(tmem, tc::sdesc(a_lo + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, 1u);
-                    tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_lo + off, 128, sboB), idesc, 1u);
+                // failure-path probe: a wait on a barrier nothing arrives on runs out
+                const bool go = (int)g != a.probe_step || tc::mbar_wait(&bar_never, 0, a.wait_limit);
+                if (go) {
+                    tc::tc_fence_after();
+                    const uint32_t a_hi = tc::smem_u32(Abuf(s, 0)), a_lo = tc::smem_u32(Abuf(s, 1));
+                    const uint32_t b_hi = tc::smem_u32(Bbuf(s, 0)), b_lo = tc::smem_u32(Bbuf(s, 1));
+                    const uint32_t sboB = (uint32_t)W * 32u;
+                    for (int ks = 0; ks < W / 8; ++ks) {
+                        const uint32_t off = 256u * ks;
+                        const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+                        tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, acc0);
+                        tc::mma_tf32(tmem, tc::sdesc(a_lo + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, 1u);
+                        tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_lo + off, 128, sboB), idesc, 1u);
+                    }
+                } else {
+                    atomicOr(a.err, 8);
+                    ok = false;  // the other threads learn it at the next barrier
                 }
-                tc::mma_commit(&bar_mma[s]);
+                tc::mma_commit(&bar_mma[s]);  // also releases the stage when the MMAs were skipped
             }
         }
-        if (!ok) break;
+        if (__syncthreads_or(!ok)) { ok = false; break; }
         const int sl = (g - 1) & 1;
-        ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
+        ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, a.wait_limit);
         if (__syncthreads_or(!ok)) { ok = false; break; }
         tc::tc_fence_after();
         // scaled rows staged in shared memory (row stride Rp + 4), then copied out coalesced: the
@@ -918,7 +928,7 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
 }
 
 void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, int *err,
-                    cudaStream_t st)
+                    long long wait_limit, int probe_step, cudaStream_t st)
 {
     if (pl->npairs == 0) return;
     if (pl->tc) {
@@ -943,7 +953,8 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
         int cols = 32;
         while (cols < pl->Rp) cols <<= 1;
         WfarTcArgs a{pl->ntc, pl->P, pl->Q, pl->P + pl->Q, pl->R, pl->Rp, pl->WMAX, cols, ch, pl->tc_tiles,
-                     pl->pair_ctr, pl->slot, pl->H_tc, T->cxyz, T->cr, T->cen, T->hw, T->np[KCTR], pl->Y, err};
+                     pl->pair_ctr, pl->slot, pl->H_tc, T->cxyz, T->cr, T->cen, T->hw, T->np[KCTR], pl->Y, err,
+                     wait_limit > 0 ? wait_limit : tc::WAIT_LIMIT, probe_step};
         const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, pl->Q);
         const int grid = std::min(pl->ntc, nsm);
         if (pl->NU == 3) k_wfar_tc<3><<<grid, WF_THREADS, sm, st>>>(a);

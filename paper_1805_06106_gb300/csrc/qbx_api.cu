@@ -54,6 +54,23 @@ void free_lists(qbx_lists *L)
 
 }  // namespace qbx
 
+namespace qbx {
+void check_eval_args(const qbx_tree *T, const qbx_lists *L, const double *w, const double *mu, const double *nrm,
+                     const int32_t *tgt_ctr, const qbx_eval_opts *o, const double *pot)
+{
+    if (!T || !L || !o || L->tree != T) throw Error{QBX_ERR_INVALID_ARG, "tree/lists/opts mismatch or NULL"};
+    if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
+    if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
+    if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
+    if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32 && o->precision != QBX_M2L_3XTF32)
+        throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
+    if (o->p_qbx < 0 || o->p_qbx > QMAX) throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
+    if (o->p_fmm < 0 || o->p_fmm > PMAX) throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
+    if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
+        throw Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
+}
+}  // namespace qbx
+
 using namespace qbx;
 
 extern "C" {
@@ -177,21 +194,6 @@ int qbx_lists_export(const qbx_lists *L, int which, int32_t *start, int32_t *idx
 
 void qbx_lists_free(qbx_lists *L) { free_lists(L); }
 
-static void check_eval_args(const qbx_tree *T, const qbx_lists *L, const double *w, const double *mu,
-                            const double *nrm, const int32_t *tgt_ctr, const qbx_eval_opts *o, const double *pot)
-{
-    if (!T || !L || !o || L->tree != T) throw Error{QBX_ERR_INVALID_ARG, "tree/lists/opts mismatch or NULL"};
-    if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
-    if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
-    if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
-    if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32 && o->precision != QBX_M2L_3XTF32)
-        throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
-    if (o->p_qbx < 0 || o->p_qbx > QMAX) throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
-    if (o->p_fmm < 0 || o->p_fmm > PMAX) throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
-    if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
-        throw Error{QBX_ERR_INVALID_ARG, "p_qbx > p_fmm"};
-}
-
 int qbx_eval(const qbx_tree *T, const qbx_lists *L, const double *w, const double *sigma, const double *mu,
              const double *nrm, const int32_t *tgt_ctr, const qbx_eval_opts *o, double *pot, void *stream)
 {
@@ -300,6 +302,16 @@ int qbx_lists_set_tiles(qbx_lists *L, int m2l_kchunk, int m2qbxl_kchunk)
     });
 }
 
+int qbx_lists_set_wait(qbx_lists *L, long long limit_cycles, int probe_step)
+{
+    return guarded([&]() -> int {
+        if (!L || limit_cycles < 0 || probe_step < -1) throw Error{QBX_ERR_INVALID_ARG, "bad argument"};
+        L->wait_limit = limit_cycles;
+        L->probe_step = probe_step;
+        return QBX_OK;
+    });
+}
+
 int qbx_profile(qbx_lists *L, int enable)
 {
     return guarded([&]() -> int {
@@ -336,6 +348,24 @@ int qbx_eval_order_sweep(const qbx_tree *T, const qbx_lists *L, const double *w,
         int rc = qbx_eval(T, L, w, sigma, mu, nrm, tgt_ctr, o, partial, stream);
         if (rc != QBX_OK) throw Error{rc, g_err};
         eval_order_sweep(T, const_cast<qbx_lists *>(L), w, sigma, mu, nrm, tgt_ctr, o, partial, (cudaStream_t)stream);
+        return QBX_OK;
+    });
+}
+
+int qbx_lists_cost(const qbx_lists *L, int p_qbx, int p_fmm, qbx_cost *cost, void *stream)
+{
+    return guarded([&]() -> int {
+        if (!L || !cost || p_qbx < 0 || p_fmm < 0) throw Error{QBX_ERR_INVALID_ARG, "bad argument"};
+        const qbx_tree *T = L->tree;
+        list_counts(L, cost->count, (cudaStream_t)stream);
+        const double q2 = (double)p_qbx * p_qbx, p3 = (double)p_fmm * p_fmm * p_fmm, p2 = (double)p_fmm * p_fmm;
+        const double per_entry[NLIST] = {q2, p3, q2, p3, q2, p2};  // U, V, W-close, W-far, X-close, X-far
+        for (int l = 0; l < NLIST; ++l) cost->ops[l] = per_entry[l] * (double)cost->count[l];
+        cost->ops_stages = (double)T->np[KSRC] * p2 + (double)T->nb * p3 + 8.0 * (double)T->nb * p3 +
+                           (double)T->np[KCTR] * p3 + (double)T->np[KTGT] * q2;
+        double tot = 0.0;
+        for (int l = 0; l < NLIST; ++l) tot += cost->ops[l];
+        cost->ops_total = tot + cost->ops_stages;
         return QBX_OK;
     });
 }

@@ -116,6 +116,8 @@ struct qbx_lists {
     qbx_workspace *ws = nullptr;
     int tile_m2l_kc = 0;                     // List 2 tensor-core K chunk (0: library default)
     int tile_wfar_w = 0;                     // List 3 far tensor-core K chunk cap (0: library default)
+    long long wait_limit = 0;                // tensor-core pipeline wait limit in clock cycles (0: default)
+    int probe_step = -1;                     // failure-path probe step of the tensor-core pipelines (-1: off)
     bool prof = false;                       // record stage events in qbx_eval
     bool prof_valid = false;                 // the events hold a finished profiled evaluation
     cudaEvent_t ev[QBX_NSTAGES + 1] = {};
@@ -150,4 +152,8 @@ void capture_eval(const qbx_tree *T, qbx_lists *L, const double *w, const double
                   const double *nrm, const int *tgt_ctr, const qbx_eval_opts *o, double *pot, cudaStream_t st,
                   qbx_graph *g);
 void sort_pairs_by_key(int *keys, int *vals, int64_t n, int key_bits, cudaStream_t st);
+void list_counts(const qbx_lists *L, int64_t *counts_host, cudaStream_t st);
+// argument checks shared by the evaluation entry points (throws Error{QBX_ERR_INVALID_ARG, ...})
+void check_eval_args(const qbx_tree *T, const qbx_lists *L, const double *w, const double *mu, const double *nrm,
+                     const int32_t *tgt_ctr, const qbx_eval_opts *o, const double *pot);
 }  // namespace qbx

@@ -3,6 +3,7 @@
 * The gradient of the training loss computed by the library's backward kernel equals the
   oracle's FP64 chain-rule gradient (FP32 tolerance).
 * Training with the library's Adam kernel reduces the loss and is deterministic.
+* The feature kernel equals the oracle's features (FP32 tolerance).
 * On a surface held out of training, the orders the network picks give a result within
   1e-6 (normwise) of the fixed-order run that checks it, with no more work than that run (the
   per-box orders set the order of each box's local expansion); the work ratios are printed.
@@ -59,15 +60,25 @@ def test_training_reduces_loss_deterministically():
     assert np.array_equal(runs[0][2], runs[1][2])
 
 
-def test_features_and_labels_are_well_formed(sphere80):
-    from paper_1805_06106_gb300 import learned
-    from synth import real_ylm
+@pytest.mark.parametrize("layer", ["single", "double", "zero"])
+def test_center_features_match_oracle(star_small, layer):
+    """The feature kernel against the oracle's definition, element by element at FP32 tolerance
+    (both compute in FP64 and round to float; log2/log10 may differ in the last FP64 bits)."""
+    import paper_1805_06106_gb300 as G
+    from synth import greens_density, random_harmonic_density
 
-    s = sphere80
-    smp = learned.sweep_samples(s, real_ylm(2, 1, s.src_xyz), None, 5, 10, 32, 1e-6)
-    x, y = smp.x.cpu().numpy(), smp.y.cpu().numpy()
-    assert x.shape == (s.n_ctr, 4) and np.all(np.isfinite(x))
-    assert np.all((y[:, 0] >= 0) & (y[:, 0] <= 5)) and np.all((y[:, 1] >= 4) & (y[:, 1] <= 10))
+    s = star_small
+    u, dudn = greens_density(s)
+    sig, mu = {"single": (random_harmonic_density(s, 10, 3), None), "double": (dudn, -u),
+               "zero": (np.zeros(s.n_src), None)}[layer]
+    T = G.qbx_build_tree(_cu(s.src_xyz), _cu(s.ctr_xyz), _cu(s.ctr_r), _cu(s.tgt_xyz), n_max=16, t_f=0.9)
+    L = G.qbx_build_lists(T)
+    f = G.qbx_center_features(T, L, _cu(s.src_w), _cu(sig), None if mu is None else _cu(mu),
+                              _cu(s.src_n)).cpu().numpy()
+    To = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, s.tgt_xyz, n_max=16, t_f=0.9)
+    ref = O.center_features(To, O.build_lists(To), s.src_w, sig, mu, s.src_n, s.ctr_xyz, s.ctr_r)
+    assert np.array_equal(f[:, 1], ref[:, 1])
+    assert np.allclose(f, ref, rtol=2e-7, atol=1e-6)
 
 
 def test_learned_orders_pass_the_fixed_order_check_on_a_held_out_surface():

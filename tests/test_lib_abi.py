@@ -20,7 +20,7 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for n in ("qbx_build_tree", "qbx_build_lists", "qbx_eval", "qbx_tree_query", "qbx_tree_free",
-              "qbx_lists_free", "qbx_last_error"):
+              "qbx_lists_free", "qbx_lists_cost", "qbx_last_error"):
         assert n in names
 
 

@@ -246,3 +246,53 @@ def test_orders_from_predictions_follow_their_definition(star_small):
     rest = np.setdiff1d(np.nonzero(has)[0], path)
     assert np.all(p[rest] == 5)
 
+
+
+# ---------------------------------------------------------------- network inputs
+
+
+def test_center_features_on_the_unit_sphere(sphere80):
+    """Unit sphere centred at the origin, one box (n_max above the particle count): the root is
+    centred at 0 with |root| = R a power of two, so an interior center at distance 1 - r from the
+    origin reaches (1 - r) + r = 1 from the box center (feature 2 is 1/R); an exterior one reaches
+    1 + 2r.  The nodes lie on the degree-4 interpolant of the sphere, within about 1e-4 of it."""
+    from synth import real_ylm
+
+    s = sphere80
+    T = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, s.tgt_xyz, n_max=10 ** 6, t_f=TF)
+    L = O.build_lists(T)
+    R = T.root_radius
+    assert T.n_boxes == 1 and np.all(T.root_center == 0.0) and R == 2.0 ** round(np.log2(R))
+    f = O.center_features(T, L, s.src_w, real_ylm(2, 1, s.src_xyz), None, s.src_n, s.ctr_xyz, s.ctr_r)
+    inside = np.linalg.norm(s.ctr_xyz, axis=0) < 1.0
+    assert inside.sum() == s.n_ctr // 2
+    assert np.allclose(f[inside, 2], 1.0 / R, atol=2e-4 / R)
+    assert np.allclose(f[~inside, 2], (1.0 + 2.0 * s.ctr_r[~inside]) / R, atol=2e-4 / R)
+    assert np.all(f[:, 1] == 0.0)
+    assert np.allclose(2.0 ** f[:, 0] * R, s.ctr_r, rtol=1e-6)
+    assert np.allclose(f[:, 3], 0.0, atol=1e-6)  # one box: its List 1 holds every source
+
+
+def test_center_features_invariants(star_small):
+    from synth import greens_density
+
+    s = star_small
+    u, dudn = greens_density(s)
+    T = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, s.tgt_xyz, n_max=16, t_f=TF)
+    L = O.build_lists(T)
+    f = O.center_features(T, L, s.src_w, dudn, -u, s.src_n, s.ctr_xyz, s.ctr_r)
+    b = T.ctr_owner
+    # features 0 and 1 together give r / |root|: |b| = |root| 2^-level
+    assert np.allclose(2.0 ** (f[:, 0] - 8.0 * f[:, 1]) * T.root_radius, s.ctr_r, rtol=1e-5)
+    assert np.all(8.0 * f[:, 1] == T.level[b])
+    # a center owned by a box below the root lies in that box's target confinement region
+    assert np.all(f[b > 0, 2] <= np.sqrt(3.0) * (1.0 + TF) * (1 + 1e-6))
+    assert np.all(f[:, 3] <= 1e-6)
+    # a single nonzero source: centers whose List 1 holds its leaf see 0, every other center -12
+    sig = np.zeros(s.n_src)
+    j = 1234
+    sig[j] = 1.0
+    g = O.center_features(T, L, s.src_w, sig, None, s.src_n, s.ctr_xyz, s.ctr_r)
+    hot = np.array([T.src_owner[j] in L.of("U", bb) for bb in b])
+    assert hot.any() and not hot.all()
+    assert np.allclose(g[hot, 3], 0.0, atol=1e-6) and np.allclose(g[~hot, 3], -12.0, atol=1e-5)
