@@ -259,6 +259,21 @@ int qbx_orders_from_mlp(const qbx_tree *tree, const qbx_lists *lists, const floa
                         const int32_t *tgt_ctr_dev, float margin_q, float margin_p, int q_lo, int q_hi, int p_lo,
                         int p_hi, int p_default, int8_t *p_qbx_per_ctr_dev, int8_t *p_fmm_per_box_dev, void *stream);
 
+/*
+ * Judge and fallback of learned orders.  `result` is an evaluation with the per-center and per-box
+ * orders below, `judge` the fixed-order evaluation (p_qbx = q_fix, p_fmm = p_fix) of the same
+ * problem, both over all n_tgt targets.  For every target t with |result[t] - judge[t]| > tol
+ * (absolute; NaN counts) the call raises, in place, the QBX order of its center to q_fix and the
+ * local-expansion order of the box owning that center (or the point target) and of every box above
+ * it to p_fix.  Those centers then see the fixed-order box expansions; repeat with a new result until
+ * *n_raised_host is 0.  *n_raised_host receives the number of targets that missed.
+ *   p_qbx_per_ctr_dev [n_ctr], p_fmm_per_box_dev [n_boxes]: the orders, updated in place.
+ * Errors: QBX_ERR_INVALID_ARG, QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_orders_fallback(const qbx_tree *tree, const double *result_dev, const double *judge_dev,
+                        const int32_t *tgt_ctr_dev, double tol, int q_fix, int p_fix, int8_t *p_qbx_per_ctr_dev,
+                        int8_t *p_fmm_per_box_dev, int64_t *n_raised_host, void *stream);
+
 /* ------------------------------------------------------------------------------------------
  * Batched problems and captured evaluations.  Not steps of the paper's method: they run
  * Algorithm 4 on many independent surfaces at once (each evaluation stage is one launch over

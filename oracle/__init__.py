@@ -95,6 +95,7 @@ def lib():
         L.orc_order_labels.argtypes = [P, i, P, i, d, P]
         L.orc_orders_from_pred.argtypes = [P, P, P, C.c_float, C.c_float, i, i, i, i, i, P, P]
         L.orc_center_features.argtypes = [P, P, P, P, P, P, P, P, P]
+        L.orc_orders_fallback.argtypes = [P, P, P, P, d, i, i, P, P]
         _lib = L
     return _lib
 
@@ -321,6 +322,15 @@ def center_features(tree: Tree, lists: Lists, src_w, sigma, mu, src_n, ctr_xyz, 
     out = np.zeros((c.shape[1], 4), np.float32)
     lib().orc_center_features(tree.handle, lists.handle, _p(w), _p(sg), _p(m_), _p(n_), _p(c), _p(r), _p(out))
     return out
+
+
+def orders_fallback(tree: Tree, res, judge, tgt_ctr, tol, q_fix, p_fix, q, pb):
+    """Raise in place the orders of centers and box chains whose targets miss the judge; returns the
+    number of such targets.  q (n_ctr,) and pb (n_boxes,) are int32 arrays."""
+    r, j = _f64(res), _f64(judge)
+    tc = np.ascontiguousarray(tgt_ctr, np.int32)
+    assert q.dtype == np.int32 and pb.dtype == np.int32 and q.flags.c_contiguous and pb.flags.c_contiguous
+    return int(lib().orc_orders_fallback(tree.handle, _p(r), _p(j), _p(tc), float(tol), q_fix, p_fix, _p(q), _p(pb)))
 
 
 def order_labels(values, orders, tol):

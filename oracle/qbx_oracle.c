@@ -1585,3 +1585,28 @@ void orc_center_features(const otree *T, const olists *Ls, const double *w, cons
     }
     free(str);
 }
+
+/*
+ * Judge and fallback of learned orders: every target t with |res[t] - judge[t]| > tol (NaN counts)
+ * raises the QBX order of its center (tgt_ctr[t] >= 0) to q_fix, and the local-expansion order of
+ * the box owning that center (or the point target) and of every box above it to p_fix.  q and pb are
+ * updated in place; returns the number of targets that missed.
+ */
+int orc_orders_fallback(const otree *T, const double *res, const double *judge, const int *tgt_ctr, double tol,
+                        int q_fix, int p_fix, int *q, int *pb)
+{
+    int raised = 0;
+    for (int t = 0; t < T->np[KTGT]; ++t) {
+        if (fabs(res[t] - judge[t]) <= tol) continue;
+        ++raised;
+        int b;
+        if (tgt_ctr[t] >= 0) {
+            q[tgt_ctr[t]] = q_fix;
+            b = T->owner[KCTR][tgt_ctr[t]];
+        } else {
+            b = T->owner[KTGT][t];
+        }
+        for (; b >= 0; b = T->parent[b]) pb[b] = p_fix;
+    }
+    return raised;
+}

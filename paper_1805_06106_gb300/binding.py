@@ -78,6 +78,7 @@ def lib():
         L.qbx_mlp_train.argtypes = [P, P, P, P, P, I64, C.c_int, C.c_int, C.c_float, P, P]
         L.qbx_orders_from_mlp.argtypes = [P, P, P, P, C.c_float, C.c_float, C.c_int, C.c_int, C.c_int, C.c_int,
                                           C.c_int, P, P, P]
+        L.qbx_orders_fallback.argtypes = [P, P, P, P, C.c_double, C.c_int, C.c_int, P, P, C.POINTER(I64), P]
         L.qbx_build_forest.argtypes = [C.c_int, P, P, C.POINTER(P), C.POINTER(P), P]
         L.qbx_forest_problems.argtypes = [P, C.POINTER(C.c_int)]
         L.qbx_forest_offsets.argtypes = [P, P]
@@ -320,6 +321,17 @@ def qbx_orders_from_mlp(tree: Tree, lists: Lists, pred, margin_q, margin_p, q_lo
                                      _ptr(tc), float(margin_q), float(margin_p), q_lo, q_hi, p_lo, p_hi, p_default,
                                      _ptr(qc), _ptr(pb), _stream()))
     return qc, pb
+
+
+def qbx_orders_fallback(tree: Tree, result, judge, tgt_ctr, tol, q_fix, p_fix, p_qbx_per_ctr, p_fmm_per_box):
+    """Raise, in place, the orders of every center / box chain whose target misses the fixed-order
+    judge by more than tol (absolute); returns the number of such targets."""
+    n = C.c_int64()
+    _check(lib().qbx_orders_fallback(tree.handle, _ptr(_dev(result, torch.float64)), _ptr(_dev(judge, torch.float64)),
+                                     _ptr(_dev(tgt_ctr, torch.int32)), float(tol), int(q_fix), int(p_fix),
+                                     _ptr(_dev(p_qbx_per_ctr, torch.int8)), _ptr(_dev(p_fmm_per_box, torch.int8)),
+                                     C.byref(n), _stream()))
+    return n.value
 
 
 def qbx_lists_set_tiles(lists: Lists, m2l_kchunk=0, m2qbxl_kchunk=0):

@@ -263,6 +263,28 @@ __global__ void k_orders_boxes(int64_t nb, const int *pbox, int p_default, int8_
     p_out[b] = (int8_t)(p >= 0 ? p : p_default);
 }
 
+// Judge and fallback: a target whose learned-order result misses the fixed-order judge by more than
+// tol raises its center's QBX order to qfix and the local order of the box owning that center (or the
+// point target) and of every box above it to pfix.  NaN differences count as misses.
+__global__ void k_orders_fallback(int64_t nt, const double *res, const double *judge, const int *tgt_ctr,
+                                  const int *ctr_owner, const int *tgt_owner, const int *parent, double tol, int qfix,
+                                  int pfix, int8_t *q, int8_t *pb, unsigned long long *count)
+{
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    if (fabs(res[t] - judge[t]) <= tol) return;
+    atomicAdd(count, 1ull);
+    const int c = tgt_ctr[t];
+    int b;
+    if (c >= 0) {
+        q[c] = (int8_t)qfix;
+        b = ctr_owner[c];
+    } else {
+        b = tgt_owner[t];
+    }
+    for (; b >= 0; b = parent[b]) pb[b] = (int8_t)pfix;  // same value from every thread
+}
+
 }  // namespace qbx
 
 using namespace qbx;
@@ -441,6 +463,37 @@ int qbx_orders_from_mlp(const qbx_tree *T, const qbx_lists *L, const float *pred
             throw;
         }
         dfree(pbox);
+        return QBX_OK;
+    });
+}
+
+int qbx_orders_fallback(const qbx_tree *T, const double *result, const double *judge, const int32_t *tgt_ctr,
+                        double tol, int q_fix, int p_fix, int8_t *p_qbx_per_ctr, int8_t *p_fmm_per_box,
+                        int64_t *n_raised, void *stream)
+{
+    return learned_guard([&]() -> int {
+        if (!T || !result || !judge || !tgt_ctr || !p_qbx_per_ctr || !p_fmm_per_box || !n_raised || !(tol >= 0.0) ||
+            q_fix < 0 || q_fix > QMAX || p_fix < 0 || p_fix > PMAX)
+            throw Error{QBX_ERR_INVALID_ARG, "bad argument"};
+        cudaStream_t st = (cudaStream_t)stream;
+        const int64_t nt = T->np[KTGT];
+        unsigned long long *cnt = dalloc<unsigned long long>(1);
+        try {
+            QBX_CUDA_TRY(cudaMemsetAsync(cnt, 0, sizeof(unsigned long long), st));
+            if (nt)
+                k_orders_fallback<<<nblocks(nt, 256), 256, 0, st>>>(nt, result, judge, tgt_ctr, T->owner[KCTR],
+                                                                    T->owner[KTGT], T->parent, tol, q_fix, p_fix,
+                                                                    p_qbx_per_ctr, p_fmm_per_box, cnt);
+            QBX_LAUNCH_CHECK();
+            unsigned long long h = 0;
+            QBX_CUDA_TRY(cudaMemcpyAsync(&h, cnt, sizeof h, cudaMemcpyDeviceToHost, st));
+            QBX_CUDA_TRY(cudaStreamSynchronize(st));
+            *n_raised = (int64_t)h;
+        } catch (...) {
+            dfree(cnt);
+            throw;
+        }
+        dfree(cnt);
         return QBX_OK;
     });
 }

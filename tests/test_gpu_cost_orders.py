@@ -83,3 +83,27 @@ def test_orders_from_predictions_match_oracle(star_small):
         q_o, p_o = O.orders_from_pred(To, pred, mq, mp, lo_q, hi_q, lo_p, hi_p, pdef, tgt_ctr=tc if with_pts else None)
         assert np.array_equal(qc.cpu().numpy().astype(np.int32), q_o)
         assert np.array_equal(pb.cpu().numpy().astype(np.int32), p_o)
+
+
+def test_orders_fallback_matches_oracle(star_small):
+    import paper_1805_06106_gb300 as G
+
+    s = star_small
+    rng = np.random.default_rng(9)
+    vol = rng.uniform(-1.5, 1.5, size=(3, 40))
+    t = np.concatenate([s.tgt_xyz, vol], axis=1)
+    tc = np.concatenate([s.tgt_ctr, -np.ones(40, np.int32)]).astype(np.int32)
+    T, L, To, Lo = _pair(s, 16, tgt=t)
+    nt = t.shape[1]
+    judge = rng.normal(size=nt)
+    res = judge + rng.normal(size=nt) * 1e-6
+    res[rng.choice(nt, 20, replace=False)] = np.nan
+    q0 = rng.integers(2, 9, s.n_ctr).astype(np.int8)
+    p0 = rng.integers(4, 17, T.n_boxes).astype(np.int8)
+    qg, pg = _cu(q0), _cu(p0)
+    n = G.qbx_orders_fallback(T, _cu(res), _cu(judge), _cu(tc), 2e-6, 8, 16, qg, pg)
+    qo, po = q0.astype(np.int32), p0.astype(np.int32)
+    no = O.orders_fallback(To, res, judge, tc, 2e-6, 8, 16, qo, po)
+    assert n == no and n > 20
+    assert np.array_equal(qg.cpu().numpy().astype(np.int32), qo)
+    assert np.array_equal(pg.cpu().numpy().astype(np.int32), po)

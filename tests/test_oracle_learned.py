@@ -296,3 +296,37 @@ def test_center_features_invariants(star_small):
     hot = np.array([T.src_owner[j] in L.of("U", bb) for bb in b])
     assert hot.any() and not hot.all()
     assert np.allclose(g[hot, 3], 0.0, atol=1e-6) and np.allclose(g[~hot, 3], -12.0, atol=1e-5)
+
+
+def test_fallback_raises_exactly_the_missing_targets(star_small):
+    s = star_small
+    vol = np.random.default_rng(8).uniform(-1.5, 1.5, size=(3, 30))
+    t = np.concatenate([s.tgt_xyz, vol], axis=1)
+    tc = np.concatenate([s.tgt_ctr, -np.ones(30, np.int32)]).astype(np.int32)
+    T = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, t, n_max=16, t_f=TF)
+    nt = t.shape[1]
+    judge = np.linspace(-1.0, 1.0, nt)
+    res = judge.copy()
+    miss = [5, 77, s.n_ctr + 3]  # two QBX targets and one point target
+    tol = 2.0 ** -20
+    res[miss[0]] += 2 * tol
+    res[miss[1]] = np.nan
+    res[miss[2]] -= 5 * tol
+    judge[9], res[9] = 0.5, 0.5 + tol  # exactly at the threshold: not a miss
+    q = np.full(s.n_ctr, 3, np.int32)
+    pb = np.full(T.n_boxes, 5, np.int32)
+    n = O.orders_fallback(T, res, judge, tc, tol, 8, 16, q, pb)
+    assert n == 3
+    want_q = np.full(s.n_ctr, 3)
+    want_p = np.full(T.n_boxes, 5)
+    for t_ in miss:
+        if tc[t_] >= 0:
+            want_q[tc[t_]] = 8
+            b = T.ctr_owner[tc[t_]]
+        else:
+            b = T.tgt_owner[t_]
+        while b >= 0:
+            want_p[b] = 16
+            b = T.parent[b]
+    assert np.array_equal(q, want_q) and np.array_equal(pb, want_p)
+    assert pb[0] == 16 and np.sum(pb == 16) < T.n_boxes  # the root is on every chain; most boxes are not
