@@ -486,10 +486,12 @@ def run_gpu(args):
         nlev = int(T.info.n_levels)
         # the fixed-order FP64 evaluation on the same tree: the judge of the learned orders, the accuracy
         # reference, and plain FP64 GIGAQBX at the mixed mode's leaf size (timed)
-        G.qbx_eval(T, L, *ev_in, Q, P)  # first evaluation on these lists sets up the workspace
-        judge = torch.empty(t.shape[1], dtype=torch.float64, device=dev)
-        fp64_same = _time_eager(torch, lambda: G.qbx_eval(T, L, *ev_in, Q, P, out=judge), stream, flush,
-                                args.fp64_steps_same, 0)
+        judge, fp64_same = None, []
+        if mode == "learned" or args.fp64_steps_same > 0:
+            G.qbx_eval(T, L, *ev_in, Q, P)  # first evaluation on these lists sets up the workspace
+            judge = torch.empty(t.shape[1], dtype=torch.float64, device=dev)
+            fp64_same = _time_eager(torch, lambda: G.qbx_eval(T, L, *ev_in, Q, P, out=judge), stream, flush,
+                                    max(1, args.fp64_steps_same), 0)
         orders = {}
         if mode == "learned":
             model, info = learned_model(G, n_max, Q, P)
@@ -511,7 +513,7 @@ def run_gpu(args):
         total_ms = max_over_ranks(float(sum(step_ms)))
         ms_per_step = total_ms / args.steps
         value = ws * n_qbx_tgt * args.steps / (total_ms * 1e-3)
-        err_vs_fp64 = float((res - judge).abs().max() / judge.abs().max())
+        err_vs_fp64 = None if judge is None else float((res - judge).abs().max() / judge.abs().max())
         # per-stage times of the same evaluation (one eager, profiled evaluation)
         L.profile(True)
         G.qbx_eval(T, L, *ev_in, Q, P, out=pot, precision=prec, **orders)
@@ -555,7 +557,8 @@ def run_gpu(args):
             L.profile(False)
             fixed_mixed = {"value": n_qbx_tgt / (statistics.mean(fms) * 1e-3), "ms_per_step": statistics.mean(fms),
                            "steps": args.fixed_steps, "stage_ms": st_f,
-                           "rel_err_vs_fp64": float((pot_f - judge).abs().max() / judge.abs().max())}
+                           "rel_err_vs_fp64": None if judge is None else
+                           float((pot_f - judge).abs().max() / judge.abs().max())}
             del g_fixed
         cost = G.qbx_lists_cost(L, Q, P)
         ex = T.export()
@@ -596,10 +599,11 @@ def run_gpu(args):
                               args.fp64_steps, 1)
             b_total = max_over_ranks(float(sum(pms)))
             plain = {"value": ws * n_qbx_tgt * args.fp64_steps / (b_total * 1e-3),
-                     "ms_per_step": b_total / args.fp64_steps, "n_max": N_MAX_FP64, "steps": args.fp64_steps,
-                     "at_mixed_n_max": {"value": n_qbx_tgt / (statistics.mean(fp64_same) * 1e-3),
-                                        "ms_per_step": statistics.mean(fp64_same), "n_max": n_max,
-                                        "steps": len(fp64_same)}}
+                     "ms_per_step": b_total / args.fp64_steps, "n_max": N_MAX_FP64, "steps": args.fp64_steps}
+            if fp64_same:
+                plain["at_mixed_n_max"] = {"value": n_qbx_tgt / (statistics.mean(fp64_same) * 1e-3),
+                                           "ms_per_step": statistics.mean(fp64_same), "n_max": n_max,
+                                           "steps": len(fp64_same)}
             del T2, L2
 
     if rank != 0:
@@ -665,7 +669,8 @@ def run_gpu(args):
     if plain is not None:
         line["plain_fp64"] = plain
         line["speedup_vs_plain_fp64"] = value / plain["value"]
-        line["speedup_vs_plain_fp64_same_n_max"] = value / plain["at_mixed_n_max"]["value"]
+        if "at_mixed_n_max" in plain:
+            line["speedup_vs_plain_fp64_same_n_max"] = value / plain["at_mixed_n_max"]["value"]
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload)
     print(json.dumps(line), flush=True)
@@ -847,7 +852,8 @@ def main():
                          "split-TF32 products; learned: 3xtf32 with per-center / per-box orders from the network")
     ap.add_argument("--fp64-steps", type=int, default=2, help="timed steps of plain FP64 at its own leaf size")
     ap.add_argument("--fp64-steps-same", type=int, default=1,
-                    help="timed steps of plain FP64 at the mixed leaf size (also the judge and accuracy reference)")
+                    help="timed steps of plain FP64 at the mixed leaf size (also the judge and accuracy "
+                         "reference; 0 skips it unless the learned mode needs the judge)")
     ap.add_argument("--fixed-steps", type=int, default=5, help="timed steps of fixed orders in the same precision")
     ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched",), default="star79k",
                     help="star79k (1.19M sources, random density, orders 8/16; default), star8k (120k, Green's "

@@ -18,10 +18,10 @@ extern "C" {
 
 /*
  * Measures the FP64 (kind QBX_PEAK_FP64) or FP32 (QBX_PEAK_FP32) fused multiply-add throughput:
- * every thread of a grid sized to the SM count runs eight independent FMA chains; the best of `reps`
- * timed launches (CUDA events on `stream`, after one warm-up launch) is written to *flops_host in
- * flop/s (an FMA counts as 2).  Allocates 8 bytes of device memory for the duration of the call and
- * synchronizes `stream`.  About 0.1 s (FP64) or 0.05 s (FP32) per launch.
+ * every thread of a grid of 2, 4 and 8 blocks of 256 threads per SM runs eight independent FMA
+ * chains; the best of `reps` timed launches per grid (CUDA events on `stream`, after one warm-up
+ * launch) is written to *flops_host in flop/s (an FMA counts as 2).  Allocates 8 bytes of device
+ * memory for the duration of the call and synchronizes `stream`.  Up to about 0.1 s per launch.
  * Errors: QBX_ERR_INVALID_ARG (bad kind, reps < 1, NULL output), QBX_ERR_OOM, QBX_ERR_CUDA.
  */
 int qbx_peak_flops(int kind, int reps, double *flops_host, void *stream);

@@ -79,9 +79,13 @@ extern "C" int qbx_peak_flops(int kind, int reps, double *flops_host, void *stre
         if (!flops_host || reps < 1 || (kind != QBX_PEAK_FP64 && kind != QBX_PEAK_FP32))
             throw Error{QBX_ERR_INVALID_ARG, "bad argument"};
         cudaStream_t st = (cudaStream_t)stream;
-        // FP64: 2 blocks of 256 threads per SM fill the FP64 pipes; FP32 needs more warps in flight
-        *flops_host = kind == QBX_PEAK_FP64 ? run_peak<double>(2, 1 << 14, reps, st)
-                                            : run_peak<float>(8, 1 << 16, reps, st);
+        // the best over several occupancies (blocks of 256 threads per SM), so that neither too few warps
+        // in flight nor register or issue limits of one shape understate the peak
+        double best = 0.0;
+        for (int bps : {2, 4, 8})
+            best = std::max(best, kind == QBX_PEAK_FP64 ? run_peak<double>(bps, 1 << 14, reps, st)
+                                                        : run_peak<float>(bps, 1 << 16, reps, st));
+        *flops_host = best;
         return QBX_OK;
     } catch (const Error &e) {
         set_error(e.msg);

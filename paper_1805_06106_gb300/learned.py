@@ -98,15 +98,24 @@ def predict_orders(tree, lists, model, src_w, sigma, mu, src_n, tgt_ctr=None, q_
 
 def judge_and_fallback(tree, lists, args, q_fix, p_fix, qc, pb, tol, precision, judge=None, max_rounds=4):
     """Evaluate with the learned orders, compare with the fixed-order FP64 judge and raise the orders
-    where a target misses tol * max|judge|; repeat until no target misses.  args = (src_w, sigma, mu,
-    src_n, tgt_ctr).  Returns (qc, pb, info); qc and pb are updated in place."""
+    where a target misses tol * scale; repeat until no target misses.  scale = max|judge| over the
+    problem, or for a forest the smallest such maximum over its problems (so that every problem meets
+    tol in its own normwise measure).  args = (src_w, sigma, mu, src_n, tgt_ctr).  Returns (qc, pb,
+    info); qc and pb are updated in place; info["err_before"] / ["err_after"] are max|res - judge| /
+    scale before and after."""
     if judge is None:
         judge = B.qbx_eval(tree, lists, *args, q_fix, p_fix)
-    thr = tol * float(judge.abs().max())
+    off = getattr(tree, "offsets", None)
+    if off is not None:
+        t = off["tgt"]
+        scale = min(float(judge[t[i]:t[i + 1]].abs().max()) for i in range(len(t) - 1) if t[i + 1] > t[i])
+    else:
+        scale = float(judge.abs().max())
+    thr = tol * scale
     info = {"rounds": 0, "raised": [], "err_before": None, "err_after": None}
     for r in range(max_rounds + 1):
         res = B.qbx_eval(tree, lists, *args, q_fix, p_fix, p_qbx_per_ctr=qc, p_fmm_per_box=pb, precision=precision)
-        err = float((res - judge).abs().max()) / (thr / tol)
+        err = float((res - judge).abs().max()) / scale
         if r == 0:
             info["err_before"] = err
         info["err_after"] = err

@@ -6,8 +6,9 @@
   p_qbx in {12, 16}.
 * The non-default K-chunk hints of the tensor-core kernels.
 * The combination the learned benchmark runs: per-center and per-box orders from the order network,
-  split-TF32 translations, a forest of surfaces, replayed as a CUDA graph; each surface against the
-  oracle with the same orders (1e-6) and against the fixed-order oracle result (1e-6).
+  checked by the fixed-order judge, split-TF32 translations, a forest of surfaces, replayed as a CUDA
+  graph; each surface against the oracle with the same orders (1e-6) and against the fixed-order
+  oracle result (1e-6).
 The oracle runs its OpenMP build (bitwise equal to the serial one) to keep these cases short.
 """
 import numpy as np
@@ -130,6 +131,10 @@ def test_learned_split_tf32_forest_graph_against_oracle():
     tc = _cu(np.concatenate([s.tgt_ctr + off["ctr"][i] for i, s in enumerate(surfs)]).astype(np.int32), torch.int32)
     qc, pb = learned.predict_orders(F, FL, model, w, sg, None, nrm, tgt_ctr=tc, q_range=(2, q_fix),
                                     p_range=(4, p_fix), p_default=p_fix)
+    # the fixed-order FP64 judge raises the orders of the targets the network's orders miss
+    qc, pb, info = learned.judge_and_fallback(F, FL, (w, sg, None, nrm, tc), q_fix, p_fix, qc, pb, 0.9 * tol,
+                                              G.QBX_M2L_3XTF32)
+    assert info["err_after"] <= 0.9 * tol
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         pot = torch.empty(int(F.info.n_tgt), dtype=torch.float64, device="cuda")
