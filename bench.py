@@ -65,8 +65,11 @@ def _dist_env():
     return ws, rank, local
 
 
-def make_workload(n_sub, name):
-    from synth import greens_density, make_surface, random_harmonic_density, star_radius, volume_targets
+def make_workload(n_sub, name, associate=None):
+    """Surface, densities and targets of a named workload.  Volume points (star8k, star40k) are
+    associated with centers (Algorithm 3, eps_tgt = 0.05, side preference) by `associate(s, points)`
+    -> (tgt_ctr, flagged): the library's GPU call in the benchmark, the oracle in the CPU baseline."""
+    from synth import greens_density, make_surface, random_harmonic_density, star_radius, volume_points
     from synth.surfaces import STAR_Y63, STAR_Y84_Y52
 
     _, shape, dens, _, nvol = WORKLOADS[name]
@@ -77,12 +80,38 @@ def make_workload(n_sub, name):
     else:
         sigma, mu = random_harmonic_density(s, 10, 4), None
     if nvol:
-        vt, vc, vflag = volume_targets(s, nvol, seed=2)
+        vt = volume_points(nvol, seed=2)
+        vc, vflag = associate(s, vt)
         t = np.concatenate([s.tgt_xyz, vt], axis=1)
         tc = np.concatenate([s.tgt_ctr, vc]).astype(np.int32)
     else:
         t, tc, vflag = s.tgt_xyz, s.tgt_ctr.astype(np.int32), np.zeros(0, bool)
     return s, sigma, mu, t, tc, vflag
+
+
+EPS_TGT = 0.05
+
+
+def oracle_associate(s, pts):
+    import oracle as O
+    from synth import danger_radius
+
+    T = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, pts, n_max=N_MAX_MIXED, t_f=T_F)
+    return O.assoc_targets(T, s.src_xyz, danger_radius(s), s.src_n, s.ctr_xyz, s.ctr_r, s.ctr_side, pts, EPS_TGT)
+
+
+def gpu_associate(G, torch, dev):
+    from synth import danger_radius
+
+    def cu(a, dt=torch.float64):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
+
+    def run(s, pts):
+        T = G.qbx_build_tree(cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(pts), n_max=N_MAX_MIXED, t_f=T_F)
+        tc, fl = G.qbx_assoc_targets(T, cu(danger_radius(s)), cu(s.src_n), cu(s.ctr_side, torch.int8), EPS_TGT)
+        return tc.cpu().numpy(), fl.cpu().numpy().astype(bool)
+
+    return run
 
 
 # ------------------------------------------------------------------ algorithmic work model
@@ -325,7 +354,7 @@ def cpu_oracle_sample(n_sub, workload, omp):
     cores (the same code, bitwise the same result) rather than the serial one."""
     import oracle as O
 
-    s, sigma, mu, t, tc, _ = make_workload(n_sub, workload)
+    s, sigma, mu, t, tc, _ = make_workload(n_sub, workload, oracle_associate)
     if workload in ("star8k", "star40k"):  # keep the sample's volume points in proportion
         keep = np.concatenate([np.arange(s.n_ctr), s.n_ctr + np.arange(min(len(tc) - s.n_ctr, s.n_ctr // 24))])
         t, tc = t[:, keep], tc[keep]
@@ -448,7 +477,7 @@ def run_gpu(args):
 
     Q, P = P_QBX, P_FMM
     t_setup = time.perf_counter()
-    s, sigma, mu, t, tc, vflag = make_workload(args.n_sub, args.workload)
+    s, sigma, mu, t, tc, vflag = make_workload(args.n_sub, args.workload, gpu_associate(G, torch, dev))
     synth_s = time.perf_counter() - t_setup
     n_qbx_tgt = int(np.sum(tc >= 0))
     n_pt_tgt = int(np.sum(tc < 0))

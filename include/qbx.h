@@ -120,6 +120,27 @@ int qbx_lists_export(const qbx_lists *lists, int which, int32_t *start_dev, int3
 
 void qbx_lists_free(qbx_lists *lists);
 
+/*
+ * Target association (Section 3.4, Algorithm 3): decides which targets of the tree need QBX and
+ * associates each of them with an expansion center.  A target t is endangered if some source s has
+ * |t - s| <= r_danger(s) (the danger zone eta_k / 2 of the source's element); an endangered target is
+ * associated with the closest center c with |t - c| <= r_c (1 + eps), ties to the lowest center index;
+ * with a side preference (src_n given) only centers on t's preferred side qualify, the side of
+ * (t - s*) . n(s*) for the source s* nearest to t (positive: ctr_side +1, otherwise -1).  Endangered
+ * targets without such a center are flagged.  The search runs from each target's point of view over
+ * the boxes of the tree that meet a cube around it (the sets Algorithm 5's area queries return).
+ *   src_danger_r_dev [n_src] (> 0), src_n_dev (3, n_src) or NULL (no side preference),
+ *   ctr_side_dev [n_ctr] (+1 / -1; required with src_n), eps >= 0;
+ *   tgt_ctr_dev [n_tgt] out: center index or -1; flagged_dev [n_tgt] out: 1 for endangered targets
+ *   left without a center, else 0.  All arrays in input order.  Not for forests.
+ * Every target of the tree is associated: build the tree with the targets to associate (points
+ * with their own centers known beforehand are simply left out).
+ * Errors: QBX_ERR_INVALID_ARG, QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+int qbx_assoc_targets(const qbx_tree *tree, const double *src_danger_r_dev, const double *src_n_dev,
+                      const int8_t *ctr_side_dev, double eps, int32_t *tgt_ctr_dev, int8_t *flagged_dev,
+                      void *stream);
+
 typedef struct {
     /* interaction counts per list (index QBX_LIST_*), n_t = QBX centers owned by the target box,
      * n_s = sources owned by the source box (its whole subtree for List 4 far):

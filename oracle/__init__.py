@@ -96,6 +96,7 @@ def lib():
         L.orc_orders_from_pred.argtypes = [P, P, P, C.c_float, C.c_float, i, i, i, i, i, P, P]
         L.orc_center_features.argtypes = [P, P, P, P, P, P, P, P, P]
         L.orc_orders_fallback.argtypes = [P, P, P, P, d, i, i, P, P]
+        L.orc_assoc_targets.argtypes = [P, P, P, P, P, P, P, P, d, P, P]
         _lib = L
     return _lib
 
@@ -331,6 +332,20 @@ def orders_fallback(tree: Tree, res, judge, tgt_ctr, tol, q_fix, p_fix, q, pb):
     tc = np.ascontiguousarray(tgt_ctr, np.int32)
     assert q.dtype == np.int32 and pb.dtype == np.int32 and q.flags.c_contiguous and pb.flags.c_contiguous
     return int(lib().orc_orders_fallback(tree.handle, _p(r), _p(j), _p(tc), float(tol), q_fix, p_fix, _p(q), _p(pb)))
+
+
+def assoc_targets(tree: Tree, src_xyz, rdanger, src_n, ctr_xyz, ctr_r, ctr_side, tgt_xyz, eps):
+    """Target association (Algorithm 3 with the area queries of Algorithm 5): (tgt_ctr int32 with -1
+    for none, flagged bool) per target of the tree.  src_n / ctr_side None: no side preference."""
+    sx, rd, c, r, t = _f64(src_xyz), _f64(rdanger), _f64(ctr_xyz), _f64(ctr_r), _f64(tgt_xyz)
+    sn = None if src_n is None else _f64(src_n)
+    cs = None if ctr_side is None else np.ascontiguousarray(ctr_side, np.int8)
+    nt = t.shape[1]
+    tc = np.zeros(nt, np.int32)
+    fl = np.zeros(nt, np.int32)
+    lib().orc_assoc_targets(tree.handle, _p(sx), _p(rd), _p(sn), _p(c), _p(r), _p(cs), _p(t), float(eps), _p(tc),
+                            _p(fl))
+    return tc, fl.astype(bool)
 
 
 def order_labels(values, orders, tol):

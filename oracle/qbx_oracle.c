@@ -1610,3 +1610,136 @@ int orc_orders_fallback(const otree *T, const double *res, const double *judge, 
     }
     return raised;
 }
+
+/* ------------------------------------------------------------------------ */
+/* target association (Section 3.4, Algorithm 3) with area queries           */
+/* (Appendix A, Algorithm 5)                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* |x - y|_2 as sqrt(dx^2 + dy^2 + dz^2), summed in that order */
+static double dist3(const double x[3], const double y[3])
+{
+    double dx = x[0] - y[0], dy = x[1] - y[1], dz = x[2] - y[2];
+    return sqrt(dx * dx + dy * dy + dz * dz);
+}
+
+/* a peer box p of b (Algorithm 5): p is b or adjacent to b, and |p| >= |b| */
+static int peer_like(const otree *T, int p, int b, int Lf)
+{
+    return T->level[p] <= T->level[b] && (p == b || adjacent(T, p, b, Lf));
+}
+
+static void leaves_meeting_cube(const otree *T, int p, const double c[3], double r, ivec *out, char *seen)
+{
+    for (int d = 0; d < 3; ++d)
+        if (fabs(c[d] - T->cen[3 * p + d]) > r + T->hw[p]) return;  /* closed cubes do not meet */
+    if (is_leaf(T, p)) {
+        if (!seen[p]) { seen[p] = 1; iv_push(out, p); }
+        return;
+    }
+    for (int o = 0; o < 8; ++o)
+        if (T->child[8 * p + o] >= 0) leaves_meeting_cube(T, T->child[8 * p + o], c, r, out, seen);
+}
+
+/*
+ * Area query (Algorithm 5): the leaf boxes that meet the closed cube of half side r around c.
+ * Guiding box: from the root, descend to the child containing c while |b| >= r (the first box with
+ * |b| < r <= 2|b|), or stop where no child contains c.  Then every leaf descendant of every peer of
+ * the guiding box is tested against the cube.  `seen` (n_boxes bytes, zero) is restored on return.
+ */
+static void area_query(const otree *T, const double c[3], double r, ivec *out, char *seen)
+{
+    int Lf = finest_level(T), b = 0;
+    out->n = 0;
+    for (;;) {
+        double h = T->hw[b];
+        if ((h < r && r <= 2.0 * h) || r > 2.0 * h) break;
+        int ch = T->child[8 * b + octant(c, &T->cen[3 * b])];
+        if (ch < 0) break;
+        b = ch;
+    }
+    for (int p = 0; p < T->nb; ++p) {
+        if (!peer_like(T, p, b, Lf)) continue;
+        int child_peer = 0;
+        for (int o = 0; o < 8 && !child_peer; ++o) {
+            int ch = T->child[8 * p + o];
+            if (ch >= 0 && peer_like(T, ch, b, Lf)) child_peer = 1;
+        }
+        if (!child_peer) leaves_meeting_cube(T, p, c, r, out, seen);
+    }
+    for (int i = 0; i < out->n; ++i) seen[out->v[i]] = 0;
+}
+
+/*
+ * Algorithm 3.  Stage 1: an area query of radius rdanger[s] around every source s marks the targets t
+ * with |t - s| <= rdanger[s] as endangered.  Stage 2: an area query of radius r_c (1 + eps) around every
+ * center c (in index order) associates an endangered target t to c when |t - c| <= r_c (1 + eps), c lies
+ * on t's preferred side, and c is strictly closer than any center before it (ties keep the lower index).
+ * The preferred side of t is +1 if (t - s*) . n(s*) > 0 and -1 otherwise, s* the source nearest to t
+ * (lowest index among equals); with snrm == NULL (no side preference) every center qualifies.  Stage 3:
+ * endangered targets left without a center are flagged.  Outputs in input order: tgt_ctr[t] (center or
+ * -1) and flagged[t] (0/1).  Targets must be the tree's targets, in input order.
+ */
+void orc_assoc_targets(const otree *T, const double *sxyz, const double *rdanger, const double *snrm,
+                       const double *cxyz, const double *cr, const signed char *cside, const double *txyz,
+                       double eps, int *tgt_ctr, int *flagged)
+{
+    int ns = T->np[KSRC], nc = T->np[KCTR], nt = T->np[KTGT];
+    char *seen = calloc(T->nb > 0 ? T->nb : 1, 1);
+    char *endangered = calloc(nt > 0 ? nt : 1, 1);
+    double *best = malloc(sizeof(double) * (nt > 0 ? nt : 1));
+    ivec leaves = {0};
+    double x[3], y[3];
+    for (int t = 0; t < nt; ++t) { tgt_ctr[t] = -1; flagged[t] = 0; best[t] = INFINITY; }
+    /* Stage 1 */
+    for (int s = 0; s < ns; ++s) {
+        get_pt(sxyz, ns, s, x);
+        area_query(T, x, rdanger[s], &leaves, seen);
+        for (int i = 0; i < leaves.n; ++i) {
+            int l = leaves.v[i];
+            for (int k = T->own_start[KTGT][l]; k < T->own_start[KTGT][l + 1]; ++k) {
+                int t = T->own_idx[KTGT][k];
+                get_pt(txyz, nt, t, y);
+                if (dist3(y, x) <= rdanger[s]) endangered[t] = 1;
+            }
+        }
+    }
+    /* preferred sides: nearest source by brute force */
+    signed char *side = calloc(nt > 0 ? nt : 1, 1);
+    if (snrm)
+        for (int t = 0; t < nt; ++t) {
+            if (!endangered[t]) continue;
+            get_pt(txyz, nt, t, y);
+            int sb = -1;
+            double db = INFINITY;
+            for (int s = 0; s < ns; ++s) {
+                get_pt(sxyz, ns, s, x);
+                double dd = dist3(y, x);
+                if (dd < db) { db = dd; sb = s; }
+            }
+            get_pt(sxyz, ns, sb, x);
+            double dot = (y[0] - x[0]) * snrm[sb] + (y[1] - x[1]) * snrm[ns + sb];
+            dot = dot + (y[2] - x[2]) * snrm[2 * ns + sb];
+            side[t] = dot > 0.0 ? 1 : -1;
+        }
+    /* Stage 2 */
+    for (int c = 0; c < nc; ++c) {
+        get_pt(cxyz, nc, c, x);
+        double rr = cr[c] * (1.0 + eps);
+        area_query(T, x, rr, &leaves, seen);
+        for (int i = 0; i < leaves.n; ++i) {
+            int l = leaves.v[i];
+            for (int k = T->own_start[KTGT][l]; k < T->own_start[KTGT][l + 1]; ++k) {
+                int t = T->own_idx[KTGT][k];
+                if (!endangered[t]) continue;
+                if (snrm && cside[c] != side[t]) continue;
+                get_pt(txyz, nt, t, y);
+                double dd = dist3(y, x);
+                if (dd <= rr && dd < best[t]) { best[t] = dd; tgt_ctr[t] = c; }
+            }
+        }
+    }
+    /* Stage 3 */
+    for (int t = 0; t < nt; ++t) flagged[t] = endangered[t] && tgt_ctr[t] < 0;
+    free(seen); free(endangered); free(best); free(side); free(leaves.v);
+}

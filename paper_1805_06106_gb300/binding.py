@@ -66,6 +66,7 @@ def lib():
         L.qbx_lists_export.argtypes = [P, C.c_int, P, P, P]
         L.qbx_lists_free.argtypes = [P]
         L.qbx_lists_free.restype = None
+        L.qbx_assoc_targets.argtypes = [P, P, P, P, C.c_double, P, P, P]
         L.qbx_lists_cost.argtypes = [P, C.c_int, C.c_int, C.POINTER(_Cost), P]
         L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_eval_noalloc.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
@@ -201,6 +202,20 @@ def qbx_build_lists(tree: Tree) -> Lists:
     h = C.c_void_p()
     _check(lib().qbx_build_lists(tree.handle, C.byref(h), _stream()))
     return Lists(h, tree)
+
+
+def qbx_assoc_targets(tree: Tree, src_danger_r, src_n=None, ctr_side=None, eps=0.05):
+    """Target association (Algorithm 3) for every target of the tree: (tgt_ctr int32, -1 = none;
+    flagged int8) on the device, input order.  src_n / ctr_side None: no side preference."""
+    rd = _dev(src_danger_r, torch.float64)
+    n = _dev(src_n, torch.float64)
+    cs = _dev(ctr_side, torch.int8)
+    nt = tree.info.n_tgt
+    tc = torch.empty(nt, dtype=torch.int32, device="cuda")
+    fl = torch.empty(nt, dtype=torch.int8, device="cuda")
+    _check(lib().qbx_assoc_targets(tree.handle, _ptr(rd), _ptr(n), _ptr(cs), float(eps), _ptr(tc), _ptr(fl),
+                                   _stream()))
+    return tc, fl
 
 
 def qbx_lists_cost(lists: Lists, p_qbx, p_fmm) -> dict:

@@ -14,7 +14,9 @@ from .surfaces import (  # noqa: F401
     triangle_rule,
     greens_density,
     random_harmonic_density,
-    volume_targets,
+    danger_radius,
+    volume_points,
+    near_surface_points,
     config_surface,
     batched_specs,
 )

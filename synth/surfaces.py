@@ -341,49 +341,27 @@ def random_harmonic_density(surf: Surface, nmax: int = 10, seed: int = 4):
     return out
 
 
-def volume_targets(surf: Surface, n: int = 10000, seed: int = 2, box: float = 2.0, eps_tgt: float = 0.05):
-    """Uniform points in [-box, box]^3 with target association (Algorithm 3).
+def danger_radius(surf: Surface) -> np.ndarray:
+    """Radius of the danger zone around each source node, eta_k / 2 of its element (Section 3.4)."""
+    return 0.5 * surf.elem_eta[surf.src_elem]
 
-    Danger radius eta_k/2 around each source; an endangered target is matched
-    to the closest center on its preferred side (sign of (t - s*) . n(s*) for the
-    nearest source s*) within r_c (1 + eps_tgt).  Returns (xyz (3, n), ctr index
-    int32 with -1 = point target, flagged bool = endangered but unassociated).
-    """
-    from scipy.spatial import cKDTree
 
+def volume_points(n: int = 10000, seed: int = 2, box: float = 2.0) -> np.ndarray:
+    """Seeded points uniform in [-box, box]^3, (3, n)."""
     rng = np.random.default_rng(seed)
-    t = rng.uniform(-box, box, size=(n, 3))
-    src = surf.src_xyz.T
-    stree = cKDTree(src)
-    rdanger = 0.5 * surf.elem_eta[surf.src_elem]
-    dmax = rdanger.max()
-    dist, near = stree.query(t)
-    ctr_idx = np.full(n, -1, np.int32)
-    flagged = np.zeros(n, bool)
-    cand = np.nonzero(dist <= dmax)[0]
-    ctree = cKDTree(surf.ctr_xyz.T)
-    rmax = surf.ctr_r.max() * (1.0 + eps_tgt)
-    for i in cand:
-        idx = stree.query_ball_point(t[i], dmax)
-        idx = np.asarray(idx)
-        dd = np.linalg.norm(src[idx] - t[i], axis=1)
-        if not np.any(dd <= rdanger[idx]):
-            continue
-        s = near[i]
-        side = 1 if np.dot(t[i] - src[s], surf.src_n[:, s]) > 0 else -1
-        cidx = np.asarray(ctree.query_ball_point(t[i], rmax))
-        best, bestd = -1, np.inf
-        for c in np.sort(cidx):
-            if surf.ctr_side[c] != side:
-                continue
-            dc = np.linalg.norm(surf.ctr_xyz[:, c] - t[i])
-            if dc <= surf.ctr_r[c] * (1.0 + eps_tgt) and dc < bestd:
-                best, bestd = c, dc
-        if best >= 0:
-            ctr_idx[i] = best
-        else:
-            flagged[i] = True
-    return np.ascontiguousarray(t.T), ctr_idx, flagged
+    return np.ascontiguousarray(rng.uniform(-box, box, size=(n, 3)).T)
+
+
+def near_surface_points(surf: Surface, n: int, seed: int = 3, spread: float = 2.0) -> np.ndarray:
+    """Seeded points near the surface: a random source node moved along its normal by a uniform
+    multiple in [-spread, spread] of its danger radius, plus a tangential jitter of the same size
+    (so that many points are endangered and both sides are represented), (3, n)."""
+    rng = np.random.default_rng(seed)
+    j = rng.integers(0, surf.n_src, n)
+    rd = danger_radius(surf)[j]
+    x = surf.src_xyz[:, j] + surf.src_n[:, j] * (rng.uniform(-spread, spread, n) * rd)
+    x = x + rng.normal(size=(3, n)) * (0.5 * rd)
+    return np.ascontiguousarray(x)
 
 
 # --------------------------------------------------------------------------

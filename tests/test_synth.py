@@ -1,9 +1,9 @@
-"""Input generator checks (no GPU): quadrature exactness, geometry and association."""
+"""Input generator checks (no GPU): quadrature exactness, geometry, seeded point sets."""
 import math
 
 import numpy as np
 
-from synth import make_surface, triangle_rule, volume_targets
+from synth import danger_radius, make_surface, near_surface_points, triangle_rule, volume_points
 from synth.surfaces import STAR_Y63, star_radius
 
 
@@ -28,15 +28,18 @@ def test_sphere_area_normals_and_radii(sphere320):
     assert np.allclose(d, s.ctr_r)
 
 
-def test_volume_target_association():
+def test_point_sets_are_seeded_and_placed():
     s = make_surface(4, star_radius(STAR_Y63))
-    t, ctr, flagged = volume_targets(s, n=2000, seed=2)
-    assoc = ctr >= 0
-    assert assoc.sum() > 0
-    d = np.linalg.norm(s.ctr_xyz[:, ctr[assoc]] - t[:, assoc], axis=0)
-    assert np.all(d <= s.ctr_r[ctr[assoc]] * 1.05 + 1e-15)
-    far = np.linalg.norm(t, axis=0) > 1.6
-    assert not np.any(assoc & far)
+    v = volume_points(500, seed=2)
+    assert v.shape == (3, 500) and np.array_equal(v, volume_points(500, seed=2))
+    assert np.all(np.abs(v) <= 2.0)
+    p = near_surface_points(s, 400, seed=3)
+    assert np.array_equal(p, near_surface_points(s, 400, seed=3))
+    rd = danger_radius(s)
+    assert np.allclose(rd, 0.5 * s.elem_eta[s.src_elem]) and np.all(rd > 0)
+    # every point lies within a few danger radii of some source
+    d = np.min(np.linalg.norm(p[:, :, None] - s.src_xyz[:, None, :], axis=0), axis=1)
+    assert np.all(d <= 4.0 * rd.max())
 
 
 def test_batched_specs_follow_the_recipe():
