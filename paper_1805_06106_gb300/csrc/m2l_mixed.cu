@@ -16,6 +16,7 @@
 // pairs of the box's List 2 in list order in compensated FP32 (deterministic), undoes the scaling
 // and adds into the FP64 local expansion.
 #include <algorithm>
+#include <cmath>
 #include <vector>
 
 #include "harmonics.cuh"
@@ -60,6 +61,25 @@ __device__ __forceinline__ double ffac_sqrt(int n, int m)  // F(n, m) = sqrt((n+
     for (int i = 2; i <= n + am; ++i) f *= i;
     for (int i = 2; i <= n - am; ++i) f *= i;
     return sqrt(f);
+}
+
+// F(n, m) for n <= PMAX, m >= 0 (tri layout), the same products and correctly rounded square root as
+// ffac_sqrt, computed on the host when a plan is built: the per-element kernels look it up (an FP64
+// product chain and square root per element would occupy the FP64 pipe)
+__device__ double g_fsq[ntri(PMAX)];
+
+static void set_fsq_table(cudaStream_t st)
+{
+    double h[ntri(PMAX)];
+    for (int n = 0; n <= PMAX; ++n)
+        for (int m = 0; m <= n; ++m) {
+            double f = 1.0;
+            for (int i = 2; i <= n + m; ++i) f *= i;
+            for (int i = 2; i <= n - m; ++i) f *= i;
+            h[tri(n, m)] = std::sqrt(f);
+        }
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(g_fsq, h, sizeof h, 0, cudaMemcpyHostToDevice, st));
+    QBX_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
 // real-layout index of (n, m >= 0, part)
@@ -164,7 +184,7 @@ __global__ void k_mhat(int64_t nb, int P, int PMT, const double2 *Mu, float *mh)
     int rr = r - n * n;
     int m = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
     double2 v = Mu[b * ntri(PMT) + tri(n, m)];
-    mh[i] = (float)((part ? v.y : v.x) * ffac_sqrt(n, m));
+    mh[i] = (float)((part ? v.y : v.x) * __ldg(&g_fsq[tri(n, m)]));
 }
 
 // FP32 SIMT GEMM per offset tile: Y[pair] = Mats[o] * Mh[src(pair)], block = 64 rows x 64 pairs.
@@ -232,7 +252,7 @@ __global__ void k_mhat_tc(int64_t nb, int P, int PMT, int Dp, const double2 *Mu,
         int rr = r - n * n;
         int m = (rr + 1) / 2, part = (rr == 0) ? 0 : ((rr & 1) ? 0 : 1);
         double2 c = Mu[b * ntri(PMT) + tri(n, m)];
-        v = (part ? c.y : c.x) * ffac_sqrt(n, m);
+        v = (part ? c.y : c.x) * __ldg(&g_fsq[tri(n, m)]);
     }
     float hi, lo;
     tc::split_tf32(v, hi, lo);
@@ -446,7 +466,7 @@ __global__ void k_m2l_reduce(int64_t nb, int P, int PMT, const int *vstart, cons
         for (int u = 0; u < 8; ++u) tc::df_add(hi, lo, v[u]);
     }
     for (; e < e1; ++e) tc::df_add(hi, lo, __ldg(y + (int64_t)pair_pos[e] * D + r));
-    double s = ((double)hi + (double)lo) * (ffac_sqrt(k, l) / hw[b]);
+    double s = ((double)hi + (double)lo) * (__ldg(&g_fsq[tri(k, l)]) / hw[b]);
     double2 *t = B + (int64_t)b * ntri(PMT) + tri(k, l);
     if (part) t->y += s;
     else t->x += s;
@@ -472,6 +492,7 @@ M2LPlan *m2l_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int PMT, c
 {
     M2LPlan *pl = new M2LPlan();
     try {
+        set_fsq_table(st);
         pl->P = P;
         pl->D = (P + 1) * (P + 1);
         pl->tc = tc;

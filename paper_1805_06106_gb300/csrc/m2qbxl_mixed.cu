@@ -47,7 +47,8 @@ struct WfarPlan {
     int Rp = 0, Kp = 0, nch = 0, WMAX = 0, ntc = 0, NU = 0;
     int cj0[WF_MAXCH] = {}, cj1[WF_MAXCH] = {}, ckoff[WF_MAXCH + 1] = {};
     float *H_tc = nullptr;     // ndsrc x Rp x Kp
-    void *recipe = nullptr;    // Rp x Kp WfarRecipe records of the H block
+    float *rec_fac = nullptr;        // Rp x Kp: |factor| of each H entry
+    uint32_t *rec_code = nullptr;    // Rp x Kp: packed terms of each H entry (see k_wfar_H_tc)
     int4 *tc_tiles = nullptr;  // (source box, first pair, last pair + 1) per 128-pair tile
 };
 
@@ -59,7 +60,7 @@ void free_wfar_plan(WfarPlan *p)
     if (!p) return;
     dfree(p->slot); dfree(p->slot_box); dfree(p->H); dfree(p->pair_ctr); dfree(p->pair_d); dfree(p->pos_cm);
     dfree(p->cm_start); dfree(p->tiles); dfree(p->Y); dfree(p->zero_start);
-    dfree(p->H_tc); dfree(p->tc_tiles); dfree(p->recipe);
+    dfree(p->H_tc); dfree(p->tc_tiles); dfree(p->rec_fac); dfree(p->rec_code);
     delete p;
 }
 
@@ -194,31 +195,55 @@ struct WfarRecipe {
     int pad;
 };
 
-__global__ void k_wfar_H_tc(int ndsrc, int P, int PMT, int64_t per, const WfarRecipe *rec, const int *slot_box,
-                            const signed char *pb, const double2 *Mu, float *H)
+// The recipe as the kernel reads it, one float and one word per entry: |f| (both terms of an entry
+// have the same magnitude D(j)/F(k,l)), and code = t1 | t2 << 10 | n << 20 | ty << 26 | s1 << 27 |
+// s2 << 28 (tri indices, 1023 for none; the degree n of both terms; ty: the terms read .y; s1, s2: the
+// terms' signs).  An entry is s1 |f| M[t1] + s2 |f| M[t2], as fmaf(s2 |f|, M[t2], s1 |f| M[t1]).
+constexpr uint32_t WF_NOTERM = 1023u;
+
+__device__ __forceinline__ float wfar_recipe_entry(float f, uint32_t c, int Pd, const float2 *Ms)
 {
-    int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)ndsrc * per) return;
-    const int s = (int)(idx / per);
-    const WfarRecipe r = rec[idx % per];
-    const int d = slot_box[s];
-    const int Pd = min((int)pb[d], P);
-    // in FP32 from the multipole coefficients rounded to nearest by integer operations: the entry is
-    // rounded to FP32 (and split into TF32 parts) anyway, and FP64 arithmetic on ~10^9 entries per
-    // evaluation would bound this kernel by the FP64 pipe
+    const uint32_t t1 = c & 1023u, t2 = (c >> 10) & 1023u;
+    const int n = (int)((c >> 20) & 63u);
+    const bool ty = (c >> 26) & 1u;
     float e = 0.f;
-    if ((r.bits >> 8) <= Pd) {
-        const double2 *M = Mu + (int64_t)d * ntri(PMT);
-        if (r.t1 >= 0) {
-            const double2 v = M[r.t1];
-            e = r.f1 * dbl_to_f32_rn((r.bits & 1) ? v.y : v.x);
+    if (n <= Pd) {
+        if (t1 != WF_NOTERM) {
+            const float2 v = Ms[t1];
+            e = ((c >> 27) & 1u ? -f : f) * (ty ? v.y : v.x);
         }
-        if (r.t2 >= 0) {
-            const double2 v = M[r.t2];
-            e = fmaf(r.f2, dbl_to_f32_rn((r.bits & 2) ? v.y : v.x), e);
+        if (t2 != WF_NOTERM) {
+            const float2 v = Ms[t2];
+            e = fmaf((c >> 28) & 1u ? -f : f, ty ? v.y : v.x, e);
         }
     }
-    H[idx] = e;
+    return e;
+}
+
+// One block per slot (source box): its multipole rounded to FP32 once into shared memory (by integer
+// operations: FP64 arithmetic on ~10^10 entries per evaluation would bound this kernel by the FP64
+// pipe), then the slot's Rp x Kp entries four at a time from the recipe (L2-resident, shared by all
+// slots), stored as float4.
+__global__ void __launch_bounds__(256) k_wfar_H_tc(int P, int PMT, int64_t per4, const float4 *fac, const uint4 *code,
+                                                   const int *slot_box, const signed char *pb, const double2 *Mu,
+                                                   float4 *H)
+{
+    __shared__ float2 Ms[ntri(PMAX)];
+    const int s = blockIdx.x, d = slot_box[s];
+    const int Pd = min((int)pb[d], P);
+    const double2 *M = Mu + (int64_t)d * ntri(PMT);
+    for (int t = threadIdx.x; t < ntri(P); t += blockDim.x) {
+        const double2 v = M[t];
+        Ms[t] = make_float2(dbl_to_f32_rn(v.x), dbl_to_f32_rn(v.y));
+    }
+    __syncthreads();
+    float4 *out = H + (int64_t)s * per4;
+    for (int64_t q = threadIdx.x; q < per4; q += blockDim.x) {
+        const float4 f = __ldg(fac + q);
+        const uint4 c = __ldg(code + q);
+        out[q] = make_float4(wfar_recipe_entry(f.x, c.x, Pd, Ms), wfar_recipe_entry(f.y, c.y, Pd, Ms),
+                             wfar_recipe_entry(f.z, c.z, Pd, Ms), wfar_recipe_entry(f.w, c.w, Pd, Ms));
+    }
 }
 
 // Unit-vector harmonics scaled per degree: Yh_j^i = |x|^{j+1} S_j^i(x) / D(j) obey
@@ -371,8 +396,9 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
         for (int c = 0; c < a.ch.nch; ++c, ++g) {
             const int s = g & 1;
             const uint32_t use = g >> 1;
+            // every thread waits for the products that last read stage s before it overwrites the stage;
+            // a failure is shared at the barrier before this chunk's products are issued
             if (g >= 2 && ok) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, a.wait_limit);
-            if (__syncthreads_or(!ok)) { ok = false; break; }
             const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
             const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c];
             {
@@ -443,7 +469,7 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
                 }
             }
             tc::fence_proxy_async();
-            __syncthreads();
+            if (__syncthreads_or(!ok)) { ok = false; break; }
             if (tid == 0) {
                 // failure-path probe: a wait on a barrier nothing arrives on runs out
                 const bool go = (int)g != a.probe_step || tc::mbar_wait(&bar_never, 0, a.wait_limit);
@@ -882,9 +908,22 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
                                              st));
             pl->H_tc = dalloc<float>((int64_t)std::max(nd, 1) * pl->Rp * pl->Kp);
             {
-                std::vector<WfarRecipe> rec = wfar_recipe(pl);
-                pl->recipe = dalloc<WfarRecipe>(rec.size());
-                QBX_CUDA_TRY(cudaMemcpyAsync(pl->recipe, rec.data(), rec.size() * sizeof(WfarRecipe),
+                const std::vector<WfarRecipe> rec = wfar_recipe(pl);
+                std::vector<float> fac(rec.size());
+                std::vector<uint32_t> code(rec.size());
+                for (size_t e = 0; e < rec.size(); ++e) {
+                    const WfarRecipe &r = rec[e];
+                    if (r.t1 >= 0 && r.t2 >= 0 && std::fabs(r.f1) != std::fabs(r.f2))
+                        throw Error{QBX_ERR_CUDA, "List 3 far recipe: terms of unequal magnitude"};
+                    fac[e] = r.t1 >= 0 ? std::fabs(r.f1) : (r.t2 >= 0 ? std::fabs(r.f2) : 0.f);
+                    code[e] = (uint32_t)(r.t1 >= 0 ? r.t1 : WF_NOTERM) | (uint32_t)(r.t2 >= 0 ? r.t2 : WF_NOTERM) << 10 |
+                              (uint32_t)(r.bits >> 8) << 20 | (uint32_t)(r.bits & 1) << 26 |
+                              (uint32_t)(r.t1 >= 0 && r.f1 < 0.f) << 27 | (uint32_t)(r.t2 >= 0 && r.f2 < 0.f) << 28;
+                }
+                pl->rec_fac = dalloc<float>(fac.size());
+                pl->rec_code = dalloc<uint32_t>(code.size());
+                QBX_CUDA_TRY(cudaMemcpyAsync(pl->rec_fac, fac.data(), fac.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+                QBX_CUDA_TRY(cudaMemcpyAsync(pl->rec_code, code.data(), code.size() * sizeof(uint32_t),
                                              cudaMemcpyHostToDevice, st));
                 QBX_CUDA_TRY(cudaStreamSynchronize(st));
             }
@@ -942,10 +981,11 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
             ch.cj1[c] = pl->cj1[c];
         }
         for (int c = 0; c <= WF_MAXCH; ++c) ch.ckoff[c] = pl->ckoff[c];
-        const int64_t per = (int64_t)pl->Rp * pl->Kp, nH = (int64_t)pl->ndsrc * per;
-        k_wfar_H_tc<<<nblocks(nH, 256), 256, 0, st>>>(pl->ndsrc, pl->P, PMT, per,
-                                                       static_cast<const WfarRecipe *>(pl->recipe), pl->slot_box, pb,
-                                                       Mu, pl->H_tc);
+        const int64_t per4 = (int64_t)pl->Rp * pl->Kp / 4;  // Rp is a multiple of 16
+        if (pl->ndsrc > 0)
+            k_wfar_H_tc<<<pl->ndsrc, 256, 0, st>>>(pl->P, PMT, per4, reinterpret_cast<const float4 *>(pl->rec_fac),
+                                                    reinterpret_cast<const uint4 *>(pl->rec_code), pl->slot_box, pb,
+                                                    Mu, reinterpret_cast<float4 *>(pl->H_tc));
         QBX_LAUNCH_CHECK();
         int dev = 0, nsm = 0;
         QBX_CUDA_TRY(cudaGetDevice(&dev));
