@@ -161,10 +161,11 @@ def m2m_macs(P):
 
 
 def pair_flops(Q, dipole):
-    """Direct P2QBXL per (source, center) pair: 16 (geometry, 1/r^2, 1/r) + 8 per irregular harmonic
-    entry up to order Q + dipole + per output coefficient 4 (charge) or 22 (charge + dipole)."""
-    K = Q + (1 if dipole else 0)
-    return 16 + 8 * (_tri(K) - 1) + (22 if dipole else 4) * _tri(Q)
+    """Direct QBX sum per (source, QBX target) pair, the Legendre form of the order-Q expansion
+    (k_qbx_direct): geometry, 1/r, cosine and ratios 20 + 3 at the end; per order n >= 1 the
+    recurrence of x^n P_n and the charge accumulation 7; with a dipole 12 more in the setup and 9 more
+    per order (the recurrence of x^n P_n' and the dipole term)."""
+    return 23 + 7 * Q + ((12 + 9 * Q) if dipole else 0)
 
 
 def p2x_flops(p, dipole):
@@ -173,12 +174,13 @@ def p2x_flops(p, dipole):
 
 
 def stage_work(cost, P, Q, dipole, mixed, ctr_order, box_order, parent, has_tgt_sub, src_boxes_nonroot,
-               n_src):
+               n_src, direct_pairs=None):
     """Algorithmic work per stage: {stage: (flops, kind)} with kind "fp64" or "tf32" (3-pass tensor)."""
     c = cost["count"]
-    direct = c["U"] + c["Wclose"] + c["Xclose"]
+    direct = c["U"] + c["Wclose"] + c["Xclose"] if direct_pairs is None else direct_pairs
     work = {}
-    # centers: direct P2QBXL, L2QBXL per center at its box's order, List 3 far M2QBXL in FP64 mode
+    # centers: direct QBX sums per (source, QBX target) pair, L2QBXL per center at its box's order, List 3
+    # far M2QBXL in FP64 mode; with one QBX target per center the pairs are the direct list counts
     l2q = sum(int(n) * (8 * _tri(int(p)) + 8 * l2qbxl_macs(int(p), Q))
               for p, n in zip(*np.unique(ctr_order, return_counts=True)))
     f_centers = pair_flops(Q, dipole) * direct + l2q
@@ -606,8 +608,19 @@ def run_gpu(args):
                 has_src[parent[b]] = True
             if has_tgt[b]:
                 has_tgt[parent[b]] = True
+        direct_pairs = None
+        qbx_t = tc[tc >= 0]
+        if len(qbx_t) != s.n_ctr or len(np.unique(qbx_t)) != s.n_ctr:
+            # (source, QBX target) pairs of the direct sums: each target takes its center box's sources
+            nsrc = np.bincount(src_owner, minlength=nb).astype(np.int64)
+            dbox = np.zeros(nb, np.int64)
+            for name in ("U", "Wclose", "Xclose"):
+                st_, ix_ = (a.cpu().numpy() for a in L.export()[name])
+                cs = np.concatenate([[0], np.cumsum(nsrc[ix_])])
+                dbox += cs[st_[1:]] - cs[st_[:-1]]
+            direct_pairs = int(np.sum(dbox[ctr_box[qbx_t]]))
         work = stage_work(cost, P, Q, mu is not None, mixed, pbn[ctr_box], pbn, parent, has_tgt,
-                          int(np.sum(has_src[1:])), int(s.n_src))
+                          int(np.sum(has_src[1:])), int(s.n_src), direct_pairs)
         roof = roofline_table(work, stage_ms, peaks)
         learned_work = None
         if orders:

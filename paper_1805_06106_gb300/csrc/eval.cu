@@ -51,6 +51,7 @@ struct qbx_workspace {
     double2 *m2l_tab = nullptr;    // 1331 offsets x ntri(2 PM): S_j^i(2 o)
     double2 *oct_tab = nullptr;    // 8 octants x ntri(PM): R_j^i(delta_o)
     double *sq = nullptr, *sd = nullptr;
+    double *pd = nullptr;          // per target: the direct sources' part of its QBX expansion (k_qbx_direct)
     signed char *qc = nullptr, *pb = nullptr, *ps = nullptr;  // per-center QBX, per-box local and multipole orders
     int *flags = nullptr;
     std::vector<int> lvl_first;    // host copies of level ranges
@@ -69,7 +70,7 @@ namespace qbx {
 void free_workspace(qbx_workspace *ws)
 {
     if (!ws) return;
-    dfree(ws->Mu); dfree(ws->B); dfree(ws->A); dfree(ws->m2l_tab); dfree(ws->oct_tab);
+    dfree(ws->Mu); dfree(ws->B); dfree(ws->A); dfree(ws->m2l_tab); dfree(ws->oct_tab); dfree(ws->pd);
     dfree(ws->sq); dfree(ws->sd); dfree(ws->qc); dfree(ws->pb); dfree(ws->ps); dfree(ws->flags);
     free_m2l_plan(ws->m2l);
     free_wfar_plan(ws->wfar);
@@ -699,7 +700,7 @@ __global__ void __launch_bounds__(128) k_centers(
     int64_t nc, const int *ctr_box, const double *cxyz, const double *cr, const signed char *qc, const signed char *pb,
     const signed char *ps, ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf, const int *own_start, const double *sxyz,
     int64_t ns, const double *sq, const double *sd, const double *cen, const double *hw, const double2 *Mu,
-    const double2 *B, double2 *A)
+    const double2 *B, double2 *A, int direct)
 {
     extern __shared__ double2 sh[];
     constexpr int NT = ntri(QM);
@@ -784,9 +785,10 @@ __global__ void __launch_bounds__(128) k_centers(
     }
 
     // Stages 3, 5(a), 6(a): direct P2QBXL from List 1, List 3 close and List 4 close sources, the three
-    // lists walked as one sequence of boxes so that partial batches of 32 sources are rare
+    // lists walked as one sequence of boxes so that partial batches of 32 sources are rare (in the
+    // coefficient form; qbx_eval sums them at the targets instead, in k_qbx_direct)
     const bool dip = sd != nullptr;
-    {
+    if (direct) {
         const int u0 = lu.start[b], n0 = lu.start[b + 1] - u0;
         const int w0 = lwc.start[b], n1 = lwc.start[b + 1] - w0;
         const int x0 = lxc.start[b], n2 = lxc.start[b + 1] - x0;
@@ -848,13 +850,132 @@ __global__ void __launch_bounds__(128) k_centers(
     }
 }
 
+// ---------------------------------------------------------------- direct QBX sums at the targets
+
+// Stages 3, 5(a), 6(a) + 9 for one QBX target: the order-Q QBX expansion about its center c of the
+// sources of List 1, List 3 close and List 4 close of c's box, evaluated at the target t.  By the
+// addition theorem the m-sum of an order-n term of the expansion (eqs. qbxcoeff, qbxlocal) collapses,
+// for charge q at s, to q rho^n / r^(n+1) P_n(u) (rho = |t - c|, r = |s - c|, u = the cosine of the
+// angle between t - c and s - c), and the dipole term is d . grad_s of it:
+//   d . grad_s [r^-(n+1) P_n(u)] = r^-(n+2) [ (d.a - u d.e) P_n'(u) - (n+1) (d.e) P_n(u) ]
+// (a, e the unit vectors of t - c and s - c).  With T_n = x^n P_n(u), T'_n = x^n P_n'(u), x = rho / r:
+//   T_n = (2n-1)/n (x u) T_{n-1} - (n-1)/n x^2 T_{n-2},   T'_n = (2n-1) x T_{n-1} + x^2 T'_{n-2}.
+// The value is sum_s [q sum_n T_n + (1/r) sum_n ((d.a - u d.e) T'_n - (n+1)(d.e) T_n)] / r, the same
+// truncated expansion as the coefficient form up to rounding, at O(Q) work per (source, target) pair
+// instead of O(Q^2) per (source, center).  One warp per target; lanes take the sources of the three
+// lists walked as one sequence of boxes.  out[t] (input order) receives the sum without 1/(4 pi); with
+// SWEEP, out[n * nt + t] receives the order-n part for n = 0..QM.
+template <int QM, bool SWEEP>
+__global__ void __launch_bounds__(128) k_qbx_direct(int64_t nt, const int *tperm, const double *txyz,
+                                                    const int *tgt_ctr, const int *ctr_rank, const int *ctr_box,
+                                                    int64_t nc, const double *cxyz, const signed char *qc, ListRef lu,
+                                                    ListRef lwc, ListRef lxc, const int *own_start,
+                                                    const double *sxyz, int64_t ns, const double *sq,
+                                                    const double *sd, double *out)
+{
+    const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t it = (int64_t)blockIdx.x * 4 + wl;
+    if (it >= nt) return;
+    const int t = tperm[it];
+    const int c = tgt_ctr[t];
+    if (c < 0 || c >= nc) return;  // point targets (out of range indices are flagged by the argument check)
+    const int i = ctr_rank[c], b = ctr_box[i];
+    const int Q = min((int)qc[i], QM);
+    const double cx = cxyz[i], cy = cxyz[nc + i], cz = cxyz[2 * nc + i];
+    double ax = txyz[it] - cx, ay = txyz[nt + it] - cy, az = txyz[2 * nt + it] - cz;
+    const double rho = sqrt(ax * ax + ay * ay + az * az);
+    const double rhoinv = rho > 0.0 ? 1.0 / rho : 0.0;  // t = c: only the n = 0 terms remain
+    ax *= rhoinv;
+    ay *= rhoinv;
+    az *= rhoinv;
+    const bool dip = sd != nullptr;
+    double acc[SWEEP ? QM + 1 : 1];
+#pragma unroll
+    for (int n = 0; n < (SWEEP ? QM + 1 : 1); ++n) acc[n] = 0.0;
+    const int u0 = lu.start[b], n0 = lu.start[b + 1] - u0;
+    const int w0 = lwc.start[b], n1 = lwc.start[b + 1] - w0;
+    const int x0 = lxc.start[b], n2 = lxc.start[b + 1] - x0;
+    const int e1 = n0 + n1 + n2;
+    for (int base = 0; base < e1; base += 32) {
+        const int e = base + lane;
+        int d = -1;
+        if (e < n0) d = lu.idx[u0 + e];
+        else if (e < n0 + n1) d = lwc.idx[w0 + e - n0];
+        else if (e < e1) d = lxc.idx[x0 + e - n0 - n1];
+        const int s0 = d >= 0 ? own_start[d] : 0;
+        const int cnt = d >= 0 ? own_start[d + 1] - s0 : 0;
+        int incl = cnt;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        for (int k0 = 0; k0 < total; k0 += 32) {
+            const int k = k0 + lane;
+            int j = 0;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+                const int v = __shfl_sync(0xffffffffu, incl, j + step - 1);
+                if (v <= k) j += step;
+            }
+            const int sj = __shfl_sync(0xffffffffu, s0, j);
+            const int ij = __shfl_sync(0xffffffffu, incl, j);
+            const int cj = __shfl_sync(0xffffffffu, cnt, j);
+            if (k >= total) continue;
+            const int s = sj + (k - (ij - cj));
+            const double ex = sxyz[s] - cx, ey = sxyz[ns + s] - cy, ez = sxyz[2 * ns + s] - cz;
+            const double rinv = rsqrt(ex * ex + ey * ey + ez * ez);
+            const double u = (ax * ex + ay * ey + az * ez) * rinv;
+            const double x = rho * rinv, x2 = x * x, xu = x * u;
+            const double q = sq[s];
+            double alpha = 0.0, dE = 0.0;
+            if (dip) {
+                const double dx = sd[s], dy = sd[ns + s], dz = sd[2 * ns + s];
+                dE = (dx * ex + dy * ey + dz * ez) * rinv;
+                alpha = (dx * ax + dy * ay + dz * az) - u * dE;
+            }
+            // n = 0: T_0 = 1, T'_0 = 0
+            double T2 = 0.0, T1 = 1.0, D2 = 0.0, D1 = 0.0;
+            double sc = q, sdp = -dE;  // charge part and dipole part (times r), order by order
+            if (SWEEP) acc[0] += rinv * (q - dE * rinv);
+#pragma unroll
+            for (int n = 1; n <= QM; ++n) {
+                if (n > Q) break;
+                const double Tn = fma((2.0 * n - 1.0) / n * xu, T1, -((n - 1.0) / n) * x2 * T2);
+                T2 = T1;
+                T1 = Tn;
+                sc = fma(q, Tn, sc);
+                if (dip) {
+                    const double Dn = fma((2.0 * n - 1.0) * x, T2, x2 * D2);
+                    D2 = D1;
+                    D1 = Dn;
+                    const double term = fma(alpha, Dn, -(n + 1.0) * dE * Tn);
+                    sdp += term;
+                    if (SWEEP) acc[n] += rinv * fma(q, Tn, term * rinv);
+                } else if (SWEEP) {
+                    acc[n] += rinv * q * Tn;
+                }
+            }
+            if (!SWEEP) acc[0] += rinv * fma(sdp, rinv, sc);
+        }
+    }
+#pragma unroll
+    for (int n = 0; n < (SWEEP ? QM + 1 : 1); ++n) {
+        double v = acc[n];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+        if (lane == 0) out[SWEEP ? (int64_t)n * nt + t : t] = v;
+    }
+}
+
 // ---------------------------------------------------------------- Stage 9
 
 // QBX targets: phi(t) = 1/(4 pi) sum A_k^l R_k^l((c - t)/rho), real part with conjugate symmetry.
 template <int QM>
 __global__ void k_qbxl2p(int64_t nt, const int *tperm, const double *txyz, const int *tgt_ctr, const int *ctr_rank,
                          int64_t nc, const double *cxyz, const double *cr, const signed char *qc, const double2 *A,
-                         double *pot)
+                         const double *pd, double *pot)
 {
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= nt) return;
@@ -888,7 +1009,8 @@ __global__ void k_qbxl2p(int64_t nt, const int *tperm, const double *txyz, const
             a1 = v;
         }
     }
-    pot[t] = INV4PI * acc;
+    // the direct sources' part, summed at this target by k_qbx_direct (null: it is in A)
+    pot[t] = INV4PI * (pd ? acc + pd[t] : acc);
 }
 
 // Point targets: P2P from List 1 / 3 close / 4 close, M2P from List 3 far, L2P of the box local.
@@ -1175,7 +1297,14 @@ static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, b
             T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc, ws->pb, ws->ps, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
             ListRef{wf_start, L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,
-            dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A);
+            dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A, 0);
+        QBX_LAUNCH_CHECK();
+    }
+    if (T->np[KTGT] > 0 && T->np[KCTR] > 0) {
+        k_qbx_direct<QM, false><<<nblocks(T->np[KTGT], 4), 128, 0, st>>>(
+            T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr, T->ctr_rank, T->ctr_box, T->np[KCTR], T->cxyz, ws->qc,
+            ListRef{L->start[LU], L->idx[LU]}, ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
+            T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq, dip ? ws->sd : nullptr, ws->pd);
         QBX_LAUNCH_CHECK();
     }
     stage_mark(L, 7, st);
@@ -1184,7 +1313,7 @@ static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, b
     if (T->np[KTGT] > 0) {
         k_qbxl2p<QM><<<nblocks(T->np[KTGT], 128), 128, 0, st>>>(T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr,
                                                                 T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->qc,
-                                                                ws->A, pot);
+                                                                ws->A, T->np[KCTR] > 0 ? ws->pd : nullptr, pot);
         QBX_LAUNCH_CHECK();
     }
 }
@@ -1212,6 +1341,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         ws->oct_tab = dalloc<double2>(8 * ntri(PM_T));
         ws->sq = dalloc<double>(ns);
         ws->sd = dalloc<double>(3 * ns);
+        ws->pd = dalloc<double>(std::max<int64_t>(nt, 1));
         ws->qc = dalloc<signed char>(nc);
         ws->pb = dalloc<signed char>(nb);
         ws->ps = dalloc<signed char>(nb);
@@ -1374,7 +1504,7 @@ namespace qbx {
 template <int QM>
 __global__ void k_qbx_partials(int64_t nt, int Q, const int *tperm, const double *txyz, const int *tgt_ctr,
                                const int *ctr_rank, int64_t nc, const double *cxyz, const double *cr,
-                               const double2 *A, double *partial)
+                               const double2 *A, const double *dir, double *partial)
 {
     int64_t it = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (it >= nt) return;
@@ -1411,7 +1541,7 @@ __global__ void k_qbx_partials(int64_t nt, int Q, const int *tperm, const double
     }
     double acc = 0.0;
     for (int k = 0; k <= Q; ++k) {
-        acc += row[k];
+        acc += row[k] + dir[(int64_t)k * nt + t];  // the direct sources' order-k part (k_qbx_direct)
         partial[(int64_t)k * nt + t] = INV4PI * acc;
     }
 }
@@ -1423,20 +1553,36 @@ void eval_order_sweep(const qbx_tree *T, qbx_lists *L, const double *w, const do
     const int64_t nt = T->np[KTGT];
     if (nt == 0) return;
     qbx_workspace *ws = L->ws;
-    switch (ws->QM) {
+    const bool dip = mu != nullptr;
+    double *dir = dalloc<double>((int64_t)(ws->QM + 1) * nt);
+    try {
+        QBX_CUDA_TRY(cudaMemsetAsync(dir, 0, (size_t)(ws->QM + 1) * nt * sizeof(double), st));
+        switch (ws->QM) {
 #define QBX_PARTIALS(QB)                                                                                        \
     case QB:                                                                                                     \
+        if (T->np[KCTR] > 0)                                                                                     \
+            k_qbx_direct<QB, true><<<nblocks(nt, 4), 128, 0, st>>>(                                              \
+                nt, T->perm[KTGT], T->txyz, tgt_ctr, T->ctr_rank, T->ctr_box, T->np[KCTR], T->cxyz, ws->qc,       \
+                ListRef{L->start[LU], L->idx[LU]}, ListRef{L->start[LWC], L->idx[LWC]},                          \
+                ListRef{L->start[LXC], L->idx[LXC]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,           \
+                dip ? ws->sd : nullptr, dir);                                                                     \
         k_qbx_partials<QB><<<nblocks(nt, 128), 128, 0, st>>>(nt, o->p_qbx, T->perm[KTGT], T->txyz, tgt_ctr,     \
                                                             T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->A,    \
-                                                            partial);                                           \
+                                                            dir, partial);                                      \
         break;
         QBX_PARTIALS(4)
         QBX_PARTIALS(8)
         QBX_PARTIALS(12)
         QBX_PARTIALS(16)
 #undef QBX_PARTIALS
+        }
+        QBX_LAUNCH_CHECK();
+        QBX_CUDA_TRY(cudaStreamSynchronize(st));
+    } catch (...) {
+        dfree(dir);
+        throw;
     }
-    QBX_LAUNCH_CHECK();
+    dfree(dir);
 }
 
 }  // namespace qbx
@@ -1495,13 +1641,13 @@ static void fixed_centers(const qbx_tree *T, const qbx_lists *L, const qbx_works
             T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws.qc, ws.pb, ws.ps, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
             ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws.sq,
-            dip ? ws.sd : nullptr, T->cen, T->hw, ws.Mu, ws.B, ws.A);
+            dip ? ws.sd : nullptr, T->cen, T->hw, ws.Mu, ws.B, ws.A, 1);
         QBX_LAUNCH_CHECK();
     }
     if (T->np[KTGT] > 0) {
         k_qbxl2p<QM><<<nblocks(T->np[KTGT], 128), 128, 0, st>>>(T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr,
                                                                 T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws.qc,
-                                                                ws.A, pot);
+                                                                ws.A, nullptr, pot);
         QBX_LAUNCH_CHECK();
     }
 }

@@ -215,3 +215,23 @@ def test_stage_profiling_leaves_results_unchanged(G, star_small):
         assert ms["centers"] > 0.0
         if prec == G.QBX_FP64:
             assert ms["m2qbxl_mixed"] < 0.05 and ms["m2qbxl_reduce"] < 0.05
+
+
+def test_order_sweep_columns_match_oracle_at_each_order(G, sphere80):
+    """Column q of qbx_eval_order_sweep is the evaluation with p_qbx = q (same p_fmm): against the oracle
+    at q = 0, 2 and the full order, double layer, with point targets (1e-10)."""
+    s = sphere80
+    u, dudn = greens_density(s)
+    vol = np.random.default_rng(4).uniform(-1.6, 1.6, size=(3, 60))
+    t = np.concatenate([s.tgt_xyz, vol], axis=1)
+    tc = np.concatenate([s.tgt_ctr, -np.ones(60, np.int32)]).astype(np.int32)
+    Q, P = 6, 10
+    T = G.qbx_build_tree(_cuda(s.src_xyz), _cuda(s.ctr_xyz), _cuda(s.ctr_r), _cuda(t), n_max=16, t_f=0.9)
+    L = G.qbx_build_lists(T)
+    part = G.qbx_eval_order_sweep(T, L, _cuda(s.src_w), _cuda(dudn), _cuda(-u), _cuda(s.src_n),
+                                  _cuda(tc, torch.int32), Q, P).cpu().numpy()
+    To = O.build_tree(s.src_xyz, s.ctr_xyz, s.ctr_r, t, n_max=16, t_f=0.9)
+    Lo = O.build_lists(To)
+    for q in (0, 2, Q):
+        ref = O.fmm_eval(To, Lo, s.src_xyz, s.src_w, dudn, -u, s.src_n, s.ctr_xyz, t, tc, q, P)
+        assert rel_linf(part[q], ref) <= 1e-10, q
