@@ -393,9 +393,9 @@ int qbx_profile_read(const qbx_lists *lists, double *stage_ms_host);
  * than qbx_eval's, so the two agree to rounding (about 1e-15 relative), not bit for bit.
  *   Scratch: one file-scope device array of QBX_NOALLOC_SCRATCH_BYTES (48 MiB) inside the
  *   library, held by every GPU that loads the library until the process exits.  The problem
- *   must fit: roughly 18.4 MB of tables + 7.4 kB per box + 16 ntri(Qb) bytes per center (Qb =
+ *   must fit: roughly 18.4 MB of tables + 11.1 kB per box + 16 ntri(Qb) bytes per center (Qb =
  *   4, 8, 12 or 16, the smallest >= p_qbx) + 33 bytes per source, each buffer rounded up to 256
- *   bytes; e.g. 2,000 boxes and 20,000 centers at p_qbx <= 8.  A larger problem returns
+ *   bytes; e.g. 1,200 boxes and 20,000 centers at p_qbx <= 8.  A larger problem returns
  *   QBX_ERR_INVALID_ARG with the exact byte counts in qbx_last_error().
  *   No call allocates: no cudaMalloc, cudaFree or allocating library routine.
  *   The first call on each device looks up the array's device address (with that device

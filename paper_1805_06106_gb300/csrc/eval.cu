@@ -20,6 +20,7 @@
 #include <math_constants.h>
 
 #include "harmonics.cuh"
+#include "df64.cuh"
 
 namespace qbx {
 
@@ -37,8 +38,8 @@ void free_wfar_plan(WfarPlan *p);
 int wfar_plan_orders(const WfarPlan *p);
 const int *wfar_empty_start(const WfarPlan *p);
 WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, int w_hint, cudaStream_t st);
-void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, int *err,
-                    long long wait_limit, int probe_step, cudaStream_t st);
+void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, const float *cf,
+                    int *err, long long wait_limit, int probe_step, cudaStream_t st);
 void wfar_mixed_reduce(const qbx_tree *T, WfarPlan *pl, int QMS, const signed char *qc, double2 *A, cudaStream_t st);
 
 
@@ -52,6 +53,9 @@ struct qbx_workspace {
     double2 *oct_tab = nullptr;    // 8 octants x ntri(PM): R_j^i(delta_o)
     double *sq = nullptr, *sd = nullptr;
     double *pd = nullptr;          // per target: the direct sources' part of its QBX expansion (k_qbx_direct)
+    float *sf = nullptr, *cf = nullptr, *tf = nullptr;  // double-float copies of sources (+ densities), centers, targets
+    float4 *Bf = nullptr;          // double-float copy of the box locals (k_l2qbxl)
+    float4 *Muf = nullptr, *octf = nullptr;  // double-float copies of the multipoles and the octant table
     signed char *qc = nullptr, *pb = nullptr, *ps = nullptr;  // per-center QBX, per-box local and multipole orders
     int *flags = nullptr;
     std::vector<int> lvl_first;    // host copies of level ranges
@@ -71,6 +75,7 @@ void free_workspace(qbx_workspace *ws)
 {
     if (!ws) return;
     dfree(ws->Mu); dfree(ws->B); dfree(ws->A); dfree(ws->m2l_tab); dfree(ws->oct_tab); dfree(ws->pd);
+    dfree(ws->sf); dfree(ws->cf); dfree(ws->tf); dfree(ws->Bf); dfree(ws->Muf); dfree(ws->octf);
     dfree(ws->sq); dfree(ws->sd); dfree(ws->qc); dfree(ws->pb); dfree(ws->ps); dfree(ws->flags);
     free_m2l_plan(ws->m2l);
     free_wfar_plan(ws->wfar);
@@ -124,6 +129,33 @@ __global__ void k_prep_src(const int *perm, int64_t ns, const double *w, const d
         sd[2 * ns + i] = a * nz;
     }
     if (bad) atomicOr(flags, 1);
+}
+
+// Double-float copies (leading parts, then trailing parts) of n points stored as 3 x n FP64 (SoA),
+// and of k further FP64 arrays of length n: out = [xh yh zh xl yl zl] then [vh vl] per extra array.
+__global__ void k_to_df(int64_t n, const double *xyz, const double *v0, const double *v1, float *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const df a = df_from(xyz[d * n + i]);
+        out[d * n + i] = a.h;
+        out[(3 + d) * n + i] = a.l;
+    }
+    if (v0) {
+        const df a = df_from(v0[i]);
+        out[6 * n + i] = a.h;
+        out[7 * n + i] = a.l;
+    }
+    if (v1) {  // three components (dipole vectors), after the charge
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const df a = df_from(v1[d * n + i]);
+            out[(8 + d) * n + i] = a.h;
+            out[(11 + d) * n + i] = a.l;
+        }
+    }
 }
 
 void prep_sources(const int *perm, int64_t ns, const double *w, const double *sigma, const double *mu,
@@ -332,6 +364,224 @@ __global__ void __launch_bounds__(256) k_m2m8(int b0, int b1, const int *lvl_box
             v.y += part[k][out].y;
         }
         Mu[(int64_t)b * ntri(PM) + out] = v;
+    }
+}
+
+// ---------------------------------------------------------------- upward pass on double-floats
+
+// Reciprocals of the regular recurrence's integer divisors as double-floats (leading, trailing):
+// c_l2q_rinv[tri(n, m)] = 1/((n+m)(n-m)) for m < n, c_l2q_half[m] = 1/(2m).  Uniform indices across a
+// warp, so constant memory broadcasts them.
+__constant__ float2 c_l2q_rinv[ntri(PMAX)];
+__constant__ float2 c_l2q_half[PMAX + 1];
+
+static float2 split_f2(double v)
+{
+    const float h = (float)v;
+    return make_float2(h, (float)(v - (double)h));
+}
+
+void set_l2q_tables(cudaStream_t st)
+{
+    static float2 rinv[ntri(PMAX)], half[PMAX + 1];
+    for (int n = 0; n <= PMAX; ++n)
+        for (int m = 0; m <= n; ++m)
+            rinv[tri(n, m)] = m < n ? split_f2(1.0 / ((double)(n + m) * (double)(n - m))) : make_float2(0.f, 0.f);
+    half[0] = make_float2(0.f, 0.f);
+    for (int m = 1; m <= PMAX; ++m) half[m] = split_f2(1.0 / (2.0 * m));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_l2q_rinv, rinv, sizeof(rinv), 0, cudaMemcpyHostToDevice, st));
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_l2q_half, half, sizeof(half), 0, cudaMemcpyHostToDevice, st));
+}
+
+__device__ __forceinline__ df df_shfl_up(df v, int off)
+{
+    return df{__shfl_up_sync(0xffffffffu, v.h, off), __shfl_up_sync(0xffffffffu, v.l, off)};
+}
+__device__ __forceinline__ df df_shfl_down(df v, int off)
+{
+    return df{__shfl_down_sync(0xffffffffu, v.h, off), __shfl_down_sync(0xffffffffu, v.l, off)};
+}
+
+
+__device__ __forceinline__ float4 df2_pack(df re, df im) { return make_float4(re.h, re.l, im.h, im.l); }
+
+// double2 array -> double-float copy (re.h, re.l, im.h, im.l)
+__global__ void k_c2df(int64_t n, const double2 *a, float4 *out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = df2_pack(df_from(a[i].x), df_from(a[i].y));
+}
+
+// value at (n, m) for any m from a double-float table holding m >= 0: X_n^{-m} = (-1)^m conj X_n^m
+__device__ __forceinline__ void df_sym_get(const float4 *tab, int n, int m, df &re, df &im)
+{
+    const float4 v = tab[tri(n, m < 0 ? -m : m)];
+    re = df{v.x, v.y};
+    im = df{v.z, v.w};
+    if (m < 0) {
+        if (m & 1) re = df_neg(re);
+        else im = df_neg(im);
+    }
+}
+
+// P2M (Stage 2) on double-floats: the structure of k_p2m (one warp per box, lane m carrying column m of
+// R_n^m((s - c_b)/h) for each source in turn, the diagonal by a prefix product over the lanes), the
+// arithmetic in double-float.  Writes the FP64 multipole and its double-float copy.
+template <int PM, int ST>
+__global__ void k_p2m_df(int64_t nb, const int *own_start, int64_t ns, const float *sf, int dip, const double *cen,
+                         const double *hw, const signed char *pb, double2 *Mu, float4 *Muf)
+{
+    const int b = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    const int m = threadIdx.x & 31;
+    if (b >= nb) return;
+    const int s0 = own_start[b], s1 = own_start[b + 1];
+    if (s0 == s1) return;
+    const int P = pb[b];
+    const float hinv = (float)(1.0 / hw[b]);  // a power of two: exact
+    const df cx = df_from(cen[3 * b]), cy = df_from(cen[3 * b + 1]), cz = df_from(cen[3 * b + 2]);
+    dacc ar[PM + 1], ai[PM + 1];
+#pragma unroll
+    for (int n = 0; n <= PM; ++n) ar[n] = ai[n] = dacc{0.f, 0.f};
+    const df fm = m ? df_from(0.5 / m) : df{0.f, 0.f};
+    for (int s = s0; s < s1; ++s) {
+        const df x = df_mul_f(df_sub(df{sf[s], sf[3 * ns + s]}, cx), hinv),
+                 y = df_mul_f(df_sub(df{sf[ns + s], sf[4 * ns + s]}, cy), hinv),
+                 z = df_mul_f(df_sub(df{sf[2 * ns + s], sf[5 * ns + s]}, cz), hinv);
+        const df r2 = df_add(df_add(df_sqr(x), df_sqr(y)), df_sqr(z));
+        const df q{sf[6 * ns + s], sf[7 * ns + s]};
+        df dwx{0.f, 0.f}, dwy{0.f, 0.f}, dz{0.f, 0.f};  // d/2 = (dwx, dwy), dz, scaled by 1/h
+        if (dip) {
+            dwx = df_mul_f(df{sf[8 * ns + s], sf[11 * ns + s]}, 0.5f * hinv);
+            dwy = df_mul_f(df{sf[9 * ns + s], sf[12 * ns + s]}, 0.5f * hinv);
+            dz = df_mul_f(df{sf[10 * ns + s], sf[13 * ns + s]}, hinv);
+        }
+        // diagonal R_m^m = w^m / (2^m m!): inclusive prefix product over the lanes of w / (2m)
+        df gr = m == 0 ? df{1.f, 0.f} : df_mul(x, fm), gi = m == 0 ? df{0.f, 0.f} : df_mul(y, fm);
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const df orr = df_shfl_up(gr, off), oi = df_shfl_up(gi, off);
+            if (m >= off) {
+                const df nr = df_sub(df_mul(orr, gr), df_mul(oi, gi));
+                gi = df_add(df_mul(orr, gi), df_mul(oi, gr));
+                gr = nr;
+            }
+        }
+        df p2r{0.f, 0.f}, p2i{0.f, 0.f}, p1r{0.f, 0.f}, p1i{0.f, 0.f};
+#pragma unroll
+        for (int n = 0; n <= PM; ++n) {
+            df cr{0.f, 0.f}, ci{0.f, 0.f};
+            if (n == m) {
+                cr = gr;
+                ci = gi;
+            } else if (n > m) {
+                const float2 iv = c_l2q_rinv[tri(n, m)];
+                const df inv{iv.x, iv.y}, c1 = df_mul_f(z, (float)(2 * n - 1));
+                cr = df_mul(df_sub(df_mul(c1, p1r), df_mul(r2, p2r)), inv);
+                ci = df_mul(df_sub(df_mul(c1, p1i), df_mul(r2, p2i)), inv);
+            }
+            if (dip) {
+                // neighbour columns of the previous row: R_{n-1}^{m+1} and R_{n-1}^{m-1}
+                df upr = df_shfl_down(p1r, 1), upi = df_shfl_down(p1i, 1);
+                df dnr = df_shfl_up(p1r, 1), dni = df_shfl_up(p1i, 1);
+                if (m == 31) upr = upi = df{0.f, 0.f};
+                if (m == 0) {
+                    dnr = df_neg(upr);  // R^{-1} = -conj R^1
+                    dni = upi;
+                }
+                if (n >= m && n <= P) {
+                    // q R_n^m - (dbar/2) R_{n-1}^{m+1} + (d/2) R_{n-1}^{m-1} + dz R_{n-1}^m
+                    dacc_add_prod(ar[n], q, cr);
+                    dacc_add_prod(ar[n], dwx, df_sub(dnr, upr));
+                    dacc_add_prod(ar[n], dwy, df_neg(df_add(upi, dni)));
+                    dacc_add_prod(ar[n], dz, p1r);
+                    dacc_add_prod(ai[n], q, ci);
+                    dacc_add_prod(ai[n], dwx, df_sub(dni, upi));
+                    dacc_add_prod(ai[n], dwy, df_add(upr, dnr));
+                    dacc_add_prod(ai[n], dz, p1i);
+                }
+            } else if (n >= m && n <= P) {
+                dacc_add_prod(ar[n], q, cr);
+                dacc_add_prod(ai[n], q, ci);
+            }
+            p2r = p1r;
+            p2i = p1i;
+            p1r = cr;
+            p1i = ci;
+        }
+    }
+    if (m <= P) {
+#pragma unroll
+        for (int n = 0; n <= PM; ++n)
+            if (n >= m && n <= P) {
+                const df vr = dacc_get(ar[n]), vi = dacc_get(ai[n]);
+                const int64_t at = (int64_t)b * ST + tri(n, m);
+                Mu[at] = make_double2(df_to(vr), df_to(vi));
+                Muf[at] = df2_pack(vr, vi);
+            }
+    }
+}
+
+// M2M (Stage 2, one level) on double-floats: the structure of k_m2m8 (a block of 8 warps per parent,
+// warp o translating child octant o with lanes over the outputs, the contributions added in octant
+// order in shared memory), reading the children's double-float copies and the octant table's.
+template <int PM>
+__global__ void __launch_bounds__(256) k_m2m8_df(int b0, int b1, const int *lvl_boxes, const int *child,
+                                                 const int *nsrc_sub, const signed char *pb, const float4 *octf,
+                                                 double2 *Mu, float4 *Muf)
+{
+    __shared__ float4 part[8][ntri(PM)];
+    int b = b0 + blockIdx.x;
+    if (b >= b1) return;
+    if (lvl_boxes) b = lvl_boxes[b];
+    if (nsrc_sub[b] == 0) return;
+    const int o = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int P = pb[b];
+    const int c = child[8 * b + o];
+    const bool live = c >= 0 && nsrc_sub[c] > 0;
+    for (int out = lane; out < ntri(P); out += 32) {
+        df vr{0.f, 0.f}, vi{0.f, 0.f};
+        if (live) {
+            int n = 0;
+            while (tri(n + 1, 0) <= out) ++n;
+            const int m = out - tri(n, 0);
+            const int Pc = pb[c];
+            const float4 *Mc = Muf + (int64_t)c * ntri(PM);
+            const float4 *R = octf + o * ntri(PM);
+            dacc tr{0.f, 0.f}, ti{0.f, 0.f};
+            float sk = 1.0f;
+            for (int k = 0; k <= n && k <= Pc; ++k, sk *= 0.5f) {
+                const int j = n - k;
+                const int lmin = max(-k, m - j), lmax = min(k, m + j);
+                for (int l = lmin; l <= lmax; ++l) {
+                    df ar, ai, rr, ri;
+                    df_sym_get(Mc, k, l, ar, ai);
+                    df_sym_get(R, j, m - l, rr, ri);
+                    ar = df_mul_f(ar, sk);  // a power of two: exact
+                    ai = df_mul_f(ai, sk);
+                    dacc_add_prod(tr, ar, rr);
+                    dacc_add_prod(tr, df_neg(ai), ri);
+                    dacc_add_prod(ti, ar, ri);
+                    dacc_add_prod(ti, ai, rr);
+                }
+            }
+            vr = dacc_get(tr);
+            vi = dacc_get(ti);
+        }
+        part[o][out] = df2_pack(vr, vi);
+    }
+    __syncthreads();
+    for (int out = threadIdx.x; out < ntri(P); out += blockDim.x) {
+        const double2 own = Mu[(int64_t)b * ntri(PM) + out];  // the box's own sources (none for non-leaves)
+        df sr = df_from(own.x), si = df_from(own.y);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 f = part[k][out];
+            sr = df_add(sr, df{f.x, f.y});
+            si = df_add(si, df{f.z, f.w});
+        }
+        Mu[(int64_t)b * ntri(PM) + out] = make_double2(df_to(sr), df_to(si));
+        Muf[(int64_t)b * ntri(PM) + out] = df2_pack(sr, si);
     }
 }
 
@@ -568,6 +818,128 @@ __global__ void __launch_bounds__(128) k_p2l4(int64_t nb, const int *xs, const i
     }
 }
 
+// Stage 6(b) on double-floats: the structure of k_p2l4 (a block of four warps per target box, the
+// List 4 far sources over the warps, lane m carrying column m of the irregular harmonics S_n^m(c_b - s)
+// scaled by the box size, the diagonal by a prefix product over the lanes), with every product and
+// sum in double-float arithmetic (df64.cuh) from double-float copies of the sources (k_to_df).
+template <int PM, int ST>
+__global__ void __launch_bounds__(128) k_p2l4_df(int64_t nb, const int *xs, const int *xi, const int *own_start,
+                                                 int64_t ns, const float *sf, int dip, const double *cen,
+                                                 const double *hw, const signed char *pb, double2 *B)
+{
+    __shared__ float4 part[4][PM + 1][PM + 1];
+    const int b = blockIdx.x;
+    if (b >= nb) return;
+    const int e0 = xs[b], e1 = xs[b + 1];
+    if (e0 == e1) return;
+    const int w = threadIdx.x >> 5, m = threadIdx.x & 31;
+    const int P = pb[b];
+    const double h = hw[b];
+    const float hinv = (float)(1.0 / h);  // h is a power of two: exact
+    const df cx = df_from(cen[3 * b]), cy = df_from(cen[3 * b + 1]), cz = df_from(cen[3 * b + 2]);
+    dacc ar[PM + 1], ai[PM + 1];
+#pragma unroll
+    for (int n = 0; n <= PM; ++n) ar[n] = ai[n] = dacc{0.f, 0.f};
+    const float fm = 2.0f * m - 1.0f;
+    for (int e = e0 + w; e < e1; e += 4) {
+        const int d = xi[e];
+        for (int s = own_start[d]; s < own_start[d + 1]; ++s) {
+            const df x = df_mul_f(df_sub(cx, df{sf[s], sf[3 * ns + s]}), hinv),
+                     y = df_mul_f(df_sub(cy, df{sf[ns + s], sf[4 * ns + s]}), hinv),
+                     z = df_mul_f(df_sub(cz, df{sf[2 * ns + s], sf[5 * ns + s]}), hinv);
+            const df rinv = df_rsqrt(df_add(df_add(df_sqr(x), df_sqr(y)), df_sqr(z)));
+            const df ir2 = df_sqr(rinv);
+            const df q{sf[6 * ns + s], sf[7 * ns + s]};
+            df dwx{0.f, 0.f}, dwy{0.f, 0.f}, dz{0.f, 0.f};  // d/2 = (dwx, dwy), dz, all scaled by 1/h
+            if (dip) {
+                dwx = df_mul_f(df{sf[8 * ns + s], sf[11 * ns + s]}, 0.5f * hinv);
+                dwy = df_mul_f(df{sf[9 * ns + s], sf[12 * ns + s]}, 0.5f * hinv);
+                dz = df_mul_f(df{sf[10 * ns + s], sf[13 * ns + s]}, hinv);
+            }
+            const df wrx = df_mul(x, ir2), wry = df_mul(y, ir2), zz = df_mul(z, ir2);
+            // diagonal S_m^m = rinv prod_{j<=m} (2j-1) wr: inclusive prefix product of the lane factors
+            df gr = m == 0 ? rinv : df_mul_f(wrx, fm), gi = m == 0 ? df{0.f, 0.f} : df_mul_f(wry, fm);
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const df orr = df_shfl_up(gr, off), oi = df_shfl_up(gi, off);
+                if (m >= off) {
+                    const df nr = df_sub(df_mul(orr, gr), df_mul(oi, gi));
+                    gi = df_add(df_mul(orr, gi), df_mul(oi, gr));
+                    gr = nr;
+                }
+            }
+            df p2r{0.f, 0.f}, p2i{0.f, 0.f}, p1r{0.f, 0.f}, p1i{0.f, 0.f};
+#pragma unroll
+            for (int n1 = 0; n1 <= PM + 1; ++n1) {  // row n1 = n + 1 closes output row n
+                df cr{0.f, 0.f}, ci{0.f, 0.f};
+                if (n1 == m) {
+                    cr = gr;
+                    ci = gi;
+                } else if (n1 > m) {
+                    const df c1 = df_mul_f(zz, (float)(2 * n1 - 1));
+                    const df c2 = df_mul_f(ir2, (float)((n1 + m - 1) * (n1 - m - 1)));
+                    cr = df_sub(df_mul(c1, p1r), df_mul(c2, p2r));
+                    ci = df_sub(df_mul(c1, p1i), df_mul(c2, p2i));
+                }
+                const int n = n1 - 1;
+                if (dip) {
+                    df upr = df_shfl_down(cr, 1), upi = df_shfl_down(ci, 1);  // S_{n+1}^{m+1}
+                    df dnr = df_shfl_up(cr, 1), dni = df_shfl_up(ci, 1);      // S_{n+1}^{m-1}
+                    if (m == 31) upr = upi = df{0.f, 0.f};
+                    if (m == 0) {
+                        dnr = df_neg(upr);  // S^{-1} = -conj S^1
+                        dni = upi;
+                    }
+                    if (n >= m && n <= P) {
+                        // conj[q S_n^m + (dbar/2) S_{n+1}^{m+1} - (d/2) S_{n+1}^{m-1} + dz S_{n+1}^m]:
+                        //   (dbar/2) up = (dwx up.r + dwy up.i) + i (dwx up.i - dwy up.r)
+                        //   (d/2) dn    = (dwx dn.r - dwy dn.i) + i (dwx dn.i + dwy dn.r)
+                        dacc_add_prod(ar[n], q, p1r);
+                        dacc_add_prod(ar[n], dwx, df_sub(upr, dnr));
+                        dacc_add_prod(ar[n], dwy, df_add(upi, dni));
+                        dacc_add_prod(ar[n], dz, cr);
+                        dacc_add_prod(ai[n], df_neg(q), p1i);
+                        dacc_add_prod(ai[n], df_neg(dwx), df_sub(upi, dni));
+                        dacc_add_prod(ai[n], dwy, df_add(upr, dnr));
+                        dacc_add_prod(ai[n], df_neg(dz), ci);
+                    }
+                } else if (n >= m && n <= P) {
+                    dacc_add_prod(ar[n], q, p1r);
+                    dacc_add_prod(ai[n], df_neg(q), p1i);
+                }
+                p2r = p1r;
+                p2i = p1i;
+                p1r = cr;
+                p1i = ci;
+            }
+        }
+    }
+    if (m <= PM) {
+#pragma unroll
+        for (int n = 0; n <= PM; ++n) {
+            const df vr = dacc_get(ar[n]), vi = dacc_get(ai[n]);
+            part[w][n][m] = make_float4(vr.h, vr.l, vi.h, vi.l);
+        }
+    }
+    __syncthreads();
+    const double dh = 1.0 / h;
+    for (int t = threadIdx.x; t < ntri(P); t += blockDim.x) {
+        int n = 0;
+        while (tri(n + 1, 0) <= t) ++n;
+        const int mm = t - tri(n, 0);
+        float4 f = part[0][n][mm];
+        df sr{f.x, f.y}, si{f.z, f.w};
+#pragma unroll
+        for (int k = 1; k < 4; ++k) {
+            f = part[k][n][mm];
+            sr = df_add(sr, df{f.x, f.y});
+            si = df_add(si, df{f.z, f.w});
+        }
+        double2 v = B[(int64_t)b * ntri(ST) + t];
+        B[(int64_t)b * ntri(ST) + t] = make_double2(v.x + df_to(sr) * dh, v.y + df_to(si) * dh);
+    }
+}
+
 // ---------------------------------------------------------------- L2L (Stage 7), by level
 
 template <int PM>
@@ -695,12 +1067,15 @@ __device__ __forceinline__ void p2qbxl_accum(double bx, double by, double bz, do
     }
 }
 
+// One warp per QBX center: List 3 far M2QBXL in FP64 (Stage 5(b); an empty list in the mixed modes) and,
+// with `direct`, the direct P2QBXL of Lists 1, 3 close and 4 close in the coefficient form (Stages 3,
+// 5(a), 6(a)); the warp's sums are reduced and stored to A.  L2QBXL (Stage 8) is k_l2qbxl.
 template <int QM, int PM>
 __global__ void __launch_bounds__(128) k_centers(
-    int64_t nc, const int *ctr_box, const double *cxyz, const double *cr, const signed char *qc, const signed char *pb,
+    int64_t nc, const int *ctr_box, const double *cxyz, const double *cr, const signed char *qc,
     const signed char *ps, ListRef lu, ListRef lwc, ListRef lxc, ListRef lwf, const int *own_start, const double *sxyz,
     int64_t ns, const double *sq, const double *sd, const double *cen, const double *hw, const double2 *Mu,
-    const double2 *B, double2 *A, int direct)
+    double2 *A, int direct)
 {
     extern __shared__ double2 sh[];
     constexpr int NT = ntri(QM);
@@ -717,40 +1092,7 @@ __global__ void __launch_bounds__(128) k_centers(
 #pragma unroll
     for (int t = 0; t < NT; ++t) ar[t] = ai[t] = 0.0;
 
-    // Stage 8: L2QBXL from the box local (inputs split over lanes)
     double *pw = reinterpret_cast<double *>(tab + TAB - (PM + 1));  // powers, at the end of the warp's table
-    {
-        const int P = min((int)pb[b], PM);
-        const double h = hw[b], hinv = 1.0 / h, ratio = rho * hinv;  // rho/h
-        __syncwarp();
-        // R_j^i((c_b - c)/h) (h/rho)^j, j <= P; pw[n] = (rho/h)^n
-        regular_table_warp(P, (cen[3 * b] - cx) * hinv, (cen[3 * b + 1] - cy) * hinv, (cen[3 * b + 2] - cz) * hinv,
-                           1.0 / ratio, tab, lane);
-        if (lane <= P) pw[lane] = pow(ratio, lane);
-        __syncwarp();
-        const double2 *Lb = B + (int64_t)b * ntri(PM);
-        for (int in = lane; in < (P + 1) * (P + 1); in += 32) {
-            int n = (int)sqrtf((float)in);
-            while (n * n > in) --n;
-            while ((n + 1) * (n + 1) <= in) ++n;
-            int m = in - n * n - n;
-            double2 bv = cscale(sym_get(Lb, n, m), pw[n]);
-            const double nby = -bv.y;
-#pragma unroll
-            for (int k = 0; k <= QM; ++k) {
-                if (k > Q || k > n) break;
-                int j = n - k;
-#pragma unroll
-                for (int l = 0; l <= k; ++l) {
-                    int mi = m - l;
-                    if (mi < -j || mi > j) continue;
-                    double2 rv = sym_get(tab, j, mi);
-                    ar[tri(k, l)] = fma(bv.x, rv.x, fma(nby, rv.y, ar[tri(k, l)]));
-                    ai[tri(k, l)] = fma(bv.x, rv.y, fma(bv.y, rv.x, ai[tri(k, l)]));
-                }
-            }
-        }
-    }
 
     // Stage 5(b): List 3 far multipoles to the QBX local
     for (int e = lwf.start[b]; e < lwf.start[b + 1]; ++e) {
@@ -850,7 +1192,266 @@ __global__ void __launch_bounds__(128) k_centers(
     }
 }
 
-// ---------------------------------------------------------------- direct QBX sums at the targets
+// ---------------------------------------------------------------- Stage 8: L2QBXL, one thread per center
+
+// Double-float copy of the box locals (re.h, re.l, im.h, im.l per coefficient), the first
+// ntri(pb[b]) coefficients of every box, same stride as B.
+__global__ void k_locals_to_df(int64_t nb, int stride, const signed char *pb, const double2 *B, float4 *Bf)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= nb * stride) return;
+    const int64_t b = q / stride;
+    const int t = (int)(q % stride);
+    if (t >= ntri(min((int)pb[b], PMAX))) return;
+    const double2 v = B[q];
+    const df re = df_from(v.x), im = df_from(v.y);
+    Bf[q] = make_float4(re.h, re.l, im.h, im.l);
+}
+
+__device__ __forceinline__ df df_negif(df a, bool f) { return f ? df{-a.h, -a.l} : a; }
+
+// Outputs k in [K0, K1] of the QBX local of one center (Algorithm 4 Stage 8).  By the addition theorem
+// R_n^m(u + v) = sum_{k,l} R_{n-k}^{m-l}(u) R_k^l(v), the box local sum B_n^m R_n^m((c_b - x)/h) regrouped
+// by the power of v = (c - x)/h gives, with u = (c_b - c)/h and the QBX local scaled by rho,
+//   A_k^l = (rho/h)^k sum_{j <= P-k} sum_{|mu| <= j} R_j^mu(u) B_{j+k}^{mu+l}.
+// The harmonics R_j^mu(u) come from their recurrence column by column (mu >= 0, rows j = mu..P-K0),
+// each value serving mu and -mu (R_j^-mu = (-1)^mu conj R_j^mu); the K1-K0+1 output rows stay in
+// registers, so nothing is reduced across threads.  Double-float arithmetic, the sums as compensated
+// dot products (df64.cuh).  Ac receives the sums (add: accumulates onto it).
+template <int K0, int K1>
+__device__ __forceinline__ void l2q_pass(int P, int Q, df ux, df uy, df uz, double ratio,
+                                         const float4 *__restrict__ Lb, double2 *__restrict__ Ac,
+                                         float4 *__restrict__ Acf, bool add, const float4 *__restrict__ Rtab = nullptr)
+{
+    if (add && Q < K0) return;
+    constexpr int T0 = K0 * (K0 + 1) / 2;  // tri(K0, 0)
+    constexpr int NA = ntri(K1) - T0;
+    dacc ar[NA], ai[NA];
+#pragma unroll
+    for (int t = 0; t < NA; ++t) ar[t] = ai[t] = dacc{0.f, 0.f};
+    const df r2 = df_add(df_add(df_sqr(ux), df_sqr(uy)), df_sqr(uz));
+    const int jmax = P - K0;
+    df dr{1.f, 0.f}, di{0.f, 0.f};  // R_mu^mu(u)
+    for (int mu = 0; mu <= jmax; ++mu) {
+        if (mu > 0 && !Rtab) {
+            const float2 hs = c_l2q_half[mu];
+            const df s{hs.x, hs.y};
+            const df nr = df_mul(df_sub(df_mul(dr, ux), df_mul(di, uy)), s);
+            const df ni = df_mul(df_add(df_mul(dr, uy), df_mul(di, ux)), s);
+            dr = nr;
+            di = ni;
+        }
+        df p1r = dr, p1i = di, p2r{0.f, 0.f}, p2i{0.f, 0.f};  // R_{j-1}^mu, R_{j-2}^mu
+        const bool smu = mu & 1;
+        for (int j = mu; j <= jmax; ++j) {
+            df rr = dr, ri = di;
+            if (Rtab) {  // R_j^mu(u) tabulated (a fixed translation)
+                const float4 v = Rtab[tri(j, mu)];
+                rr = df{v.x, v.y};
+                ri = df{v.z, v.w};
+            } else if (j > mu) {
+                const float2 iv = c_l2q_rinv[tri(j, mu)];
+                const df inv{iv.x, iv.y}, c1 = df_mul_f(uz, (float)(2 * j - 1));
+                rr = df_mul(df_sub(df_mul(c1, p1r), df_mul(r2, p2r)), inv);
+                ri = df_mul(df_sub(df_mul(c1, p1i), df_mul(r2, p2i)), inv);
+                p2r = p1r;
+                p2i = p1i;
+                p1r = rr;
+                p1i = ri;
+            }
+            const df nri = df_neg(ri);
+#pragma unroll
+            for (int k = K0; k <= K1; ++k) {
+                if (k > Q || j + k > P) break;
+                const float4 *Bn = Lb + tri(j + k, 0);
+#pragma unroll
+                for (int l = 0; l <= k; ++l) {
+                    const int t = tri(k, l) - T0;
+                    const float4 b1 = Bn[mu + l];
+                    const df b1x{b1.x, b1.y}, b1y{b1.z, b1.w};
+                    dacc_add_prod(ar[t], rr, b1x);
+                    dacc_add_prod(ar[t], nri, b1y);
+                    dacc_add_prod(ai[t], rr, b1y);
+                    dacc_add_prod(ai[t], ri, b1x);
+                    if (mu > 0) {
+                        // B_n^{m2}, m2 = l - mu: (-1)^m2 conj B_n^{-m2} when m2 < 0; times (-1)^mu, then
+                        // conj(R_j^mu) B'': Re = rr b''x + ri b''y, Im = rr b''y - ri b''x
+                        const int m2 = l - mu;
+                        const float4 b2 = Bn[m2 < 0 ? -m2 : m2];
+                        const bool neg = m2 < 0, sm2 = neg && (m2 & 1);
+                        const df bx = df_negif(df{b2.x, b2.y}, smu != sm2);
+                        const df by = df_negif(df{b2.z, b2.w}, smu != (neg != sm2));
+                        dacc_add_prod(ar[t], rr, bx);
+                        dacc_add_prod(ar[t], ri, by);
+                        dacc_add_prod(ai[t], rr, by);
+                        dacc_add_prod(ai[t], nri, bx);
+                    }
+                }
+            }
+        }
+    }
+    double pk = 1.0;
+#pragma unroll
+    for (int k = 0; k < K0; ++k) pk *= ratio;
+#pragma unroll
+    for (int k = K0; k <= K1; ++k) {
+        if (add && k > Q) break;
+#pragma unroll
+        for (int l = 0; l <= k; ++l) {
+            const int t = tri(k, l) - T0;
+            double2 v = make_double2(df_to(dacc_get(ar[t])) * pk, df_to(dacc_get(ai[t])) * pk);
+            if (add) {
+                const double2 o = Ac[tri(k, l)];
+                v = make_double2(o.x + v.x, o.y + v.y);
+            }
+            Ac[tri(k, l)] = v;
+            if (Acf) {
+                const df re = df_from(v.x), im = df_from(v.y);
+                Acf[tri(k, l)] = make_float4(re.h, re.l, im.h, im.l);
+            }
+        }
+        pk *= ratio;
+    }
+}
+
+// All output rows k <= KMAX (at most Q of them used) in passes whose accumulators fit in registers.
+template <int KMAX>
+__device__ __forceinline__ void l2x_passes(int P, int Q, df ux, df uy, df uz, double ratio, const float4 *Lb,
+                                           double2 *Ac, float4 *Acf, bool add)
+{
+    if constexpr (KMAX <= 4) {
+        l2q_pass<0, 4>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+    } else {
+        l2q_pass<0, 5>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        l2q_pass<6, 8>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 9) l2q_pass<9, 10>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 11) l2q_pass<11, 12>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 13) l2q_pass<13, 14>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 15) l2q_pass<15, 15>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 16) l2q_pass<16, 16>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 17) l2q_pass<17, 17>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 18) l2q_pass<18, 18>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 19) l2q_pass<19, 19>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+        if constexpr (KMAX >= 20) l2q_pass<20, 20>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add);
+    }
+}
+
+// One thread per QBX center (sorted order): A (+)= L2QBXL of its box's local at the box's order.
+template <int QM>
+__global__ void __launch_bounds__(128) k_l2qbxl(int64_t nc, const int *ctr_box, const double *cxyz, const double *cr,
+                                                const signed char *qc, const signed char *pb, const double *cen,
+                                                const double *hw, const float4 *Bf, int pm_stride, double2 *A, int add)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nc) return;
+    const int b = ctr_box[i];
+    const int Q = min((int)qc[i], QM), P = min((int)pb[b], PMAX);
+    const double h = hw[b], hinv = 1.0 / h;
+    const df ux = df_from((cen[3 * b] - cxyz[i]) * hinv), uy = df_from((cen[3 * b + 1] - cxyz[nc + i]) * hinv),
+             uz = df_from((cen[3 * b + 2] - cxyz[2 * nc + i]) * hinv);
+    const double ratio = cr[i] * hinv;
+    const float4 *Lb = Bf + (int64_t)b * pm_stride;
+    l2x_passes<QM>(P, Q, ux, uy, uz, ratio, Lb, A + i * ntri(QM), nullptr, add);
+}
+
+// Stage 7, one level: one thread per box b of the level with targets below it; its local receives
+// its parent's local translated to b's center (the same regrouping with u = (c_parent - c_b)/h_parent,
+// a corner of the parent's half-width cube, and the box scaling ratio 1/2), at b's order from the
+// parent's order.  B (FP64) is updated and its double-float copy Bf written for b's children and
+// for L2QBXL.
+// Number of output passes of l2x_passes<KMAX> and one of them by index.
+__host__ __device__ constexpr int l2x_npass(int kmax)
+{
+    return kmax <= 4 ? 1 : kmax <= 8 ? 2 : kmax <= 10 ? 3 : kmax <= 12 ? 4 : kmax <= 14 ? 5 : kmax - 9;
+}
+
+template <int KMAX>
+__device__ __forceinline__ void l2x_one_pass(int pass, int P, int Q, df ux, df uy, df uz, double ratio,
+                                             const float4 *Lb, double2 *Ac, float4 *Acf, bool add, const float4 *Rtab)
+{
+    static_assert(KMAX >= 10, "passes of the box-to-box translations");
+    switch (pass) {
+    case 0: l2q_pass<0, 5>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 1: l2q_pass<6, 8>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 2: l2q_pass<9, 10>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 3: if constexpr (KMAX >= 11) l2q_pass<11, 12>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 4: if constexpr (KMAX >= 13) l2q_pass<13, 14>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 5: if constexpr (KMAX >= 15) l2q_pass<15, 15>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 6: if constexpr (KMAX >= 16) l2q_pass<16, 16>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 7: if constexpr (KMAX >= 17) l2q_pass<17, 17>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 8: if constexpr (KMAX >= 18) l2q_pass<18, 18>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 9: if constexpr (KMAX >= 19) l2q_pass<19, 19>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    case 10: if constexpr (KMAX >= 20) l2q_pass<20, 20>(P, Q, ux, uy, uz, ratio, Lb, Ac, Acf, add, Rtab); break;
+    default: break;
+    }
+}
+
+// Stage 7, one level: one thread per (box b of the level with targets below it, output pass); b's
+// local receives its parent's local translated to b's center (the same regrouping with
+// u = (c_parent - c_b)/h_parent, a corner of the parent's half-width cube, whose harmonics are
+// tabulated, and the box scaling ratio 1/2), at b's order from the parent's order.  The passes of
+// a box write disjoint rows.  B (FP64) is updated and its double-float copy Bf written for b's
+// children and for L2QBXL.  Thread index = pass * (boxes of the level) + box, so a warp runs one pass.
+template <int PB>
+__global__ void __launch_bounds__(128) k_l2l_df(int b0, int b1, const int *lvl_boxes, const int *parent,
+                                                const int *ntgt_sub, const int *child, const signed char *pb,
+                                                const float4 *octf, int stride, double2 *B, float4 *Bf)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nbl = b1 - b0;
+    if (g >= (int64_t)nbl * l2x_npass(PB)) return;
+    const int pass = (int)(g / nbl);
+    int b = b0 + (int)(g % nbl);
+    if (lvl_boxes) b = lvl_boxes[b];
+    if (ntgt_sub[b] == 0) return;
+    const int pa = parent[b];
+    if (pa < 0) return;
+    int o = 0;
+    while (o < 8 && child[8 * pa + o] != b) ++o;
+    if (o == 8) return;
+    const df ux{(o & 1) ? -0.5f : 0.5f, 0.f}, uy{(o & 2) ? -0.5f : 0.5f, 0.f}, uz{(o & 4) ? -0.5f : 0.5f, 0.f};
+    l2x_one_pass<PB>(pass, min((int)pb[pa], PMAX), min((int)pb[b], PB), ux, uy, uz, 0.5, Bf + (int64_t)pa * stride,
+                     B + (int64_t)b * stride, Bf + (int64_t)b * stride, true, octf + (7 - o) * stride);
+}
+
+// Double-float copy of the locals of the boxes [b0, b1) of one level (the roots before Stage 7).
+__global__ void k_level_to_df(int b0, int b1, const int *lvl_boxes, int stride, const signed char *pb,
+                              const double2 *B, float4 *Bf)
+{
+    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= (int64_t)(b1 - b0) * stride) return;
+    int b = b0 + (int)(q / stride);
+    if (lvl_boxes) b = lvl_boxes[b];
+    const int t = (int)(q % stride);
+    if (t >= ntri(min((int)pb[b], PMAX))) return;
+    const double2 v = B[(int64_t)b * stride + t];
+    const df re = df_from(v.x), im = df_from(v.y);
+    Bf[(int64_t)b * stride + t] = make_float4(re.h, re.l, im.h, im.l);
+}
+
+// Legendre-recurrence coefficients of T_n = A_n (x u) T_{n-1} - B_n x^2 T_{n-2}, A_n = (2n-1)/n,
+// B_n = (n-1)/n, as double-floats (leading, trailing): c_leg[n] = (A_h, A_l, B_h, B_l).
+__constant__ float4 c_leg[QMAX + 1];
+
+void set_leg_table(cudaStream_t st)
+{
+    static float4 t[QMAX + 1];
+    for (int n = 1; n <= QMAX; ++n) {
+        const double A = (2.0 * n - 1.0) / n, B = (n - 1.0) / n;
+        const float ah = (float)A, bh = (float)B;
+        t[n] = make_float4(ah, (float)(A - (double)ah), bh, (float)(B - (double)bh));
+    }
+    t[0] = make_float4(0.f, 0.f, 0.f, 0.f);
+    QBX_CUDA_TRY(cudaMemcpyToSymbolAsync(c_leg, t, sizeof(t), 0, cudaMemcpyHostToDevice, st));
+}
+
+__device__ __forceinline__ df df_warp_sum(df v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1)
+        v = df_add(v, df{__shfl_xor_sync(0xffffffffu, v.h, off), __shfl_xor_sync(0xffffffffu, v.l, off)});
+    return v;
+}
 
 // Stages 3, 5(a), 6(a) + 9 for one QBX target: the order-Q QBX expansion about its center c of the
 // sources of List 1, List 3 close and List 4 close of c's box, evaluated at the target t.  By the
@@ -862,16 +1463,16 @@ __global__ void __launch_bounds__(128) k_centers(
 //   T_n = (2n-1)/n (x u) T_{n-1} - (n-1)/n x^2 T_{n-2},   T'_n = (2n-1) x T_{n-1} + x^2 T'_{n-2}.
 // The value is sum_s [q sum_n T_n + (1/r) sum_n ((d.a - u d.e) T'_n - (n+1)(d.e) T_n)] / r, the same
 // truncated expansion as the coefficient form up to rounding, at O(Q) work per (source, target) pair
-// instead of O(Q^2) per (source, center).  One warp per target; lanes take the sources of the three
-// lists walked as one sequence of boxes.  out[t] (input order) receives the sum without 1/(4 pi); with
-// SWEEP, out[n * nt + t] receives the order-n part for n = 0..QM.
+// instead of O(Q^2) per (source, center).  Arithmetic in double-float (df64.cuh) from double-float
+// copies of the points and densities (k_to_df).  One warp per target; lanes take the sources of the
+// three lists walked as one sequence of boxes.  out[t] (input order) receives the sum without
+// 1/(4 pi); with SWEEP, out[n * nt + t] receives the order-n part for n = 0..QM.
 template <int QM, bool SWEEP>
-__global__ void __launch_bounds__(128) k_qbx_direct(int64_t nt, const int *tperm, const double *txyz,
-                                                    const int *tgt_ctr, const int *ctr_rank, const int *ctr_box,
-                                                    int64_t nc, const double *cxyz, const signed char *qc, ListRef lu,
-                                                    ListRef lwc, ListRef lxc, const int *own_start,
-                                                    const double *sxyz, int64_t ns, const double *sq,
-                                                    const double *sd, double *out)
+__global__ void __launch_bounds__(128) k_qbx_direct(int64_t nt, const int *tperm, const float *tf, const int *tgt_ctr,
+                                                    const int *ctr_rank, const int *ctr_box, int64_t nc,
+                                                    const float *cf, const signed char *qc, ListRef lu, ListRef lwc,
+                                                    ListRef lxc, const int *own_start, int64_t ns, const float *sf,
+                                                    int dip, double *out)
 {
     const int wl = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t it = (int64_t)blockIdx.x * 4 + wl;
@@ -881,17 +1482,21 @@ __global__ void __launch_bounds__(128) k_qbx_direct(int64_t nt, const int *tperm
     if (c < 0 || c >= nc) return;  // point targets (out of range indices are flagged by the argument check)
     const int i = ctr_rank[c], b = ctr_box[i];
     const int Q = min((int)qc[i], QM);
-    const double cx = cxyz[i], cy = cxyz[nc + i], cz = cxyz[2 * nc + i];
-    double ax = txyz[it] - cx, ay = txyz[nt + it] - cy, az = txyz[2 * nt + it] - cz;
-    const double rho = sqrt(ax * ax + ay * ay + az * az);
-    const double rhoinv = rho > 0.0 ? 1.0 / rho : 0.0;  // t = c: only the n = 0 terms remain
-    ax *= rhoinv;
-    ay *= rhoinv;
-    az *= rhoinv;
-    const bool dip = sd != nullptr;
-    double acc[SWEEP ? QM + 1 : 1];
+    const df cx{cf[i], cf[3 * nc + i]}, cy{cf[nc + i], cf[4 * nc + i]}, cz{cf[2 * nc + i], cf[5 * nc + i]};
+    df ax = df_sub(df{tf[it], tf[3 * nt + it]}, cx), ay = df_sub(df{tf[nt + it], tf[4 * nt + it]}, cy),
+       az = df_sub(df{tf[2 * nt + it], tf[5 * nt + it]}, cz);
+    const df rho2 = df_add(df_add(df_sqr(ax), df_sqr(ay)), df_sqr(az));
+    df rho{0.f, 0.f};
+    if (rho2.h > 0.f) {  // t = c: a = 0 and rho = 0, only the n = 0 terms remain
+        const df ri = df_rsqrt(rho2);
+        rho = df_mul(rho2, ri);
+        ax = df_mul(ax, ri);
+        ay = df_mul(ay, ri);
+        az = df_mul(az, ri);
+    }
+    df acc[SWEEP ? QM + 1 : 1];
 #pragma unroll
-    for (int n = 0; n < (SWEEP ? QM + 1 : 1); ++n) acc[n] = 0.0;
+    for (int n = 0; n < (SWEEP ? QM + 1 : 1); ++n) acc[n] = df{0.f, 0.f};
     const int u0 = lu.start[b], n0 = lu.start[b + 1] - u0;
     const int w0 = lwc.start[b], n1 = lwc.start[b + 1] - w0;
     const int x0 = lxc.start[b], n2 = lxc.start[b + 1] - x0;
@@ -924,48 +1529,49 @@ __global__ void __launch_bounds__(128) k_qbx_direct(int64_t nt, const int *tperm
             const int cj = __shfl_sync(0xffffffffu, cnt, j);
             if (k >= total) continue;
             const int s = sj + (k - (ij - cj));
-            const double ex = sxyz[s] - cx, ey = sxyz[ns + s] - cy, ez = sxyz[2 * ns + s] - cz;
-            const double rinv = rsqrt(ex * ex + ey * ey + ez * ez);
-            const double u = (ax * ex + ay * ey + az * ez) * rinv;
-            const double x = rho * rinv, x2 = x * x, xu = x * u;
-            const double q = sq[s];
-            double alpha = 0.0, dE = 0.0;
+            const df ex = df_sub(df{sf[s], sf[3 * ns + s]}, cx), ey = df_sub(df{sf[ns + s], sf[4 * ns + s]}, cy),
+                     ez = df_sub(df{sf[2 * ns + s], sf[5 * ns + s]}, cz);
+            const df rinv = df_rsqrt(df_add(df_add(df_sqr(ex), df_sqr(ey)), df_sqr(ez)));
+            const df u = df_mul(df_add(df_add(df_mul(ax, ex), df_mul(ay, ey)), df_mul(az, ez)), rinv);
+            const df x = df_mul(rho, rinv), x2 = df_sqr(x), xu = df_mul(x, u);
+            const df q{sf[6 * ns + s], sf[7 * ns + s]};
+            df alpha{0.f, 0.f}, dE{0.f, 0.f};
             if (dip) {
-                const double dx = sd[s], dy = sd[ns + s], dz = sd[2 * ns + s];
-                dE = (dx * ex + dy * ey + dz * ez) * rinv;
-                alpha = (dx * ax + dy * ay + dz * az) - u * dE;
+                const df dx{sf[8 * ns + s], sf[11 * ns + s]}, dy{sf[9 * ns + s], sf[12 * ns + s]},
+                    dz{sf[10 * ns + s], sf[13 * ns + s]};
+                dE = df_mul(df_add(df_add(df_mul(dx, ex), df_mul(dy, ey)), df_mul(dz, ez)), rinv);
+                alpha = df_sub(df_add(df_add(df_mul(dx, ax), df_mul(dy, ay)), df_mul(dz, az)), df_mul(u, dE));
             }
             // n = 0: T_0 = 1, T'_0 = 0
-            double T2 = 0.0, T1 = 1.0, D2 = 0.0, D1 = 0.0;
-            double sc = q, sdp = -dE;  // charge part and dipole part (times r), order by order
-            if (SWEEP) acc[0] += rinv * (q - dE * rinv);
+            df T2{0.f, 0.f}, T1{1.f, 0.f}, D2{0.f, 0.f}, D1{0.f, 0.f};
+            df L{1.f, 0.f}, sdp = df_neg(dE);  // sum of T_n; dipole part (times r), order by order
+            if (SWEEP) acc[0] = df_add(acc[0], df_mul(rinv, df_sub(q, df_mul(dE, rinv))));
 #pragma unroll
             for (int n = 1; n <= QM; ++n) {
                 if (n > Q) break;
-                const double Tn = fma((2.0 * n - 1.0) / n * xu, T1, -((n - 1.0) / n) * x2 * T2);
+                const float4 cl = c_leg[n];
+                const df Tn = df_sub(df_mul(df_mul(df{cl.x, cl.y}, xu), T1), df_mul(df_mul(df{cl.z, cl.w}, x2), T2));
                 T2 = T1;
                 T1 = Tn;
-                sc = fma(q, Tn, sc);
+                if (!SWEEP) L = df_add(L, Tn);
                 if (dip) {
-                    const double Dn = fma((2.0 * n - 1.0) * x, T2, x2 * D2);
+                    const df Dn = df_add(df_mul(df_mul_f(x, 2.0f * n - 1.0f), T2), df_mul(x2, D2));
                     D2 = D1;
                     D1 = Dn;
-                    const double term = fma(alpha, Dn, -(n + 1.0) * dE * Tn);
-                    sdp += term;
-                    if (SWEEP) acc[n] += rinv * fma(q, Tn, term * rinv);
+                    const df term = df_sub(df_mul(alpha, Dn), df_mul(df_mul_f(dE, n + 1.0f), Tn));
+                    if (SWEEP) acc[n] = df_add(acc[n], df_mul(rinv, df_add(df_mul(q, Tn), df_mul(term, rinv))));
+                    else sdp = df_add(sdp, term);
                 } else if (SWEEP) {
-                    acc[n] += rinv * q * Tn;
+                    acc[n] = df_add(acc[n], df_mul(df_mul(rinv, q), Tn));
                 }
             }
-            if (!SWEEP) acc[0] += rinv * fma(sdp, rinv, sc);
+            if (!SWEEP) acc[0] = df_add(acc[0], df_mul(rinv, df_add(df_mul(q, L), df_mul(sdp, rinv))));
         }
     }
 #pragma unroll
     for (int n = 0; n < (SWEEP ? QM + 1 : 1); ++n) {
-        double v = acc[n];
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-        if (lane == 0) out[SWEEP ? (int64_t)n * nt + t : t] = v;
+        const df v = df_warp_sum(acc[n]);
+        if (lane == 0) out[SWEEP ? (int64_t)n * nt + t : t] = df_to(v);
     }
 }
 
@@ -1292,19 +1898,27 @@ static void launch_centers(const qbx_tree *T, qbx_lists *L, qbx_workspace *ws, b
         QBX_CUDA_TRY(cudaFuncSetAttribute(k_centers<QM, PM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         attr_set = true;
     }
-    if (T->np[KCTR] > 0) {
+    // k_centers runs when it has work (List 3 far in FP64); k_l2qbxl then adds the box local's part
+    const bool far64 = wf == nullptr;
+    if (T->np[KCTR] > 0 && far64) {
         k_centers<QM, PM_T><<<nblocks(T->np[KCTR], WPB), 32 * WPB, smem, st>>>(
-            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc, ws->pb, ws->ps, ListRef{L->start[LU], L->idx[LU]},
+            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc, ws->ps, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
             ListRef{wf_start, L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,
-            dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->B, ws->A, 0);
+            dip ? ws->sd : nullptr, T->cen, T->hw, ws->Mu, ws->A, 0);
+        QBX_LAUNCH_CHECK();
+    }
+    if (T->np[KCTR] > 0) {
+        k_l2qbxl<QM><<<nblocks(T->np[KCTR], 128), 128, 0, st>>>(T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws->qc,
+                                                                ws->pb, T->cen, T->hw, ws->Bf, ntri(PM_T), ws->A,
+                                                                far64 ? 1 : 0);
         QBX_LAUNCH_CHECK();
     }
     if (T->np[KTGT] > 0 && T->np[KCTR] > 0) {
         k_qbx_direct<QM, false><<<nblocks(T->np[KTGT], 4), 128, 0, st>>>(
-            T->np[KTGT], T->perm[KTGT], T->txyz, tgt_ctr, T->ctr_rank, T->ctr_box, T->np[KCTR], T->cxyz, ws->qc,
+            T->np[KTGT], T->perm[KTGT], ws->tf, tgt_ctr, T->ctr_rank, T->ctr_box, T->np[KCTR], ws->cf, ws->qc,
             ListRef{L->start[LU], L->idx[LU]}, ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
-            T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq, dip ? ws->sd : nullptr, ws->pd);
+            T->own_start[KSRC], T->np[KSRC], ws->sf, dip ? 1 : 0, ws->pd);
         QBX_LAUNCH_CHECK();
     }
     stage_mark(L, 7, st);
@@ -1336,24 +1950,36 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
         ws->nb = nb; ws->nc = nc; ws->ns = ns;
         ws->Mu = dalloc<double2>(nb * ntri(PM_T));
         ws->B = dalloc<double2>(nb * ntri(PM_T));
+        ws->Bf = dalloc<float4>(nb * ntri(PM_T));
+        ws->Muf = dalloc<float4>(nb * ntri(PM_T));
+        ws->octf = dalloc<float4>(8 * ntri(PM_T));
         ws->A = dalloc<double2>(std::max<int64_t>(nc, 1) * ntri(QM));
         ws->m2l_tab = dalloc<double2>((int64_t)1331 * ntri(2 * PM_T));
         ws->oct_tab = dalloc<double2>(8 * ntri(PM_T));
         ws->sq = dalloc<double>(ns);
         ws->sd = dalloc<double>(3 * ns);
         ws->pd = dalloc<double>(std::max<int64_t>(nt, 1));
+        ws->sf = dalloc<float>(14 * std::max<int64_t>(ns, 1));
+        ws->cf = dalloc<float>(6 * std::max<int64_t>(nc, 1));
+        ws->tf = dalloc<float>(6 * std::max<int64_t>(nt, 1));
         ws->qc = dalloc<signed char>(nc);
         ws->pb = dalloc<signed char>(nb);
         ws->ps = dalloc<signed char>(nb);
         ws->flags = dalloc<int>(1);
+        set_l2q_tables(st);
+        set_leg_table(st);
         k_m2l_table<<<nblocks(1331, 64), 64, 0, st>>>(2 * PM_T, ws->m2l_tab);
         k_oct_table<<<1, 32, 0, st>>>(PM_T, ws->oct_tab);
+        k_c2df<<<nblocks(8 * ntri(PM_T), 256), 256, 0, st>>>(8 * ntri(PM_T), ws->oct_tab, ws->octf);
         QBX_LAUNCH_CHECK();
     }
     (void)pot;
     stage_mark(L, 0, st);
     QBX_CUDA_TRY(cudaMemsetAsync(ws->flags, 0, sizeof(int), st));
     k_prep_src<<<nblocks(ns, 256), 256, 0, st>>>(T->perm[KSRC], ns, w, sigma, mu, nrm, ws->sq, ws->sd, ws->flags);
+    if (ns > 0) k_to_df<<<nblocks(ns, 256), 256, 0, st>>>(ns, T->sxyz, ws->sq, mu ? ws->sd : nullptr, ws->sf);
+    if (nc > 0) k_to_df<<<nblocks(nc, 256), 256, 0, st>>>(nc, T->cxyz, nullptr, nullptr, ws->cf);
+    if (nt > 0) k_to_df<<<nblocks(nt, 256), 256, 0, st>>>(nt, T->txyz, nullptr, nullptr, ws->tf);
     k_prep_orders<<<nblocks(std::max(nb, nc), 256), 256, 0, st>>>(T->perm[KCTR], nc, o->p_qbx_per_ctr, o->p_qbx, nb,
                                                                   o->p_fmm_per_box, o->p_fmm, ws->qc, ws->pb, ws->ps,
                                                                   ws->flags);
@@ -1376,8 +2002,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     stage_mark(L, 1, st);
     // the P2M and P2L kernels unroll their rows: instantiate them for the smallest order bound that covers p_fmm
 #define QBX_P2M(PB)                                                                                                 \
-    k_p2m<PB, PM_T><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], T->sxyz, ns, ws->sq,              \
-                                                           dip ? ws->sd : nullptr, T->cen, T->hw, ws->ps, ws->Mu)
+    k_p2m_df<PB, ntri(PM_T)><<<nblocks(nb, WPB), 32 * WPB, 0, st>>>(nb, T->own_start[KSRC], ns, ws->sf, dip ? 1 : 0,   \
+                                                                    T->cen, T->hw, ws->ps, ws->Mu, ws->Muf)
     if (pmax <= 10) QBX_P2M(10);
     else if (pmax <= 16) QBX_P2M(16);
     else QBX_P2M(PM_T);
@@ -1386,7 +2012,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     for (int l = (int)T->nlev - 2; l >= 0; --l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
         if (b1 > b0)
-            k_m2m8<PM_T><<<b1 - b0, 256, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws->ps, ws->oct_tab, ws->Mu);
+            k_m2m8_df<PM_T><<<b1 - b0, 256, 0, st>>>(b0, b1, T->lvl_boxes, T->child, T->nsrc_sub, ws->ps, ws->octf,
+                                                     ws->Mu, ws->Muf);
         QBX_LAUNCH_CHECK();
     }
     // Stage 4
@@ -1411,8 +2038,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     // Stage 6(b)
     stage_mark(L, 3, st);
 #define QBX_P2L(PB)                                                                                                 \
-    k_p2l4<PB, PM_T><<<(unsigned)nb, 128, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], T->sxyz, ns,   \
-                                                   ws->sq, dip ? ws->sd : nullptr, T->cen, T->hw, ws->pb, ws->B)
+    k_p2l4_df<PB, PM_T><<<(unsigned)nb, 128, 0, st>>>(nb, L->start[LXF], L->idx[LXF], T->own_start[KSRC], ns, ws->sf, \
+                                                      dip ? 1 : 0, T->cen, T->hw, ws->pb, ws->B)
     if (pmax <= 10) QBX_P2L(10);
     else if (pmax <= 16) QBX_P2L(16);
     else QBX_P2L(PM_T);
@@ -1420,10 +2047,21 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     QBX_LAUNCH_CHECK();
     // Stage 7
     stage_mark(L, 4, st);
+    {
+        const int r0 = T->level_start[0], r1 = T->level_start[1];
+        k_level_to_df<<<nblocks((int64_t)(r1 - r0) * ntri(PM_T), 256), 256, 0, st>>>(r0, r1, T->lvl_boxes, ntri(PM_T),
+                                                                                      ws->pb, ws->B, ws->Bf);
+        QBX_LAUNCH_CHECK();
+    }
     for (int l = 1; l < T->nlev; ++l) {
         int b0 = T->level_start[l], b1 = T->level_start[l + 1];
-        k_l2l<PM_T><<<nblocks(b1 - b0, WPB), 32 * WPB, 0, st>>>(b0, b1, T->lvl_boxes, T->parent, T->ntgt_sub, T->child, ws->pb,
-                                                                ws->oct_tab, ws->B);
+#define QBX_L2L(PB)                                                                                                 \
+    k_l2l_df<PB><<<nblocks((int64_t)(b1 - b0) * l2x_npass(PB), 128), 128, 0, st>>>(                                  \
+        b0, b1, T->lvl_boxes, T->parent, T->ntgt_sub, T->child, ws->pb, ws->octf, ntri(PM_T), ws->B, ws->Bf)
+        if (pmax <= 10) QBX_L2L(10);
+        else if (pmax <= 16) QBX_L2L(16);
+        else QBX_L2L(PM_T);
+#undef QBX_L2L
         QBX_LAUNCH_CHECK();
     }
     // Stage 5(b) in mixed precision: List 3 far products, reduced into the QBX locals below
@@ -1440,7 +2078,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
             ws->wfar_key = wkey;
         }
         wf = ws->wfar;
-        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->ps, ws->flags, L->wait_limit, L->probe_step, st);
+        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->ps, ws->cf, ws->flags, L->wait_limit, L->probe_step, st);
     }
     // Stages 3, 5, 6(a), 8, 9 at QBX centers and their targets
     switch (QM) {
@@ -1562,10 +2200,9 @@ void eval_order_sweep(const qbx_tree *T, qbx_lists *L, const double *w, const do
     case QB:                                                                                                     \
         if (T->np[KCTR] > 0)                                                                                     \
             k_qbx_direct<QB, true><<<nblocks(nt, 4), 128, 0, st>>>(                                              \
-                nt, T->perm[KTGT], T->txyz, tgt_ctr, T->ctr_rank, T->ctr_box, T->np[KCTR], T->cxyz, ws->qc,       \
+                nt, T->perm[KTGT], ws->tf, tgt_ctr, T->ctr_rank, T->ctr_box, T->np[KCTR], ws->cf, ws->qc,         \
                 ListRef{L->start[LU], L->idx[LU]}, ListRef{L->start[LWC], L->idx[LWC]},                          \
-                ListRef{L->start[LXC], L->idx[LXC]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws->sq,           \
-                dip ? ws->sd : nullptr, dir);                                                                     \
+                ListRef{L->start[LXC], L->idx[LXC]}, T->own_start[KSRC], T->np[KSRC], ws->sf, dip ? 1 : 0, dir);     \
         k_qbx_partials<QB><<<nblocks(nt, 128), 128, 0, st>>>(nt, o->p_qbx, T->perm[KTGT], T->txyz, tgt_ctr,     \
                                                             T->ctr_rank, T->np[KCTR], T->cxyz, T->cr, ws->A,    \
                                                             dir, partial);                                      \
@@ -1617,6 +2254,7 @@ size_t fixed_workspace_bytes(const qbx_tree *T, const qbx_eval_opts *o)
     size_t off = 0;
     carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2));                 // Mu
     carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2));                 // B
+    carve(off, (size_t)nb * ntri(PM_T) * sizeof(float4));                  // B as double-floats
     carve(off, (size_t)std::max<int64_t>(nc, 1) * ntri(QM) * sizeof(double2));  // A
     carve(off, (size_t)1331 * ntri(2 * PM_T) * sizeof(double2));           // List 2 offset table
     carve(off, (size_t)8 * ntri(PM_T) * sizeof(double2));                  // octant table
@@ -1638,10 +2276,14 @@ static void fixed_centers(const qbx_tree *T, const qbx_lists *L, const qbx_works
     QBX_CUDA_TRY(cudaFuncSetAttribute(k_centers<QM, PM_T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     if (T->np[KCTR] > 0) {
         k_centers<QM, PM_T><<<nblocks(T->np[KCTR], WPB), 32 * WPB, smem, st>>>(
-            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws.qc, ws.pb, ws.ps, ListRef{L->start[LU], L->idx[LU]},
+            T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws.qc, ws.ps, ListRef{L->start[LU], L->idx[LU]},
             ListRef{L->start[LWC], L->idx[LWC]}, ListRef{L->start[LXC], L->idx[LXC]},
             ListRef{L->start[LWF], L->idx[LWF]}, T->own_start[KSRC], T->sxyz, T->np[KSRC], ws.sq,
-            dip ? ws.sd : nullptr, T->cen, T->hw, ws.Mu, ws.B, ws.A, 1);
+            dip ? ws.sd : nullptr, T->cen, T->hw, ws.Mu, ws.A, 1);
+        QBX_LAUNCH_CHECK();
+        k_locals_to_df<<<nblocks(T->nb * ntri(PM_T), 256), 256, 0, st>>>(T->nb, ntri(PM_T), ws.pb, ws.B, ws.Bf);
+        k_l2qbxl<QM><<<nblocks(T->np[KCTR], 128), 128, 0, st>>>(T->np[KCTR], T->ctr_box, T->cxyz, T->cr, ws.qc, ws.pb,
+                                                                T->cen, T->hw, ws.Bf, ntri(PM_T), ws.A, 1);
         QBX_LAUNCH_CHECK();
     }
     if (T->np[KTGT] > 0) {
@@ -1663,6 +2305,7 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     size_t off = 0;
     ws.Mu = reinterpret_cast<double2 *>(base + carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2)));
     ws.B = reinterpret_cast<double2 *>(base + carve(off, (size_t)nb * ntri(PM_T) * sizeof(double2)));
+    ws.Bf = reinterpret_cast<float4 *>(base + carve(off, (size_t)nb * ntri(PM_T) * sizeof(float4)));
     ws.A = reinterpret_cast<double2 *>(base + carve(off, (size_t)std::max<int64_t>(nc, 1) * ntri(QM) * sizeof(double2)));
     ws.m2l_tab = reinterpret_cast<double2 *>(base + carve(off, (size_t)1331 * ntri(2 * PM_T) * sizeof(double2)));
     ws.oct_tab = reinterpret_cast<double2 *>(base + carve(off, (size_t)8 * ntri(PM_T) * sizeof(double2)));
@@ -1675,6 +2318,8 @@ void eval_fixed(const qbx_tree *T, const qbx_lists *L, unsigned char *base, size
     ws.PM = PM_T;
     ws.QM = QM;
 
+    set_l2q_tables(st);
+    set_leg_table(st);
     k_m2l_table<<<nblocks(1331, 64), 64, 0, st>>>(2 * PM_T, ws.m2l_tab);
     k_oct_table<<<1, 32, 0, st>>>(PM_T, ws.oct_tab);
     QBX_LAUNCH_CHECK();
