@@ -160,78 +160,120 @@ def m2m_macs(P):
     return n_mac
 
 
+# FP32 instructions of the double-float operations (csrc/df64.cuh): a double-float sum 11, product 7,
+# product by a float 6, square 7, compensated product-accumulate 12, reciprocal square root 38
+DF_ADD, DF_MUL, DF_MULF, DF_SQR, DF_DOT, DF_RSQRT = 11, 7, 6, 7, 12, 38
+
+
+def direct_pair_instr(Q, dipole):
+    """FP32 instructions of the direct QBX sum per (source, QBX target) pair (k_qbx_direct, the Legendre
+    form in double-float): the geometry, 1/r, cosine and ratios, then per order n >= 1 the recurrence of
+    x^n P_n and its running sum, and the final scaling; with a dipole its two projections and per order the
+    recurrence of x^n P_n' and the dipole term."""
+    setup = 3 * DF_ADD + 3 * DF_SQR + 2 * DF_ADD + DF_RSQRT + 3 * DF_MUL + 2 * DF_ADD + 4 * DF_MUL + DF_SQR
+    per_n = 4 * DF_MUL + 2 * DF_ADD
+    end = 4 * DF_MUL + 2 * DF_ADD
+    n = setup + Q * per_n + end
+    if dipole:
+        n += 2 * (4 * DF_MUL + 2 * DF_ADD) + DF_ADD + DF_MUL
+        n += Q * (2 * DF_MULF + 4 * DF_MUL + 3 * DF_ADD)
+    return n
+
+
 def pair_flops(Q, dipole):
-    """Direct QBX sum per (source, QBX target) pair, the Legendre form of the order-Q expansion
-    (k_qbx_direct): geometry, 1/r, cosine and ratios 20 + 3 at the end; per order n >= 1 the
-    recurrence of x^n P_n and the charge accumulation 7; with a dipole 12 more in the setup and 9 more
-    per order (the recurrence of x^n P_n' and the dipole term)."""
+    """FP64-equivalent flops of the same pair: 20 + 3 for the geometry, 7 per order, 12 + 9 per order with a dipole."""
     return 23 + 7 * Q + ((12 + 9 * Q) if dipole else 0)
 
 
-def p2x_flops(p, dipole):
-    """P2M / P2L per (source, box) pair of order p: harmonics to p + 1 plus the accumulation."""
-    return 8 * _tri(p + 1) + (22 if dipole else 4) * _tri(p)
+def p2x_instr(p, dipole):
+    """FP32 instructions of P2M / P2L per (source, box) pair of order p (k_p2m_df, k_p2l4_df): per lane
+    of the p + 1 columns the geometry and the diagonal's prefix product over five lane steps, per
+    coefficient its recurrence step and the compensated accumulation (four products with a dipole)."""
+    lane = 3 * DF_ADD + 3 * DF_MULF + 3 * DF_SQR + 2 * DF_ADD + DF_RSQRT + 3 * DF_MUL + 5 * (4 * DF_MUL + 2 * DF_ADD)
+    coef = 2 * DF_MULF + 4 * DF_MUL + 2 * DF_ADD + (8 if dipole else 2) * DF_DOT
+    return (p + 1) * lane + _tri(p) * coef
 
 
 def stage_work(cost, P, Q, dipole, mixed, ctr_order, box_order, parent, has_tgt_sub, src_boxes_nonroot,
                n_src, direct_pairs=None):
-    """Algorithmic work per stage: {stage: (flops, kind)} with kind "fp64" or "tf32" (3-pass tensor)."""
+    """Algorithmic work per stage: {stage: (amount, kind)}.  kind "df": FP32 instructions of the
+    double-float kernels (amount in instructions); "fp64": FP64 flops; "tf32": FP32-equivalent flops of
+    the 3-pass tensor products."""
     c = cost["count"]
     direct = c["U"] + c["Wclose"] + c["Xclose"] if direct_pairs is None else direct_pairs
     work = {}
-    # centers: direct QBX sums per (source, QBX target) pair, L2QBXL per center at its box's order, List 3
-    # far M2QBXL in FP64 mode; with one QBX target per center the pairs are the direct list counts
-    l2q = sum(int(n) * (8 * _tri(int(p)) + 8 * l2qbxl_macs(int(p), Q))
+    # centers: direct QBX sums per (source, QBX target) pair, L2QBXL per center at its box's order (each
+    # complex multiply-add four compensated products; the harmonics' recurrence per pass), List 3 far
+    # M2QBXL in FP64 mode; with one QBX target per center the pairs are the direct list counts
+    npass = 1 if Q <= 4 else 2 if Q <= 8 else 4 if Q <= 12 else 7
+    l2q = sum(int(n) * (4 * DF_DOT * l2qbxl_macs(int(p), Q) + npass * _tri(int(p)) * (2 * DF_MULF + 6 * DF_MUL
+                                                                                         + 2 * DF_ADD))
               for p, n in zip(*np.unique(ctr_order, return_counts=True)))
-    f_centers = pair_flops(Q, dipole) * direct + l2q
-    if not mixed:
-        f_centers += c["Wfar"] * (8 * _tri(P + Q) + 8 * (P + 1) ** 2 * _tri(Q) + 2 * (P + 1) ** 2)
-    work["centers"] = (float(f_centers), "fp64")
+    work["centers"] = (float(direct_pair_instr(Q, dipole) * direct + l2q), "df")
     if mixed:
         D = (P + 1) ** 2
         work["m2l"] = (3.0 * 2.0 * D * D * c["V"], "tf32")
         work["m2qbxl_mixed"] = (3.0 * 2.0 * (Q + 1) ** 2 * (P + Q + 1) ** 2 * c["Wfar"], "tf32")
     else:
         work["m2l"] = (8.0 * _tri(P) * (P + 1) ** 2 * c["V"], "fp64")  # m >= 0 outputs x all inputs
-    work["p2l"] = (float(p2x_flops(P, dipole)) * c["Xfar"], "fp64")
+    work["p2l"] = (float(p2x_instr(P, dipole)) * c["Xfar"], "df")
     # L2L: every box with targets below it receives its parent's local at the parent's order
     b = np.nonzero(has_tgt_sub & (parent >= 0))[0]
     keys, counts = np.unique(box_order[b].astype(np.int64) * 64 + box_order[parent[b]], return_counts=True)
-    work["l2l"] = (float(sum(8 * l2l_macs(int(k) // 64, int(k) % 64) * int(n) for k, n in zip(keys, counts))), "fp64")
-    work["p2m_m2m"] = (float(p2x_flops(P, dipole)) * n_src + 8.0 * m2m_macs(P) * src_boxes_nonroot, "fp64")
+    work["l2l"] = (float(sum(4 * DF_DOT * l2l_macs(int(k) // 64, int(k) % 64) * int(n)
+                             for k, n in zip(keys, counts))), "df")
+    work["p2m_m2m"] = (float(p2x_instr(P, dipole)) * n_src + 4.0 * DF_DOT * m2m_macs(P) * src_boxes_nonroot, "df")
     return work
 
 
 def roofline_table(work, stage_ms, peaks):
-    """Per stage above 2% of the step: achieved rate against the measured peak of its arithmetic."""
+    """Per stage above 2% of the step: achieved rate against the measured peak of its arithmetic.  The
+    double-float stages count FP32 instructions against the FP32 FMA pipe's instruction rate (half the
+    measured FP32 flop rate)."""
     tot = sum(stage_ms.values())
     out = {}
-    for k, (flops, kind) in work.items():
+    for k, (amount, kind) in work.items():
         ms = stage_ms.get(k, 0.0)
         if ms <= 0 or ms < 0.02 * tot:
             continue
-        peak = peaks["fp64_tflops"] if kind == "fp64" else peaks["tf32_tflops"]
-        ach = flops / (ms * 1e-3) / 1e12
-        out[k] = {"ms": ms, "share": ms / tot, "bound": "alu" if kind == "fp64" else "tensor",
-                  "arith": "FP64 FMA pipe" if kind == "fp64" else "TF32 tensor (3 passes per split-TF32 product)",
-                  "tflop": flops / 1e12, "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak}
+        if kind == "df":
+            peak, unit, bound, arith = peaks["fp32_tflops"] / 2, "Tinst/s", "alu", "FP32 pipe (double-float)"
+        elif kind == "fp64":
+            peak, unit, bound, arith = peaks["fp64_tflops"], "TFLOP/s", "alu", "FP64 FMA pipe"
+        else:
+            peak, unit, bound, arith = (peaks["tf32_tflops"], "TFLOP/s", "tensor",
+                                        "TF32 tensor (3 passes per split-TF32 product)")
+        ach = amount / (ms * 1e-3) / 1e12
+        out[k] = {"ms": ms, "share": ms / tot, "bound": bound, "arith": arith, "work_T": amount / 1e12,
+                  "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak}
     return out
 
 
-def kernel_traffic():
-    """DRAM bytes per launch of the center kernel from the committed ncu summary, or None when the
-    kernel source changed since those counters were taken."""
+STAGE_KERNELS = {
+    "centers": ("k_qbx_direct + k_l2qbxl (direct QBX sums and L2QBXL, double-float)", ("eval.cu", "df64.cuh")),
+    "m2qbxl_mixed": ("k_wfar_H_tc + k_wfar_tc (List 3 far M2QBXL, split-TF32 tcgen05)", ("m2qbxl_mixed.cu",)),
+    "m2l": ("k_mhat_tc + k_m2l_tc + k_m2l_reduce (List 2 M2L, split-TF32 tcgen05)", ("m2l_mixed.cu",)),
+    "l2l": ("k_l2l_df (L2L, double-float)", ("eval.cu", "df64.cuh")),
+    "p2l": ("k_p2l4_df (List 4 far P2L, double-float)", ("eval.cu", "df64.cuh")),
+    "p2m_m2m": ("k_p2m_df + k_m2m8_df (P2M, M2M, double-float)", ("eval.cu", "df64.cuh")),
+}
+
+
+def kernel_traffic(stage):
+    """DRAM bytes per launch of a stage's kernels from the committed ncu summary
+    (profiles/traffic.json), or None when there is none or the kernels' sources changed since."""
     import hashlib
 
-    prof_path = os.path.join(ROOT, "profiles", "traffic_centers_star8k.json")
     try:
-        rec = json.load(open(prof_path))
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json"))).get(stage)
+        if not rec:
+            return None
         src = b"".join(open(os.path.join(ROOT, "paper_1805_06106_gb300", "csrc", f), "rb").read()
-                       for f in ("eval.cu", "harmonics.cuh"))
+                       for f in STAGE_KERNELS[stage][1])
         if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
             return None
         return rec.get("bytes_per_launch")
-    except (OSError, ValueError):
+    except (OSError, ValueError, KeyError):
         return None
 
 
@@ -653,10 +695,9 @@ def run_gpu(args):
             torch.distributed.destroy_process_group()
         return
 
-    c_roof = roof.get("centers")
-    centers_flops = work["centers"][0]
-    centers_ms = stage_ms["centers"]
-    achieved = centers_flops / (centers_ms * 1e-3) / 1e12
+    # the dominant stage's kernels (largest share of the step among the modelled stages)
+    top = max(roof, key=lambda k: roof[k]["ms"])
+    t_roof = roof[top]
     line = {
         "metric": METRIC, "value": value, "unit": "QBX target evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -692,17 +733,18 @@ def run_gpu(args):
         "e2e": {"value": e2e_value, "unit": "QBX target evals/s", "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "matches_device_result": e2e_ok},
         "gpu_launches": library_launches(nlev, mixed) * args.steps,
-        "roofline": {"kernel": "k_centers (L2QBXL + direct P2QBXL" + ("" if mixed else ", List 3 far M2QBXL")
-                               + ", FP64)", "bound": "alu", "achieved": achieved, "peak": peaks["fp64_tflops"],
-                     "unit": "TFLOP/s", "frac": achieved / peaks["fp64_tflops"], "traffic": kernel_traffic(),
-                     "flops_per_launch": centers_flops,
-                     "peak_source": "measured FP64 FMA throughput (qbx_peak_flops) in this run"},
+        "roofline": {"stage": top, "kernel": STAGE_KERNELS.get(top, (top,))[0], "bound": t_roof["bound"],
+                     "achieved": t_roof["achieved"], "peak": t_roof["peak"], "unit": t_roof["unit"],
+                     "frac": t_roof["frac"], "traffic": kernel_traffic(top), "work_per_launch": work[top][0],
+                     "ms_per_launch": t_roof["ms"], "arith": t_roof["arith"],
+                     "peak_source": ("measured in this run: FP32 FMA throughput (qbx_peak_flops) / 2 = FP32 "
+                                     "instructions/s" if t_roof["unit"] == "Tinst/s" else
+                                     "measured in this run: TF32 cuBLAS GEMM" if t_roof["bound"] == "tensor" else
+                                     "measured in this run: FP64 FMA throughput (qbx_peak_flops)")},
         "roofline_stages": roof,
         "peaks": peaks,
         "clocks": clk.summary(),
     }
-    if c_roof is None:
-        line["roofline"]["note"] = "center kernel below 2% of the step"
     if mode == "learned":
         line["learned_orders"] = {**info, **(learned_work or {})}
     if fixed_mixed is not None:
