@@ -38,8 +38,8 @@ void free_wfar_plan(WfarPlan *p);
 int wfar_plan_orders(const WfarPlan *p);
 const int *wfar_empty_start(const WfarPlan *p);
 WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, bool tc, int w_hint, cudaStream_t st);
-void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, int *err,
-                    long long wait_limit, int probe_step, cudaStream_t st);
+void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, const float *cf,
+                    int *err, long long wait_limit, int probe_step, cudaStream_t st);
 void wfar_mixed_reduce(const qbx_tree *T, WfarPlan *pl, int QMS, const signed char *qc, double2 *A, cudaStream_t st);
 
 
@@ -2078,7 +2078,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
             ws->wfar_key = wkey;
         }
         wf = ws->wfar;
-        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->ps, ws->flags, L->wait_limit, L->probe_step, st);
+        wfar_mixed_run(T, wf, PM_T, ws->Mu, ws->ps, ws->cf, ws->flags, L->wait_limit, L->probe_step, st);
     }
     // Stages 3, 5, 6(a), 8, 9 at QBX centers and their targets
     switch (QM) {

@@ -17,6 +17,7 @@
 
 #include "harmonics.cuh"
 #include "tc_common.cuh"
+#include "df64.cuh"
 
 namespace qbx {
 
@@ -47,6 +48,7 @@ struct WfarPlan {
     int Rp = 0, Kp = 0, nch = 0, WMAX = 0, ntc = 0, NU = 0;
     int cj0[WF_MAXCH] = {}, cj1[WF_MAXCH] = {}, ckoff[WF_MAXCH + 1] = {};
     float *H_tc = nullptr;     // ndsrc x Rp x Kp
+    float *cenf = nullptr;     // n_boxes x 8: box centers as double-floats and 1/h
     float *rec_fac = nullptr;        // Rp x Kp: |factor| of each H entry
     uint32_t *rec_code = nullptr;    // Rp x Kp: packed terms of each H entry (see k_wfar_H_tc)
     int4 *tc_tiles = nullptr;  // (source box, first pair, last pair + 1) per 128-pair tile
@@ -60,7 +62,7 @@ void free_wfar_plan(WfarPlan *p)
     if (!p) return;
     dfree(p->slot); dfree(p->slot_box); dfree(p->H); dfree(p->pair_ctr); dfree(p->pair_d); dfree(p->pos_cm);
     dfree(p->cm_start); dfree(p->tiles); dfree(p->Y); dfree(p->zero_start);
-    dfree(p->H_tc); dfree(p->tc_tiles); dfree(p->rec_fac); dfree(p->rec_code);
+    dfree(p->H_tc); dfree(p->tc_tiles); dfree(p->rec_fac); dfree(p->rec_code); dfree(p->cenf);
     delete p;
 }
 
@@ -261,12 +263,14 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b)
 }
 
 struct WfarTcArgs {
-    int ntiles, P, Q, PQ, R, Rp, WMAX, tmem_cols;
+    int ntiles, P, Q, PQ, R, Rp, WMAX, acc_cols, tmem_cols;
     WfarChunks ch;
     const int4 *tiles;
     const int *pair_ctr, *slot;
     const float *H;
-    const double *cxyz, *cr, *cen, *hw;
+    const float *cf;    // centers as double-floats: [xh yh zh xl yl zl] x nc (sorted order)
+    const float *cenf;  // per box: xh yh zh xl yl zl, 1/h (exact: h is a power of two), pad
+    const double *cr;
     int64_t nc;
     float *Y;
     int *err;
@@ -274,22 +278,37 @@ struct WfarTcArgs {
     int probe_step;        // failure-path probe: pipeline step at which the wait on bar_never runs out (-1: off)
 };
 
-// Tensor-core List 3 far products.  Persistent CTAs of 512 threads walk 128-pair tiles of one
-// source box d: per K chunk (whole harmonic degrees) the threads generate the scaled irregular
-// harmonics of their pairs in FP32 (four threads per pair, warps 4r..4r+3, each carrying the
-// recurrences of every fourth 16-byte column group in registers), split them into TF32 parts in
-// shared memory, load and split the chunk of H_d; one thread issues a_hi b_hi + a_lo b_hi +
-// a_hi b_lo into a 128 x Rp FP32 accumulator in tensor memory.  Epilogue: Y[pair][row] =
-// acc F(k,l) (rho/h)^k / h.
-constexpr int WF_THREADS = 512;  // 4 threads per pair of the 128-pair tile
-constexpr int WF_SPLIT = WF_THREADS / 128;
-constexpr int WF_BREG = 4;  // float4 registers per thread for one chunk of H: Rp * W <= 4 * 4 * WF_THREADS
+// Tensor-core List 3 far products, warp-specialised and persistent (one CTA per SM walking 128-pair
+// tiles of one source box d):
+//   warps 0-11  producers: three threads per pair of the tile (pair p = tid % 128; r = tid / 128 takes
+//               the harmonic column groups g = r (mod 3)); per K chunk (whole degrees) they generate
+//               the scaled irregular harmonics of their pairs in FP32 and split them into TF32 parts,
+//               and load and split their share of the chunk of H_d, into one of two shared-memory
+//               stages; the pair geometry and the radial powers run in double-float.  Once every
+//               producer has filled a stage, one thread of warp 0 issues a_hi b_hi + a_lo b_hi +
+//               a_hi b_lo per 8-column step into one of two 128 x Rp FP32 accumulators in tensor
+//               memory and releases the stage by a commit.
+//   warps 12-15 epilogue, one TMEM lane quadrant each: Y[pair][row] = acc F(k,l) (rho/h)^k / h,
+//               drained while the next tile accumulates in the other buffer.
+// Stages and accumulators hand over on mbarriers; no block-wide barrier inside the tile loop.  Every
+// wait is bounded (wait_limit): a role that gives up records the failure and leaves its loop, the
+// others then give up too, the issued products are drained and the tensor memory is freed.
+constexpr int WF_PROD = 384;                       // producer threads
+constexpr int WF_THREADS = WF_PROD + 128;          // + 4 epilogue warps
+constexpr int WF_SPLIT = WF_PROD / 128;            // producer threads per pair
+constexpr int WF_BREG = 6;                         // float4 registers per producer for one chunk of H
+constexpr int WF_STAGES = 2;
+
+__device__ __forceinline__ void mbar_arrive1(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
 
 template <int NU>
 __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
-    __shared__ uint64_t bar_mma[2], bar_never;  // bar_never: nothing ever arrives on it
+    __shared__ uint64_t bar_full[WF_STAGES], bar_empty[WF_STAGES], bar_afull[2], bar_aempty[2], bar_drain, bar_never;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Q = a.Q, PQ = a.PQ, Rp = a.Rp, WMAX = a.WMAX;
@@ -297,22 +316,27 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
     const uint32_t bytesA = 16u * sboA, bytesB = (uint32_t)Rp * WMAX * 4u;
     // stage s, part 0 (hi) / 1 (lo) of the A and B tiles
     auto Abuf = [&](int s, int part) { return smem_tc + (size_t)(2 * s + part) * bytesA; };
-    auto Bbuf = [&](int s, int part) { return smem_tc + (size_t)4 * bytesA + (size_t)(2 * s + part) * bytesB; };
-    // the epilogue stage (128 x (Rp + 4) floats) reuses the operand tiles; Pw and the column tables follow both
-    const size_t ops = std::max((size_t)4 * bytesA + (size_t)4 * bytesB, (size_t)128 * (Rp + 4) * 4);
-    float *Pw = reinterpret_cast<float *>(smem_tc + ops);  // 128 x (Q+1)
-    float *colF = Pw + 128 * (Q + 1);                                                     // Rp
-    int *colK = reinterpret_cast<int *>(colF + Rp);                                       // Rp
-    double *geo = reinterpret_cast<double *>(smem_tc + ops + (((size_t)128 * (Q + 1) * 4 + (size_t)Rp * 8 + 15) & ~(size_t)15));  // 128 x 4
+    auto Bbuf = [&](int s, int part) {
+        return smem_tc + (size_t)2 * WF_STAGES * bytesA + (size_t)(2 * s + part) * bytesB;
+    };
+    float *colF = reinterpret_cast<float *>(smem_tc + (size_t)2 * WF_STAGES * (bytesA + bytesB));  // Rp
+    int *colK = reinterpret_cast<int *>(colF + Rp);                                                 // Rp
     for (int r = tid; r < Rp; r += WF_THREADS) {
         int k = 0, l = 0, part = 0;
         if (r < a.R) decode(r, k, l, part);
         colF[r] = (float)Fnm(k, l);
-        colK[r] = k;
+        colK[r] = r < a.R ? k : Q + 1;
     }
     if (tid == 0) {
-        tc::mbar_init(&bar_mma[0], 1);
-        tc::mbar_init(&bar_mma[1], 1);
+        for (int s = 0; s < WF_STAGES; ++s) {
+            tc::mbar_init(&bar_full[s], WF_PROD / 32);
+            tc::mbar_init(&bar_empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            tc::mbar_init(&bar_afull[b], 1);
+            tc::mbar_init(&bar_aempty[b], 4);
+        }
+        tc::mbar_init(&bar_drain, 1);
         tc::mbar_init(&bar_never, 1);
         tc::fence_mbar_init();
     }
@@ -321,209 +345,232 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = tmem_base;
-    const uint32_t idesc = tc::idesc_tf32(128, Rp);
-    // pair p = tid % 128; warps 4r .. 4r+3 take the column groups g = r (mod 4), so the column
-    // conditions are uniform within each warp
-    const int p = tid & 127, par = tid >> 7;
     bool ok = true;
-    uint32_t g = 0;
-    for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x) {
-        const int4 tl = a.tiles[t];
-        const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
-        const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
-        const bool valid = p < np;
-        // pair geometry, once per pair (the first of its 4 threads), shared through shared memory
-        float a1r[NU][2], a1i[NU][2], a2r[NU][2], a2i[NU][2];
-        if (par == 0) {
-            const double h = a.hw[d], hinv = 1.0 / h;
-            double x = 3.0, y = 0.0, z = 0.0;
-            int c = 0;
+
+    if (tid < WF_PROD) {
+        // ------------------------------------------------------------ producers (+ the MMA issue)
+        const int p = tid & 127, par = tid >> 7;  // warps 4 par .. 4 par + 3 (uniform per warp)
+        const bool issuer = tid == 0;             // also issues the products
+        const uint32_t idesc = tc::idesc_tf32(128, Rp);
+        uint32_t g = 0, tt = 0;
+        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tt) {
+            const int4 tl = a.tiles[t];
+            const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
+            const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
+            const bool valid = p < np;
+            // pair geometry X = (c - c_d)/h in double-float; an idle row takes X = (3, 0, 0)
+            const float *bc = a.cenf + 8 * (int64_t)d;
+            const float hinv = bc[6];
+            df x{3.f, 0.f}, y{0.f, 0.f}, z{0.f, 0.f};
             if (valid) {
-                c = a.pair_ctr[p0 + p];
-                x = (a.cxyz[c] - a.cen[3 * d]) * hinv;
-                y = (a.cxyz[a.nc + c] - a.cen[3 * d + 1]) * hinv;
-                z = (a.cxyz[2 * a.nc + c] - a.cen[3 * d + 2]) * hinv;
+                const int64_t c = a.pair_ctr[p0 + p], nc = a.nc;
+                x = df_mul_f(df_sub(df{a.cf[c], a.cf[3 * nc + c]}, df{bc[0], bc[3]}), hinv);
+                y = df_mul_f(df_sub(df{a.cf[nc + c], a.cf[4 * nc + c]}, df{bc[1], bc[4]}), hinv);
+                z = df_mul_f(df_sub(df{a.cf[2 * nc + c], a.cf[5 * nc + c]}, df{bc[2], bc[5]}), hinv);
             }
-            const double ri = 1.0 / sqrt(x * x + y * y + z * z);
-            geo[4 * p + 0] = z * ri;
-            geo[4 * p + 1] = ri;
-            geo[4 * p + 2] = x * ri;
-            geo[4 * p + 3] = y * ri;
-            const double ratio = valid ? a.cr[c] * hinv : 0.0;
-            double pk = hinv;
-            for (int k = 0; k <= Q; ++k, pk *= ratio) Pw[p * (Q + 1) + k] = (float)pk;
-        }
-        __syncthreads();
-        const float zh = (float)geo[4 * p + 0];
-        const double rinv = geo[4 * p + 1];
-        double rpj = rinv;  // |x|^{-(j+1)} at the current degree j (starts at j = 0)
-        {
-            // diagonals Yh_i^i = cd_i w^i (w = (x + iy)/|x|, cd_i = a_1 ... a_i) of this thread's groups:
-            // group g = par + 4u holds column 0 (g = 0) or columns 2g-1, 2g
-            const float2 w1 = make_float2((float)geo[4 * p + 2], (float)geo[4 * p + 3]);
-            const float2 w2 = cmulf(w1, w1), w4 = cmulf(w2, w2), w8 = cmulf(w4, w4);
-            // w^(first column of group par): 1 (par 0), w (1), w^3 (2), w^5 (3)
-            float2 cur = par == 0 ? make_float2(1.f, 0.f)
-                                  : par == 1 ? w1 : par == 2 ? cmulf(w2, w1) : cmulf(w4, w1);
-#pragma unroll
-            for (int u = 0; u < NU; ++u) {
-                const int g0 = par + WF_SPLIT * u;
-                const int i0 = g0 == 0 ? 0 : 2 * g0 - 1;
-                a2r[u][0] = a2i[u][0] = a2r[u][1] = a2i[u][1] = 0.f;
-                const float c0 = c_cd[min(i0, 40)], c1 = c_cd[min(i0 + 1, 40)];
-                a1r[u][0] = c0 * cur.x;
-                a1i[u][0] = c0 * cur.y;
-                const float2 nxt = cmulf(cur, w1);
-                a1r[u][1] = c1 * nxt.x;
-                a1i[u][1] = c1 * nxt.y;
-                // next group of this thread: 8 columns on (from column 0: group 4 starts at column 7)
-                cur = (g0 == 0) ? cmulf(cmulf(w4, w2), w1) : cmulf(cur, w8);
-            }
-        }
-        // B: the chunks of H_d pass through registers (WF_BREG float4 per thread), the next chunk's
-        // loads issued before this chunk's harmonics are generated so that their latency overlaps
-        float4 bpre[WF_BREG];
-        auto load_b = [&](int cc) {
-            const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[cc] * Rp);
-            const int nq = Rp * (a.ch.ckoff[cc + 1] - a.ch.ckoff[cc]) / 4;
-#pragma unroll
-            for (int k = 0; k < WF_BREG; ++k) {
-                const int q = tid + k * WF_THREADS;
-                bpre[k] = q < nq ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-        };
-        load_b(0);
-        for (int c = 0; c < a.ch.nch; ++c, ++g) {
-            const int s = g & 1;
-            const uint32_t use = g >> 1;
-            // every thread waits for the products that last read stage s before it overwrites the stage;
-            // a failure is shared at the barrier before this chunk's products are issued
-            if (g >= 2 && ok) ok = tc::mbar_wait(&bar_mma[s], (use - 1) & 1, a.wait_limit);
-            const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
-            const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c];
+            const df rinv = df_rsqrt(df_add(df_add(df_sqr(x), df_sqr(y)), df_sqr(z)));
+            const float zh = df_mul(z, rinv).h;
+            df rpj = rinv;  // |X|^{-(j+1)} at the current degree j (starts at j = 0)
+            float a1r[NU][2], a1i[NU][2], a2r[NU][2], a2i[NU][2];
             {
-                float4 *dh = reinterpret_cast<float4 *>(Bbuf(s, 0)), *dl = reinterpret_cast<float4 *>(Bbuf(s, 1));
-                const int nq = Rp * W / 4;
+                // diagonals Yh_i^i = cd_i w^i (w = (x + iy)/|x|, cd_i = a_1 ... a_i) of this thread's groups:
+                // group g = par + 3u holds column 0 (g = 0) or columns 2g-1, 2g
+                const float2 w1 = make_float2(df_mul(x, rinv).h, df_mul(y, rinv).h);
+                const float2 w2 = cmulf(w1, w1), w3 = cmulf(w2, w1), w5 = cmulf(w3, w2), w6 = cmulf(w3, w3);
+                // w^(first column of group par): 1 (par 0), w (1), w^3 (2)
+                float2 cur = par == 0 ? make_float2(1.f, 0.f) : par == 1 ? w1 : w3;
+#pragma unroll
+                for (int u = 0; u < NU; ++u) {
+                    const int g0 = par + WF_SPLIT * u;
+                    const int i0 = g0 == 0 ? 0 : 2 * g0 - 1;
+                    a2r[u][0] = a2i[u][0] = a2r[u][1] = a2i[u][1] = 0.f;
+                    const float c0 = c_cd[min(i0, 40)], c1 = c_cd[min(i0 + 1, 40)];
+                    a1r[u][0] = c0 * cur.x;
+                    a1i[u][0] = c0 * cur.y;
+                    const float2 nxt = cmulf(cur, w1);
+                    a1r[u][1] = c1 * nxt.x;
+                    a1i[u][1] = c1 * nxt.y;
+                    // next group of this thread: 6 columns on (from column 0: group 3 starts at column 5)
+                    cur = (g0 == 0) ? w5 : cmulf(cur, w6);
+                }
+            }
+            // B: the chunks of H_d pass through registers, the next chunk's loads issued before this
+            // chunk's harmonics are generated so that their latency overlaps
+            float4 bpre[WF_BREG];
+            auto load_b = [&](int cc) {
+                const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[cc] * Rp);
+                const int nq = Rp * (a.ch.ckoff[cc + 1] - a.ch.ckoff[cc]) / 4;
 #pragma unroll
                 for (int k = 0; k < WF_BREG; ++k) {
-                    const int q = tid + k * WF_THREADS;
-                    if (q < nq) {
-                        float4 v = bpre[k], hi, lo;
-                        tc::split_tf32(v.x, hi.x, lo.x);
-                        tc::split_tf32(v.y, hi.y, lo.y);
-                        tc::split_tf32(v.z, hi.z, lo.z);
-                        tc::split_tf32(v.w, hi.w, lo.w);
-                        dh[q] = hi;
-                        dl[q] = lo;
-                    }
+                    const int q = tid + k * WF_PROD;
+                    bpre[k] = q < nq ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-            }
-            if (c + 1 < a.ch.nch) load_b(c + 1);
-            // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's column groups;
-            // the recurrence in FP32, the radial factor (a product of FP64 powers) rounded to FP32,
-            // one 16-byte store per group and TF32 part
-            if (valid) {
-                unsigned char *Ah = Abuf(s, 0), *Al = Abuf(s, 1);
-                const uint32_t rowoff = (uint32_t)(p >> 3) * sboA + (uint32_t)(p & 7) * 16u;
-                int kb = 0;
-                for (int j = j0; j < j1; kb += wfar_degree_slots(j), ++j) {
-                    const float c1 = c_al[j] * zh;
-                    const float rf = dbl_to_f32_rn(rpj);
-                    rpj *= rinv;
+            };
+            load_b(0);
+            for (int c = 0; c < a.ch.nch; ++c, ++g) {
+                const int s = g % WF_STAGES;
+                const uint32_t use = g / WF_STAGES;
+                // the products that last read stage s must have completed (lane 0 waits for the warp)
+                if (use > 0) {
+                    bool w = true;
+                    if (lane == 0) w = tc::mbar_wait(&bar_empty[s], (use - 1) & 1, a.wait_limit);
+                    ok = __shfl_sync(0xffffffffu, w, 0);
+                    if (!ok) break;
+                }
+                const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
+                const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c];
+                {
+                    float4 *dh = reinterpret_cast<float4 *>(Bbuf(s, 0)), *dl = reinterpret_cast<float4 *>(Bbuf(s, 1));
+                    const int nq = Rp * W / 4;
 #pragma unroll
-                    for (int u = 0; u < NU; ++u) {
-                        const int gg = par + WF_SPLIT * u;
-                        const int i0 = gg == 0 ? 0 : 2 * gg - 1;  // first column of the group
-                        if (i0 > j || i0 > PQ) continue;
-                        float v[4];
-#pragma unroll
-                        for (int h2 = 0; h2 < 2; ++h2) {
-                            const int i = i0 + h2;
-                            v[2 * h2] = v[2 * h2 + 1] = 0.f;
-                            if ((gg == 0 && h2 == 1) || i > j) continue;
-                            float vr = a1r[u][h2], vi = a1i[u][h2];
-                            if (j > i) {
-                                const float bb = c_be[tri(j, i)];
-                                vr = fmaf(c1, a1r[u][h2], -bb * a2r[u][h2]);
-                                vi = fmaf(c1, a1i[u][h2], -bb * a2i[u][h2]);
-                                a2r[u][h2] = a1r[u][h2]; a2i[u][h2] = a1i[u][h2];
-                                a1r[u][h2] = vr; a1i[u][h2] = vi;
-                            }
-                            v[2 * h2] = vr * rf;
-                            v[2 * h2 + 1] = (i == 0) ? 0.f : vi * rf;
+                    for (int k = 0; k < WF_BREG; ++k) {
+                        const int q = tid + k * WF_PROD;
+                        if (q < nq) {
+                            float4 v = bpre[k], hi, lo;
+                            tc::split_tf32(v.x, hi.x, lo.x);
+                            tc::split_tf32(v.y, hi.y, lo.y);
+                            tc::split_tf32(v.z, hi.z, lo.z);
+                            tc::split_tf32(v.w, hi.w, lo.w);
+                            dh[q] = hi;
+                            dl[q] = lo;
                         }
-                        float4 hv, lv;
-                        tc::split_tf32(v[0], hv.x, lv.x);
-                        tc::split_tf32(v[1], hv.y, lv.y);
-                        tc::split_tf32(v[2], hv.z, lv.z);
-                        tc::split_tf32(v[3], hv.w, lv.w);
-                        const uint32_t off = (uint32_t)((kb + 4 * gg) >> 2) * 128u + rowoff;
-                        *reinterpret_cast<float4 *>(Ah + off) = hv;
-                        *reinterpret_cast<float4 *>(Al + off) = lv;
                     }
                 }
-                if (par == 0 && kb < W) {  // chunk padding to a multiple of 8 columns (one 16-byte group)
-                    const uint32_t off = (uint32_t)(kb >> 2) * 128u + rowoff;
-                    *reinterpret_cast<float4 *>(Ah + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-                    *reinterpret_cast<float4 *>(Al + off) = make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-            tc::fence_proxy_async();
-            if (__syncthreads_or(!ok)) { ok = false; break; }
-            if (tid == 0) {
-                // failure-path probe: a wait on a barrier nothing arrives on runs out
-                const bool go = (int)g != a.probe_step || tc::mbar_wait(&bar_never, 0, a.wait_limit);
-                if (go) {
-                    tc::tc_fence_after();
-                    const uint32_t a_hi = tc::smem_u32(Abuf(s, 0)), a_lo = tc::smem_u32(Abuf(s, 1));
-                    const uint32_t b_hi = tc::smem_u32(Bbuf(s, 0)), b_lo = tc::smem_u32(Bbuf(s, 1));
-                    const uint32_t sboB = (uint32_t)W * 32u;
-                    for (int ks = 0; ks < W / 8; ++ks) {
-                        const uint32_t off = 256u * ks;
-                        const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
-                        tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, acc0);
-                        tc::mma_tf32(tmem, tc::sdesc(a_lo + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB), idesc, 1u);
-                        tc::mma_tf32(tmem, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_lo + off, 128, sboB), idesc, 1u);
+                if (c + 1 < a.ch.nch) load_b(c + 1);
+                // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's column groups;
+                // the recurrence in FP32, the radial factor (a double-float power) rounded to FP32, one
+                // 16-byte store per group and TF32 part
+                {
+                    unsigned char *Ah = Abuf(s, 0), *Al = Abuf(s, 1);
+                    const uint32_t rowoff = (uint32_t)(p >> 3) * sboA + (uint32_t)(p & 7) * 16u;
+                    int kb = 0;
+                    for (int j = j0; j < j1; kb += wfar_degree_slots(j), ++j) {
+                        const float c1 = c_al[j] * zh;
+                        const float rf = rpj.h;
+                        rpj = df_mul(rpj, rinv);
+#pragma unroll
+                        for (int u = 0; u < NU; ++u) {
+                            const int gg = par + WF_SPLIT * u;
+                            const int i0 = gg == 0 ? 0 : 2 * gg - 1;  // first column of the group
+                            if (i0 > j || i0 > PQ) continue;
+                            float v[4];
+#pragma unroll
+                            for (int h2 = 0; h2 < 2; ++h2) {
+                                const int i = i0 + h2;
+                                v[2 * h2] = v[2 * h2 + 1] = 0.f;
+                                if ((gg == 0 && h2 == 1) || i > j) continue;
+                                float vr = a1r[u][h2], vi = a1i[u][h2];
+                                if (j > i) {
+                                    const float bb = c_be[tri(j, i)];
+                                    vr = fmaf(c1, a1r[u][h2], -bb * a2r[u][h2]);
+                                    vi = fmaf(c1, a1i[u][h2], -bb * a2i[u][h2]);
+                                    a2r[u][h2] = a1r[u][h2]; a2i[u][h2] = a1i[u][h2];
+                                    a1r[u][h2] = vr; a1i[u][h2] = vi;
+                                }
+                                v[2 * h2] = vr * rf;
+                                v[2 * h2 + 1] = (i == 0) ? 0.f : vi * rf;
+                            }
+                            float4 hv, lv;
+                            tc::split_tf32(v[0], hv.x, lv.x);
+                            tc::split_tf32(v[1], hv.y, lv.y);
+                            tc::split_tf32(v[2], hv.z, lv.z);
+                            tc::split_tf32(v[3], hv.w, lv.w);
+                            const uint32_t off = (uint32_t)((kb + 4 * gg) >> 2) * 128u + rowoff;
+                            *reinterpret_cast<float4 *>(Ah + off) = hv;
+                            *reinterpret_cast<float4 *>(Al + off) = lv;
+                        }
                     }
-                } else {
-                    atomicOr(a.err, 8);
-                    ok = false;  // the other threads learn it at the next barrier
+                    if (par == 0 && kb < W) {  // chunk padding to a multiple of 8 columns (one 16-byte group)
+                        const uint32_t off = (uint32_t)(kb >> 2) * 128u + rowoff;
+                        *reinterpret_cast<float4 *>(Ah + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+                        *reinterpret_cast<float4 *>(Al + off) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
                 }
-                tc::mma_commit(&bar_mma[s]);  // also releases the stage when the MMAs were skipped
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive1(&bar_full[s]);
+                if (warp == 0) {
+                    bool w = true;
+                    if (issuer) {
+                        const int ab = tt & 1;
+                        const uint32_t v = tt >> 1;
+                        // the accumulator's previous tile must have been drained; every producer must have
+                        // filled the stage
+                        if (c == 0 && v > 0) w = tc::mbar_wait(&bar_aempty[ab], (v - 1) & 1, a.wait_limit);
+                        if (w) w = tc::mbar_wait(&bar_full[s], use & 1, a.wait_limit);
+                        // failure-path probe: a wait on a barrier nothing arrives on runs out
+                        if (w && (int)g == a.probe_step) w = tc::mbar_wait(&bar_never, 0, a.wait_limit);
+                        if (w) {
+                            tc::tc_fence_after();
+                            const uint32_t dt = tmem + (uint32_t)(ab * a.acc_cols);
+                            const uint32_t a_hi = tc::smem_u32(Abuf(s, 0)), a_lo = tc::smem_u32(Abuf(s, 1));
+                            const uint32_t b_hi = tc::smem_u32(Bbuf(s, 0)), b_lo = tc::smem_u32(Bbuf(s, 1));
+                            const uint32_t sboB = (uint32_t)W * 32u;
+                            for (int ks = 0; ks < W / 8; ++ks) {
+                                const uint32_t off = 256u * ks;
+                                const uint32_t acc0 = (c > 0 || ks > 0) ? 1u : 0u;
+                                tc::mma_tf32(dt, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB),
+                                             idesc, acc0);
+                                tc::mma_tf32(dt, tc::sdesc(a_lo + off, 128, sboA), tc::sdesc(b_hi + off, 128, sboB),
+                                             idesc, 1u);
+                                tc::mma_tf32(dt, tc::sdesc(a_hi + off, 128, sboA), tc::sdesc(b_lo + off, 128, sboB),
+                                             idesc, 1u);
+                            }
+                            tc::mma_commit(&bar_empty[s]);  // releases the stage when these products complete
+                            if (c + 1 == a.ch.nch) tc::mma_commit(&bar_afull[ab]);
+                        }
+                    }
+                    ok = __shfl_sync(0xffffffffu, w, 0);
+                    if (!ok) break;
+                }
             }
         }
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        const int sl = (g - 1) & 1;
-        ok = tc::mbar_wait(&bar_mma[sl], ((g - 1) >> 1) & 1, a.wait_limit);
-        if (__syncthreads_or(!ok)) { ok = false; break; }
-        tc::tc_fence_after();
-        // scaled rows staged in shared memory (row stride Rp + 4), then copied out coalesced: the
-        // tile's rows are contiguous in Y
-        const int qd = warp & 3, row = 32 * qd + lane, RS = Rp + 4;
-        float *stage = reinterpret_cast<float *>(smem_tc);  // 128 x (Rp + 4) floats
-        for (int cg = warp >> 2; cg * 16 < Rp; cg += WF_THREADS / 128) {
-            float v[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(cg * 16), v);
-            const float *pw = Pw + row * (Q + 1);
+        if (issuer) {
+            // every product issued so far completes before the tensor memory is released
+            tc::mma_commit(&bar_drain);
+            tc::mbar_wait(&bar_drain, 0, tc::WAIT_LIMIT);
+        }
+    } else {
+        // ------------------------------------------------------------ epilogue
+        const int qd = warp & 3, row = 32 * qd + lane;
+        uint32_t tt = 0;
+        for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tt) {
+            const int4 tl = a.tiles[t];
+            const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
+            const int ab = tt & 1;
+            const uint32_t v = tt >> 1;
+            // (rho/h)^k / h, k = 0, 1, ... in double-float, advanced as the columns' degree grows
+            const float hinv = a.cenf[8 * (int64_t)d + 6];
+            const bool valid = row < np;
+            const df ratio = valid ? df_mul_f(df_from(a.cr[a.pair_ctr[p0 + row]]), hinv) : df{0.f, 0.f};
+            bool w = true;
+            if (lane == 0) w = tc::mbar_wait(&bar_afull[ab], v & 1, a.wait_limit);
+            ok = __shfl_sync(0xffffffffu, w, 0);
+            if (!ok) break;
+            tc::tc_fence_after();
+            df pw{hinv, 0.f};
+            int kc = 0;
+            float *yrow = a.Y + (int64_t)(p0 + row) * a.R;
+            for (int cg = 0; cg * 16 < Rp; ++cg) {
+                float vals[16];
+                tc::tmem_ld16(tmem + (uint32_t)(ab * a.acc_cols) + ((uint32_t)(32 * qd) << 16) + (uint32_t)(cg * 16),
+                              vals);
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = cg * 16 + j;
-                v[j] *= colF[col] * pw[colK[col]];
+                for (int j = 0; j < 16; ++j) {
+                    const int col = cg * 16 + j;
+                    while (kc < colK[col] && kc <= Q) {  // uniform across the warp
+                        pw = df_mul(pw, ratio);
+                        ++kc;
+                    }
+                    if (valid && col < a.R) yrow[col] = vals[j] * colF[col] * pw.h;
+                }
             }
-            float4 *dst = reinterpret_cast<float4 *>(stage + row * RS + cg * 16);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) dst[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive1(&bar_aempty[ab]);
         }
-        __syncthreads();
-        for (int q = tid; q < np * a.R; q += WF_THREADS) {
-            const int r = q / a.R, cc = q % a.R;
-            a.Y[(int64_t)(p0 + r) * a.R + cc] = stage[r * RS + cc];
-        }
-        tc::tc_fence_before();
-        __syncthreads();
     }
-    if (!ok && tid == 0) atomicOr(a.err, 8);
-    if (g > 0 && tid == 0) tc::mbar_wait(&bar_mma[(g - 1) & 1], ((g - 1) >> 1) & 1, tc::WAIT_LIMIT);
+    if (!ok) atomicOr(a.err, 8);
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
@@ -532,8 +579,8 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
 
 static size_t wfar_tc_smem(int Rp, int WMAX, int Q)
 {
-    const size_t ops = std::max((size_t)4 * 16 * (WMAX * 32 + 16) + (size_t)4 * Rp * WMAX * 4, (size_t)128 * (Rp + 4) * 4);
-    return ops + (((size_t)128 * (Q + 1) * 4 + (size_t)Rp * 8 + 15) & ~(size_t)15) + (size_t)128 * 4 * 8;
+    (void)Q;
+    return (size_t)2 * WF_STAGES * 16 * (WMAX * 32 + 16) + (size_t)2 * WF_STAGES * Rp * WMAX * 4 + (size_t)Rp * 8;
 }
 
 constexpr int WKC = 32;  // K chunk of the H tile
@@ -701,6 +748,21 @@ __global__ void k_wfar_reduce(int64_t nc, int Q, int QMS, const int *cm_start, c
     else a->x += s;
 }
 
+// Box centers as double-floats (xh yh zh xl yl zl) and 1/h (h a power of two, so exact in FP32).
+__global__ void k_cen_to_df(int nb, const double *cen, const double *hw, float *out)
+{
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const df v = df_from(cen[3 * b + d]);
+        out[8 * b + d] = v.h;
+        out[8 * b + 3 + d] = v.l;
+    }
+    out[8 * b + 6] = (float)(1.0 / hw[b]);
+    out[8 * b + 7] = 0.f;
+}
+
 // Degree chunks of the tensor-core form and its shared-memory budget; false when the orders do not fit.
 
 static bool wfar_tc_layout(WfarPlan *pl, int w_hint)
@@ -708,12 +770,13 @@ static bool wfar_tc_layout(WfarPlan *pl, int w_hint)
     const int P = pl->P, Q = pl->Q, PQ = P + Q;
     pl->Rp = (pl->R + 15) / 16 * 16;
     if (pl->Rp > 256 || PQ > 35) return false;
-    pl->NU = PQ <= 22 ? 3 : 5;  // 16-byte groups per thread: ceil((1 + ceil(PQ/2)) / 4)
+    pl->NU = PQ <= 28 ? 5 : 7;  // 16-byte groups per thread: ceil((1 + ceil(PQ/2)) / 3)
     const int wmin = (wfar_degree_slots(PQ) + 7) / 8 * 8;
     int W = std::max(w_hint > 0 ? w_hint / 8 * 8 : 64, wmin);
     while (W > wmin && wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) W -= 8;
     if (wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) return false;
-    if (pl->Rp * W / 4 > WF_BREG * WF_THREADS) return false;  // one chunk of H per register set
+    if (pl->Rp * W / 4 > WF_BREG * WF_PROD) return false;  // one chunk of H per register set
+    if (pl->Rp > 256) return false;                          // two accumulators in 512 TMEM columns
     pl->WMAX = W;
     int nch = 0, j = 0, koff = 0;
     while (j <= PQ) {
@@ -929,10 +992,13 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
             }
             pl->Y = dalloc<float>((int64_t)std::max(np, 1) * pl->R);
             const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, Q);
-            if (pl->NU == 3)
-                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-            else
+            if (pl->NU == 5)
                 QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            else
+                QBX_CUDA_TRY(cudaFuncSetAttribute(k_wfar_tc<7>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            pl->cenf = dalloc<float>((int64_t)std::max(nb, 1) * 8);
+            if (nb > 0) k_cen_to_df<<<nblocks(nb, 256), 256, 0, st>>>(nb, T->cen, T->hw, pl->cenf);
+            QBX_LAUNCH_CHECK();
             QBX_CUDA_TRY(cudaStreamSynchronize(st));
             dfree(cm_cnt); dfree(d_cnt); dfree(d_start); dfree(flag); dfree(tot);
             return pl;
@@ -966,8 +1032,8 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
     return pl;
 }
 
-void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, int *err,
-                    long long wait_limit, int probe_step, cudaStream_t st)
+void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu, const signed char *pb, const float *cf,
+                    int *err, long long wait_limit, int probe_step, cudaStream_t st)
 {
     if (pl->npairs == 0) return;
     if (pl->tc) {
@@ -991,14 +1057,14 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
         QBX_CUDA_TRY(cudaGetDevice(&dev));
         QBX_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         int cols = 32;
-        while (cols < pl->Rp) cols <<= 1;
-        WfarTcArgs a{pl->ntc, pl->P, pl->Q, pl->P + pl->Q, pl->R, pl->Rp, pl->WMAX, cols, ch, pl->tc_tiles,
-                     pl->pair_ctr, pl->slot, pl->H_tc, T->cxyz, T->cr, T->cen, T->hw, T->np[KCTR], pl->Y, err,
+        while (cols < pl->Rp) cols <<= 1;  // one accumulator; two are allocated
+        WfarTcArgs a{pl->ntc, pl->P, pl->Q, pl->P + pl->Q, pl->R, pl->Rp, pl->WMAX, cols, 2 * cols, ch, pl->tc_tiles,
+                     pl->pair_ctr, pl->slot, pl->H_tc, cf, pl->cenf, T->cr, T->np[KCTR], pl->Y, err,
                      wait_limit > 0 ? wait_limit : tc::WAIT_LIMIT, probe_step};
         const size_t sm = wfar_tc_smem(pl->Rp, pl->WMAX, pl->Q);
         const int grid = std::min(pl->ntc, nsm);
-        if (pl->NU == 3) k_wfar_tc<3><<<grid, WF_THREADS, sm, st>>>(a);
-        else k_wfar_tc<5><<<grid, WF_THREADS, sm, st>>>(a);
+        if (pl->NU == 5) k_wfar_tc<5><<<grid, WF_THREADS, sm, st>>>(a);
+        else k_wfar_tc<7><<<grid, WF_THREADS, sm, st>>>(a);
         QBX_LAUNCH_CHECK();
         return;
     }
