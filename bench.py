@@ -41,8 +41,8 @@ METRIC = "QBX target evals/s at 1e-6 rel err: learned+mixed vs plain FP64 GIGAQB
 T_F = 0.9
 TOL = 1e-6             # acceptance: normwise relative l-infinity distance to the fixed-order FP64 result
 JUDGE_FRAC = 0.9       # the fallback keeps every target within 0.9 TOL of the judge (margin for rounding)
-N_MAX_FP64 = 256       # leaf size of plain FP64 (best of its n_max sweep)
-N_MAX_MIXED = 48       # leaf size of the mixed-precision modes (profiles/nmax_sweep_star8k.md)
+N_MAX_FP64 = 512       # leaf size of plain FP64 (best of its n_max sweep, profiles/nmax_sweep_star79k.md)
+N_MAX_MIXED = 128      # leaf size of the mixed-precision modes (profiles/nmax_sweep_star79k.md)
 L2_FLUSH_BYTES = 512 << 20
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates of the part
 
@@ -820,7 +820,7 @@ def run_batched(args):
     stream = torch.cuda.Stream(device=dev)
     with torch.cuda.stream(stream):
         tuned = autotune.tuned_n_max(G, surfs, dens, Q, P, G.QBX_M2L_3XTF32, default=N_MAX_MIXED,
-                                     candidates=(32, 48, 64, 96), enabled=not args.no_tune)
+                                     candidates=(64, 96, 128, 160, 192), enabled=not args.no_tune)
         n_max = args.n_max or tuned["n_max"]
         fi = forest_inputs(G, torch, dev, surfs, dens, n_max)
         F, FL, ev = fi["F"], fi["FL"], fi["ev"]
