@@ -251,8 +251,9 @@ def roofline_table(work, stage_ms, peaks):
 
 STAGE_KERNELS = {
     "centers": ("k_qbx_direct + k_l2qbxl (direct QBX sums and L2QBXL, double-float)", ("eval.cu", "df64.cuh")),
-    "m2qbxl_mixed": ("k_wfar_H_tc + k_wfar_tc (List 3 far M2QBXL, split-TF32 tcgen05)", ("m2qbxl_mixed.cu",)),
-    "m2l": ("k_mhat_tc + k_m2l_tc + k_m2l_reduce (List 2 M2L, split-TF32 tcgen05)", ("m2l_mixed.cu",)),
+    "m2qbxl_mixed": ("k_wfar_H_tc + k_wfar_tc (List 3 far M2QBXL, split-TF32 tcgen05)",
+                     ("m2qbxl_mixed.cu", "tc_common.cuh", "df64.cuh")),
+    "m2l": ("k_mhat_tc + k_m2l_tc + k_m2l_reduce (List 2 M2L, split-TF32 tcgen05)", ("m2l_mixed.cu", "tc_common.cuh")),
     "l2l": ("k_l2l_df (L2L, double-float)", ("eval.cu", "df64.cuh")),
     "p2l": ("k_p2l4_df (List 4 far P2L, double-float)", ("eval.cu", "df64.cuh")),
     "p2m_m2m": ("k_p2m_df + k_m2m8_df (P2M, M2M, double-float)", ("eval.cu", "df64.cuh")),

@@ -144,11 +144,14 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar)
 
 // ---------------------------------------------------------------- split TF32
 
+// x rounded to TF32 (10 explicit significand bits), to nearest with ties away from zero: half a TF32 unit
+// in the last place (bit 12) is added to the bit pattern and the 13 low bits are cleared.  The sign bit
+// is apart from the magnitude, so this rounds the magnitude; a carry out of the significand moves into
+// the exponent (the next power of two), and an infinity stays infinite.  The same result as
+// cvt.rna.tf32.f32 for every finite or infinite input, in two integer operations.
 __device__ __forceinline__ float tf32_rna(float x)
 {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
 }
 
 __device__ __forceinline__ void split_tf32(float x, float &hi, float &lo)
