@@ -47,7 +47,7 @@ struct WfarPlan {
     bool tc = false;
     int Rp = 0, Kp = 0, nch = 0, WMAX = 0, ntc = 0, NU = 0;
     int cj0[WF_MAXCH] = {}, cj1[WF_MAXCH] = {}, ckoff[WF_MAXCH + 1] = {};
-    float *H_tc = nullptr;     // ndsrc x Rp x Kp
+    float *H_tc = nullptr;     // ndsrc x 2 x Rp x Kp: per K chunk the TF32 hi tile then the lo tile
     float *cenf = nullptr;     // n_boxes x 8: box centers as double-floats and 1/h
     float *rec_fac = nullptr;        // Rp x Kp: |factor| of each H entry
     uint32_t *rec_code = nullptr;    // Rp x Kp: packed terms of each H entry (see k_wfar_H_tc)
@@ -225,10 +225,12 @@ __device__ __forceinline__ float wfar_recipe_entry(float f, uint32_t c, int Pd, 
 // One block per slot (source box): its multipole rounded to FP32 once into shared memory (by integer
 // operations: FP64 arithmetic on ~10^10 entries per evaluation would bound this kernel by the FP64
 // pipe), then the slot's Rp x Kp entries four at a time from the recipe (L2-resident, shared by all
-// slots), stored as float4.
-__global__ void __launch_bounds__(256) k_wfar_H_tc(int P, int PMT, int64_t per4, const float4 *fac, const uint4 *code,
-                                                   const int *slot_box, const signed char *pb, const double2 *Mu,
-                                                   float4 *H)
+// slots), split into TF32 hi and lo parts once here rather than by every tile that reads them.  Layout
+// per slot and K chunk c: the hi tile (Rp x W_c, K-major) then the lo tile, so that the products fetch
+// each part of a chunk with one bulk copy.
+__global__ void __launch_bounds__(256) k_wfar_H_tc(int P, int PMT, int Rp, WfarChunks ch, const float4 *fac,
+                                                   const uint4 *code, const int *slot_box, const signed char *pb,
+                                                   const double2 *Mu, float4 *H)
 {
     __shared__ float2 Ms[ntri(PMAX)];
     const int s = blockIdx.x, d = slot_box[s];
@@ -239,12 +241,23 @@ __global__ void __launch_bounds__(256) k_wfar_H_tc(int P, int PMT, int64_t per4,
         Ms[t] = make_float2(dbl_to_f32_rn(v.x), dbl_to_f32_rn(v.y));
     }
     __syncthreads();
-    float4 *out = H + (int64_t)s * per4;
-    for (int64_t q = threadIdx.x; q < per4; q += blockDim.x) {
-        const float4 f = __ldg(fac + q);
-        const uint4 c = __ldg(code + q);
-        out[q] = make_float4(wfar_recipe_entry(f.x, c.x, Pd, Ms), wfar_recipe_entry(f.y, c.y, Pd, Ms),
-                             wfar_recipe_entry(f.z, c.z, Pd, Ms), wfar_recipe_entry(f.w, c.w, Pd, Ms));
+    float4 *out = H + (int64_t)s * (2 * (int64_t)Rp * ch.Kp / 4);
+    for (int c = 0; c < ch.nch; ++c) {
+        const int q0 = ch.ckoff[c] * Rp / 4, n4 = (ch.ckoff[c + 1] - ch.ckoff[c]) * Rp / 4;
+        float4 *hi = out + 2 * q0, *lo = hi + n4;
+        for (int q = threadIdx.x; q < n4; q += blockDim.x) {
+            const float4 f = __ldg(fac + q0 + q);
+            const uint4 cd = __ldg(code + q0 + q);
+            const float4 v = make_float4(wfar_recipe_entry(f.x, cd.x, Pd, Ms), wfar_recipe_entry(f.y, cd.y, Pd, Ms),
+                                         wfar_recipe_entry(f.z, cd.z, Pd, Ms), wfar_recipe_entry(f.w, cd.w, Pd, Ms));
+            float4 h, l;
+            tc::split_tf32(v.x, h.x, l.x);
+            tc::split_tf32(v.y, h.y, l.y);
+            tc::split_tf32(v.z, h.z, l.z);
+            tc::split_tf32(v.w, h.w, l.w);
+            hi[q] = h;
+            lo[q] = l;
+        }
     }
 }
 
@@ -296,7 +309,6 @@ struct WfarTcArgs {
 constexpr int WF_PROD = 384;                       // producer threads
 constexpr int WF_THREADS = WF_PROD + 128;          // + 4 epilogue warps
 constexpr int WF_SPLIT = WF_PROD / 128;            // producer threads per pair
-constexpr int WF_BREG = 6;                         // float4 registers per producer for one chunk of H
 constexpr int WF_STAGES = 2;
 
 __device__ __forceinline__ void mbar_arrive1(uint64_t *bar)
@@ -308,7 +320,8 @@ template <int NU>
 __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_tc[];
-    __shared__ uint64_t bar_full[WF_STAGES], bar_empty[WF_STAGES], bar_afull[2], bar_aempty[2], bar_drain, bar_never;
+    __shared__ uint64_t bar_full[WF_STAGES], bar_empty[WF_STAGES], bar_b[WF_STAGES], bar_afull[2], bar_aempty[2],
+        bar_drain, bar_never;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int Q = a.Q, PQ = a.PQ, Rp = a.Rp, WMAX = a.WMAX;
@@ -331,6 +344,7 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
         for (int s = 0; s < WF_STAGES; ++s) {
             tc::mbar_init(&bar_full[s], WF_PROD / 32);
             tc::mbar_init(&bar_empty[s], 1);
+            tc::mbar_init(&bar_b[s], 1);
         }
         for (int b = 0; b < 2; ++b) {
             tc::mbar_init(&bar_afull[b], 1);
@@ -350,13 +364,14 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
     if (tid < WF_PROD) {
         // ------------------------------------------------------------ producers (+ the MMA issue)
         const int p = tid & 127, par = tid >> 7;  // warps 4 par .. 4 par + 3 (uniform per warp)
-        const bool issuer = tid == 0;             // also issues the products
+        const bool issuer = tid == 0;             // also fetches the operator chunks and issues the products
         const uint32_t idesc = tc::idesc_tf32(128, Rp);
         uint32_t g = 0, tt = 0;
+        uint32_t pend = 0, pend_par = 0;          // stages with an operator copy not yet waited for, its phase
         for (int t = blockIdx.x; t < a.ntiles && ok; t += gridDim.x, ++tt) {
             const int4 tl = a.tiles[t];
             const int d = tl.x, p0 = tl.y, np = tl.z - tl.y;
-            const float *Hd = a.H + (int64_t)a.slot[d] * Rp * a.ch.Kp;
+            const float *Hd = a.H + (int64_t)a.slot[d] * 2 * Rp * a.ch.Kp;  // hi / lo tiles per chunk
             const bool valid = p < np;
             // pair geometry X = (c - c_d)/h in double-float; an idle row takes X = (3, 0, 0)
             const float *bc = a.cenf + 8 * (int64_t)d;
@@ -394,19 +409,6 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
                     cur = (g0 == 0) ? w5 : cmulf(cur, w6);
                 }
             }
-            // B: the chunks of H_d pass through registers, the next chunk's loads issued before this
-            // chunk's harmonics are generated so that their latency overlaps
-            float4 bpre[WF_BREG];
-            auto load_b = [&](int cc) {
-                const float4 *src = reinterpret_cast<const float4 *>(Hd + (int64_t)a.ch.ckoff[cc] * Rp);
-                const int nq = Rp * (a.ch.ckoff[cc + 1] - a.ch.ckoff[cc]) / 4;
-#pragma unroll
-                for (int k = 0; k < WF_BREG; ++k) {
-                    const int q = tid + k * WF_PROD;
-                    bpre[k] = q < nq ? __ldg(src + q) : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            };
-            load_b(0);
             for (int c = 0; c < a.ch.nch; ++c, ++g) {
                 const int s = g % WF_STAGES;
                 const uint32_t use = g / WF_STAGES;
@@ -419,24 +421,16 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
                 }
                 const int j0 = a.ch.cj0[c], j1 = a.ch.cj1[c];
                 const int W = a.ch.ckoff[c + 1] - a.ch.ckoff[c];
-                {
-                    float4 *dh = reinterpret_cast<float4 *>(Bbuf(s, 0)), *dl = reinterpret_cast<float4 *>(Bbuf(s, 1));
-                    const int nq = Rp * W / 4;
-#pragma unroll
-                    for (int k = 0; k < WF_BREG; ++k) {
-                        const int q = tid + k * WF_PROD;
-                        if (q < nq) {
-                            float4 v = bpre[k], hi, lo;
-                            tc::split_tf32(v.x, hi.x, lo.x);
-                            tc::split_tf32(v.y, hi.y, lo.y);
-                            tc::split_tf32(v.z, hi.z, lo.z);
-                            tc::split_tf32(v.w, hi.w, lo.w);
-                            dh[q] = hi;
-                            dl[q] = lo;
-                        }
-                    }
+                if (issuer) {
+                    // the chunk of H_d, TF32 hi and lo tiles, by two bulk copies into the free stage
+                    const uint32_t bytes = (uint32_t)Rp * W * 4u;
+                    const float *src = Hd + (int64_t)2 * a.ch.ckoff[c] * Rp;
+                    tc::mbar_arrive_expect_tx(&bar_b[s], 2u * bytes);
+                    tc::bulk_g2s(Bbuf(s, 0), src, bytes, &bar_b[s]);
+                    tc::bulk_g2s(Bbuf(s, 1), src + (int64_t)W * Rp, bytes, &bar_b[s]);
+                    pend |= 1u << s;
+                    pend_par = (pend_par & ~(1u << s)) | ((use & 1u) << s);
                 }
-                if (c + 1 < a.ch.nch) load_b(c + 1);
                 // A: S_j^i / D(j) = Yh_j^i |x|^{-(j+1)} for degrees j0 .. j1-1 of this thread's column groups;
                 // the recurrence in FP32, the radial factor (a double-float power) rounded to FP32, one
                 // 16-byte store per group and TF32 part
@@ -498,6 +492,10 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
                         // filled the stage
                         if (c == 0 && v > 0) w = tc::mbar_wait(&bar_aempty[ab], (v - 1) & 1, a.wait_limit);
                         if (w) w = tc::mbar_wait(&bar_full[s], use & 1, a.wait_limit);
+                        if (w) {
+                            w = tc::mbar_wait(&bar_b[s], use & 1, a.wait_limit);
+                            if (w) pend &= ~(1u << s);
+                        }
                         // failure-path probe: a wait on a barrier nothing arrives on runs out
                         if (w && (int)g == a.probe_step) w = tc::mbar_wait(&bar_never, 0, a.wait_limit);
                         if (w) {
@@ -526,9 +524,12 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
             }
         }
         if (issuer) {
-            // every product issued so far completes before the tensor memory is released
+            // every product issued so far completes before the tensor memory is released, and every
+            // operator copy still in flight lands before the shared memory is
             tc::mma_commit(&bar_drain);
             tc::mbar_wait(&bar_drain, 0, tc::WAIT_LIMIT);
+            for (int s2 = 0; s2 < WF_STAGES; ++s2)
+                if (pend & (1u << s2)) tc::mbar_wait(&bar_b[s2], (pend_par >> s2) & 1u, tc::WAIT_LIMIT);
         }
     } else {
         // ------------------------------------------------------------ epilogue
@@ -775,7 +776,6 @@ static bool wfar_tc_layout(WfarPlan *pl, int w_hint)
     int W = std::max(w_hint > 0 ? w_hint / 8 * 8 : 64, wmin);
     while (W > wmin && wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) W -= 8;
     if (wfar_tc_smem(pl->Rp, W, Q) > 220 * 1024) return false;
-    if (pl->Rp * W / 4 > WF_BREG * WF_PROD) return false;  // one chunk of H per register set
     if (pl->Rp > 256) return false;                          // two accumulators in 512 TMEM columns
     pl->WMAX = W;
     int nch = 0, j = 0, koff = 0;
@@ -969,7 +969,7 @@ WfarPlan *wfar_plan_build(const qbx_tree *T, const qbx_lists *L, int P, int Q, b
             if (!tct.empty())
                 QBX_CUDA_TRY(cudaMemcpyAsync(pl->tc_tiles, tct.data(), tct.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                              st));
-            pl->H_tc = dalloc<float>((int64_t)std::max(nd, 1) * pl->Rp * pl->Kp);
+            pl->H_tc = dalloc<float>((int64_t)std::max(nd, 1) * 2 * pl->Rp * pl->Kp);  // TF32 hi and lo tiles
             {
                 const std::vector<WfarRecipe> rec = wfar_recipe(pl);
                 std::vector<float> fac(rec.size());
@@ -1047,9 +1047,8 @@ void wfar_mixed_run(const qbx_tree *T, WfarPlan *pl, int PMT, const double2 *Mu,
             ch.cj1[c] = pl->cj1[c];
         }
         for (int c = 0; c <= WF_MAXCH; ++c) ch.ckoff[c] = pl->ckoff[c];
-        const int64_t per4 = (int64_t)pl->Rp * pl->Kp / 4;  // Rp is a multiple of 16
         if (pl->ndsrc > 0)
-            k_wfar_H_tc<<<pl->ndsrc, 256, 0, st>>>(pl->P, PMT, per4, reinterpret_cast<const float4 *>(pl->rec_fac),
+            k_wfar_H_tc<<<pl->ndsrc, 256, 0, st>>>(pl->P, PMT, pl->Rp, ch, reinterpret_cast<const float4 *>(pl->rec_fac),
                                                     reinterpret_cast<const uint4 *>(pl->rec_code), pl->slot_box, pb,
                                                     Mu, reinterpret_cast<float4 *>(pl->H_tc));
         QBX_LAUNCH_CHECK();
