@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(WF_THREADS, 1) k_wfar_tc(WfarTcArgs a)
                         for (int u = 0; u < NU; ++u) {
                             const int gg = par + WF_SPLIT * u;
                             const int i0 = gg == 0 ? 0 : 2 * gg - 1;  // first column of the group
-                            if (i0 > j || i0 > PQ) continue;
+                            if (i0 > j || i0 > PQ) break;  // later groups start at higher columns
                             float v[4];
 #pragma unroll
                             for (int h2 = 0; h2 < 2; ++h2) {
