@@ -209,7 +209,13 @@ def stage_work(cost, P, Q, dipole, mixed, ctr_order, box_order, parent, has_tgt_
     l2q = sum(int(n) * (4 * DF_DOT * l2qbxl_macs(int(p), Q) + npass * _tri(int(p)) * (2 * DF_MULF + 6 * DF_MUL
                                                                                          + 2 * DF_ADD))
               for p, n in zip(*np.unique(ctr_order, return_counts=True)))
-    work["centers"] = (float(direct_pair_instr(Q, dipole) * direct + l2q), "df")
+    if mixed:
+        work["centers"] = (float(direct_pair_instr(Q, dipole) * direct + l2q), "df")
+    else:
+        # plain FP64: the List 3 far M2QBXL on the FP64 pipe (k_centers) is nearly all of the stage; the
+        # double-float direct sums and L2QBXL beside it (under 2 % of it) are left out of the count
+        work["centers"] = (float(c["Wfar"] * (8 * _tri(P + Q) + 8 * (P + 1) ** 2 * _tri(Q) + 2 * (P + 1) ** 2)),
+                           "fp64")
     if mixed:
         D = (P + 1) ** 2
         work["m2l"] = (3.0 * 2.0 * D * D * c["V"], "tf32")
