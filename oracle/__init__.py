@@ -74,7 +74,7 @@ def lib():
         L.orc_p2p.restype = d
         for f in (L.orc_m2m, L.orc_l2l, L.orc_m2l):
             f.argtypes = [i, P, P, i, P, P]
-        L.orc_build_tree.argtypes = [P, i, P, P, i, P, i, i, d, i]
+        L.orc_build_tree.argtypes = [P, i, P, P, i, P, i, i, d, i, i]
         L.orc_build_tree.restype = P
         L.orc_tree_free.argtypes = [P]
         L.orc_tree_info.argtypes = [P, P, P]
@@ -199,10 +199,15 @@ class Tree:
             self.handle = 0
 
 
-def build_tree(src_xyz, ctr_xyz, ctr_r, tgt_xyz, n_max=32, t_f=0.9, max_depth=40) -> Tree:
+def build_tree(src_xyz, ctr_xyz, ctr_r, tgt_xyz, n_max=32, t_f=0.9, max_depth=40, linf_tcr=False,
+               level_restrict=False) -> Tree:
+    """Stage 1 tree.  linf_tcr: the box-shaped (l-infinity) TCR of Table l2-comparison's left
+    columns; level_restrict: adjacent leaves differ by at most one level (Remark on level
+    restriction, Section 5.3)."""
     s, c, r, t = _f64(src_xyz), _f64(ctr_xyz), _f64(ctr_r), _f64(tgt_xyz)
     ns, nc, nt = s.shape[1], c.shape[1], t.shape[1]
-    h = lib().orc_build_tree(_p(s), ns, _p(c), _p(r), nc, _p(t), nt, n_max, t_f, max_depth)
+    flags = (1 if linf_tcr else 0) | (2 if level_restrict else 0)
+    h = lib().orc_build_tree(_p(s), ns, _p(c), _p(r), nc, _p(t), nt, n_max, t_f, max_depth, flags)
     info = np.zeros(6, np.int64)
     root = np.zeros(4)
     lib().orc_tree_info(h, _p(info), _p(root))

@@ -406,7 +406,12 @@ typedef struct {
     int n_overfull;    /* leaves left above n_max because max_depth was reached */
     double root_c[3], root_h;
     double tf;
+    int linf;          /* 1: the l-infinity TCR of the two-dimensional method (Table l2-comparison) */
 } otree;
+
+/* tree variants (orc_build_tree's flags) */
+#define ORC_TREE_LINF_TCR 1
+#define ORC_TREE_LEVEL_RESTRICT 2
 
 static void tree_grow(otree *T)
 {
@@ -436,10 +441,17 @@ static int tree_add(otree *T, int lev, const int64_t ic[3], const double c[3], d
 }
 
 /* Center fits inside the target confinement region B2(sqrt(3)|b|(1+t_f), c_b) of a box
- * with center cc and l-infinity radius h (Section 5.2.2): |x - cc|_2 + r <= sqrt(3) h (1 + t_f). */
-static int fits_tcr(const double x[3], double r, const double cc[3], double h, double tf)
+ * with center cc and l-infinity radius h (Section 5.2.2): |x - cc|_2 + r <= sqrt(3) h (1 + t_f).
+ * With linf set, the TCR is the cube of l-infinity radius h (1 + t_f) about cc (the box-shaped
+ * region of the two-dimensional method that Section 5 compares against):
+ * |x - cc|_inf + r <= h (1 + t_f). */
+static int fits_tcr(const double x[3], double r, const double cc[3], double h, double tf, int linf)
 {
     double dx = x[0] - cc[0], dy = x[1] - cc[1], dz = x[2] - cc[2];
+    if (linf) {
+        double m = fmax(fmax(fabs(dx), fabs(dy)), fabs(dz));
+        return m + r <= h * (1.0 + tf);
+    }
     double dist = sqrt(dx * dx + dy * dy + dz * dz);
     return dist + r <= (sqrt(3.0) * h) * (1.0 + tf);
 }
@@ -457,6 +469,137 @@ static void get_pt(const double *xyz, int n, int i, double out[3])
     out[2] = xyz[2 * n + i];
 }
 
+static int is_leaf(const otree *T, int b);
+static int adjacent(const otree *T, int a, int b, int Lf);
+static int morton_less(const int64_t *a, const int64_t *b);
+
+/* Subdivides leaf b by the Stage 1 rule for which particles move (points to the octant
+ * "coordinate >= center", a center only into a child whose TCR holds its ball); only
+ * children that receive a particle are made, appended after the existing boxes.
+ * Returns the number of children made (0: no particle can move, b stays a leaf). */
+static int split_leaf(otree *T, int b, const double *xyz_k[3], const double *cr)
+{
+    int cmask = 0;
+    double hc = 0.5 * T->hw[b], x[3], cc[3];
+    int *dest[3];
+    for (int k = 0; k < 3; ++k) {
+        dest[k] = malloc(sizeof(int) * (T->np[k] > 0 ? T->np[k] : 1));
+        for (int i = 0; i < T->np[k]; ++i) {
+            dest[k][i] = -1;
+            if (T->owner[k][i] != b) continue;
+            get_pt(xyz_k[k], T->np[k], i, x);
+            int oc = octant(x, &T->cen[3 * b]);
+            if (k == KCTR) {
+                for (int d = 0; d < 3; ++d) cc[d] = T->cen[3 * b + d] + (((oc >> d) & 1) ? hc : -hc);
+                if (!fits_tcr(x, cr[i], cc, hc, T->tf, T->linf)) continue;
+            }
+            dest[k][i] = oc;
+            cmask |= 1 << oc;
+        }
+    }
+    int made = 0;
+    for (int oc = 0; oc < 8; ++oc) {
+        if (!((cmask >> oc) & 1)) continue;
+        int64_t ic[3];
+        for (int d = 0; d < 3; ++d) {
+            int bit = (oc >> d) & 1;
+            ic[d] = 2 * T->ic[3 * b + d] + bit;
+            cc[d] = T->cen[3 * b + d] + (bit ? hc : -hc);
+        }
+        int c = tree_add(T, T->level[b] + 1, ic, cc, hc, b);
+        T->child[8 * b + oc] = c;
+        ++made;
+    }
+    for (int k = 0; k < 3; ++k) {
+        for (int i = 0; i < T->np[k]; ++i)
+            if (dest[k][i] >= 0) T->owner[k][i] = T->child[8 * b + dest[k][i]];
+        free(dest[k]);
+    }
+    return made;
+}
+
+static const otree *g_order_tree;
+
+static int box_order_cmp(const void *pa, const void *pb)
+{
+    int a = *(const int *)pa, b = *(const int *)pb;
+    const otree *T = g_order_tree;
+    if (T->level[a] != T->level[b]) return T->level[a] < T->level[b] ? -1 : 1;
+    if (morton_less(&T->ic[3 * a], &T->ic[3 * b])) return -1;
+    if (morton_less(&T->ic[3 * b], &T->ic[3 * a])) return 1;
+    return 0;
+}
+
+/* Renumbers the boxes into (level, Morton code) order and rebuilds level_start. */
+static void tree_renumber(otree *T)
+{
+    int nb = T->nb;
+    int *ord = malloc(sizeof(int) * nb), *nid = malloc(sizeof(int) * nb);
+    for (int i = 0; i < nb; ++i) ord[i] = i;
+    g_order_tree = T;
+    qsort(ord, nb, sizeof(int), box_order_cmp);
+    for (int i = 0; i < nb; ++i) nid[ord[i]] = i;
+    int *level = malloc(sizeof(int) * T->cap), *parent = malloc(sizeof(int) * T->cap);
+    int *child = malloc(sizeof(int) * 8 * T->cap);
+    int64_t *ic = malloc(sizeof(int64_t) * 3 * T->cap);
+    double *cen = malloc(sizeof(double) * 3 * T->cap), *hw = malloc(sizeof(double) * T->cap);
+    for (int j = 0; j < nb; ++j) {
+        int i = ord[j];
+        level[j] = T->level[i];
+        hw[j] = T->hw[i];
+        parent[j] = T->parent[i] >= 0 ? nid[T->parent[i]] : -1;
+        for (int d = 0; d < 3; ++d) {
+            ic[3 * j + d] = T->ic[3 * i + d];
+            cen[3 * j + d] = T->cen[3 * i + d];
+        }
+        for (int o = 0; o < 8; ++o) child[8 * j + o] = T->child[8 * i + o] >= 0 ? nid[T->child[8 * i + o]] : -1;
+    }
+    free(T->level); free(T->parent); free(T->child); free(T->ic); free(T->cen); free(T->hw);
+    T->level = level; T->parent = parent; T->child = child; T->ic = ic; T->cen = cen; T->hw = hw;
+    for (int k = 0; k < 3; ++k)
+        for (int i = 0; i < T->np[k]; ++i) T->owner[k][i] = nid[T->owner[k][i]];
+    T->nlev = level[nb - 1] + 1;
+    free(T->level_start);
+    T->level_start = malloc(sizeof(int) * (T->nlev + 1));
+    for (int l = 0, j = 0; l <= T->nlev; ++l) {
+        while (j < nb && level[j] < l) ++j;
+        T->level_start[l] = j;
+    }
+    free(ord);
+    free(nid);
+}
+
+/*
+ * Level restriction (Remark "Effect of level-restriction on List 3 complexity", Section 5.3):
+ * adjacent leaves may differ by at most one level; a tree is made so by repeatedly
+ * subdividing the larger leaf of a pair that violates this.  Taken here in rounds: a round
+ * finds, on the current tree, every leaf that has an adjacent leaf two or more levels finer
+ * (literally, over all pairs of leaves) and subdivides all of them (split_leaf); rounds repeat
+ * until one subdivides nothing.  A violating leaf none of whose particles can move stays a leaf.
+ */
+static void level_restrict(otree *T, const double *xyz_k[3], const double *cr, int max_depth)
+{
+    for (;;) {
+        int nb = T->nb, Lf = 0;
+        for (int b = 0; b < nb; ++b)
+            if (T->level[b] > Lf) Lf = T->level[b];
+        char *leaf = malloc(nb), *viol = calloc(nb, 1);
+        for (int b = 0; b < nb; ++b) leaf[b] = (char)is_leaf(T, b);
+        for (int b = 0; b < nb; ++b) {
+            if (!leaf[b]) continue;
+            for (int a = 0; a < nb && !viol[b]; ++a)
+                if (leaf[a] && T->level[a] >= T->level[b] + 2 && adjacent(T, a, b, Lf)) viol[b] = 1;
+        }
+        int made = 0;
+        for (int b = 0; b < nb; ++b)
+            if (viol[b] && T->level[b] < max_depth) made += split_leaf(T, b, xyz_k, cr);
+        free(leaf);
+        free(viol);
+        if (!made) break;
+        tree_renumber(T);
+    }
+}
+
 /*
  * Builds the tree.  Readings of Stage 1:
  *  - root: centered at the midpoint of the bounding box of all points and balls,
@@ -469,12 +612,15 @@ static void get_pt(const double *xyz, int n, int i, double out[3])
  *  - no box below level max_depth is made;
  *  - boxes are numbered level by level, children in octant order, which is the
  *    (level, Morton code) order.
+ * flags: ORC_TREE_LINF_TCR selects the l-infinity TCR (fits_tcr, sep_a_tcrb);
+ * ORC_TREE_LEVEL_RESTRICT makes the finished tree level-restricted (level_restrict).
  */
 otree *orc_build_tree(const double *sxyz, int ns, const double *cxyz, const double *cr, int nc,
-                      const double *txyz, int nt, int nmax, double tf, int max_depth)
+                      const double *txyz, int nt, int nmax, double tf, int max_depth, int flags)
 {
     init_tables();
     otree *T = calloc(1, sizeof(otree));
+    T->linf = (flags & ORC_TREE_LINF_TCR) ? 1 : 0;
     T->np[KSRC] = ns;
     T->np[KCTR] = nc;
     T->np[KTGT] = nt;
@@ -542,7 +688,7 @@ otree *orc_build_tree(const double *sxyz, int ns, const double *cxyz, const doub
                 if (k == KCTR) {
                     double hc = 0.5 * T->hw[o], cc[3];
                     for (int d = 0; d < 3; ++d) cc[d] = T->cen[3 * o + d] + (((oc >> d) & 1) ? hc : -hc);
-                    if (!fits_tcr(x, cr[i], cc, hc, tf)) continue;
+                    if (!fits_tcr(x, cr[i], cc, hc, tf, T->linf)) continue;
                 }
                 dest[g] = oc;
                 movers[o - b0]++;
@@ -580,6 +726,7 @@ otree *orc_build_tree(const double *sxyz, int ns, const double *cxyz, const doub
     for (int l = 0; l < nlev; ++l) T->level_start[l] = lev_start[l];
     T->level_start[nlev] = T->nb;
     free(lev_start);
+    if (flags & ORC_TREE_LEVEL_RESTRICT) level_restrict(T, xyz_k, cr, max_depth);
 
     /* owned particles grouped by box (counting sort, stable in the particle index) */
     for (int k = 0; k < 3; ++k) {
@@ -695,6 +842,13 @@ static int colleague(const otree *T, int a, int b, int k)
  * TCR(b), taken as signed (negative inside), is at least 3|a|. */
 static int sep_a_tcrb(const otree *T, int a, int b)
 {
+    if (T->linf) {
+        /* l-infinity TCR: l-infinity distance from the center of a to the boundary of the cube
+         * of radius |b|(1 + t_f), signed, is at least 3|a| */
+        double m = 0.0;
+        for (int d = 0; d < 3; ++d) m = fmax(m, fabs(T->cen[3 * a + d] - T->cen[3 * b + d]));
+        return m - T->hw[b] * (1.0 + T->tf) >= 3.0 * T->hw[a];
+    }
     double dx = T->cen[3 * a] - T->cen[3 * b], dy = T->cen[3 * a + 1] - T->cen[3 * b + 1],
            dz = T->cen[3 * a + 2] - T->cen[3 * b + 2];
     double dist = sqrt(dx * dx + dy * dy + dz * dz);
