@@ -97,6 +97,7 @@ def lib():
         L.orc_center_features.argtypes = [P, P, P, P, P, P, P, P, P]
         L.orc_orders_fallback.argtypes = [P, P, P, P, d, i, i, P, P]
         L.orc_assoc_targets.argtypes = [P, P, P, P, P, P, P, P, d, P, P]
+        L.orc_refine_marks.argtypes = [i, P, i, P, P, i, P, P, i, d, P]
         _lib = L
     return _lib
 
@@ -371,3 +372,16 @@ def orders_from_pred(tree: Tree, pred, margin_q, margin_p, q_lo, q_hi, p_lo, p_h
     lib().orc_orders_from_pred(tree.handle, _p(pr), _p(tc), float(margin_q), float(margin_p), q_lo, q_hi, p_lo, p_hi,
                                p_default, _p(q), _p(pb))
     return q, pb
+
+
+def refine_marks(which, src_xyz, ctr_xyz, ctr_r, elem, n_elem, elem_eta=None, eps=0.025):
+    """Bisection marks per element (bool[n_elem]): which = 0, Algorithm 1 (a source strictly inside
+    (1 - eps) r of a center; elem per center), which = 1, Algorithm 2 (a center within 0.375 eta_k of a
+    source of element k; elem per source, elem_eta per element)."""
+    s, c, r = _f64(src_xyz), _f64(ctr_xyz), _f64(ctr_r)
+    e = np.ascontiguousarray(elem, np.int32)
+    eta = _f64(np.zeros(n_elem) if elem_eta is None else elem_eta)
+    out = np.zeros(max(n_elem, 1), np.uint8)
+    lib().orc_refine_marks(int(which), _p(s), s.shape[1], _p(c), _p(r), c.shape[1], _p(e), _p(eta), int(n_elem),
+                           float(eps), _p(out))
+    return out[:n_elem].astype(bool)

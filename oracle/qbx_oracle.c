@@ -1897,3 +1897,43 @@ void orc_assoc_targets(const otree *T, const double *sxyz, const double *rdanger
     for (int t = 0; t < nt; ++t) flagged[t] = endangered[t] && tgt_ctr[t] < 0;
     free(seen); free(endangered); free(best); free(side); free(leaves.v);
 }
+
+/* ------------------------------------------------------------------------ */
+/* refinement marks of the geometry processing (Section 3.2 and 3.3)        */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * The tests that decide which elements Algorithms 1 and 2 bisect, as their definitions read,
+ * over all (center, source) pairs (no tree):
+ *  which = 0, Algorithm 1 (interfering source geometry, Section 3.2): the element elem[i] that
+ *    spawned center i is marked if some source s has |c_i - s| < (1 - eps) r_i, eps the
+ *    disturbance tolerance (0.025 in the paper);
+ *  which = 1, Algorithm 2 (quadrature resolution, Section 3.3): the element elem[j] of source j is
+ *    marked if some center c has |c - s_j| <= 0.5 (3/4) eta_k = 0.375 eta_k, k = elem[j].
+ * marks[n_elem] receives 0 or 1.
+ */
+void orc_refine_marks(int which, const double *sxyz, int ns, const double *cxyz, const double *cr, int nc,
+                      const int *elem, const double *eta, int n_elem, double eps, unsigned char *marks)
+{
+    double x[3], y[3];
+    memset(marks, 0, (size_t)n_elem);
+    if (which == 0) {
+        for (int i = 0; i < nc; ++i) {
+            get_pt(cxyz, nc, i, x);
+            double rad = (1.0 - eps) * cr[i];
+            for (int j = 0; j < ns && !marks[elem[i]]; ++j) {
+                get_pt(sxyz, ns, j, y);
+                if (dist3(x, y) < rad) marks[elem[i]] = 1;
+            }
+        }
+    } else {
+        for (int j = 0; j < ns; ++j) {
+            get_pt(sxyz, ns, j, y);
+            double rad = 0.375 * eta[elem[j]];
+            for (int i = 0; i < nc && !marks[elem[j]]; ++i) {
+                get_pt(cxyz, nc, i, x);
+                if (dist3(x, y) <= rad) marks[elem[j]] = 1;
+            }
+        }
+    }
+}

@@ -8,6 +8,10 @@ spherical-harmonic expansions, translations, trees or interaction lists.
 from .surfaces import (  # noqa: F401
     Surface,
     make_surface,
+    surface_from_flat,
+    flat_mesh,
+    bisect_flat,
+    scaled_curvature,
     sphere_radius,
     star_radius,
     real_ylm,

@@ -138,6 +138,23 @@ def _lagrange_eval(u: np.ndarray, v: np.ndarray):
     return mono @ _LAG, du @ _LAG, dv @ _LAG
 
 
+def _lagrange_eval2(u: np.ndarray, v: np.ndarray):
+    """Second derivatives (d2/du2, d2/dudv, d2/dv2) of the 15 degree-4 Lagrange basis functions."""
+    def mono(a, b, da, db):
+        c = 1.0
+        for k in range(da):
+            c *= a - k
+        for k in range(db):
+            c *= b - k
+        if c == 0.0:
+            return 0 * u
+        return c * u ** (a - da) * v ** (b - db)
+    uu = np.stack([mono(a, b, 2, 0) for a, b in _MONO], axis=-1)
+    uv = np.stack([mono(a, b, 1, 1) for a, b in _MONO], axis=-1)
+    vv = np.stack([mono(a, b, 0, 2) for a, b in _MONO], axis=-1)
+    return uu @ _LAG, uv @ _LAG, vv @ _LAG
+
+
 def _icosahedron():
     phi = (1.0 + math.sqrt(5.0)) / 2.0
     verts = []
@@ -163,6 +180,24 @@ def _icosahedron():
                     faces.append((a, b2, c2))
     assert len(faces) == 20
     return verts, np.array(faces)
+
+
+def flat_mesh(n_sub: int) -> np.ndarray:
+    """The uniform starting mesh: (K, 3, 3) flat sub-triangles of the icosahedron's faces."""
+    return _flat_subtriangles(n_sub)
+
+
+def bisect_flat(flat: np.ndarray, marks: np.ndarray) -> np.ndarray:
+    """Mesh after bisection of the marked elements (Section 3.1): each marked flat triangle
+    (A, B, C) is replaced by its four midpoint children, orientation kept; unmarked elements keep
+    their index order, the children follow them in order of their parents."""
+    marks = np.asarray(marks, bool)
+    keep = flat[~marks]
+    A, B, C = flat[marks, 0], flat[marks, 1], flat[marks, 2]
+    ab, bc, ca = 0.5 * (A + B), 0.5 * (B + C), 0.5 * (C + A)
+    kids = np.stack([np.stack([A, ab, ca], 1), np.stack([ab, B, bc], 1), np.stack([ca, bc, C], 1),
+                     np.stack([ab, bc, ca], 1)], axis=1).reshape(-1, 3, 3)
+    return np.concatenate([keep, kids], axis=0)
 
 
 def _flat_subtriangles(n_sub: int) -> np.ndarray:
@@ -204,6 +239,8 @@ class Surface:
     tgt_xyz: np.ndarray  # (3, N_T) on-surface targets, one per center
     tgt_ctr: np.ndarray  # (N_T,) int32 associated center
     radius_fn: object = field(repr=False, default=None)
+    ctr_elem: np.ndarray = field(repr=False, default=None)     # (N_C,) element that spawned each center
+    ctr_elem_eta: np.ndarray = field(repr=False, default=None)  # eta of the centers' elements (stage 1)
 
     @property
     def n_src(self) -> int:
@@ -258,7 +295,12 @@ def make_surface(n_sub: int, radius_fn=sphere_radius, scale: float = 1.0, offset
     sources are those nodes too (upsample = 1), or the 15 f^2 nodes of the rule repeated on the
     f^2 sub-triangles of every element (upsample = f), a finer source quadrature on the same
     elements and expansion radii (the role of the paper's stage-2 quadrature, Section 3)."""
-    flat = _flat_subtriangles(n_sub)  # (K, 3, 3)
+    return surface_from_flat(_flat_subtriangles(n_sub), radius_fn, scale, offset, upsample)
+
+
+def _element_geometry(flat, radius_fn, scale, offset):
+    """(K, 15, 3) geometry nodes: the 15 equispaced points of each flat triangle projected radially
+    onto r(x_hat), scaled and shifted."""
     K = flat.shape[0]
     V0, V1, V2 = flat[:, 0], flat[:, 1], flat[:, 2]
     gi = np.array([i for i, _ in _GEO_IJ]) / 4.0
@@ -266,7 +308,69 @@ def make_surface(n_sub: int, radius_fn=sphere_radius, scale: float = 1.0, offset
     pts = V0[:, None, :] + gi[None, :, None] * (V1 - V0)[:, None, :] + gj[None, :, None] * (V2 - V0)[:, None, :]
     xhat = pts / np.linalg.norm(pts, axis=-1, keepdims=True)
     rad = radius_fn(xhat.reshape(-1, 3).T).reshape(K, 15)
-    geo = xhat * rad[..., None] * scale + np.asarray(offset)[None, None, :]  # (K, 15, 3)
+    return xhat * rad[..., None] * scale + np.asarray(offset)[None, None, :]
+
+
+def _eta_elements(geo):
+    """eta_k: max over the 15 quadrature and 15 geometry nodes of 2 sigma_1(J A^-1) (eq. stretch-factor)."""
+    qu, qv, _ = triangle_rule()
+    gi = np.array([i for i, _ in _GEO_IJ]) / 4.0
+    gj = np.array([j for _, j in _GEO_IJ]) / 4.0
+    out = None
+    for u, v in ((qu, qv), (gi, gj)):
+        _, du_b, dv_b = _lagrange_eval(u, v)
+        e = _stretch(np.einsum("qb,kbd->kqd", du_b, geo), np.einsum("qb,kbd->kqd", dv_b, geo)).max(axis=1)
+        out = e if out is None else np.maximum(out, e)
+    return out
+
+
+def scaled_curvature(flat: np.ndarray, radius_fn=sphere_radius, scale: float = 1.0,
+                     offset=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """kappa_k = max over the element's 15 quadrature and 15 geometry nodes x of
+    max(|k_1(x)|, |k_2(x)|) eta_k(x) (eq. curvature-criterion, Section 3.2.1): the principal
+    curvatures are the eigenvalues of the shape operator I^-1 II of the degree-4 element map,
+    eta_k(x) = 2 sigma_1(J A^-1) at x."""
+    geo = _element_geometry(flat, radius_fn, scale, offset)
+    qu, qv, _ = triangle_rule()
+    gi = np.array([i for i, _ in _GEO_IJ]) / 4.0
+    gj = np.array([j for _, j in _GEO_IJ]) / 4.0
+    u = np.concatenate([qu, gi])
+    v = np.concatenate([qv, gj])
+    _, du_b, dv_b = _lagrange_eval(u, v)
+    uu_b, uv_b, vv_b = _lagrange_eval2(u, v)
+    xu = np.einsum("qb,kbd->kqd", du_b, geo)
+    xv = np.einsum("qb,kbd->kqd", dv_b, geo)
+    xuu = np.einsum("qb,kbd->kqd", uu_b, geo)
+    xuv = np.einsum("qb,kbd->kqd", uv_b, geo)
+    xvv = np.einsum("qb,kbd->kqd", vv_b, geo)
+    n = np.cross(xu, xv)
+    n /= np.linalg.norm(n, axis=-1, keepdims=True)
+    E, F, Gm = np.sum(xu * xu, -1), np.sum(xu * xv, -1), np.sum(xv * xv, -1)
+    L, M, N = np.sum(xuu * n, -1), np.sum(xuv * n, -1), np.sum(xvv * n, -1)
+    # eigenvalues of I^-1 II: k^2 det(I) - k (E N - 2 F M + G L) + det(II) = 0
+    detI = E * Gm - F * F
+    H2 = (E * N - 2.0 * F * M + Gm * L) / detI        # k1 + k2
+    K = (L * N - M * M) / detI                        # k1 k2
+    disc = np.sqrt(np.maximum(0.25 * H2 * H2 - K, 0.0))
+    kmax = np.maximum(np.abs(0.5 * H2 + disc), np.abs(0.5 * H2 - disc))
+    return (kmax * _stretch(xu, xv)).max(axis=1)
+
+
+def surface_from_flat(flat: np.ndarray, radius_fn=sphere_radius, scale: float = 1.0, offset=(0.0, 0.0, 0.0),
+                      upsample: int = 1, src_flat: np.ndarray = None) -> Surface:
+    """Surface on the mesh of flat triangles `flat` (projected radially onto r(x_hat)): the body of
+    make_surface for any (e.g. locally bisected) mesh.  With src_flat (a bisection of `flat`: the
+    stage-2 mesh of Section 3.3) the sources are the nodes of src_flat's elements (and elem_eta their
+    eta), while centers, radii and targets stay those of `flat` (the stage-1 mesh)."""
+    if src_flat is not None:
+        s1 = surface_from_flat(flat, radius_fn, scale, offset)
+        s2 = surface_from_flat(src_flat, radius_fn, scale, offset, upsample)
+        return Surface(s2.n_elem, s2.src_xyz, s2.src_w, s2.src_n, s2.src_elem, s2.elem_eta, s1.ctr_xyz, s1.ctr_r,
+                       s1.ctr_side, s1.tgt_xyz, s1.tgt_ctr, radius_fn, s1.ctr_elem, s1.elem_eta)
+    K = flat.shape[0]
+    geo = _element_geometry(flat, radius_fn, scale, offset)  # (K, 15, 3)
+    gi = np.array([i for i, _ in _GEO_IJ]) / 4.0
+    gj = np.array([j for _, j in _GEO_IJ]) / 4.0
 
     qu, qv, qw = triangle_rule()
     phi, dphu, dphv = _lagrange_eval(qu, qv)  # (15 quad, 15 basis)
@@ -309,7 +413,7 @@ def make_surface(n_sub: int, radius_fn=sphere_radius, scale: float = 1.0, offset
     tgt = np.concatenate([node_xyz, node_xyz], axis=1)
     tctr = np.arange(2 * N, dtype=np.int32)
     return Surface(K, src_xyz, src_w, src_n, src_elem, eta, np.ascontiguousarray(ctr), ctr_r, side,
-                   np.ascontiguousarray(tgt), tctr, radius_fn)
+                   np.ascontiguousarray(tgt), tctr, radius_fn, np.concatenate([node_elem, node_elem]), eta)
 
 
 # --------------------------------------------------------------------------
