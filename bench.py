@@ -266,9 +266,10 @@ STAGE_KERNELS = {
 }
 
 
-def kernel_traffic(stage):
+def kernel_traffic(stage, units):
     """DRAM bytes per launch of a stage's kernels from the committed ncu summary
-    (profiles/traffic.json), or None when there is none or the kernels' sources changed since."""
+    (profiles/traffic.json): bytes per unit of work measured there times the units of this launch,
+    or None when there is no record or the kernels' sources changed since."""
     import hashlib
 
     try:
@@ -279,8 +280,8 @@ def kernel_traffic(stage):
                        for f in STAGE_KERNELS[stage][1])
         if hashlib.sha256(src).hexdigest()[:16] != rec.get("source_sha256_16"):
             return None
-        return rec.get("bytes_per_launch")
-    except (OSError, ValueError, KeyError):
+        return rec["bytes_per_unit"] * units
+    except (OSError, ValueError, KeyError, TypeError):
         return None
 
 
@@ -557,7 +558,8 @@ def run_gpu(args):
         ev_in = (cu(s.src_w), cu(sigma), None if mu is None else cu(mu), cu(s.src_n), cu(tc, torch.int32))
         torch.cuda.synchronize()
         tb0 = time.perf_counter()
-        T = G.qbx_build_tree(*geo, n_max=n_max, t_f=T_F)
+        lr = args.tree == "level-restricted"
+        T = G.qbx_build_tree(*geo, n_max=n_max, t_f=T_F, level_restrict=lr)
         torch.cuda.synchronize()
         tb1 = time.perf_counter()
         L = G.qbx_build_lists(T)
@@ -640,6 +642,15 @@ def run_gpu(args):
                            "rel_err_vs_fp64": None if judge is None else
                            float((pot_f - judge).abs().max() / judge.abs().max())}
             del g_fixed
+        # the error of each reduced-precision stage alone (fixed orders; the other stage in FP64)
+        err_by_stage = None
+        if mixed and judge is not None:
+            err_by_stage = {}
+            pot_s = torch.empty_like(pot)
+            for name, only in (("m2l", G.QBX_MIXED_M2L_ONLY), ("m2qbxl", G.QBX_MIXED_M2QBXL_ONLY)):
+                G.qbx_eval(T, L, *ev_in, Q, P, out=pot_s, precision=prec | only)
+                err_by_stage[name] = float((pot_s - judge).abs().max() / judge.abs().max())
+            del pot_s
         cost = G.qbx_lists_cost(L, Q, P)
         ex = T.export()
         ctr_box = ex["ctr_owner"].cpu().numpy()
@@ -682,20 +693,28 @@ def run_gpu(args):
         plain = None
         if mixed and not args.no_fp64_baseline:
             del flush
-            T2 = G.qbx_build_tree(*geo, n_max=N_MAX_FP64, t_f=T_F)
-            L2 = G.qbx_build_lists(T2)
-            flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
-            out2 = torch.empty_like(pot)
-            pms = _time_eager(torch, lambda: G.qbx_eval(T2, L2, *ev_in, Q, P, out=out2), stream, flush,
-                              args.fp64_steps, 1)
-            b_total = max_over_ranks(float(sum(pms)))
-            plain = {"value": ws * n_qbx_tgt * args.fp64_steps / (b_total * 1e-3),
-                     "ms_per_step": b_total / args.fp64_steps, "n_max": N_MAX_FP64, "steps": args.fp64_steps}
+            flush = None
+            # plain FP64 at its leaf size on both tree variants; the faster is the baseline
+            arms = {}
+            for variant in ("level-restricted", "plain"):
+                T2 = G.qbx_build_tree(*geo, n_max=N_MAX_FP64, t_f=T_F, level_restrict=variant == "level-restricted")
+                L2 = G.qbx_build_lists(T2)
+                if flush is None:
+                    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+                out2 = torch.empty_like(pot)
+                pms = _time_eager(torch, lambda: G.qbx_eval(T2, L2, *ev_in, Q, P, out=out2), stream, flush,
+                                  args.fp64_steps, 1)
+                b_total = max_over_ranks(float(sum(pms)))
+                arms[variant] = {"value": ws * n_qbx_tgt * args.fp64_steps / (b_total * 1e-3),
+                                 "ms_per_step": b_total / args.fp64_steps, "tree": variant}
+                del T2, L2
+            best = max(arms, key=lambda k: arms[k]["value"])
+            plain = {**arms[best], "n_max": N_MAX_FP64, "steps": args.fp64_steps,
+                     "other_tree": arms["plain" if best == "level-restricted" else "level-restricted"]}
             if fp64_same:
                 plain["at_mixed_n_max"] = {"value": n_qbx_tgt / (statistics.mean(fp64_same) * 1e-3),
                                            "ms_per_step": statistics.mean(fp64_same), "n_max": n_max,
                                            "steps": len(fp64_same)}
-            del T2, L2
 
     if rank != 0:
         if ws > 1:
@@ -725,7 +744,7 @@ def run_gpu(args):
                             "learned": "learned orders (network + fixed-order judge) + mixed precision (" + (
                                 "split-TF32 tensor-core" if args.mixed_form == "3xtf32" else "FP32")
                             + " translation products)"}[mode],
-                   "p_qbx": Q, "p_fmm": P, "n_max": n_max, "t_f": T_F, "n_src": int(s.n_src),
+                   "p_qbx": Q, "p_fmm": P, "n_max": n_max, "t_f": T_F, "tree": args.tree, "n_src": int(s.n_src),
                    "n_ctr": int(s.n_ctr), "n_qbx_targets": n_qbx_tgt, "n_point_targets": n_pt_tgt,
                    "n_flagged": int(vflag.sum()), "n_boxes": int(T.n_boxes), "n_levels": nlev,
                    "timing": "CUDA-graph replays of one evaluation, CUDA events on the launching stream",
@@ -735,6 +754,7 @@ def run_gpu(args):
         "stage_ms": stage_ms,
         "deterministic": det,
         "rel_err_vs_fp64_same_tree": err_vs_fp64,
+        "rel_err_vs_fp64_by_stage": err_by_stage,
         "modeled_ops": {"per_list": cost["ops"], "stages": cost["stages"], "total": cost["total"],
                         "counts": cost["count"]},
         "e2e": {"value": e2e_value, "unit": "QBX target evals/s", "h2d_bytes_per_step": int(h2d),
@@ -742,7 +762,8 @@ def run_gpu(args):
         "gpu_launches": library_launches(nlev, mixed) * args.steps,
         "roofline": {"stage": top, "kernel": STAGE_KERNELS.get(top, (top,))[0], "bound": t_roof["bound"],
                      "achieved": t_roof["achieved"], "peak": t_roof["peak"], "unit": t_roof["unit"],
-                     "frac": t_roof["frac"], "traffic": kernel_traffic(top), "work_per_launch": work[top][0],
+                     "frac": t_roof["frac"], "traffic": kernel_traffic(top, cost["count"]["Wfar"]),
+                     "work_per_launch": work[top][0],
                      "ms_per_launch": t_roof["ms"], "arith": t_roof["arith"],
                      "peak_source": ("measured in this run: FP32 FMA throughput (qbx_peak_flops) / 2 = FP32 "
                                      "instructions/s" if t_roof["unit"] == "Tinst/s" else
@@ -925,6 +946,83 @@ def run_batched(args):
         torch.distributed.destroy_process_group()
 
 
+TCR_VARIANTS = (("l2", False, False), ("linf", True, False), ("l2+level_restricted", False, True),
+                ("linf+level_restricted", True, True))
+
+
+def run_tcr(args):
+    """Table l2-comparison on the synthetic star family: the modeled operations of each list
+    (Table ilist-operation-counts, from qbx_lists_cost on the built lists) with the l2 TCR of this
+    method and the box-shaped l-infinity TCR of the two-dimensional one, each also level-restricted,
+    at the table's orders (p_qbx 5, p_fmm 15) and leaf size (512); and, per tree variant, the measured
+    time of one evaluation (split-TF32 products, fixed orders 8 / 16, leaf size 128, CUDA graph
+    replays with L2 flushed between them).  One JSON line."""
+    import torch
+
+    import paper_1805_06106_gb300 as G
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    s, sigma, mu, t, tc, _ = make_workload(args.n_sub, "star79k")
+    n_qbx_tgt = int(np.sum(tc >= 0))
+
+    def cu(a, dt=torch.float64):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
+
+    stream = torch.cuda.Stream(device=dev)
+    rows = {}
+    ref = None
+    with torch.cuda.stream(stream):
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        geo = [cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(t)]
+        ev_in = (cu(s.src_w), cu(sigma), None if mu is None else cu(mu), cu(s.src_n), cu(tc, torch.int32))
+        for name, linf, lr in TCR_VARIANTS:
+            row = {}
+            for n_max, (q, p) in ((512, (5, 15)), (N_MAX_MIXED, (P_QBX, P_FMM))):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                T = G.qbx_build_tree(*geo, n_max=n_max, t_f=T_F, linf_tcr=linf, level_restrict=lr)
+                torch.cuda.synchronize()
+                t1 = time.perf_counter()
+                L = G.qbx_build_lists(T)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
+                c = G.qbx_lists_cost(L, q, p)
+                key = f"n_max{n_max}_q{q}_p{p}"
+                row[key] = {"n_boxes": int(T.n_boxes), "n_levels": int(T.info.n_levels),
+                            "tree_ms": 1e3 * (t1 - t0), "lists_ms": 1e3 * (t2 - t1),
+                            "list_count": c["count"], "list_ops": c["ops"], "stage_ops": c["stages"],
+                            "total_ops": c["total"]}
+                if n_max == N_MAX_MIXED:
+                    pot = torch.empty(t.shape[1], dtype=torch.float64, device=dev)
+                    G.qbx_eval(T, L, *ev_in, q, p, out=pot, precision=G.QBX_M2L_3XTF32)
+                    graph = G.qbx_graph_create(T, L, *ev_in, q, p, pot, precision=G.QBX_M2L_3XTF32)
+                    ms = _time_graph(torch, graph, stream, flush, args.steps, max(args.warmup, 3))
+                    L.profile(True)
+                    G.qbx_eval(T, L, *ev_in, q, p, out=pot, precision=G.QBX_M2L_3XTF32)
+                    row[key]["stage_ms"] = L.stage_ms()
+                    L.profile(False)
+                    row[key]["eval_ms"] = statistics.median(ms)
+                    row[key]["qbx_evals_per_s"] = n_qbx_tgt / (statistics.median(ms) * 1e-3)
+                    if ref is None:
+                        ref = pot.clone()
+                    row[key]["rel_diff_vs_l2"] = float((pot - ref).abs().max() / ref.abs().max())
+                    del graph
+                del L, T
+                torch.cuda.synchronize()
+            rows[name] = row
+    base = rows["l2"]["n_max512_q5_p15"]["total_ops"]
+    out = {"metric": "modeled operations per tree variant (Table l2-comparison) and split-TF32 evaluation time",
+           "unit": "modeled ops", "value": base,
+           "config": {"workload": f"star r=1+0.25ReY84+0.15ReY52, {20 * args.n_sub ** 2} curved triangles x 15 "
+                                  f"nodes ({s.n_src} sources, {n_qbx_tgt} on-surface QBX targets), random Y_n^m "
+                                  f"density", "t_f": T_F, "steps": args.steps, "warmup": max(args.warmup, 3),
+                      "l2": "flushed between timed steps (512 MiB write)"},
+           "total_ops_vs_l2": {k: v["n_max512_q5_p15"]["total_ops"] / base for k, v in rows.items()},
+           "eval_ms": {k: v[f"n_max{N_MAX_MIXED}_q{P_QBX}_p{P_FMM}"]["eval_ms"] for k, v in rows.items()},
+           "variants": rows}
+    print(json.dumps(out))
+
 def main():
     global P_QBX, P_FMM
     ap = argparse.ArgumentParser()
@@ -946,25 +1044,31 @@ def main():
                     help="timed steps of plain FP64 at the mixed leaf size (also the judge and accuracy "
                          "reference; 0 skips it unless the learned mode needs the judge)")
     ap.add_argument("--fixed-steps", type=int, default=5, help="timed steps of fixed orders in the same precision")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched",), default="star79k",
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched", "tcr"), default="star79k",
                     help="star79k (1.19M sources, random density, orders 8/16; default), star8k (120k, Green's "
-                         "formula, orders 7/15), star40k (607k), or batched: many surfaces in one forest and graph")
+                         "formula, orders 7/15), star40k (607k), batched: many surfaces in one forest and graph, "
+                         "or tcr: Table l2-comparison's tree variants on the 1.19M-source surface")
     ap.add_argument("--batch", type=int, default=64, help="surfaces of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the leaf-size autotuner")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--tree", choices=("level-restricted", "plain"), default="level-restricted",
+                    help="single-surface workloads: the tree of the evaluated arms (Section 5.3's level "
+                         "restriction, the faster on the 1.19M-source surface, or Stage 1 as is)")
     args = ap.parse_args()
-    if args.workload in WORKLOADS:
-        n_sub, _, _, (P_QBX, P_FMM), _ = WORKLOADS[args.workload]
+    if args.workload in WORKLOADS or args.workload == "tcr":
+        n_sub, _, _, (P_QBX, P_FMM), _ = WORKLOADS["star79k" if args.workload == "tcr" else args.workload]
         if args.n_sub is None:
             args.n_sub = n_sub
     elif args.n_sub is None:
         args.n_sub = 20
     if args.impl == "reference":
-        if args.workload == "batched":
+        if args.workload in ("batched", "tcr"):
             args.workload = "star79k"
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
+    elif args.workload == "tcr":
+        run_tcr(args)
     else:
         run_gpu(args)
 

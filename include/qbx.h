@@ -39,6 +39,10 @@ extern "C" {
 #define QBX_FP64 0         /* every stage in FP64 */
 #define QBX_M2L_FP32 1     /* List 2 M2L and List 3-far M2QBXL in FP32; the rest FP64 */
 #define QBX_M2L_3XTF32 2   /* the same two stages as split-TF32 tensor-core products, FP32 accumulation */
+/* OR'ed into QBX_M2L_FP32 or QBX_M2L_3XTF32 to reduce the precision of one of the two stages only,
+   so that the error of each reduced-precision stage can be measured on its own: */
+#define QBX_MIXED_M2L_ONLY 0x10     /* List 2 M2L reduced; List 3-far M2QBXL stays FP64 */
+#define QBX_MIXED_M2QBXL_ONLY 0x20  /* List 3-far M2QBXL reduced; List 2 M2L stays FP64 */
 
 /* list identifiers for qbx_lists_nnz / qbx_lists_export (Section 5.2.3-5.2.4) */
 #define QBX_LIST_U 0      /* List 1 */
@@ -52,11 +56,16 @@ typedef struct qbx_tree qbx_tree;
 typedef struct qbx_lists qbx_lists;
 typedef struct qbx_graph qbx_graph;
 
+/* qbx_tree_opts.flags: tree variants (both off = the method of Section 5.2) */
+#define QBX_TREE_LINF_TCR 1u       /* box-shaped TCR of the two-dimensional method (Table l2-comparison) */
+#define QBX_TREE_LEVEL_RESTRICT 2u /* adjacent leaves differ by at most one level (Section 5.3, Remark
+                                      "Effect of level-restriction on List 3 complexity") */
+
 typedef struct {
     int n_max;       /* split boxes owning more than n_max particles (Algorithm 4, Stage 1); >= 1 */
     double t_f;      /* target confinement factor t_f (Section 5.2.2); >= 0 */
     int max_depth;   /* deepest level created; 0 < max_depth <= 50 */
-    unsigned flags;  /* reserved, must be 0 */
+    unsigned flags;  /* 0 or an OR of QBX_TREE_LINF_TCR, QBX_TREE_LEVEL_RESTRICT */
 } qbx_tree_opts;
 
 typedef struct {
@@ -75,6 +84,15 @@ typedef struct {
  * octant "coordinate >= box center", a center goes to its octant child only if its
  * ball lies inside the child's TCR, B2(sqrt(3)|child|(1+t_f)).  Only non-empty
  * children are made.  Boxes are numbered by (level, Morton code).
+ * Variants (opts->flags):
+ *   QBX_TREE_LINF_TCR: the TCR of a box is the cube of l-infinity radius |b|(1+t_f) about its
+ *     center (the region of the two-dimensional method that Table l2-comparison compares with),
+ *     both for where a center goes and in the relation a < TCR(b) of the lists, which then
+ *     measures the l-infinity distance to that cube;
+ *   QBX_TREE_LEVEL_RESTRICT: after Stage 1 the tree is made level-restricted in rounds; a round
+ *     splits every leaf that touches (closed cubes meet) a leaf two or more levels finer, moving
+ *     its particles by the Stage 1 rule, until a round splits nothing (a leaf none of whose
+ *     particles can move stays a leaf).
  *   src_xyz_dev (3,n_src), ctr_xyz_dev (3,n_ctr), ctr_r_dev (n_ctr, > 0), tgt_xyz_dev (3,n_tgt):
  *   device arrays, read during the call only.  n_* >= 0, n_src + n_ctr + n_tgt >= 1.
  *   out: receives a new handle.
@@ -172,8 +190,35 @@ typedef struct {
     const int8_t *p_fmm_per_box;  /* optional device array [n_boxes], order in [0, p_fmm] of each box's local
                                      expansion (List 2 M2L and List 4 far P2L outputs, L2L, L2QBXL, L2P);
                                      multipoles always have the order p_fmm */
-    int precision;                /* QBX_FP64, QBX_M2L_FP32 or QBX_M2L_3XTF32 */
+    int precision;                /* QBX_FP64, QBX_M2L_FP32 or QBX_M2L_3XTF32 (the latter two optionally
+                                     OR QBX_MIXED_M2L_ONLY or QBX_MIXED_M2QBXL_ONLY) */
 } qbx_eval_opts;
+
+/*
+ * Element marks of the geometry processing (Section 3): the tests by which Algorithm 1
+ * (stage-1 refinement: expansion balls disturbed by source geometry, Section 3.2) and
+ * Algorithm 2 (stage-2 refinement: quadrature resolution near centers, Section 3.3) choose the
+ * elements to bisect, evaluated over `tree`, a tree of the sources and the expansion centers
+ * (targets are not needed).  Each query point searches the boxes of the tree that meet a cube
+ * around it (the area queries of Appendix A):
+ *   which = QBX_REFINE_INTERFERING (Algorithm 1): for every center c_i, the element elem_dev[i]
+ *     that spawned it is marked if some source s has |c_i - s| < (1 - eps) r_i; eps is the
+ *     disturbance tolerance (0.025 in the paper; 0 <= eps < 1) that keeps the source point
+ *     below the center out of the test.  elem_dev[n_ctr] in input center order; elem_eta unused.
+ *   which = QBX_REFINE_QUAD_RES (Algorithm 2): for every source s_j, its element k = elem_dev[j]
+ *     is marked if some center c has |c - s_j| <= 0.5 (3/4) eta_k; elem_dev[n_src] in input source
+ *     order, elem_eta_dev[n_elem] the elements' resolution measure eta_k (eq. stretch-factor).
+ *   marks_dev[n_elem] out: 1 for marked elements, 0 otherwise.
+ * Distances are sqrt(dx^2 + dy^2 + dz^2) with correctly rounded operations in that order.  The
+ * bisection itself and the loop until nothing is marked belong to the caller, who owns the mesh.
+ * Not for forests.
+ * Errors: QBX_ERR_INVALID_ARG (NULL array, bad `which` or eps, element index outside [0, n_elem)),
+ * QBX_ERR_OOM, QBX_ERR_CUDA.
+ */
+#define QBX_REFINE_INTERFERING 0
+#define QBX_REFINE_QUAD_RES 1
+int qbx_refine_marks(const qbx_tree *tree, int which, const int32_t *elem_dev, const double *elem_eta_dev,
+                     int64_t n_elem, double eps, uint8_t *marks_dev, void *stream);
 
 /*
  * GIGAQBX FMM evaluation (Algorithm 4, Stages 2-9) of

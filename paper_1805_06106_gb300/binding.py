@@ -15,6 +15,9 @@ import torch
 from . import build as _build
 
 QBX_FP64, QBX_M2L_FP32, QBX_M2L_3XTF32 = 0, 1, 2
+QBX_MIXED_M2L_ONLY, QBX_MIXED_M2QBXL_ONLY = 0x10, 0x20
+QBX_TREE_LINF_TCR, QBX_TREE_LEVEL_RESTRICT = 1, 2
+QBX_REFINE_INTERFERING, QBX_REFINE_QUAD_RES = 0, 1
 LIST_NAMES = ("U", "V", "Wclose", "Wfar", "Xclose", "Xfar")
 STAGE_NAMES = ("prep", "p2m_m2m", "m2l", "p2l", "l2l", "m2qbxl_mixed", "centers", "m2qbxl_reduce", "qbx_targets",
                "point_targets")
@@ -67,6 +70,7 @@ def lib():
         L.qbx_lists_free.argtypes = [P]
         L.qbx_lists_free.restype = None
         L.qbx_assoc_targets.argtypes = [P, P, P, P, C.c_double, P, P, P]
+        L.qbx_refine_marks.argtypes = [P, C.c_int, P, P, I64, C.c_double, P, P]
         L.qbx_lists_cost.argtypes = [P, C.c_int, C.c_int, C.POINTER(_Cost), P]
         L.qbx_eval.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
         L.qbx_eval_noalloc.argtypes = [P, P, P, P, P, P, P, C.POINTER(_EvalOpts), P, P]
@@ -188,10 +192,13 @@ class Lists:
             self.handle = None
 
 
-def qbx_build_tree(src_xyz, ctr_xyz, ctr_r, tgt_xyz, n_max=32, t_f=0.9, max_depth=40) -> Tree:
-    """Octree with target confinement (Algorithm 4 Stage 1). Inputs: CUDA float64 (3, N) / (N,)."""
+def qbx_build_tree(src_xyz, ctr_xyz, ctr_r, tgt_xyz, n_max=32, t_f=0.9, max_depth=40, linf_tcr=False,
+                   level_restrict=False) -> Tree:
+    """Octree with target confinement (Algorithm 4 Stage 1). Inputs: CUDA float64 (3, N) / (N,).
+    linf_tcr / level_restrict select QBX_TREE_LINF_TCR / QBX_TREE_LEVEL_RESTRICT."""
     s, c, r, t = (_dev(x, torch.float64) for x in (src_xyz, ctr_xyz, ctr_r, tgt_xyz))
-    opts = _TreeOpts(n_max, t_f, max_depth, 0)
+    flags = (QBX_TREE_LINF_TCR if linf_tcr else 0) | (QBX_TREE_LEVEL_RESTRICT if level_restrict else 0)
+    opts = _TreeOpts(n_max, t_f, max_depth, flags)
     h = C.c_void_p()
     _check(lib().qbx_build_tree(_ptr(s), s.shape[1], _ptr(c), _ptr(r), c.shape[1], _ptr(t), t.shape[1],
                                 C.byref(opts), C.byref(h), _stream()))
@@ -216,6 +223,17 @@ def qbx_assoc_targets(tree: Tree, src_danger_r, src_n=None, ctr_side=None, eps=0
     _check(lib().qbx_assoc_targets(tree.handle, _ptr(rd), _ptr(n), _ptr(cs), float(eps), _ptr(tc), _ptr(fl),
                                    _stream()))
     return tc, fl
+
+
+def qbx_refine_marks(tree: Tree, which, elem, n_elem, elem_eta=None, eps=0.025):
+    """Element marks of Algorithm 1 (which = QBX_REFINE_INTERFERING, elem per center) or Algorithm 2
+    (QBX_REFINE_QUAD_RES, elem per source, elem_eta per element): uint8[n_elem] on the device."""
+    e = _dev(elem, torch.int32)
+    eta = _dev(elem_eta, torch.float64)
+    out = torch.empty(max(int(n_elem), 1), dtype=torch.uint8, device="cuda")
+    _check(lib().qbx_refine_marks(tree.handle, int(which), _ptr(e), _ptr(eta), int(n_elem), float(eps), _ptr(out),
+                                  _stream()))
+    return out[:int(n_elem)]
 
 
 def qbx_lists_cost(lists: Lists, p_qbx, p_fmm) -> dict:

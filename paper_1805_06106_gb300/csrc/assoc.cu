@@ -137,6 +137,75 @@ __global__ void k_assoc(AssocArgs a)
     a.flagged[ti] = cidx < 0 ? 1 : 0;
 }
 
+
+// ---------------------------------------------------------------- refinement marks (Section 3)
+
+// Algorithms 1 and 2 mark elements for bisection from per-point tests over a tree of the sources
+// and centers; one thread per query point searches the tree from the root for the boxes whose
+// closed cube meets the query cube (padded by a relative 1e-12 against rounding in the box test;
+// the distance test itself is exact in the same expression as a CPU evaluation):
+//   which 0 (Algorithm 1): query = center i, radius (1 - eps) r_i, hit = a source strictly
+//           inside; marks the element that spawned the center (sources live in leaves);
+//   which 1 (Algorithm 2): query = source j of element k, radius 0.375 eta_k (0.5 (3/4) eta_k),
+//           hit = a center at most that far, owned by any box (centers may sit above the leaves);
+//           marks element k.
+struct RefineArgs {
+    int which;
+    int64_t nq, ns, nc, n_elem;
+    const int *qperm;                           // sorted query slot -> input index
+    const double *qxyz;                         // sorted query points
+    const double *qr;                           // which 0: sorted center radii
+    const double *sxyz, *cxyz;
+    const double *cen, *hw;
+    const int *child, *own_src, *own_ctr;
+    const int *elem;                            // input order: element of each query point
+    const double *eta;                          // which 1: eta per element
+    double eps;
+    unsigned char *mark;
+    int *err;                                   // 1: stack overflow, 2: element index out of range
+};
+
+__global__ void k_refine_marks(RefineArgs a)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.nq) return;
+    const int e = a.elem[a.qperm[i]];
+    if (e < 0 || e >= a.n_elem) {
+        atomicOr(a.err, 2);
+        return;
+    }
+    if (a.mark[e]) return;  // already marked by another point of the element (a benign read)
+    const double x = a.qxyz[i], y = a.qxyz[a.nq + i], z = a.qxyz[2 * a.nq + i];
+    const double R = a.which == 0 ? __dmul_rn(__dsub_rn(1.0, a.eps), a.qr[i]) : __dmul_rn(0.375, a.eta[e]);
+    int stack[ASSOC_STACK];
+    int sp = 0;
+    stack[sp++] = 0;
+    bool hit = false;
+    while (sp > 0 && !hit) {
+        const int b = stack[--sp];
+        const double ext = __dmul_rn(__dadd_rn(R, a.hw[b]), 1.0 + 1e-12);
+        if (!(fabs(__dsub_rn(x, a.cen[3 * b])) <= ext && fabs(__dsub_rn(y, a.cen[3 * b + 1])) <= ext &&
+              fabs(__dsub_rn(z, a.cen[3 * b + 2])) <= ext))
+            continue;
+        bool leaf = true;
+        for (int o = 0; o < 8; ++o) {
+            const int ch = a.child[8 * b + o];
+            if (ch < 0) continue;
+            leaf = false;
+            if (sp < ASSOC_STACK) stack[sp++] = ch;
+            else atomicOr(a.err, 1);
+        }
+        if (a.which == 0) {
+            if (!leaf) continue;
+            for (int j = a.own_src[b]; j < a.own_src[b + 1] && !hit; ++j)
+                hit = rn_dist(x, y, z, a.sxyz[j], a.sxyz[a.ns + j], a.sxyz[2 * a.ns + j]) < R;
+        } else {
+            for (int k = a.own_ctr[b]; k < a.own_ctr[b + 1] && !hit; ++k)
+                hit = rn_dist(x, y, z, a.cxyz[k], a.cxyz[a.nc + k], a.cxyz[2 * a.nc + k]) <= R;
+        }
+    }
+    if (hit) a.mark[e] = 1;
+}
 }  // namespace qbx
 
 using namespace qbx;
@@ -179,6 +248,54 @@ extern "C" int qbx_assoc_targets(const qbx_tree *T, const double *rdanger, const
             throw;
         }
         dfree(rmax);
+        dfree(err);
+        return QBX_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (...) {
+        set_error("unexpected exception");
+        return QBX_ERR_CUDA;
+    }
+}
+
+extern "C" int qbx_refine_marks(const qbx_tree *T, int which, const int32_t *elem, const double *elem_eta,
+                                int64_t n_elem, double eps, uint8_t *marks, void *stream)
+{
+    try {
+        set_error("");
+        if (!T || !elem || !marks || n_elem < 0 || T->nprob != 1 || (which != QBX_REFINE_INTERFERING &&
+                                                                     which != QBX_REFINE_QUAD_RES))
+            throw Error{QBX_ERR_INVALID_ARG, "bad argument (NULL array, which, n_elem < 0, or a forest)"};
+        if (which == QBX_REFINE_INTERFERING && !(eps >= 0.0 && eps < 1.0))
+            throw Error{QBX_ERR_INVALID_ARG, "eps must lie in [0, 1)"};
+        if (which == QBX_REFINE_QUAD_RES && !elem_eta) throw Error{QBX_ERR_INVALID_ARG, "elem_eta is NULL"};
+        cudaStream_t st = (cudaStream_t)stream;
+        if (n_elem == 0) return QBX_OK;
+        QBX_CUDA_TRY(cudaMemsetAsync(marks, 0, (size_t)n_elem, st));
+        const bool q_is_ctr = which == QBX_REFINE_INTERFERING;
+        const int64_t nq = q_is_ctr ? T->np[KCTR] : T->np[KSRC];
+        if (nq == 0) return QBX_OK;
+        int *err = dalloc<int>(1);
+        try {
+            QBX_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
+            RefineArgs a{which,        nq,       T->np[KSRC],  T->np[KCTR],
+                         n_elem,       q_is_ctr ? T->perm[KCTR] : T->perm[KSRC],
+                         q_is_ctr ? T->cxyz : T->sxyz,          T->cr,
+                         T->sxyz,      T->cxyz,  T->cen,       T->hw,
+                         T->child,     T->own_start[KSRC], T->own_start[KCTR], elem, elem_eta, eps,
+                         reinterpret_cast<unsigned char *>(marks), err};
+            k_refine_marks<<<nblocks(nq, 128), 128, 0, st>>>(a);
+            QBX_LAUNCH_CHECK();
+            int e = 0;
+            QBX_CUDA_TRY(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+            QBX_CUDA_TRY(cudaStreamSynchronize(st));
+            if (e & 2) throw Error{QBX_ERR_INVALID_ARG, "element index out of range"};
+            if (e & 1) throw Error{QBX_ERR_CUDA, "refinement marks: traversal stack overflow"};
+        } catch (...) {
+            dfree(err);
+            throw;
+        }
         dfree(err);
         return QBX_OK;
     } catch (const Error &e) {

@@ -2016,16 +2016,20 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
                                                      ws->Mu, ws->Muf);
         QBX_LAUNCH_CHECK();
     }
+    // reduced precision per stage: QBX_MIXED_*_ONLY keeps the other stage in FP64
+    const int pbase = o->precision & 0xF;
+    const bool tc = pbase == QBX_M2L_3XTF32;
+    const bool m2l_mixed = pbase != QBX_FP64 && !(o->precision & QBX_MIXED_M2QBXL_ONLY);
+    const bool wfar_mixed = pbase != QBX_FP64 && !(o->precision & QBX_MIXED_M2L_ONLY);
     // Stage 4
     stage_mark(L, 2, st);
-    if (o->precision == QBX_FP64) {
+    if (!m2l_mixed) {
         size_t smem = (size_t)WPB * ntri(PM_T) * sizeof(double2);
         k_m2l<PM_T><<<nblocks(nb, WPB), 32 * WPB, smem, st>>>(nb, L->start[LV], L->idx[LV], T->ic, T->hw, ws->pb,
                                                               ws->ps, ws->Mu, ws->m2l_tab, ws->B);
         QBX_LAUNCH_CHECK();
     } else {
         const int Pm = o->p_fmm;
-        const bool tc = o->precision == QBX_M2L_3XTF32;
         const int mkey = (Pm * 2 + (tc ? 1 : 0)) * 64 + L->tile_m2l_kc;
         if (!ws->m2l || ws->m2l_key != mkey) {
             free_m2l_plan(ws->m2l);
@@ -2067,9 +2071,8 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     // Stage 5(b) in mixed precision: List 3 far products, reduced into the QBX locals below
     stage_mark(L, 5, st);
     WfarPlan *wf = nullptr;
-    if (o->precision != QBX_FP64 && T->np[KCTR] > 0) {
+    if (wfar_mixed && T->np[KCTR] > 0) {
         const int Pm = o->p_fmm, Qm = o->p_qbx;
-        const bool tc = o->precision == QBX_M2L_3XTF32;
         const int wkey = ((Pm * 100 + Qm) * 2 + (tc ? 1 : 0)) * 256 + L->tile_wfar_w;
         if (!ws->wfar || ws->wfar_key != wkey) {
             free_wfar_plan(ws->wfar);
@@ -2127,7 +2130,7 @@ void eval(const qbx_tree *T, qbx_lists *L, const double *w, const double *sigma,
     }
     stage_mark(L, 10, st);
     L->prof_valid = L->prof;
-    if (o->precision == QBX_M2L_3XTF32 && cap == cudaStreamCaptureStatusNone) {
+    if (tc && cap == cudaStreamCaptureStatusNone) {
         // the tensor-core kernels report a wait that gave up through the flags word
         if (read_flags(ws->flags, st) & 8) throw Error{QBX_ERR_TIMEOUT, "a tensor-core pipeline wait timed out"};
     }

@@ -67,6 +67,7 @@ void build_forest(int n, const qbx_tree *const *trees, const qbx_lists *const *l
     F->nlev = nlev;
     for (int k = 0; k < 3; ++k) F->np[k] = np[k];
     F->tf = trees[0]->tf;
+    F->flags = trees[0]->flags;
     for (int d = 0; d < 3; ++d) F->root_c[d] = trees[0]->root_c[d];
     F->root_h = trees[0]->root_h;
 

@@ -22,6 +22,7 @@ struct TreeView {
     const int *parent, *child, *nsrc_sub, *ntgt_sub;
     const int *own_start_src, *own_start_ctr, *own_start_tgt;
     double tf;
+    bool linf;  // the l-infinity TCR (QBX_TREE_LINF_TCR)
     int *err;
 
     __device__ bool leaf(int b) const
@@ -56,9 +57,16 @@ struct TreeView {
         }
         return true;
     }
-    // a adequately separated from TCR(b) (l2, signed distance to the TCR boundary >= 3|a|)
+    // a adequately separated from TCR(b) (l2, signed distance to the TCR boundary >= 3|a|);
+    // with the l-infinity TCR, the l-infinity distance from the center of a to the boundary of
+    // the cube of radius |b|(1 + t_f), signed, is >= 3|a|
     __device__ bool sep_a_tcrb(int a, int b) const
     {
+        if (linf) {
+            double m = 0.0;
+            for (int d = 0; d < 3; ++d) m = fmax(m, fabs(__dsub_rn(cen[3 * a + d], cen[3 * b + d])));
+            return __dsub_rn(m, __dmul_rn(hw[b], __dadd_rn(1.0, tf))) >= __dmul_rn(3.0, hw[a]);
+        }
         double dx = __dsub_rn(cen[3 * a], cen[3 * b]), dy = __dsub_rn(cen[3 * a + 1], cen[3 * b + 1]),
                dz = __dsub_rn(cen[3 * a + 2], cen[3 * b + 2]);
         double dist = __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz)));
@@ -364,7 +372,7 @@ void build_lists(qbx_lists *L, cudaStream_t st)
         QBX_CUDA_TRY(cudaMemsetAsync(err, 0, sizeof(int), st));
         TreeView T{nb, (int)Tr->nlev, (int)Tr->nlev - 1, ls, Tr->level, Tr->ic, Tr->cen, Tr->hw, Tr->parent,
                    Tr->child, Tr->nsrc_sub, Tr->ntgt_sub, Tr->own_start[KSRC], Tr->own_start[KCTR],
-                   Tr->own_start[KTGT], Tr->tf, err};
+                   Tr->own_start[KTGT], Tr->tf, (Tr->flags & QBX_TREE_LINF_TCR) != 0, err};
         for (int l = 0; l < NLIST; ++l) {
             cnt[l] = dalloc<int>(nb + 1);
             L->start[l] = dalloc<int>(nb + 1);

@@ -62,8 +62,11 @@ void check_eval_args(const qbx_tree *T, const qbx_lists *L, const double *w, con
     if (T->np[0] && !w) throw Error{QBX_ERR_INVALID_ARG, "src_w is NULL"};
     if (mu && !nrm) throw Error{QBX_ERR_INVALID_ARG, "mu given without normals"};
     if (T->np[2] && (!tgt_ctr || !pot)) throw Error{QBX_ERR_INVALID_ARG, "tgt_ctr/pot is NULL"};
-    if (o->precision != QBX_FP64 && o->precision != QBX_M2L_FP32 && o->precision != QBX_M2L_3XTF32)
+    const int base = o->precision & 0xF, only = o->precision & ~0xF;
+    if (base != QBX_FP64 && base != QBX_M2L_FP32 && base != QBX_M2L_3XTF32)
         throw Error{QBX_ERR_INVALID_ARG, "precision mode not available"};
+    if (only != 0 && (base == QBX_FP64 || (only != QBX_MIXED_M2L_ONLY && only != QBX_MIXED_M2QBXL_ONLY)))
+        throw Error{QBX_ERR_INVALID_ARG, "stage selection needs QBX_M2L_FP32 or QBX_M2L_3XTF32 and one stage"};
     if (o->p_qbx < 0 || o->p_qbx > QMAX) throw Error{QBX_ERR_INVALID_ARG, "p_qbx out of range"};
     if (o->p_fmm < 0 || o->p_fmm > PMAX) throw Error{QBX_ERR_INVALID_ARG, "p_fmm out of range"};
     if (!o->p_qbx_per_ctr && !o->p_fmm_per_box && o->p_qbx > o->p_fmm)
@@ -88,7 +91,8 @@ int qbx_build_tree(const double *src_xyz_dev, int64_t n_src, const double *ctr_x
         if (n_src + n_ctr + n_tgt >= (int64_t(1) << 31)) throw Error{QBX_ERR_INVALID_ARG, "too many particles"};
         if ((n_src && !src_xyz_dev) || (n_ctr && (!ctr_xyz_dev || !ctr_r_dev)) || (n_tgt && !tgt_xyz_dev))
             throw Error{QBX_ERR_INVALID_ARG, "NULL particle array"};
-        if (opts->n_max < 1 || !(opts->t_f >= 0.0) || !std::isfinite(opts->t_f) || opts->flags != 0 ||
+        if (opts->n_max < 1 || !(opts->t_f >= 0.0) || !std::isfinite(opts->t_f) ||
+            (opts->flags & ~(unsigned)(QBX_TREE_LINF_TCR | QBX_TREE_LEVEL_RESTRICT)) != 0 ||
             opts->max_depth < 1)
             throw Error{QBX_ERR_INVALID_ARG, "bad tree options"};
         if (opts->max_depth > 50) throw Error{QBX_ERR_DEPTH, "max_depth > 50"};
@@ -99,6 +103,7 @@ int qbx_build_tree(const double *src_xyz_dev, int64_t n_src, const double *ctr_x
         T->n_max = opts->n_max;
         T->max_depth = opts->max_depth;
         T->tf = opts->t_f;
+        T->flags = opts->flags;
         try {
             build_tree(T, src_xyz_dev, ctr_xyz_dev, ctr_r_dev, tgt_xyz_dev, (cudaStream_t)stream);
         } catch (...) {

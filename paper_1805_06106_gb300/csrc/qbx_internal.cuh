@@ -74,6 +74,7 @@ struct qbx_tree {
     int64_t nb = 0, nlev = 0, np[3] = {0, 0, 0}, n_overfull = 0;
     int n_max = 0, max_depth = 0;
     double tf = 0.0;
+    unsigned flags = 0;  // QBX_TREE_LINF_TCR, QBX_TREE_LEVEL_RESTRICT
     double root_c[3] = {0, 0, 0}, root_h = 0.0;
     std::vector<int> level_start;  // host copy, nlev + 1
     // device box arrays

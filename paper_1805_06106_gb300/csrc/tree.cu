@@ -177,6 +177,16 @@ __device__ __forceinline__ bool fits_tcr(double x, double y, double z, double r,
     return lhs <= rhs;
 }
 
+// The box-shaped TCR of the two-dimensional method (the l-infinity columns of Table
+// l2-comparison): the cube of l-infinity radius h (1 + t_f) about c holds the ball,
+// |x - c|_inf + r <= h (1 + t_f).
+__device__ __forceinline__ bool fits_tcr_linf(double x, double y, double z, double r, double cx, double cy,
+                                              double cz, double h, double tf)
+{
+    double m = fmax(fmax(fabs(__dsub_rn(x, cx)), fabs(__dsub_rn(y, cy))), fabs(__dsub_rn(z, cz)));
+    return __dadd_rn(m, r) <= __dmul_rn(h, __dadd_rn(1.0, tf));
+}
+
 struct Particles {
     const double *xyz[3];
     const double *cr;
@@ -284,8 +294,11 @@ __global__ void k_count(Particles P, int b0, int b1, int *cnt)
 }
 
 // Destination octant of every particle owned by a splitting box at this level, or -1.
+// A box splits when it owns more than n_max particles or, in a rebuild for level
+// restriction, when its box of the previous tree (oid) had children or was marked (oforce).
 __global__ void k_dest(Particles P, int b0, int b1, const int *cnt, int n_max, bool can_split, const double *cen,
-                       const double *hw, double tf, signed char *dest, int *cmask)
+                       const double *hw, double tf, bool linf, const int *oid, const unsigned char *oforce,
+                       signed char *dest, int *cmask)
 {
     int64_t N = P.n[0] + P.n[1] + P.n[2];
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < N; g += (int64_t)gridDim.x * blockDim.x) {
@@ -294,7 +307,8 @@ __global__ void k_dest(Particles P, int b0, int b1, const int *cnt, int n_max, b
         P.locate(g, k, i);
         signed char dd = -1;
         int o = P.owner[k][i];
-        if (can_split && o >= b0 && o < b1 && cnt[o - b0] > n_max) {
+        if (can_split && o >= b0 && o < b1 &&
+            (cnt[o - b0] > n_max || (oid && oid[o] >= 0 && oforce[oid[o]]))) {
             double x = P.xyz[k][i], y = P.xyz[k][P.n[k] + i], z = P.xyz[k][2 * P.n[k] + i];
             double cx = cen[3 * o], cy = cen[3 * o + 1], cz = cen[3 * o + 2];
             int oc = (x >= cx ? 1 : 0) | (y >= cy ? 2 : 0) | (z >= cz ? 4 : 0);
@@ -304,7 +318,8 @@ __global__ void k_dest(Particles P, int b0, int b1, const int *cnt, int n_max, b
                 double ccx = __dadd_rn(cx, (oc & 1) ? hc : -hc);
                 double ccy = __dadd_rn(cy, (oc & 2) ? hc : -hc);
                 double ccz = __dadd_rn(cz, (oc & 4) ? hc : -hc);
-                ok = fits_tcr(x, y, z, P.cr[i], ccx, ccy, ccz, hc, tf);
+                ok = linf ? fits_tcr_linf(x, y, z, P.cr[i], ccx, ccy, ccz, hc, tf)
+                          : fits_tcr(x, y, z, P.cr[i], ccx, ccy, ccz, hc, tf);
             }
             if (ok) {
                 dd = (signed char)oc;
@@ -324,8 +339,11 @@ __global__ void k_popc(const int *cmask, const int *cnt, int nbl, int n_max, boo
     if (at_max_depth && cnt[b] > n_max) atomicAdd(overfull, 1);
 }
 
+// Children of the splitting boxes of one level, in (parent, octant) = Morton order.  In a
+// rebuild, oid maps each new box to the same box of the previous tree (ochild), or -1.
 __global__ void k_children(int b0, int nbl, int first_new, int lev, const int *cmask, const int *choff, int *level,
-                           int64_t *ic, double *cen, double *hw, int *parent, int *child)
+                           int64_t *ic, double *cen, double *hw, int *parent, int *child, const int *ochild,
+                           int *oid)
 {
     int bb = blockIdx.x * blockDim.x + threadIdx.x;
     if (bb >= nbl) return;
@@ -346,6 +364,63 @@ __global__ void k_children(int b0, int nbl, int first_new, int lev, const int *c
         parent[c] = b;
         for (int o = 0; o < 8; ++o) child[8 * c + o] = -1;
         child[8 * b + oc] = c;
+        if (oid) oid[c] = oid[b] >= 0 ? ochild[8 * oid[b] + oc] : -1;
+    }
+}
+
+// Level restriction (Remark "Effect of level-restriction on List 3 complexity", Section
+// 5.3): one round's marks on the current tree.  force[b] = 1 for boxes with children (they
+// stay split) and for every leaf that touches a leaf two or more levels finer (closed cubes
+// meet; distinct leaves never overlap, so that is adjacency), found by a depth-first walk
+// from the root over the boxes whose closed cube meets b's, exact in integer units of the
+// finest level lf.  nviol counts the marked leaves; a stack overflow sets *err.
+constexpr int RESTRICT_STACK = 8 * 64;
+
+__global__ void k_restrict_marks(int nb, int lf, int max_depth, const int *level, const int64_t *ic,
+                                 const int *child, unsigned char *force, int *nviol, int *err)
+{
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nb) return;
+    bool has_child = false;
+    for (int o = 0; o < 8; ++o) has_child |= child[8 * b + o] >= 0;
+    force[b] = has_child ? 1 : 0;
+    const int lb = level[b];
+    if (has_child || lb + 2 > lf || lb >= max_depth) return;
+    int64_t lo[3], hi[3];
+    for (int d = 0; d < 3; ++d) {
+        lo[d] = ic[3 * b + d] << (lf - lb);
+        hi[d] = (ic[3 * b + d] + 1) << (lf - lb);
+    }
+    int stack[RESTRICT_STACK];
+    int n = 0;
+    stack[n++] = 0;
+    bool viol = false;
+    while (n && !viol) {
+        int c = stack[--n];
+        if (c == b) continue;
+        const int sh = lf - level[c];
+        bool meets = true;
+        for (int d = 0; d < 3; ++d) {
+            int64_t l = ic[3 * c + d] << sh, h = (ic[3 * c + d] + 1) << sh;
+            if (l > hi[d] || lo[d] > h) meets = false;
+        }
+        if (!meets) continue;
+        bool leaf = true;
+        for (int o = 0; o < 8; ++o) {
+            int ch = child[8 * c + o];
+            if (ch < 0) continue;
+            leaf = false;
+            if (n >= RESTRICT_STACK) {
+                atomicOr(err, 1);
+                return;
+            }
+            stack[n++] = ch;
+        }
+        if (leaf && level[c] >= lb + 2) viol = true;
+    }
+    if (viol) {
+        force[b] = 1;
+        atomicAdd(nviol, 1);
     }
 }
 
@@ -454,7 +529,7 @@ void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const doubl
     int *flags = dalloc<int>(4);  // [0] bad input, [1] overfull, [2] scan total
     double rootp_h[4];
     signed char *dest = dalloc<signed char>(N);
-    int *cnt = nullptr, *cmask = nullptr, *nch = nullptr;
+    int *cnt = nullptr, *cmask = nullptr, *nch = nullptr, *oid = nullptr;
     try {
         QBX_CUDA_TRY(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st));
         k_bbox<<<nbb, 256, 0, st>>>(P, part, flags);
@@ -469,47 +544,126 @@ void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const doubl
         for (int d = 0; d < 3; ++d) T->root_c[d] = rootp_h[d];
         T->root_h = rootp_h[3];
 
-        int b0 = 0, b1 = 1, lev = 0;
-        T->level_start.assign(1, 0);
-        int64_t lvcap = 0;
+        const bool linf = (T->flags & QBX_TREE_LINF_TCR) != 0;
         const unsigned gp = std::min<unsigned>(nblocks(N, 256), 152 * 16);
-        for (;; ++lev) {
-            T->level_start.push_back(b1);
-            int nbl = b1 - b0;
-            if (nbl > lvcap) {
-                dfree(cnt); dfree(cmask); dfree(nch);
-                lvcap = std::max<int64_t>(nbl, 2 * lvcap);
-                cnt = dalloc<int>(lvcap);
-                cmask = dalloc<int>(lvcap);
-                nch = dalloc<int>(lvcap);
+        int64_t lvcap = 0, oid_cap = 0;
+        // Stage 1 level by level from the root.  With ochild/oforce (a rebuild for level
+        // restriction), oid tracks each new box's box in the previous tree, whose split is kept
+        // (it had children) or made (it was marked).
+        auto run_levels = [&](const int *ochild, const unsigned char *oforce) {
+            int b0 = 0, b1 = 1, lev = 0;
+            T->level_start.assign(1, 0);
+            if (ochild) {
+                if (oid_cap < cap) {
+                    dfree(oid);
+                    oid = dalloc<int>(cap);
+                    oid_cap = cap;
+                }
+                QBX_CUDA_TRY(cudaMemsetAsync(oid, 0, sizeof(int), st));  // the root is the root
             }
-            QBX_CUDA_TRY(cudaMemsetAsync(cnt, 0, nbl * sizeof(int), st));
-            QBX_CUDA_TRY(cudaMemsetAsync(cmask, 0, nbl * sizeof(int), st));
-            bool can_split = lev < T->max_depth;
-            k_count<<<gp, 256, 0, st>>>(P, b0, b1, cnt);
-            QBX_LAUNCH_CHECK();
-            k_dest<<<gp, 256, 0, st>>>(P, b0, b1, cnt, T->n_max, can_split, T->cen, T->hw, T->tf, dest, cmask);
-            QBX_LAUNCH_CHECK();
-            k_popc<<<nblocks(nbl, 256), 256, 0, st>>>(cmask, cnt, nbl, T->n_max, !can_split, nch, flags + 1);
-            QBX_LAUNCH_CHECK();
-            exclusive_scan(nch, nch, nbl, 0, flags + 2, st);
-            int total = 0;
-            QBX_CUDA_TRY(cudaMemcpyAsync(&total, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
-            QBX_CUDA_TRY(cudaStreamSynchronize(st));
-            if (total == 0) break;
-            grow(T, cap, (int64_t)b1 + total, st);
-            k_children<<<nblocks(nbl, 128), 128, 0, st>>>(b0, nbl, b1, lev, cmask, nch, T->level, T->ic, T->cen,
-                                                          T->hw, T->parent, T->child);
-            QBX_LAUNCH_CHECK();
-            k_move<<<gp, 256, 0, st>>>(P, dest, T->child);
-            QBX_LAUNCH_CHECK();
-            b0 = b1;
-            b1 += total;
+            QBX_CUDA_TRY(cudaMemsetAsync(flags + 1, 0, sizeof(int), st));
+            for (;; ++lev) {
+                T->level_start.push_back(b1);
+                int nbl = b1 - b0;
+                if (nbl > lvcap) {
+                    dfree(cnt); dfree(cmask); dfree(nch);
+                    cnt = cmask = nch = nullptr;
+                    lvcap = std::max<int64_t>(nbl, 2 * lvcap);
+                    cnt = dalloc<int>(lvcap);
+                    cmask = dalloc<int>(lvcap);
+                    nch = dalloc<int>(lvcap);
+                }
+                QBX_CUDA_TRY(cudaMemsetAsync(cnt, 0, nbl * sizeof(int), st));
+                QBX_CUDA_TRY(cudaMemsetAsync(cmask, 0, nbl * sizeof(int), st));
+                bool can_split = lev < T->max_depth;
+                k_count<<<gp, 256, 0, st>>>(P, b0, b1, cnt);
+                QBX_LAUNCH_CHECK();
+                k_dest<<<gp, 256, 0, st>>>(P, b0, b1, cnt, T->n_max, can_split, T->cen, T->hw, T->tf, linf,
+                                           ochild ? oid : nullptr, oforce, dest, cmask);
+                QBX_LAUNCH_CHECK();
+                k_popc<<<nblocks(nbl, 256), 256, 0, st>>>(cmask, cnt, nbl, T->n_max, !can_split, nch, flags + 1);
+                QBX_LAUNCH_CHECK();
+                exclusive_scan(nch, nch, nbl, 0, flags + 2, st);
+                int total = 0;
+                QBX_CUDA_TRY(cudaMemcpyAsync(&total, flags + 2, sizeof(int), cudaMemcpyDeviceToHost, st));
+                QBX_CUDA_TRY(cudaStreamSynchronize(st));
+                if (total == 0) break;
+                grow(T, cap, (int64_t)b1 + total, st);
+                if (ochild && oid_cap < cap) {  // keep the old-box map as long as the box arrays
+                    int *o2 = dalloc<int>(cap);
+                    QBX_CUDA_TRY(cudaMemcpyAsync(o2, oid, b1 * sizeof(int), cudaMemcpyDeviceToDevice, st));
+                    QBX_CUDA_TRY(cudaStreamSynchronize(st));
+                    dfree(oid);
+                    oid = o2;
+                    oid_cap = cap;
+                }
+                k_children<<<nblocks(nbl, 128), 128, 0, st>>>(b0, nbl, b1, lev, cmask, nch, T->level, T->ic, T->cen,
+                                                              T->hw, T->parent, T->child, ochild,
+                                                              ochild ? oid : nullptr);
+                QBX_LAUNCH_CHECK();
+                k_move<<<gp, 256, 0, st>>>(P, dest, T->child);
+                QBX_LAUNCH_CHECK();
+                b0 = b1;
+                b1 += total;
+            }
+            T->nb = b1;
+            T->nlev = lev + 1;
+            T->level_start.resize(T->nlev + 1);
+            T->level_start[T->nlev] = b1;
+        };
+        run_levels(nullptr, nullptr);
+
+        // Level restriction (Remark "Effect of level-restriction on List 3 complexity", Section
+        // 5.3), in rounds: mark every leaf touching a leaf two or more levels finer, then rebuild
+        // with those leaves split as well (a rebuild equals splitting them in place: the boxes
+        // above are unchanged, and a split leaf owned at most n_max particles, so its children
+        // do not split on count); stop when a round marks nothing or splits nothing.
+        if (T->flags & QBX_TREE_LEVEL_RESTRICT) {
+            for (int round = 0; round < 4 * 64; ++round) {
+                const int nb0 = (int)T->nb;
+                unsigned char *force = dalloc<unsigned char>(nb0);
+                QBX_CUDA_TRY(cudaMemsetAsync(flags + 2, 0, 2 * sizeof(int), st));
+                k_restrict_marks<<<nblocks(nb0, 128), 128, 0, st>>>(nb0, (int)T->nlev - 1, T->max_depth, T->level,
+                                                                     T->ic, T->child, force, flags + 2, flags + 3);
+                int marks[2] = {0, 0};
+                try {
+                    QBX_LAUNCH_CHECK();
+                    QBX_CUDA_TRY(cudaMemcpyAsync(marks, flags + 2, sizeof(marks), cudaMemcpyDeviceToHost, st));
+                    QBX_CUDA_TRY(cudaStreamSynchronize(st));
+                    if (marks[1]) throw Error{QBX_ERR_CUDA, "level restriction: search stack overflow"};
+                } catch (...) {
+                    dfree(force);
+                    throw;
+                }
+                if (marks[0] == 0) {
+                    dfree(force);
+                    break;
+                }
+                // keep the previous tree's child array and marks; rebuild into fresh box arrays
+                int *ochild = T->child;
+                T->child = nullptr;
+                dfree(T->level); dfree(T->ic); dfree(T->cen); dfree(T->hw); dfree(T->parent);
+                T->level = T->parent = nullptr;
+                T->ic = nullptr;
+                T->cen = T->hw = nullptr;
+                cap = 0;
+                try {
+                    grow(T, cap, std::max<int64_t>(1024, nb0), st);
+                    k_root<<<1, 32, 0, st>>>(part, nbb, rootp, T->cen, T->hw, T->level, T->ic, T->parent, T->child);
+                    QBX_LAUNCH_CHECK();
+                    for (int k = 0; k < 3; ++k)
+                        QBX_CUDA_TRY(cudaMemsetAsync(T->owner[k], 0, std::max<int64_t>(T->np[k], 1) * sizeof(int), st));
+                    run_levels(ochild, force);
+                } catch (...) {
+                    dfree(ochild);
+                    dfree(force);
+                    throw;
+                }
+                dfree(ochild);
+                dfree(force);
+                if (T->nb == nb0) break;  // the marked leaves could not move a particle
+            }
         }
-        T->nb = b1;
-        T->nlev = lev + 1;
-        T->level_start.resize(T->nlev + 1);
-        T->level_start[T->nlev] = b1;
         int ov = 0;
         QBX_CUDA_TRY(cudaMemcpyAsync(&ov, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
         QBX_CUDA_TRY(cudaStreamSynchronize(st));
@@ -575,10 +729,10 @@ void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const doubl
         QBX_LAUNCH_CHECK();
         QBX_CUDA_TRY(cudaStreamSynchronize(st));
     } catch (...) {
-        dfree(part); dfree(rootp); dfree(flags); dfree(dest); dfree(cnt); dfree(cmask); dfree(nch);
+        dfree(part); dfree(rootp); dfree(flags); dfree(dest); dfree(cnt); dfree(cmask); dfree(nch); dfree(oid);
         throw;
     }
-    dfree(part); dfree(rootp); dfree(flags); dfree(dest); dfree(cnt); dfree(cmask); dfree(nch);
+    dfree(part); dfree(rootp); dfree(flags); dfree(dest); dfree(cnt); dfree(cmask); dfree(nch); dfree(oid);
 }
 
 }  // namespace qbx
