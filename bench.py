@@ -790,7 +790,7 @@ def run_gpu(args):
         torch.distributed.destroy_process_group()
 
 
-def forest_inputs(G, torch, dev, surfs, dens, n_max):
+def forest_inputs(G, torch, dev, surfs, dens, n_max, level_restrict=False):
     """Trees, lists and the forest of many surfaces; concatenated evaluation inputs (single layer)."""
     def cu(a, dt=torch.float64):
         return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
@@ -799,7 +799,8 @@ def forest_inputs(G, torch, dev, surfs, dens, n_max):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for s in surfs:
-        T = G.qbx_build_tree(cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(s.tgt_xyz), n_max=n_max, t_f=T_F)
+        T = G.qbx_build_tree(cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(s.tgt_xyz), n_max=n_max, t_f=T_F,
+                             level_restrict=level_restrict)
         trees.append(T)
         lists.append(G.qbx_build_lists(T))
     torch.cuda.synchronize()
@@ -850,7 +851,7 @@ def run_batched(args):
         tuned = autotune.tuned_n_max(G, surfs, dens, Q, P, G.QBX_M2L_3XTF32, default=N_MAX_MIXED,
                                      candidates=(64, 96, 128, 160, 192), enabled=not args.no_tune)
         n_max = args.n_max or tuned["n_max"]
-        fi = forest_inputs(G, torch, dev, surfs, dens, n_max)
+        fi = forest_inputs(G, torch, dev, surfs, dens, n_max, level_restrict=args.tree == "level-restricted")
         F, FL, ev = fi["F"], fi["FL"], fi["ev"]
         model, info = learned_model(G, n_max, Q, P)
         tl0 = time.perf_counter()
@@ -902,7 +903,7 @@ def run_batched(args):
             errs.append(float((a - b).abs().max() / b.abs().max()))
         build_ms, forest_ms = fi["build_ms"], fi["forest_ms"]
         del fi, graph
-        fp = forest_inputs(G, torch, dev, surfs, dens, N_MAX_FP64)
+        fp = forest_inputs(G, torch, dev, surfs, dens, N_MAX_FP64, level_restrict=args.tree == "level-restricted")
         ptmp = torch.empty_like(pot)
         pt = _time_eager(torch, lambda: G.qbx_eval(fp["F"], fp["FL"], *fp["ev"], Q, P, out=ptmp), stream, flush,
                          args.fp64_steps, 1)
@@ -927,6 +928,7 @@ def run_batched(args):
                                f"lognormal sizes ({int(sum(s.n_src for s in surfs))} sources, {n_qbx} QBX targets), "
                                "random Y_n^m (n<=10) single-layer densities; one forest, one CUDA graph",
                    "p_qbx": Q, "p_fmm": P, "n_max": n_max, "n_max_source": tuned["source"], "t_f": T_F,
+                   "tree": args.tree,
                    "sizes_src": [300 * n * n for n, _, _ in all_specs], "n_boxes_rank0": int(F.n_boxes),
                    "parallelism": f"surfaces split over {ws} GPUs by cost (LPT), no exchange" if ws > 1
                    else "single GPU",
