@@ -25,17 +25,31 @@ def _tree(src_xyz, ctr_xyz, ctr_r, n_max):
     return B.qbx_build_tree(cu(src_xyz), cu(ctr_xyz), cu(ctr_r), empty, n_max=n_max)
 
 
+def gpu_marks(d, which, eps=EPS_DISTURB, n_max=64):
+    """Element marks of one discretization on the GPU: a tree of its sources and centers, then
+    qbx_refine_marks (which = QBX_REFINE_INTERFERING or QBX_REFINE_QUAD_RES).  bool[n_elem] on the host."""
+    T = _tree(d.src_xyz, d.ctr_xyz, d.ctr_r, n_max)
+    if which == B.QBX_REFINE_INTERFERING:
+        ce = torch.from_numpy(np.ascontiguousarray(d.ctr_elem, np.int32)).cuda()
+        m = B.qbx_refine_marks(T, which, ce, d.n_elem, eps=eps)
+    else:
+        se = torch.from_numpy(np.ascontiguousarray(d.src_elem, np.int32)).cuda()
+        eta = torch.from_numpy(np.ascontiguousarray(d.elem_eta, np.float64)).cuda()
+        m = B.qbx_refine_marks(T, which, se, d.n_elem, elem_eta=eta)
+    return m.cpu().numpy().astype(bool)
+
+
 def stage1(mesh, discretize, bisect, curvature=None, eps=EPS_DISTURB, kappa_max=KAPPA_MAX, n_max=64,
-           max_rounds=16):
+           max_rounds=16, marks_fn=None):
     """Algorithm 1 (+ the scaled-curvature criterion when `curvature(mesh)` gives kappa per element).
     discretize(mesh) -> object with src_xyz, ctr_xyz, ctr_r, ctr_elem (element of each center) and
-    n_elem; bisect(mesh, marks) -> refined mesh.  Returns (mesh, discretization, marked per round)."""
+    n_elem; bisect(mesh, marks) -> refined mesh; marks_fn(d, which, eps) replaces the GPU marks
+    (gpu_marks) when given.  Returns (mesh, discretization, marked per round)."""
     history = []
     for _ in range(max_rounds):
         d = discretize(mesh)
-        T = _tree(d.src_xyz, d.ctr_xyz, d.ctr_r, n_max)
-        ce = torch.from_numpy(np.ascontiguousarray(d.ctr_elem, np.int32)).cuda()
-        marks = B.qbx_refine_marks(T, B.QBX_REFINE_INTERFERING, ce, d.n_elem, eps=eps).cpu().numpy().astype(bool)
+        marks = (marks_fn(d, B.QBX_REFINE_INTERFERING, eps) if marks_fn else
+                 gpu_marks(d, B.QBX_REFINE_INTERFERING, eps, n_max))
         if curvature is not None:
             marks |= np.asarray(curvature(mesh)) > kappa_max
         history.append(int(marks.sum()))
@@ -45,18 +59,16 @@ def stage1(mesh, discretize, bisect, curvature=None, eps=EPS_DISTURB, kappa_max=
     raise RuntimeError(f"stage-1 refinement still marking after {max_rounds} rounds: {history}")
 
 
-def stage2(mesh1, discretize2, bisect, n_max=64, max_rounds=16):
+def stage2(mesh1, discretize2, bisect, n_max=64, max_rounds=16, marks_fn=None):
     """Algorithm 2 from the stage-1 mesh.  discretize2(mesh1, mesh2) -> object with the sources of
-    mesh2 (src_xyz, src_elem, elem_eta, n_elem) and the centers of mesh1 (ctr_xyz, ctr_r).
-    Returns (stage-2 mesh, discretization, marked per round)."""
+    mesh2 (src_xyz, src_elem, elem_eta, n_elem) and the centers of mesh1 (ctr_xyz, ctr_r); marks_fn as
+    in stage1.  Returns (stage-2 mesh, discretization, marked per round)."""
     mesh2 = mesh1
     history = []
     for _ in range(max_rounds):
         d = discretize2(mesh1, mesh2)
-        T = _tree(d.src_xyz, d.ctr_xyz, d.ctr_r, n_max)
-        se = torch.from_numpy(np.ascontiguousarray(d.src_elem, np.int32)).cuda()
-        eta = torch.from_numpy(np.ascontiguousarray(d.elem_eta, np.float64)).cuda()
-        marks = B.qbx_refine_marks(T, B.QBX_REFINE_QUAD_RES, se, d.n_elem, elem_eta=eta).cpu().numpy().astype(bool)
+        marks = (marks_fn(d, B.QBX_REFINE_QUAD_RES, EPS_DISTURB) if marks_fn else
+                 gpu_marks(d, B.QBX_REFINE_QUAD_RES, n_max=n_max))
         history.append(int(marks.sum()))
         if not marks.any():
             return mesh2, d, history

@@ -8,7 +8,7 @@ import pytest
 import oracle as O
 from synth import bisect_flat, flat_mesh, scaled_curvature, star_radius, surface_from_flat
 
-from conftest import rel_linf
+from conftest import rel_linf, two_spheres as _two_spheres
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -16,31 +16,6 @@ pytestmark = pytest.mark.gpu
 
 def _cu(a, dt=torch.float64):
     return torch.from_numpy(np.ascontiguousarray(a)).to(dt).cuda()
-
-
-class _Union:
-    """Several surfaces discretized together (elements, sources and centers concatenated)."""
-
-    def __init__(self, parts):
-        self.parts = parts
-        off = np.cumsum([0] + [p.n_elem for p in parts])
-        self.n_elem = int(off[-1])
-        cat = lambda k: np.concatenate([getattr(p, k) for p in parts], axis=-1)  # noqa: E731
-        self.src_xyz, self.src_w, self.src_n = cat("src_xyz"), cat("src_w"), cat("src_n")
-        self.ctr_xyz, self.ctr_r = cat("ctr_xyz"), cat("ctr_r")
-        self.src_elem = np.concatenate([p.src_elem + o for p, o in zip(parts, off)]).astype(np.int32)
-        self.ctr_elem = np.concatenate([p.ctr_elem + o for p, o in zip(parts, off)]).astype(np.int32)
-        self.elem_eta = cat("elem_eta")
-        nct = np.cumsum([0] + [p.n_ctr for p in parts])
-        self.tgt_xyz = cat("tgt_xyz")
-        self.tgt_ctr = np.concatenate([p.tgt_ctr + o for p, o in zip(parts, nct)]).astype(np.int32)
-
-
-def _two_spheres(meshes, gap, src_meshes=None):
-    offs = [(0.0, 0.0, 0.0), (2.0 + gap, 0.0, 0.0)]
-    if src_meshes is None:
-        return _Union([surface_from_flat(m, offset=o) for m, o in zip(meshes, offs)])
-    return _Union([surface_from_flat(m, offset=o, src_flat=m2) for m, m2, o in zip(meshes, src_meshes, offs)])
 
 
 def _gpu_marks(import_G, d, which, n_max):
@@ -122,7 +97,6 @@ def test_refinement_loops_and_their_effect(G):
         L = G.qbx_build_lists(T)
         pot = G.qbx_eval(T, L, _cu(d.src_w), _cu(dudn), _cu(-u), _cu(d.src_n), _cu(d.tgt_ctr, torch.int32), 8, 16)
         pot = pot.cpu().numpy()
-        half = d.tgt_xyz.shape[1] // 2
         ut = 1.0 / np.linalg.norm(d.tgt_xyz - x0[:, None], axis=0)
         # the average of the exterior and interior limits of each node is u/2
         parts, i0 = [], 0
@@ -130,7 +104,6 @@ def test_refinement_loops_and_their_effect(G):
             n = p.n_ctr // 2
             parts.append(0.5 * (pot[i0:i0 + n] + pot[i0 + n:i0 + 2 * n]) - 0.5 * ut[i0:i0 + n])
             i0 += 2 * n
-        del half
         return float(np.max(np.abs(np.concatenate(parts)))) / float(np.max(np.abs(ut)))
 
     e0 = greens_error(_two_spheres(m0, gap))
