@@ -1,10 +1,10 @@
 """qbx_eval_noalloc: the no-allocation variant of qbx_eval.
 
-Callers that cannot call cudaMalloc while they evaluate (code running under someone
-else's stream capture, real-time loops with a fixed memory budget, hosts whose
-allocator owns the device) use qbx_eval_noalloc, which takes its scratch from a fixed
-array inside the library.  This file is collected last so that a failure here leaves
-every other test already run; it also passes on its own in a fresh process.
+Callers that cannot call cudaMalloc while they evaluate (real-time loops with a fixed
+memory budget, hosts whose allocator owns the device) use qbx_eval_noalloc, which takes
+its scratch from a fixed array inside the library.  This file is collected last so that a
+failure here leaves every other test already run; it also passes on its own in a fresh
+process.
 """
 import numpy as np
 import pytest
