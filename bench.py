@@ -1025,6 +1025,54 @@ def run_tcr(args):
            "variants": rows}
     print(json.dumps(out))
 
+
+def run_nmax(args):
+    """Leaf-size sweep on the 1.19M-source surface: for each n_max of --n-max-list, the tree (of
+    --tree's kind), its lists and the measured time of one split-TF32 fixed-order evaluation (CUDA-graph
+    replays, L2 flushed between them), with the stage split of one profiled evaluation.  One JSON line."""
+    import torch
+
+    import paper_1805_06106_gb300 as G
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    s, sigma, mu, t, tc, _ = make_workload(args.n_sub, "star79k")
+    n_qbx_tgt = int(np.sum(tc >= 0))
+
+    def cu(a, dt=torch.float64):
+        return torch.from_numpy(np.ascontiguousarray(a)).to(dt).to(dev)
+
+    stream = torch.cuda.Stream(device=dev)
+    rows = {}
+    with torch.cuda.stream(stream):
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+        geo = [cu(s.src_xyz), cu(s.ctr_xyz), cu(s.ctr_r), cu(t)]
+        ev_in = (cu(s.src_w), cu(sigma), None if mu is None else cu(mu), cu(s.src_n), cu(tc, torch.int32))
+        for n_max in (int(x) for x in args.n_max_list.split(",")):
+            T = G.qbx_build_tree(*geo, n_max=n_max, t_f=T_F, level_restrict=args.tree == "level-restricted")
+            L = G.qbx_build_lists(T)
+            c = G.qbx_lists_cost(L, P_QBX, P_FMM)
+            pot = torch.empty(t.shape[1], dtype=torch.float64, device=dev)
+            G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM, out=pot, precision=G.QBX_M2L_3XTF32)
+            graph = G.qbx_graph_create(T, L, *ev_in, P_QBX, P_FMM, pot, precision=G.QBX_M2L_3XTF32)
+            ms = _time_graph(torch, graph, stream, flush, args.steps, max(args.warmup, 3))
+            L.profile(True)
+            G.qbx_eval(T, L, *ev_in, P_QBX, P_FMM, out=pot, precision=G.QBX_M2L_3XTF32)
+            rows[n_max] = {"n_boxes": int(T.n_boxes), "eval_ms": statistics.median(ms),
+                           "qbx_evals_per_s": n_qbx_tgt / (statistics.median(ms) * 1e-3), "stage_ms": L.stage_ms(),
+                           "list3_far_pairs": c["count"]["Wfar"], "direct_list_count": c["count"]["U"] +
+                           c["count"]["Wclose"] + c["count"]["Xclose"]}
+            L.profile(False)
+            del graph, L, T
+            torch.cuda.synchronize()
+    best = min(rows, key=lambda k: rows[k]["eval_ms"])
+    print(json.dumps({"metric": "split-TF32 evaluation time per leaf size", "unit": "ms", "value": rows[best]["eval_ms"],
+                      "best_n_max": best, "config": {"workload": f"star79k family, {s.n_src} sources, {n_qbx_tgt} "
+                                                                 "on-surface QBX targets", "tree": args.tree,
+                                                     "p_qbx": P_QBX, "p_fmm": P_FMM, "steps": args.steps,
+                                                     "l2": "flushed between timed steps (512 MiB write)"},
+                      "rows": rows}))
+
 def main():
     global P_QBX, P_FMM
     ap = argparse.ArgumentParser()
@@ -1046,31 +1094,35 @@ def main():
                     help="timed steps of plain FP64 at the mixed leaf size (also the judge and accuracy "
                          "reference; 0 skips it unless the learned mode needs the judge)")
     ap.add_argument("--fixed-steps", type=int, default=5, help="timed steps of fixed orders in the same precision")
-    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched", "tcr"), default="star79k",
+    ap.add_argument("--workload", choices=tuple(WORKLOADS) + ("batched", "tcr", "nmax"), default="star79k",
                     help="star79k (1.19M sources, random density, orders 8/16; default), star8k (120k, Green's "
                          "formula, orders 7/15), star40k (607k), batched: many surfaces in one forest and graph, "
-                         "or tcr: Table l2-comparison's tree variants on the 1.19M-source surface")
+                         "tcr: Table l2-comparison's tree variants on the 1.19M-source surface, or nmax: a leaf-size "
+                         "sweep of the split-TF32 evaluation on that surface (--n-max-list)")
     ap.add_argument("--batch", type=int, default=64, help="surfaces of the batched workload")
     ap.add_argument("--no-tune", action="store_true", help="batched: skip the leaf-size autotuner")
     ap.add_argument("--no-fp64-baseline", action="store_true")
+    ap.add_argument("--n-max-list", default="96,128,160,192", help="leaf sizes of --workload nmax")
     ap.add_argument("--tree", choices=("level-restricted", "plain"), default="level-restricted",
                     help="single-surface workloads: the tree of the evaluated arms (Section 5.3's level "
                          "restriction, the faster on the 1.19M-source surface, or Stage 1 as is)")
     args = ap.parse_args()
-    if args.workload in WORKLOADS or args.workload == "tcr":
-        n_sub, _, _, (P_QBX, P_FMM), _ = WORKLOADS["star79k" if args.workload == "tcr" else args.workload]
+    if args.workload in WORKLOADS or args.workload in ("tcr", "nmax"):
+        n_sub, _, _, (P_QBX, P_FMM), _ = WORKLOADS[args.workload if args.workload in WORKLOADS else "star79k"]
         if args.n_sub is None:
             args.n_sub = n_sub
     elif args.n_sub is None:
         args.n_sub = 20
     if args.impl == "reference":
-        if args.workload in ("batched", "tcr"):
+        if args.workload in ("batched", "tcr", "nmax"):
             args.workload = "star79k"
         run_reference(args)
     elif args.workload == "batched":
         run_batched(args)
     elif args.workload == "tcr":
         run_tcr(args)
+    elif args.workload == "nmax":
+        run_nmax(args)
     else:
         run_gpu(args)
 
