@@ -238,8 +238,13 @@ int qbx_refine_marks(const qbx_tree *tree, int which, const int32_t *elem_dev, c
  * All arrays are in the input order given to qbx_build_tree.  The first call with a
  * given (orders, precision) allocates the library's workspace; later calls allocate
  * nothing and may be captured in a CUDA graph.
+ * Precision: QBX_FP64; QBX_M2L_FP32 or QBX_M2L_3XTF32 reduce List 2 M2L and List 3-far M2QBXL
+ * (Stages 4 and 5(b)); OR'ed with QBX_MIXED_M2L_ONLY or QBX_MIXED_M2QBXL_ONLY they reduce only
+ * that stage and keep the other in FP64.
  * Errors: QBX_ERR_INVALID_ARG (orders out of range, p_qbx > p_fmm for fixed orders,
- * mu without normals, tgt_ctr out of range), QBX_ERR_OOM, QBX_ERR_CUDA.
+ * mu without normals, tgt_ctr out of range, a stage selection without a reduced mode or with
+ * both stages), QBX_ERR_TIMEOUT (a bounded wait of a tensor-core pipeline gave up),
+ * QBX_ERR_OOM, QBX_ERR_CUDA.
  */
 int qbx_eval(const qbx_tree *tree, const qbx_lists *lists, const double *src_w_dev, const double *sigma_dev,
              const double *mu_dev, const double *src_n_dev, const int32_t *tgt_ctr_dev,
