@@ -42,7 +42,7 @@ T_F = 0.9
 TOL = 1e-6             # acceptance: normwise relative l-infinity distance to the fixed-order FP64 result
 JUDGE_FRAC = 0.9       # the fallback keeps every target within 0.9 TOL of the judge (margin for rounding)
 N_MAX_FP64 = 512       # leaf size of plain FP64 (best of its n_max sweep, profiles/nmax_sweep_star79k.md)
-N_MAX_MIXED = 128      # leaf size of the mixed-precision modes (profiles/nmax_sweep_star79k.md)
+N_MAX_MIXED = 128      # leaf size of the mixed-precision modes (profiles/nmax_sweep_star79k*.md)
 L2_FLUSH_BYTES = 512 << 20
 TF32_OVER_BF16 = 1.1 / 2.25  # nominal dense TF32 / BF16 tensor rates of the part
 
