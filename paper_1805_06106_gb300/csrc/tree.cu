@@ -619,7 +619,10 @@ void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const doubl
         // above are unchanged, and a split leaf owned at most n_max particles, so its children
         // do not split on count); stop when a round marks nothing or splits nothing.
         if (T->flags & QBX_TREE_LEVEL_RESTRICT) {
-            for (int round = 0; round < 4 * 64; ++round) {
+            // every round that changes the tree makes new leaves; a few rounds per level are plenty
+            const int max_rounds = 4 * (T->max_depth + 1);
+            bool settled = false;
+            for (int round = 0; round < max_rounds && !settled; ++round) {
                 const int nb0 = (int)T->nb;
                 unsigned char *force = dalloc<unsigned char>(nb0);
                 QBX_CUDA_TRY(cudaMemsetAsync(flags + 2, 0, 2 * sizeof(int), st));
@@ -637,6 +640,7 @@ void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const doubl
                 }
                 if (marks[0] == 0) {
                     dfree(force);
+                    settled = true;
                     break;
                 }
                 // keep the previous tree's child array and marks; rebuild into fresh box arrays
@@ -661,8 +665,9 @@ void build_tree(qbx_tree *T, const double *sxyz, const double *cxyz, const doubl
                 }
                 dfree(ochild);
                 dfree(force);
-                if (T->nb == nb0) break;  // the marked leaves could not move a particle
+                if (T->nb == nb0) settled = true;  // the marked leaves could not move a particle
             }
+            if (!settled) throw Error{QBX_ERR_CUDA, "level restriction did not settle"};
         }
         int ov = 0;
         QBX_CUDA_TRY(cudaMemcpyAsync(&ov, flags + 1, sizeof(int), cudaMemcpyDeviceToHost, st));
