@@ -727,6 +727,7 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": "QBX target evals/s", "n_gpus": ws, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step_median": statistics.median(step_ms),
         "vs_baseline": None,
         "dtype": "f64" if not mixed else (
             "f64 (List 2 M2L and List 3 far M2QBXL products in f32)" if prec == G.QBX_M2L_FP32 else
