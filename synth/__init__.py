@@ -12,6 +12,10 @@ from .surfaces import (  # noqa: F401
     flat_mesh,
     bisect_flat,
     scaled_curvature,
+    urchin_radius,
+    adaptive_flat_mesh,
+    map_tail,
+    conical_rule,
     sphere_radius,
     star_radius,
     real_ylm,

@@ -72,6 +72,45 @@ def star_radius(terms):
     return radius
 
 
+def urchin_radius(k: int):
+    """The 'urchin' gamma_k of Section 6.1 (eq. urchin-warping): r_k = 0.2 + (Re Y_k^{floor(k/2)} - m_k) /
+    (M_k - m_k), M_k and m_k the largest and smallest value of Re Y_k^{floor(k/2)} on the sphere.  Re Y
+    is N P_k^m(cos theta) cos(m phi), so for m > 0 the extremes are +- N max |P_k^m| (cos(m phi) = +-1),
+    found by dense sampling in theta refined by golden-section search; for m = 0 they are the extremes
+    of N P_k(cos theta)."""
+    m = k // 2
+    norm = math.sqrt((2 * k + 1) / (4 * math.pi) * math.factorial(k - m) / math.factorial(k + m))
+
+    def f(t):
+        return norm * _legendre_nocs(k, m, np.cos(np.atleast_1d(t)))
+
+    def extreme(sign):
+        t = np.linspace(0.0, math.pi, 20001)
+        v = sign * f(t)
+        i = int(np.argmax(v))
+        lo, hi = t[max(i - 1, 0)], t[min(i + 1, len(t) - 1)]
+        g = (math.sqrt(5.0) - 1.0) / 2.0
+        for _ in range(200):  # golden-section refinement of the sampled maximum
+            a_, b_ = hi - g * (hi - lo), lo + g * (hi - lo)
+            if sign * f(a_)[0] > sign * f(b_)[0]:
+                hi = b_
+            else:
+                lo = a_
+        return float(sign * max(sign * f(lo)[0], sign * f(hi)[0], v[i]))
+
+    if m > 0:
+        M = max(extreme(1.0), -extreme(-1.0))
+        mk = -M
+    else:
+        M, mk = extreme(1.0), extreme(-1.0)
+
+    def radius(xhat: np.ndarray) -> np.ndarray:
+        return 0.2 + (real_ylm(k, m, xhat) - mk) / (M - mk)
+
+    radius.extremes = (mk, M)
+    return radius
+
+
 # --------------------------------------------------------------------------
 # reference-triangle quadrature
 # --------------------------------------------------------------------------
@@ -180,6 +219,71 @@ def _icosahedron():
                     faces.append((a, b2, c2))
     assert len(faces) == 20
     return verts, np.array(faces)
+
+
+def conical_rule(n: int):
+    """Conical-product rule on the unit right triangle with n x n nodes (n-point Gauss-Jacobi(1, 0) in
+    the collapsed direction, n-point Gauss-Legendre along it), exact to total degree 2n - 1."""
+    tj, wj = _golub_welsch_jacobi(n, 1.0, 0.0)
+    xi, wxi = 0.5 * (tj + 1.0), wj / 4.0
+    tl, wl = np.polynomial.legendre.leggauss(n)
+    eta, weta = 0.5 * (tl + 1.0), 0.5 * wl
+    u = np.repeat(xi, n)
+    return u, (1.0 - u) * np.tile(eta, n), np.repeat(wxi, n) * np.tile(weta, n)
+
+
+def _orthonormal_by_degree():
+    """Values at a degree-9 rule of an L2-orthonormal basis of P_4 on the unit triangle, ordered by
+    total degree (Gram-Schmidt of the monomials in the order of _MONO sorted by degree), with each
+    function's degree: the hierarchical split P_d = P_{d-1} + (its orthogonal complement) that a
+    Dubiner (Koornwinder) basis also has."""
+    u, v, w = conical_rule(5)
+    order = sorted(range(len(_MONO)), key=lambda i: (sum(_MONO[i]), _MONO[i][1]))
+    vals, degs = [], []
+    for i in order:
+        a, b = _MONO[i]
+        q = u ** a * v ** b
+        for p in vals:  # twice, for stability
+            q = q - np.sum(w * q * p) * p
+        for p in vals:
+            q = q - np.sum(w * q * p) * p
+        q = q / math.sqrt(np.sum(w * q * q))
+        vals.append(q)
+        degs.append(a + b)
+    return u, v, w, np.array(vals), np.array(degs)
+
+
+def map_tail(flat: np.ndarray, radius_fn=sphere_radius) -> np.ndarray:
+    """Per element, the l2 norm of the coefficients of total degree 3 and 4 (the two highest) of the
+    degree-4 element map in an orthonormal basis of the triangle, relative to the norm of all of them
+    (the resolution measure of the adaptive meshing of Section 6.1)."""
+    return _tail_of_geometry(_element_geometry(flat, radius_fn, 1.0, (0.0, 0.0, 0.0)))
+
+
+def _tail_of_geometry(geo: np.ndarray) -> np.ndarray:
+    """map_tail of degree-4 element maps given by their 15 geometry nodes (K, 15, 3)."""
+    u, v, w, B, deg = _orthonormal_by_degree()
+    phi, _, _ = _lagrange_eval(u, v)
+    x = np.einsum("qb,kbd->kqd", phi, geo)                    # the map at the rule's nodes
+    c = np.einsum("jq,q,kqd->kjd", B, w, x)                   # coefficients per basis function
+    hi = deg >= 3
+    return np.sqrt(np.sum(c[:, hi] ** 2, axis=(1, 2)) / np.sum(c ** 2, axis=(1, 2)))
+
+
+def adaptive_flat_mesh(radius_fn, tol: float = 1e-4, max_rounds: int = 12):
+    """Mesh of the surface r(x_hat) refined where its degree-4 element maps are not resolved (Section
+    6.1): start from the icosahedron's faces and bisect every element whose map_tail exceeds tol,
+    re-evaluating the map on the children, until none does.  Returns (flat mesh, tails per round)."""
+    flat = _flat_subtriangles(1)
+    hist = []
+    for _ in range(max_rounds):
+        t = map_tail(flat, radius_fn)
+        marks = t > tol
+        hist.append(int(marks.sum()))
+        if not marks.any():
+            return flat, hist
+        flat = bisect_flat(flat, marks)
+    raise RuntimeError(f"adaptive meshing did not resolve the maps in {max_rounds} rounds: {hist}")
 
 
 def flat_mesh(n_sub: int) -> np.ndarray:
