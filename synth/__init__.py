@@ -1,8 +1,8 @@
 """Seeded synthetic inputs shared by the oracle tests, the CUDA-path tests and bench.py.
 
 This package only produces geometry and densities (mesh nodes, quadrature
-weights, normals, expansion centers and radii, targets and their center
-association).  It contains none of the evaluation method's arithmetic: no
+rules and weights, normals, expansion centers and radii, targets, locally
+bisected and adaptive meshes).  It contains none of the evaluation method's arithmetic: no
 spherical-harmonic expansions, translations, trees or interaction lists.
 """
 from .surfaces import (  # noqa: F401

@@ -461,14 +461,17 @@ def scaled_curvature(flat: np.ndarray, radius_fn=sphere_radius, scale: float = 1
 
 
 def surface_from_flat(flat: np.ndarray, radius_fn=sphere_radius, scale: float = 1.0, offset=(0.0, 0.0, 0.0),
-                      upsample: int = 1, src_flat: np.ndarray = None) -> Surface:
+                      upsample: int = 1, src_flat: np.ndarray = None, src_degree: int = None) -> Surface:
     """Surface on the mesh of flat triangles `flat` (projected radially onto r(x_hat)): the body of
     make_surface for any (e.g. locally bisected) mesh.  With src_flat (a bisection of `flat`: the
     stage-2 mesh of Section 3.3) the sources are the nodes of src_flat's elements (and elem_eta their
-    eta), while centers, radii and targets stay those of `flat` (the stage-1 mesh)."""
+    eta), while centers, radii and targets stay those of `flat` (the stage-1 mesh).  With src_degree
+    the sources are the nodes of a rule exact to that total degree built by node elimination
+    (synth.rules, the stage-2 quadrature of Section 3.1) instead of the 15-node rule (upsample is
+    then ignored)."""
     if src_flat is not None:
         s1 = surface_from_flat(flat, radius_fn, scale, offset)
-        s2 = surface_from_flat(src_flat, radius_fn, scale, offset, upsample)
+        s2 = surface_from_flat(src_flat, radius_fn, scale, offset, upsample, src_degree=src_degree)
         return Surface(s2.n_elem, s2.src_xyz, s2.src_w, s2.src_n, s2.src_elem, s2.elem_eta, s1.ctr_xyz, s1.ctr_r,
                        s1.ctr_side, s1.tgt_xyz, s1.tgt_ctr, radius_fn, s1.ctr_elem, s1.elem_eta)
     K = flat.shape[0]
@@ -495,8 +498,13 @@ def surface_from_flat(flat: np.ndarray, radius_fn=sphere_radius, scale: float = 
     node_xyz = np.ascontiguousarray(x.reshape(-1, 3).T)
     node_n = np.ascontiguousarray(nrm.reshape(-1, 3).T)
     node_elem = np.repeat(np.arange(K, dtype=np.int32), 15)
-    if upsample > 1:
-        fu, fv, fw = _upsampled_rule(upsample)
+    if upsample > 1 or src_degree is not None:
+        if src_degree is not None:
+            from .rules import eliminated_rule
+
+            fu, fv, fw = eliminated_rule(int(src_degree))
+        else:
+            fu, fv, fw = _upsampled_rule(upsample)
         fphi, fdu, fdv = _lagrange_eval(fu, fv)
         xs = np.einsum("qb,kbd->kqd", fphi, geo)
         crs = np.cross(np.einsum("qb,kbd->kqd", fdu, geo), np.einsum("qb,kbd->kqd", fdv, geo))
