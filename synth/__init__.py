@@ -9,6 +9,7 @@ from .surfaces import (  # noqa: F401
     Surface,
     make_surface,
     surface_from_flat,
+    collocation_surface,
     flat_mesh,
     bisect_flat,
     scaled_curvature,

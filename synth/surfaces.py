@@ -345,6 +345,7 @@ class Surface:
     radius_fn: object = field(repr=False, default=None)
     ctr_elem: np.ndarray = field(repr=False, default=None)     # (N_C,) element that spawned each center
     ctr_elem_eta: np.ndarray = field(repr=False, default=None)  # eta of the centers' elements (stage 1)
+    interp: np.ndarray = field(repr=False, default=None)  # (sources, nodes) per element: node values -> sources
 
     @property
     def n_src(self) -> int:
@@ -458,6 +459,52 @@ def scaled_curvature(flat: np.ndarray, radius_fn=sphere_radius, scale: float = 1
     disc = np.sqrt(np.maximum(0.25 * H2 * H2 - K, 0.0))
     kmax = np.maximum(np.abs(0.5 * H2 + disc), np.abs(0.5 * H2 - disc))
     return (kmax * _stretch(xu, xv)).max(axis=1)
+
+
+def collocation_surface(flat: np.ndarray, radius_fn=sphere_radius, src_degree: int = 10, shrink: float = 0.8,
+                        scale: float = 1.0, offset=(0.0, 0.0, 0.0)) -> Surface:
+    """Discretization for solving with the evaluation as the operator: the unknowns live at 15 nodes per
+    element, the equispaced degree-4 nodes shrunk toward the centroid by `shrink` (interior and
+    unisolvent for the polynomials of degree 4, so a density is a degree-4 polynomial per element); the
+    centers and on-surface targets sit at those nodes (eq. expansion-centers, r = eta / 2), and the
+    sources are the nodes of a node-elimination rule exact to degree src_degree (the oversampled stage-2
+    quadrature of Section 3.1), whose density values come from the node values by `interp`."""
+    from .rules import eliminated_rule
+
+    K = flat.shape[0]
+    geo = _element_geometry(flat, radius_fn, scale, offset)
+    gi = np.array([i for i, _ in _GEO_IJ]) / 4.0
+    gj = np.array([j for _, j in _GEO_IJ]) / 4.0
+    c = 1.0 / 3.0
+    nu, nv = c + shrink * (gi - c), c + shrink * (gj - c)
+    fu, fv, fw = eliminated_rule(int(src_degree))
+
+    def at(u, v):
+        ph, du, dv = _lagrange_eval(u, v)
+        return (np.einsum("qb,kbd->kqd", ph, geo), np.einsum("qb,kbd->kqd", du, geo),
+                np.einsum("qb,kbd->kqd", dv, geo))
+
+    xn, dun, dvn = at(nu, nv)
+    nrm = np.cross(dun, dvn)
+    nrm /= np.linalg.norm(nrm, axis=-1, keepdims=True)
+    eta = _eta_elements(geo)
+    xs, dus, dvs = at(fu, fv)
+    crs = np.cross(dus, dvs)
+    ars = np.linalg.norm(crs, axis=-1)
+    vand = lambda u, v: np.stack([u ** a * v ** b for a, b in _MONO], axis=1)  # noqa: E731
+    interp = vand(fu, fv) @ np.linalg.inv(vand(nu, nv))
+    node_xyz = np.ascontiguousarray(xn.reshape(-1, 3).T)
+    node_n = np.ascontiguousarray(nrm.reshape(-1, 3).T)
+    node_elem = np.repeat(np.arange(K, dtype=np.int32), 15)
+    r = 0.5 * eta[node_elem]
+    N = node_xyz.shape[1]
+    ctr = np.concatenate([node_xyz + r * node_n, node_xyz - r * node_n], axis=1)
+    return Surface(K, np.ascontiguousarray(xs.reshape(-1, 3).T), np.ascontiguousarray((fw[None, :] * ars).reshape(-1)),
+                   np.ascontiguousarray((crs / ars[..., None]).reshape(-1, 3).T),
+                   np.repeat(np.arange(K, dtype=np.int32), fu.size), eta, np.ascontiguousarray(ctr),
+                   np.concatenate([r, r]), np.concatenate([np.ones(N, np.int8), -np.ones(N, np.int8)]),
+                   np.ascontiguousarray(np.concatenate([node_xyz, node_xyz], axis=1)), np.arange(2 * N, dtype=np.int32),
+                   radius_fn, np.concatenate([node_elem, node_elem]), eta, interp)
 
 
 def surface_from_flat(flat: np.ndarray, radius_fn=sphere_radius, scale: float = 1.0, offset=(0.0, 0.0, 0.0),
