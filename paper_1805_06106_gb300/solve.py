@@ -1,4 +1,5 @@
-"""Boundary-value problems solved with the evaluation as the operator (the use of Section 6.2).
+"""Boundary-value problems solved with the evaluation as the operator (the use of Section 6.2), and the
+normal derivative S' of the single layer at targets from the same evaluation.
 
 The QBX evaluation gives one-sided limits of layer potentials on the surface: a target evaluated
 through its interior center receives the interior limit.  For the interior Dirichlet problem of the
@@ -101,3 +102,30 @@ def interior_dirichlet(tree, lists, src_w, src_n, tgt_ctr, interp, f, p_qbx, p_f
         return out.clone()
 
     return dirichlet_double_layer(apply, interp, f, tol=tol, restart=restart, maxiter=maxiter)
+
+
+def normal_derivative_targets(tgt_xyz, tgt_n, h):
+    """Targets for S' (the normal derivative at the targets of the single layer, Section 2): the points
+    t + h n_t (first half) and t - h n_t (second half), (3, 2 N_T); evaluate both halves through the
+    centers of the targets t (tgt_ctr repeated twice) and pass the result to normal_derivative."""
+    t, n = np.asarray(tgt_xyz), np.asarray(tgt_n)
+    h = np.broadcast_to(np.asarray(h, dtype=np.float64), (t.shape[1],))
+    return np.concatenate([t + h * n, t - h * n], axis=1)
+
+
+def normal_derivative(pot_pm, h):
+    """S'[sigma] = d/dn_t S[sigma] at each target from the potentials at t +- h n_t: the central difference
+    of the target's QBX local expansion (a polynomial in t - c, the same expansion for both points, so
+    the limit from the center's side is kept and the error is O(h^2) plus rounding / h; h about 1e-2
+    of the expansion radius)."""
+    n = pot_pm.shape[0] // 2
+    return (pot_pm[:n] - pot_pm[n:]) / (2.0 * h)
+
+
+def single_layer_normal_derivative(tree, lists, src_w, sigma, src_n, tgt_ctr_pm, h, p_qbx, p_fmm,
+                                   precision=B.QBX_FP64):
+    """S'[sigma] at N_T targets on the GPU: `tree` built with normal_derivative_targets' points as its
+    targets, tgt_ctr_pm the targets' centers twice (device int32, 2 N_T), h the step per target
+    (a device tensor or a number).  One qbx_eval, then normal_derivative."""
+    pot = B.qbx_eval(tree, lists, src_w, sigma, None, src_n, tgt_ctr_pm, p_qbx, p_fmm, precision=precision)
+    return normal_derivative(pot, h)

@@ -69,3 +69,25 @@ def test_constant_boundary_values(sphere_dirichlet):
     mu_src = (mu.numpy().reshape(-1, 15) @ s.interp.T).reshape(-1)
     u = O.direct_eval(s.src_xyz, s.src_w, None, mu_src, s.src_n, s.ctr_xyz, pts, -np.ones(40, np.int32), 5)
     assert np.max(np.abs(u - 1.0)) < 1e-4
+
+
+@pytest.mark.parametrize("n,m", [(2, 1), (3, -2)])
+def test_single_layer_normal_derivative_on_the_sphere(n, m):
+    """S'[Y_n^m] on the unit sphere: the exterior limit is -(n+1)/(2n+1) Y_n^m and the interior one
+    n/(2n+1) Y_n^m (S[Y_n^m] = r^n Y_n^m/(2n+1) inside, r^-(n+1) Y_n^m/(2n+1) outside).  Sources from a 4x
+    finer mesh than the centers, as in the potential's closed-form pin."""
+    from paper_1805_06106_gb300.solve import normal_derivative, normal_derivative_targets
+    from synth import make_surface, real_ylm
+
+    sc, ss = make_surface(2), make_surface(8)
+    sub = np.random.default_rng(0).choice(sc.n_src, 40, replace=False)
+    k = sub.size
+    sig = real_ylm(n, m, ss.src_xyz)
+    Y = real_ylm(n, m, sc.src_xyz[:, sub])
+    for offset, limit in ((0, -(n + 1) / (2 * n + 1)), (sc.n_src, n / (2 * n + 1))):
+        h = 1e-2 * sc.ctr_r[sub]
+        tp = normal_derivative_targets(sc.src_xyz[:, sub], sc.src_n[:, sub], h)
+        ctr = np.concatenate([sc.ctr_xyz[:, sub + offset]] * 2, axis=1)
+        pot = O.direct_eval(ss.src_xyz, ss.src_w, sig, None, ss.src_n, ctr, tp, np.arange(2 * k, dtype=np.int32), 7)
+        d = normal_derivative(pot, h)
+        assert np.max(np.abs(d - limit * Y)) / np.max(np.abs(limit * Y)) < 1e-2
